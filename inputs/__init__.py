@@ -1,0 +1,129 @@
+"""Seeded synthetic inputs shared by the CPU oracle and the CUDA path.
+
+This module holds input generation only: random gauge links, sources and the
+random starting test vectors that the adaptive setup draws.  It contains none
+of the method's arithmetic (no Dirac operator, smoother, aggregation or
+solver), so both sides may import it without sharing code.
+
+The paper measures on real ensembles (cA2.09.48, 48^3x96, Sec. 1; cA2.09.64,
+64^3x128, Sec. 3) that are not available here.  The stand-ins are random
+near-unit gauge fields U = exp(i*eps*H) with H a Gaussian traceless Hermitian
+3x3 matrix per link, on lattices of the same shapes.
+
+Conventions
+-----------
+* Lattice extents are (T, Z, Y, X) with X fastest; the lexicographic order
+  TZYX is the one the paper fixes for its library interface (Sec. 2).
+* Gauge field: complex128 array [T, Z, Y, X, 4, 3, 3]; direction index
+  0..3 = T, Z, Y, X; colour matrices row-major.
+* Spinor field: complex128 array [T, Z, Y, X, 4, 3] (spin, colour).
+* Random generator: numpy PCG64.  Gauge seed s, right-hand sides s + 1000,
+  test vectors s + 2000.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "gell_mann",
+    "random_hermitian_traceless",
+    "gauge_field",
+    "unit_gauge",
+    "gaussian_spinor",
+    "point_sources",
+    "random_test_vectors",
+    "random_gauge_transform",
+    "RHS_SEED_OFFSET",
+    "TV_SEED_OFFSET",
+]
+
+RHS_SEED_OFFSET = 1000
+TV_SEED_OFFSET = 2000
+
+
+def gell_mann() -> np.ndarray:
+    """The eight Gell-Mann matrices, shape [8, 3, 3], complex128."""
+    lam = np.zeros((8, 3, 3), dtype=np.complex128)
+    lam[0][0, 1] = lam[0][1, 0] = 1
+    lam[1][0, 1] = -1j
+    lam[1][1, 0] = 1j
+    lam[2][0, 0] = 1
+    lam[2][1, 1] = -1
+    lam[3][0, 2] = lam[3][2, 0] = 1
+    lam[4][0, 2] = -1j
+    lam[4][2, 0] = 1j
+    lam[5][1, 2] = lam[5][2, 1] = 1
+    lam[6][1, 2] = -1j
+    lam[6][2, 1] = 1j
+    lam[7][0, 0] = lam[7][1, 1] = 1 / np.sqrt(3)
+    lam[7][2, 2] = -2 / np.sqrt(3)
+    return lam
+
+
+def random_hermitian_traceless(rng: np.random.Generator, shape) -> np.ndarray:
+    """H = sum_a h_a lambda_a / 2 with h_a ~ N(0, 1) i.i.d.; shape + (3, 3)."""
+    h = rng.standard_normal(tuple(shape) + (8,))
+    return np.einsum("...a,aij->...ij", h, gell_mann() / 2)
+
+
+def _expi_hermitian(H: np.ndarray, eps: float) -> np.ndarray:
+    """exp(i*eps*H) for Hermitian H via the eigendecomposition H = W e W^H."""
+    e, W = np.linalg.eigh(H)
+    ph = np.exp(1j * eps * e)
+    return np.einsum("...ik,...k,...jk->...ij", W, ph, W.conj())
+
+
+def gauge_field(L, eps: float, seed: int) -> np.ndarray:
+    """Random SU(3) links U_mu(x) = exp(i*eps*H_mu(x)), shape [T,Z,Y,X,4,3,3]."""
+    T, Z, Y, X = (int(v) for v in L)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    H = random_hermitian_traceless(rng, (T, Z, Y, X, 4))
+    return _expi_hermitian(H, eps)
+
+
+def unit_gauge(L) -> np.ndarray:
+    """The free field U_mu(x) = 1."""
+    T, Z, Y, X = (int(v) for v in L)
+    U = np.zeros((T, Z, Y, X, 4, 3, 3), dtype=np.complex128)
+    U[..., 0, 0] = U[..., 1, 1] = U[..., 2, 2] = 1
+    return U
+
+
+def gaussian_spinor(L, seed: int, nrhs: int | None = None) -> np.ndarray:
+    """Spinor(s) with re, im ~ N(0, 1) i.i.d.; shape [nrhs?, T,Z,Y,X,4,3]."""
+    T, Z, Y, X = (int(v) for v in L)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (T, Z, Y, X, 4, 3) if nrhs is None else (nrhs, T, Z, Y, X, 4, 3)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def point_sources(L, seed: int) -> tuple[np.ndarray, tuple]:
+    """Twelve spin-colour point sources at one random site x0.
+
+    Returns (sources [12, T,Z,Y,X,4,3], x0) with source k = 3*s0 + c0 equal
+    to delta_{x,x0} delta_{s,s0} delta_{c,c0}.
+    """
+    T, Z, Y, X = (int(v) for v in L)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x0 = tuple(int(rng.integers(0, n)) for n in (T, Z, Y, X))
+    b = np.zeros((12, T, Z, Y, X, 4, 3), dtype=np.complex128)
+    for s in range(4):
+        for c in range(3):
+            b[(3 * s + c,) + x0 + (s, c)] = 1.0
+    return b, x0
+
+
+def random_test_vectors(L, nv: int, seed: int) -> np.ndarray:
+    """The random starting vectors v_1..v_Nv of the adaptive setup.
+
+    Shape [Nv, T,Z,Y,X,4,3]; re, im ~ N(0, 1) i.i.d.
+    """
+    return gaussian_spinor(L, seed, nrhs=nv)
+
+
+def random_gauge_transform(L, seed: int, eps: float = 1.0) -> np.ndarray:
+    """A random SU(3) matrix g(x) per site, shape [T,Z,Y,X,3,3]."""
+    T, Z, Y, X = (int(v) for v in L)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    H = random_hermitian_traceless(rng, (T, Z, Y, X))
+    return _expi_hermitian(H, eps)

@@ -1,0 +1,133 @@
+"""Two-level DD-alphaAMG: K-cycle of eq. (1), adaptive setup, FGMRES solve (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Paper passages followed
+-----------------------
+* Sec. 1, eq. (1): the preconditioner's error propagation is
+  (I - M D)^k (I - P D_c^-1 P^dagger D) (I - M D)^j: j pre-smoothing SAP
+  sweeps, a coarse-grid correction, k post-smoothing sweeps.
+* Sec. 1: the test vectors come from an adaptive setup phase; Fig. 1 uses
+  three setup iterations for few right-hand sides and five for many.
+* Sec. 1: mu_coarse = delta * mu on the coarsest grid, delta >= 1.
+* Sec. 3: odd-even preconditioning on the coarsest level; the full fine
+  operator is used by the outer solver.
+
+Readings (listed in the design doc)
+------------------------------
+* B(v): x = 0; j sweeps of SAP on D x = v; r = v - D x; e_c = coarse solve of
+  D_c(delta*mu) e_c = P^dagger r; x += P e_c; k sweeps of SAP on D x = v.
+* Coarse solve: GMRES(coarse_restart) on the odd-even Schur complement of
+  D_c(delta*mu) from zero, to a residual ``coarse_tol`` relative to the
+  reduced right-hand side, at most ``coarse_maxit`` steps.
+* Setup: each random v_i gets ``init_sweeps`` SAP sweeps on D v = 0 (i.e.
+  v_i <- (I - M D) v_i) and is normalised; P and D_c are built; then
+  ``setup_iters`` times: every v_i <- B(v_i) with the current P, D_c,
+  normalised; P and D_c are rebuilt after each full pass over i.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .dirac import Operator
+from .sap import SAP
+from .coarse import Interpolation, CoarseOperator, OddEvenCoarse
+from .krylov import gmres
+
+
+@dataclass
+class AMGParams:
+    m0: float
+    c_sw: float
+    mu: float
+    delta: float = 1.0
+    bc_t: float = -1.0
+    nv: int = 8
+    agg: tuple = (2, 2, 2, 2)
+    sap_block: tuple = (2, 2, 2, 2)
+    mr_iters: int = 4
+    pre_smooth: int = 0
+    post_smooth: int = 4
+    block_oe: bool = False
+    init_sweeps: int = 3
+    setup_iters: int = 3
+    coarse_tol: float = 5e-2
+    coarse_restart: int = 30
+    coarse_maxit: int = 200
+    restart: int = 25
+    maxit: int = 1000
+    extra: dict = field(default_factory=dict)
+
+
+def normalise(v: np.ndarray) -> np.ndarray:
+    """v_i / ||v_i|| for a stack of vectors [n, ...]."""
+    n = np.sqrt((np.abs(v) ** 2).reshape(v.shape[0], -1).sum(axis=1))
+    return v / n.reshape((-1,) + (1,) * (v.ndim - 1))
+
+
+class TwoLevel:
+    """Operators of a two-level hierarchy for a fixed gauge field."""
+
+    def __init__(self, U: np.ndarray, prm: AMGParams):
+        self.prm = prm
+        self.op = Operator(U, prm.m0, prm.c_sw, prm.mu, prm.bc_t)
+        self.sap = SAP(self.op, prm.sap_block, prm.mr_iters, prm.block_oe)
+        self.P = None
+        self.Dc = None
+        self.oe = None
+        self.coarse_iters = []
+
+    # -- hierarchy -----------------------------------------------------------------
+    def build_coarse(self, test_vectors: np.ndarray) -> None:
+        """P from the test vectors, D_c(delta*mu), odd-even Schur data."""
+        self.P = Interpolation(test_vectors, self.prm.agg)
+        self.Dc = CoarseOperator.build(self.op, self.P, self.prm.delta * self.prm.mu)
+        self.oe = OddEvenCoarse(self.Dc)
+
+    def coarse_solve(self, rc: np.ndarray, tol=None, maxit=None) -> np.ndarray:
+        """Odd-even GMRES on D_c(delta*mu) e = rc (one coarse vector)."""
+        prm = self.prm
+        tol = prm.coarse_tol if tol is None else tol
+        maxit = prm.coarse_maxit if maxit is None else maxit
+        bh = self.oe.reduced_rhs(rc)
+        res = gmres(self.oe.schur, bh, tol=tol, restart=prm.coarse_restart, maxit=maxit)
+        self.coarse_iters.append(res.iters)
+        return self.oe.reconstruct(rc, res.x)
+
+    def kcycle(self, v: np.ndarray, coarse_tol=None, coarse_maxit=None) -> np.ndarray:
+        """z = B(v), eq. (1)."""
+        prm = self.prm
+        x = np.zeros_like(v)
+        x = self.sap.smooth(v, x, prm.pre_smooth)
+        r = v - self.op.apply(x) if prm.pre_smooth else v
+        rc = self.P.restrict(r)
+        ec = self.coarse_solve(rc, coarse_tol, coarse_maxit)
+        x = x + self.P.prolong(ec)
+        x = self.sap.smooth(v, x, prm.post_smooth)
+        return x
+
+    # -- setup -------------------------------------------------------------------------
+    def setup(self, v0: np.ndarray, setup_iters=None) -> np.ndarray:
+        """Adaptive setup from random vectors v0 [Nv, T,Z,Y,X,4,3]; returns the v_i."""
+        prm = self.prm
+        iters = prm.setup_iters if setup_iters is None else setup_iters
+        v = v0.copy()
+        zero = np.zeros_like(v)
+        for _ in range(prm.init_sweeps):
+            v = self.sap.sweep(zero, v)
+        v = normalise(v)
+        self.build_coarse(v)
+        for _ in range(iters):
+            v = np.stack([self.kcycle(v[i]) for i in range(v.shape[0])])
+            v = normalise(v)
+            self.build_coarse(v)
+        self.test_vectors = v
+        return v
+
+    # -- solve -----------------------------------------------------------------------
+    def solve(self, b: np.ndarray, tol: float = 1e-10, x0=None):
+        prm = self.prm
+        return gmres(self.op.apply, b, x0=x0, tol=tol, restart=prm.restart,
+                     maxit=prm.maxit, M=self.kcycle)
