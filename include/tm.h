@@ -1,0 +1,214 @@
+/*
+ * tm.h -- C ABI of the GB300 twisted-mass DD-alphaAMG library.
+ *
+ * The library solves D(mu) x = b for the twisted-mass Wilson-clover operator
+ * D(mu) = D_W + i mu Gamma5 (Bacchio et al., "DDalphaAMG for Twisted Mass
+ * Fermions", Sec. 1) with flexible GMRES preconditioned at every step by the
+ * multigrid error propagation of eq. (1):
+ *     eps <- (I - M D)^k (I - P D_c^-1 P^dagger D) (I - M D)^j eps,
+ * M the SAP smoother, P the Gamma5-compatible aggregation interpolation,
+ * D_c = P^dagger D_W P + i delta mu Gamma5_c the coarse operator with the
+ * coarse twisted mass shifted by delta >= 1 (Sec. 1).  Everything runs on one
+ * GPU in hand-written sm_103a kernels; there is no CPU fallback.
+ *
+ * Conventions (Sec. 2 of the paper fixes gamma5 = diag(-1,-1,+1,+1) and the
+ * lexicographic site order TZYX; everything else below is this library's):
+ *   - Lattice extents L = {T, Z, Y, X}, X fastest.  Direction index 0..3 is
+ *     T, Z, Y, X and carries gamma_4, gamma_3, gamma_2, gamma_1 of the chiral
+ *     basis gamma_k = [[0, -i sigma_k], [i sigma_k, 0]], gamma_4 = [[0,-1],[-1,0]].
+ *   - D_W has (m0 + 4) plus the clover term c_sw on the diagonal and the hops
+ *     -1/2 [(1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu)];
+ *     hops across the T boundary are multiplied by bc_t.
+ *   - "Natural" arrays are complex128 with interleaved re/im:
+ *       gauge  [T][Z][Y][X][mu=4][3][3]   (links U_mu(x), rows x columns)
+ *       spinor [nrhs][T][Z][Y][X][spin 4][colour 3]
+ *       coarse [nrhs][Tc][Zc][Yc][Xc][2 Nv]   (chirality -1 first, then +1)
+ *   - "Fields" are the library's internal device layout (tm_field_bytes).
+ *
+ * Ownership: the caller owns every buffer it passes; the handle owns its
+ * internal storage (packed gauge, clover, P, D_c, workspaces) and frees it in
+ * tm_destroy.  Pointers marked "host or device" may be either; the library
+ * copies host data itself.  Pointers marked "device" must be device memory.
+ *
+ * Errors: no call aborts or throws; each returns a tm_status and keeps a
+ * message readable with tm_last_error().  Kernels never trap: device-side
+ * checks set a flag that the host turns into a status.
+ *
+ * Streams: every call enqueues on the stream given to tm_create.  Calls that
+ * return results to the host (tm_solve, tm_setup, tm_load_gauge,
+ * tm_coarse_solve, tm_export) synchronise that stream before returning;
+ * tm_apply, tm_sap, tm_restrict, tm_prolong, tm_kcycle, tm_pack and
+ * tm_unpack are asynchronous.
+ */
+#ifndef TM_H
+#define TM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tm_handle tm_handle;
+
+typedef enum {
+  TM_OK = 0,
+  TM_ERR_ARG = -1,           /* invalid argument or parameter combination */
+  TM_ERR_CUDA = -2,          /* a CUDA runtime call or kernel launch failed */
+  TM_ERR_OOM = -3,           /* device allocation failed */
+  TM_ERR_NOT_CONVERGED = -4, /* solve hit maxit; x holds the best iterate */
+  TM_ERR_TIMEOUT = -5,       /* reserved for bounded device-side waits */
+  TM_ERR_NOT_SU3 = -6,       /* a link is not unitary with det 1 (tolerance 1e-10) */
+  TM_ERR_NONFINITE = -7,     /* NaN or Inf in an input or a reduction */
+  TM_ERR_STATE = -8          /* call out of order (e.g. solve before setup) */
+} tm_status;
+
+/* storage/arithmetic precision of a field */
+enum { TM_F64 = 0, TM_F32 = 1 };
+
+/* what tm_export copies out */
+enum {
+  TM_EXPORT_P = 0,       /* P columns as fine fields, natural [2Nv][T][Z][Y][X][4][3] */
+  TM_EXPORT_DC = 1,      /* D_c blocks, [Tc][Zc][Yc][Xc][9][2Nv row][2Nv col], mu-free;
+                            block 0 self, 1 + 2 mu forward (to x+mu), 2 + 2 mu backward */
+  TM_EXPORT_CLOVER = 2,  /* A(x) chiral blocks incl. (m0+4), [T][Z][Y][X][2][6][6] */
+  TM_EXPORT_TV = 3       /* current test vectors, natural [Nv][T][Z][Y][X][4][3] */
+};
+
+typedef struct {
+  int L[4];             /* T, Z, Y, X; each divisible by agg and sap_block */
+  double m0;            /* bare mass (kappa = 1 / (2 (m0 + 4))) */
+  double c_sw;          /* clover coefficient */
+  double mu;            /* twisted mass of D(mu) (Sec. 1) */
+  double delta;         /* coarse twisted mass mu_c = delta * mu, delta >= 1 (Sec. 1) */
+  double bc_t;          /* -1 antiperiodic (default) or +1 periodic in T */
+  int nv;               /* number of test vectors N_v (Sec. 1, O(20)) */
+  int agg[4];           /* aggregate dims; coarse extents must be even */
+  int sap_block[4];     /* SAP block dims; block counts per dimension even */
+  int mr_iters;         /* minimal-residual steps per block solve */
+  int pre_smooth;       /* j of eq. (1) */
+  int post_smooth;      /* k of eq. (1) */
+  int init_sweeps;      /* SAP sweeps on D v = 0 applied to the random vectors */
+  int setup_iters;      /* adaptive setup iterations (Fig. 1: 3 few rhs, 5 many) */
+  double coarse_tol;    /* coarse GMRES tolerance, relative to the reduced rhs */
+  int coarse_restart;   /* coarse GMRES restart length */
+  int coarse_maxit;     /* coarse GMRES iteration cap */
+  int restart;          /* outer FGMRES restart length */
+  int maxit;            /* outer FGMRES iteration cap */
+  int cycle_prec;       /* TM_F64 or TM_F32: precision of smoother, P, D_c, coarse solve */
+  int max_rhs;          /* largest nrhs passed to field-level calls */
+} tm_params;
+
+typedef struct {
+  int iters;              /* outer FGMRES iterations (summed over rhs) */
+  int restarts;           /* restart cycles (summed over rhs) */
+  int converged;          /* 1 if every rhs reached tol */
+  double true_relres;     /* max over rhs of ||b - D x|| / ||b||, FP64 on the GPU */
+  long long coarse_iters; /* coarse GMRES iterations in the solve */
+  int kcycles;            /* preconditioner applications */
+} tm_solve_info;
+
+/* Fill p with the defaults: bc_t = -1, delta = 1, nv = 20, agg = sap_block
+ * = 4^4, mr_iters = 4, pre = 0, post = 4, init_sweeps = 3, setup_iters = 3,
+ * coarse_tol = 5e-2, coarse_restart = 30, coarse_maxit = 200, restart = 25,
+ * maxit = 1000, cycle_prec = TM_F32, max_rhs = 1.  L, m0, c_sw, mu are 0. */
+void tm_params_default(tm_params* p);
+
+/* Validate p and allocate a handle bound to a CUDA stream (cudaStream_t,
+ * may be NULL for the legacy default stream) on the current device.
+ * Errors: TM_ERR_ARG (divisibility, even block/coarse counts, nv in 1..28,
+ * aggregate and block volume <= 1024), TM_ERR_OOM, TM_ERR_CUDA. */
+tm_status tm_create(tm_handle** h, const tm_params* p, void* stream);
+
+/* Free everything the handle owns.  NULL is ignored. */
+void tm_destroy(tm_handle* h);
+
+/* Static text of a status code. */
+const char* tm_status_string(int status);
+
+/* Message of the last failing call on h (empty string if none). */
+const char* tm_last_error(const tm_handle* h);
+
+/* A0: take the gauge field (natural layout, host or device, complex128),
+ * check every link is SU(3) to 1e-10 (TM_ERR_NOT_SU3 otherwise), pack the
+ * links as 12 reals in FP64 and FP32 and build the clover term A(x) =
+ * (m0+4) - (c_sw/32) sum_{mu,nu} gamma_mu gamma_nu (Q_mu_nu - Q_nu_mu)
+ * as two Hermitian 6x6 blocks (D_W of Sec. 1).  Invalidates any setup. */
+tm_status tm_load_gauge(tm_handle* h, const double* gauge);
+
+/* A8: adaptive setup (Sec. 1; Fig. 1 setup iterations).  test_vectors
+ * (natural, [nv] spinors, host or device) are the random starting vectors.
+ * Each gets init_sweeps SAP sweeps on D v = 0 and is normalised; P
+ * (per aggregate and chirality thin QR, Gamma5 P = P Gamma5_c) and
+ * D_c(delta mu) are built; then setup_iters times every v_i <- B(v_i) with
+ * the current K-cycle B, normalised, and P, D_c rebuilt.
+ * Errors: TM_ERR_STATE (no gauge), TM_ERR_ARG (rank-deficient aggregate),
+ * TM_ERR_NONFINITE. */
+tm_status tm_setup(tm_handle* h, const double* test_vectors);
+
+/* Build P and D_c directly from the given vectors (no smoothing, no
+ * iterations): the interpolation of Sec. 1 for a fixed set of v_i. */
+tm_status tm_setup_from_vectors(tm_handle* h, const double* test_vectors);
+
+/* Change mu and delta without a new setup (Sec. 1: D_c(mu) = D_c +
+ * i mu Gamma5_c, so only the diagonal shift and the odd-site inverses of the
+ * coarse Schur complement change; one setup serves D(+mu) and D(-mu)). */
+tm_status tm_set_mu(tm_handle* h, double mu, double delta);
+
+/* A7: solve D(mu) x_r = b_r for nrhs right-hand sides to ||b - D x|| <=
+ * tol ||b|| by FGMRES(restart) preconditioned with the K-cycle of eq. (1).
+ * b, x natural spinors (host or device); x holds the start vector on entry
+ * and the solution on return.  The outer iteration, Arnoldi (CGS2) and the
+ * true residual are FP64; the K-cycle runs in cycle_prec.  info may be NULL.
+ * Errors: TM_ERR_STATE (no setup), TM_ERR_NOT_CONVERGED (x = best iterate,
+ * info filled), TM_ERR_NONFINITE. */
+tm_status tm_solve(tm_handle* h, const double* b, double* x, int nrhs, double tol, tm_solve_info* info);
+
+/* Bytes of one field of nrhs vectors: level 0 = fine spinors, level 1 =
+ * coarse vectors; prec TM_F64 or TM_F32.  0 for invalid arguments. */
+size_t tm_field_bytes(const tm_handle* h, int level, int prec, int nrhs);
+
+/* Convert natural complex128 vectors (device) to a field of the given
+ * level and precision (device), and back.  Level 1 is a plain cast. */
+tm_status tm_pack(tm_handle* h, int level, int prec, const double* natural, void* field, int nrhs);
+tm_status tm_unpack(tm_handle* h, int level, int prec, const void* field, double* natural, int nrhs);
+
+/* A1 (level 0): out = D(mu) in, fine fields, prec TM_F64 or TM_F32.
+ * A4 (level 1): out = D_c(delta mu) in, coarse fields, prec = cycle_prec,
+ * after a setup.  in and out are distinct device fields of nrhs vectors. */
+tm_status tm_apply(tm_handle* h, int level, int prec, const void* in, void* out, int nrhs);
+
+/* A2: sweeps SAP sweeps (red blocks, then black) on D x = b with mr_iters MR
+ * steps per block solve (Sec. 1: the smoother M).  b may be NULL (b = 0).
+ * Fine fields, prec TM_F64 or TM_F32; x is updated in place. */
+tm_status tm_sap(tm_handle* h, int prec, const void* b, void* x, int sweeps, int nrhs);
+
+/* A3: coarse = P^dagger fine.  A6: fine = P coarse (accumulate = 0) or
+ * fine += P coarse (accumulate = 1).  prec = cycle_prec, after a setup. */
+tm_status tm_restrict(tm_handle* h, int prec, const void* fine, void* coarse, int nrhs);
+tm_status tm_prolong(tm_handle* h, int prec, const void* coarse, void* fine, int nrhs, int accumulate);
+
+/* A5: solve D_c(delta mu) x = b on the coarse lattice by GMRES(coarse_restart)
+ * on the odd-even Schur complement (Sec. 3), from zero, to tol relative to
+ * the reduced right-hand side or maxit steps.  One coarse field each (device,
+ * cycle_prec).  *iters (may be NULL) receives the step count. */
+tm_status tm_coarse_solve(tm_handle* h, int prec, const void* b, void* x, double tol, int maxit, int* iters);
+
+/* A7 preconditioner: z = B(v), one application of eq. (1) from a zero start
+ * (pre SAP sweeps, coarse correction, post SAP sweeps).  Fine fields in
+ * cycle_prec, nrhs vectors. */
+tm_status tm_kcycle(tm_handle* h, int prec, const void* v, void* z, int nrhs);
+
+/* Copy internal data out as natural complex128 (host or device pointer of
+ * at least `bytes` bytes); see the TM_EXPORT_* layouts. */
+tm_status tm_export(tm_handle* h, int what, double* out, size_t bytes);
+
+/* Wait for all work queued on the handle's stream; reports asynchronous
+ * kernel errors. */
+tm_status tm_synchronize(tm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TM_H */

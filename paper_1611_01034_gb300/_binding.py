@@ -1,0 +1,225 @@
+"""ctypes declarations of ``include/tm.h`` (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_longlong, c_size_t, c_void_p, c_char_p
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libtmamg.so")
+
+TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_OOM = 0, -1, -2, -3
+TM_ERR_NOT_CONVERGED, TM_ERR_TIMEOUT, TM_ERR_NOT_SU3 = -4, -5, -6
+TM_ERR_NONFINITE, TM_ERR_STATE = -7, -8
+TM_F64, TM_F32 = 0, 1
+TM_EXPORT_P, TM_EXPORT_DC, TM_EXPORT_CLOVER, TM_EXPORT_TV = 0, 1, 2, 3
+
+
+class tm_params(ctypes.Structure):
+    _fields_ = [
+        ("L", c_int * 4), ("m0", c_double), ("c_sw", c_double), ("mu", c_double),
+        ("delta", c_double), ("bc_t", c_double), ("nv", c_int), ("agg", c_int * 4),
+        ("sap_block", c_int * 4), ("mr_iters", c_int), ("pre_smooth", c_int),
+        ("post_smooth", c_int), ("init_sweeps", c_int), ("setup_iters", c_int),
+        ("coarse_tol", c_double), ("coarse_restart", c_int), ("coarse_maxit", c_int),
+        ("restart", c_int), ("maxit", c_int), ("cycle_prec", c_int), ("max_rhs", c_int),
+    ]
+
+
+class tm_solve_info(ctypes.Structure):
+    _fields_ = [
+        ("iters", c_int), ("restarts", c_int), ("converged", c_int),
+        ("true_relres", c_double), ("coarse_iters", c_longlong), ("kcycles", c_int),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{tm_status_string(status)} ({status}): {message}")
+        self.status = status
+
+
+_lib = None
+
+_SIGS = {
+    "tm_params_default": (None, [POINTER(tm_params)]),
+    "tm_create": (c_int, [POINTER(c_void_p), POINTER(tm_params), c_void_p]),
+    "tm_destroy": (None, [c_void_p]),
+    "tm_status_string": (c_char_p, [c_int]),
+    "tm_last_error": (c_char_p, [c_void_p]),
+    "tm_load_gauge": (c_int, [c_void_p, c_void_p]),
+    "tm_setup": (c_int, [c_void_p, c_void_p]),
+    "tm_setup_from_vectors": (c_int, [c_void_p, c_void_p]),
+    "tm_set_mu": (c_int, [c_void_p, c_double, c_double]),
+    "tm_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
+    "tm_field_bytes": (c_size_t, [c_void_p, c_int, c_int, c_int]),
+    "tm_pack": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
+    "tm_unpack": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
+    "tm_apply": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
+    "tm_sap": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
+    "tm_restrict": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
+    "tm_prolong": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
+    "tm_coarse_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, POINTER(c_int)]),
+    "tm_kcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
+    "tm_export": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
+    "tm_synchronize": (c_int, [c_void_p]),
+}
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C ABI entry points this binding declares."""
+    return list(_SIGS)
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libtmamg.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise RuntimeError(
+                f"{library_path} is missing: build it with "
+                "`python -m paper_1611_01034_gb300.build` (there is no CPU fallback)")
+        L = ctypes.CDLL(library_path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Address of a torch tensor, numpy array, ctypes object or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "__array_interface__"):
+        return x.__array_interface__["data"][0]
+    if isinstance(x, ctypes.c_void_p):
+        return x.value
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int, h=None) -> None:
+    if status != TM_OK:
+        msg = tm_last_error(h) if h is not None else ""
+        raise TMError(status, msg)
+
+
+def tm_status_string(status: int) -> str:
+    return lib().tm_status_string(status).decode()
+
+
+def tm_last_error(h) -> str:
+    return lib().tm_last_error(h).decode()
+
+
+def tm_params_default() -> tm_params:
+    p = tm_params()
+    lib().tm_params_default(ctypes.byref(p))
+    return p
+
+
+def params(**kw) -> tm_params:
+    """tm_params_default() with the given fields replaced (sequences for arrays)."""
+    p = tm_params_default()
+    for k, v in kw.items():
+        if k in ("L", "agg", "sap_block"):
+            getattr(p, k)[:] = [int(t) for t in v]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def tm_create(p: tm_params, stream=None):
+    h = c_void_p()
+    _check(lib().tm_create(ctypes.byref(h), ctypes.byref(p), _stream(stream)))
+    return h
+
+
+def tm_destroy(h) -> None:
+    lib().tm_destroy(h)
+
+
+def tm_load_gauge(h, gauge) -> None:
+    _check(lib().tm_load_gauge(h, _ptr(gauge)), h)
+
+
+def tm_setup(h, test_vectors) -> None:
+    _check(lib().tm_setup(h, _ptr(test_vectors)), h)
+
+
+def tm_setup_from_vectors(h, test_vectors) -> None:
+    _check(lib().tm_setup_from_vectors(h, _ptr(test_vectors)), h)
+
+
+def tm_set_mu(h, mu: float, delta: float) -> None:
+    _check(lib().tm_set_mu(h, mu, delta), h)
+
+
+def tm_solve(h, b, x, nrhs: int, tol: float):
+    info = tm_solve_info()
+    st = lib().tm_solve(h, _ptr(b), _ptr(x), nrhs, tol, ctypes.byref(info))
+    if st not in (TM_OK, TM_ERR_NOT_CONVERGED):
+        _check(st, h)
+    return st, info
+
+
+def tm_field_bytes(h, level: int, prec: int, nrhs: int) -> int:
+    return int(lib().tm_field_bytes(h, level, prec, nrhs))
+
+
+def tm_pack(h, level, prec, natural, field, nrhs) -> None:
+    _check(lib().tm_pack(h, level, prec, _ptr(natural), _ptr(field), nrhs), h)
+
+
+def tm_unpack(h, level, prec, field, natural, nrhs) -> None:
+    _check(lib().tm_unpack(h, level, prec, _ptr(field), _ptr(natural), nrhs), h)
+
+
+def tm_apply(h, level, prec, inp, out, nrhs) -> None:
+    _check(lib().tm_apply(h, level, prec, _ptr(inp), _ptr(out), nrhs), h)
+
+
+def tm_sap(h, prec, b, x, sweeps, nrhs) -> None:
+    _check(lib().tm_sap(h, prec, _ptr(b), _ptr(x), sweeps, nrhs), h)
+
+
+def tm_restrict(h, prec, fine, coarse, nrhs) -> None:
+    _check(lib().tm_restrict(h, prec, _ptr(fine), _ptr(coarse), nrhs), h)
+
+
+def tm_prolong(h, prec, coarse, fine, nrhs, accumulate) -> None:
+    _check(lib().tm_prolong(h, prec, _ptr(coarse), _ptr(fine), nrhs, int(accumulate)), h)
+
+
+def tm_coarse_solve(h, prec, b, x, tol, maxit) -> int:
+    it = c_int(0)
+    _check(lib().tm_coarse_solve(h, prec, _ptr(b), _ptr(x), tol, maxit, ctypes.byref(it)), h)
+    return it.value
+
+
+def tm_kcycle(h, prec, v, z, nrhs) -> None:
+    _check(lib().tm_kcycle(h, prec, _ptr(v), _ptr(z), nrhs), h)
+
+
+def tm_export(h, what, out, nbytes) -> None:
+    _check(lib().tm_export(h, what, _ptr(out), nbytes), h)
+
+
+def tm_synchronize(h) -> None:
+    _check(lib().tm_synchronize(h), h)

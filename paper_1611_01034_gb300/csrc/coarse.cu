@@ -1,0 +1,619 @@
+// Aggregation-based interpolation P, restriction P^dagger, the coarse
+// operator D_c = P^dagger D_W P (+ i mu_c Gamma5_c) and its odd-even Schur
+// complement (Sec. 1 of the paper: P aggregates N_v test vectors and is
+// Gamma5-compatible, D_c keeps Gamma5-hermiticity, the twisted-mass term stays
+// diagonal, mu_c = delta mu on the coarsest grid; Sec. 3: odd-even
+// preconditioning on the coarsest level).
+//
+// P is stored as N_v fine fields in the chunked spinor layout: field i holds
+// column i of P_{a,0} on spins {0,1} and column i of P_{a,1} on spins {2,3}
+// of every aggregate a.  The two chirality halves of a site are whole 16-byte
+// chunks (12 reals each).  A coarse vector is [Vc][2 N_v] complex with index
+// chi * N_v + i.  D_c is stored per coarse site as 9 blocks (self, then
+// forward/backward per direction T, Z, Y, X), each column-major [col][row] so
+// that one thread per row reads consecutive addresses.
+#include "tm_kernels.h"
+#include "tm_stencil.cuh"
+
+namespace tmamg {
+
+// fine site of thread l of aggregate a, with its local and global coordinates
+__device__ __forceinline__ int agg_site(const AggGeom& ag, int a, int l, int lc[4], int c[4]) {
+  int ac[4];
+  site_coords(ag.gc, a, ac);
+  int q = l;
+  lc[3] = q % ag.agg[3];
+  q /= ag.agg[3];
+  lc[2] = q % ag.agg[2];
+  q /= ag.agg[2];
+  lc[1] = q % ag.agg[1];
+  lc[0] = q / ag.agg[1];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) c[d] = ac[d] * ag.agg[d] + lc[d];
+  return ((c[0] * ag.g.L[1] + c[1]) * ag.g.L[2] + c[2]) * ag.g.L[3] + c[3];
+}
+
+__device__ __forceinline__ int coarse_of(const AggGeom& ag, const int c[4]) {
+  return (((c[0] / ag.agg[0]) * ag.gc.L[1] + c[1] / ag.agg[1]) * ag.gc.L[2] + c[2] / ag.agg[2]) * ag.gc.L[3] +
+         c[3] / ag.agg[3];
+}
+
+// ===========================================================================
+// orthonormalisation: per (aggregate, chirality) classical Gram-Schmidt
+// applied twice, giving the Q of the thin QR with a real positive R diagonal
+// ===========================================================================
+template <typename T>
+__global__ void k_orthonormalise(T* P, AggGeom ag, int* err) {
+  __shared__ double red[32 * 16];
+  const int a = blockIdx.x, chi = blockIdx.y, nv = ag.nv;
+  const int l = threadIdx.x;
+  const bool act = l < ag.asites;
+  int lc[4], c[4];
+  const int s = act ? agg_site(ag, a, l, lc, c) : 0;
+  const long V = ag.g.V;
+  const long fstride = (long)NR_SPINOR * V;
+  const long choff = 12L * chi * V;  // chunk offset of this chirality's 6 complex numbers
+  for (int j = 0; j < nv; ++j) {
+    cx<T> v[6];
+    if (act) ld_cx<T, 6>(P + j * fstride + choff, V, s, v);
+    else
+      for (int k = 0; k < 6; ++k) v[k] = cx<T>{0, 0};
+    double t0[1] = {0};
+    for (int k = 0; k < 6; ++k) t0[0] += (double)norm2(v[k]);
+    block_allreduce<double, 1>(t0, red);
+    const double n0 = t0[0];
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i0 = 0; i0 < j; i0 += 8) {
+        double d[16];
+        for (int m = 0; m < 16; ++m) d[m] = 0;
+        if (act) {
+          for (int ii = 0; ii < 8 && i0 + ii < j; ++ii) {
+            cx<T> q[6];
+            ld_cx<T, 6>(P + (i0 + ii) * fstride + choff, V, s, q);
+            for (int k = 0; k < 6; ++k) {
+              d[2 * ii] += (double)q[k].r * v[k].r + (double)q[k].i * v[k].i;
+              d[2 * ii + 1] += (double)q[k].r * v[k].i - (double)q[k].i * v[k].r;
+            }
+          }
+        }
+        block_allreduce<double, 16>(d, red);
+        if (act) {
+          for (int ii = 0; ii < 8 && i0 + ii < j; ++ii) {
+            cx<T> q[6];
+            ld_cx<T, 6>(P + (i0 + ii) * fstride + choff, V, s, q);
+            const cx<T> cc{(T)d[2 * ii], (T)d[2 * ii + 1]};
+            for (int k = 0; k < 6; ++k) v[k] = v[k] - cc * q[k];
+          }
+        }
+      }
+    }
+    double t1[1] = {0};
+    for (int k = 0; k < 6; ++k) t1[0] += (double)norm2(v[k]);
+    block_allreduce<double, 1>(t1, red);
+    double nn = t1[0];
+    if (!(nn > 1e-24 * n0) || !(nn > 0)) {
+      if (l == 0) atomicOr(err, ERRF_RANK);
+      nn = 1;
+    }
+    const T inv = (T)(1.0 / sqrt(nn));
+    if (act) {
+      for (int k = 0; k < 6; ++k) v[k] = inv * v[k];
+      st_cx<T, 6>(P + j * fstride + choff, V, s, v);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_orthonormalise(T* P, const AggGeom& ag, int* err, cudaStream_t st) {
+  const int threads = (ag.asites + 31) / 32 * 32;
+  dim3 grid(ag.gc.V, 2);
+  k_orthonormalise<T><<<grid, threads, 0, st>>>(P, ag, err);
+}
+
+// ===========================================================================
+// restriction  coarse(a, chi*Nv + i) = sum_{x in a, comp in chi} conj(P_i) fine
+// ===========================================================================
+template <typename T>
+__global__ void k_restrict(const T* __restrict__ P, const T* __restrict__ fine, T* __restrict__ coarse,
+                           AggGeom ag) {
+  __shared__ T red[32 * 16];
+  const int a = blockIdx.x, rhs = blockIdx.y, nv = ag.nv;
+  const int l = threadIdx.x;
+  const bool act = l < ag.asites;
+  int lc[4], c[4];
+  const int s = act ? agg_site(ag, a, l, lc, c) : 0;
+  const long V = ag.g.V;
+  cx<T> r[12];
+  if (act) ld_cx<T, 12>(fine + (long)rhs * NR_SPINOR * V, V, s, r);
+  cx<T>* out = reinterpret_cast<cx<T>*>(coarse) + ((long)rhs * ag.gc.V + a) * 2 * nv;
+  for (int i0 = 0; i0 < nv; i0 += 4) {
+    T d[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) d[m] = 0;
+    if (act) {
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii) {
+        if (i0 + ii < nv) {
+          cx<T> p[12];
+          ld_cx<T, 12>(P + (long)(i0 + ii) * NR_SPINOR * V, V, s, p);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            cx<T> acc{0, 0};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) cfmac(acc, p[6 * h + k], r[6 * h + k]);
+            d[4 * ii + 2 * h] = acc.r;
+            d[4 * ii + 2 * h + 1] = acc.i;
+          }
+        }
+      }
+    }
+    block_allreduce<T, 16>(d, red);
+    if (l < 8) {
+      const int ii = l >> 1, h = l & 1;
+      if (i0 + ii < nv) out[h * nv + i0 + ii] = cx<T>{d[4 * ii + 2 * h], d[4 * ii + 2 * h + 1]};
+    }
+  }
+}
+
+template <typename T>
+void launch_restrict(const T* P, const T* fine, T* coarse, const AggGeom& ag, int nrhs, cudaStream_t st) {
+  const int threads = (ag.asites + 31) / 32 * 32;
+  dim3 grid(ag.gc.V, nrhs);
+  k_restrict<T><<<grid, threads, 0, st>>>(P, fine, coarse, ag);
+}
+
+// ===========================================================================
+// prolongation  fine(x, comp in chi) (+)= sum_i P_i(x, comp) coarse(a(x), chi*Nv + i)
+// ===========================================================================
+template <typename T, bool ACC>
+__global__ void k_prolong(const T* __restrict__ P, const T* __restrict__ coarse, T* __restrict__ fine,
+                          AggGeom ag) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y, nv = ag.nv;
+  const long V = ag.g.V;
+  if (s >= V) return;
+  int c[4];
+  site_coords(ag.g, s, c);
+  const int a = coarse_of(ag, c);
+  const cx<T>* e = reinterpret_cast<const cx<T>*>(coarse) + ((long)rhs * ag.gc.V + a) * 2 * nv;
+  T* f = fine + (long)rhs * NR_SPINOR * V;
+  cx<T> out[12];
+  if (ACC) ld_cx<T, 12>(f, V, s, out);
+  else
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = cx<T>{0, 0};
+  for (int i = 0; i < nv; ++i) {
+    cx<T> p[12];
+    ld_cx<T, 12>(P + (long)i * NR_SPINOR * V, V, s, p);
+    const cx<T> e0 = e[i], e1 = e[nv + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      cfma(out[k], p[k], e0);
+      cfma(out[6 + k], p[6 + k], e1);
+    }
+  }
+  st_cx<T, 12>(f, V, s, out);
+}
+
+template <typename T>
+void launch_prolong(const T* P, const T* coarse, T* fine, const AggGeom& ag, int nrhs, bool accumulate,
+                    cudaStream_t st) {
+  dim3 grid((ag.g.V + 127) / 128, nrhs);
+  if (accumulate)
+    k_prolong<T, true><<<grid, 128, 0, st>>>(P, coarse, fine, ag);
+  else
+    k_prolong<T, false><<<grid, 128, 0, st>>>(P, coarse, fine, ag);
+}
+
+// ===========================================================================
+// coarse operator build (local Galerkin projection, mu-free)
+//   block 0:        P_a^dagger [A + hops inside a] P_a
+//   block 1 + 2 mu: P_a^dagger [hops from a's upper mu-face into a + mu] P_{a+mu}
+//   block 2 + 2 mu: P_a^dagger [hops from a's lower mu-face into a - mu] P_{a-mu}
+// One CTA per (column k, block t, aggregate a); thread = fine site of a.
+// ===========================================================================
+template <typename T>
+__device__ __forceinline__ void src_column(const T* __restrict__ P, long V, int s, int j, int chi, cx<T> (&p)[12]) {
+  ld_cx<T, 12>(P + (long)j * NR_SPINOR * V, V, s, p);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[6 * (1 - chi) + k] = cx<T>{0, 0};
+}
+
+template <typename T, int MU>
+__device__ __forceinline__ void build_hops(const T* __restrict__ P, const T* __restrict__ gauge, const AggGeom& ag,
+                                           int s, const int c[4], const int lc[4], int j, int chi, int t, T bc,
+                                           bool& on, cx<T> (&acc)[12]) {
+  const Lat& g = ag.g;
+  const bool up = lc[MU] == ag.agg[MU] - 1, lo = lc[MU] == 0;
+  // forward hop: inside a for t == 0 unless on the upper face; block 1+2MU on it
+  if ((t == 0 && !up) || (t == 1 + 2 * MU && up)) {
+    const int sf = nb_fwd(g, s, c, MU);
+    cx<T> p[12];
+    src_column<T>(P, g.V, sf, j, chi, p);
+    const T sign = (MU == 0 && c[0] == g.L[0] - 1) ? bc : T(1);
+    hop_fwd_p<T, MU>(p, gauge, g.V, s, sign, acc);
+    on = true;
+  }
+  if ((t == 0 && !lo) || (t == 2 + 2 * MU && lo)) {
+    const int sb = nb_bwd(g, s, c, MU);
+    cx<T> p[12];
+    src_column<T>(P, g.V, sb, j, chi, p);
+    const T sign = (MU == 0 && c[0] == 0) ? bc : T(1);
+    hop_bwd_p<T, MU>(p, gauge, g.V, sb, sign, acc);
+    on = true;
+  }
+}
+
+template <typename T>
+__global__ void k_coarse_build(const T* __restrict__ gauge, const T* __restrict__ clover, const T* __restrict__ P,
+                               T* __restrict__ Dc, AggGeom ag, T bc) {
+  __shared__ T red[32 * 16];
+  const int nv = ag.nv, n = 2 * nv;
+  const int kk = blockIdx.x, t = blockIdx.y, a = blockIdx.z;
+  const int chi = kk / nv, j = kk % nv;
+  const int l = threadIdx.x;
+  const bool act = l < ag.asites;
+  int lc[4], c[4];
+  const int s = act ? agg_site(ag, a, l, lc, c) : 0;
+  const long V = ag.g.V;
+  cx<T> u[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) u[k] = cx<T>{0, 0};
+  bool on = false;
+  if (act) {
+    cx<T> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = cx<T>{0, 0};
+    build_hops<T, 0>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
+    build_hops<T, 1>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
+    build_hops<T, 2>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
+    build_hops<T, 3>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
+    if (t == 0) {
+      cx<T> p[12];
+      src_column<T>(P, V, s, j, chi, p);
+      site_diag<T>(clover, (int)V, s, T(0), p, u);
+      on = true;
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) u[k] = u[k] - T(0.5) * acc[k];
+  }
+  T* out = Dc + (((long)a * 9 + t) * n + kk) * n * 2;  // column kk of block t, [row] complex
+  for (int i0 = 0; i0 < nv; i0 += 4) {
+    T d[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) d[m] = 0;
+    if (act && on) {
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii) {
+        if (i0 + ii < nv) {
+          cx<T> p[12];
+          ld_cx<T, 12>(P + (long)(i0 + ii) * NR_SPINOR * V, V, s, p);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            cx<T> acc{0, 0};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) cfmac(acc, p[6 * h + k], u[6 * h + k]);
+            d[4 * ii + 2 * h] = acc.r;
+            d[4 * ii + 2 * h + 1] = acc.i;
+          }
+        }
+      }
+    }
+    block_allreduce<T, 16>(d, red);
+    if (l < 8) {
+      const int ii = l >> 1, h = l & 1;
+      if (i0 + ii < nv) {
+        const int row = h * nv + i0 + ii;
+        out[2 * row] = d[4 * ii + 2 * h];
+        out[2 * row + 1] = d[4 * ii + 2 * h + 1];
+      }
+    }
+  }
+}
+
+template <typename T>
+void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, const AggGeom& ag, double bc_t,
+                         cudaStream_t st) {
+  const int threads = (ag.asites + 31) / 32 * 32;
+  dim3 grid(2 * ag.nv, 9, ag.gc.V);
+  k_coarse_build<T><<<grid, threads, 0, st>>>(gauge, clover, P, Dc, ag, (T)bc_t);
+}
+
+// ===========================================================================
+// coarse stencil helpers
+// ===========================================================================
+// neighbour of coarse site a for block t (t = 0 self)
+__device__ __forceinline__ int coarse_nb(const Lat& gc, int a, int t) {
+  if (t == 0) return a;
+  int c[4];
+  site_coords(gc, a, c);
+  const int mu = (t - 1) >> 1;
+  return ((t - 1) & 1) ? nb_bwd(gc, a, c, mu) : nb_fwd(gc, a, c, mu);
+}
+
+// y = D_c(mu_c) v on the full coarse lattice; CTA per coarse site,
+// threads (t, row): partial sums over columns, reduced over t in shared memory
+template <typename T>
+__global__ void k_coarse_apply(const T* __restrict__ Dc, const T* __restrict__ v, T* __restrict__ y, Lat gc, int nv,
+                               T mu_c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);  // [9][n]
+  const int n = 2 * nv;
+  const int a = blockIdx.x, rhs = blockIdx.y;
+  const int row = threadIdx.x % n, t = threadIdx.x / n;
+  const cx<T>* vv = reinterpret_cast<const cx<T>*>(v) + (long)rhs * gc.V * n;
+  if (t < 9) {
+    const int nb = coarse_nb(gc, a, t);
+    const cx<T>* src = vv + (long)nb * n;
+    const cx<T>* B = reinterpret_cast<const cx<T>*>(Dc) + ((long)a * 9 + t) * n * n;
+    cx<T> acc{0, 0};
+    for (int col = 0; col < n; ++col) cfma(acc, B[(long)col * n + row], src[col]);
+    part[t * n + row] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    cx<T> acc = part[row];
+    for (int q = 1; q < 9; ++q) acc = acc + part[q * n + row];
+    const cx<T> x = vv[(long)a * n + row];
+    const T sg = row < nv ? -mu_c : mu_c;  // i mu_c Gamma5_c
+    acc.r -= sg * x.i;
+    acc.i += sg * x.r;
+    reinterpret_cast<cx<T>*>(y)[(long)rhs * gc.V * n + (long)a * n + row] = acc;
+  }
+}
+
+template <typename T>
+void launch_coarse_apply(const T* Dc, const T* v, T* y, const Lat& gc, int nv, double mu_c, int nrhs,
+                         cudaStream_t st) {
+  const int n = 2 * nv;
+  const int threads = (9 * n + 31) / 32 * 32;
+  dim3 grid(gc.V, nrhs);
+  k_coarse_apply<T><<<grid, threads, 9 * n * sizeof(cx<T>), st>>>(Dc, v, y, gc, nv, (T)mu_c);
+}
+
+// ===========================================================================
+// odd-even on the coarse lattice
+// ===========================================================================
+// Gauss-Jordan inverse with partial pivoting of (self block + i mu_c G5c) at each odd site
+template <typename T>
+__global__ void k_oe_invert(const T* __restrict__ Dc, T* __restrict__ Dinv, OEGeom oe, T mu_c, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = 2 * oe.nv, w = 2 * n;
+  cx<T>* M = reinterpret_cast<cx<T>*>(smem_raw);  // [n][2n] row-major augmented
+  __shared__ int piv;
+  __shared__ T fac_r[128], fac_i[128];
+  const int k = blockIdx.x;
+  const int a = oe.odd_site[k];
+  const cx<T>* B = reinterpret_cast<const cx<T>*>(Dc) + (long)a * 9 * n * n;
+  for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
+    const int r = e / w, cc = e % w;
+    cx<T> val{0, 0};
+    if (cc < n) {
+      val = B[(long)cc * n + r];
+      if (cc == r) val.i += (r < oe.nv ? -mu_c : mu_c);
+    } else if (cc - n == r) {
+      val = cx<T>{1, 0};
+    }
+    M[r * w + cc] = val;
+  }
+  __syncthreads();
+  for (int col = 0; col < n; ++col) {
+    if (threadIdx.x == 0) {
+      int p = col;
+      T best = norm2(M[col * w + col]);
+      for (int r = col + 1; r < n; ++r) {
+        const T v = norm2(M[r * w + col]);
+        if (v > best) {
+          best = v;
+          p = r;
+        }
+      }
+      if (!(best > T(0))) atomicOr(err, ERRF_SINGULAR);
+      piv = p;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != col) {
+      for (int cc = threadIdx.x; cc < w; cc += blockDim.x) {
+        const cx<T> tmp = M[col * w + cc];
+        M[col * w + cc] = M[p * w + cc];
+        M[p * w + cc] = tmp;
+      }
+    }
+    __syncthreads();
+    cx<T> pv = M[col * w + col];
+    const T den = norm2(pv);
+    const cx<T> inv = den > T(0) ? cx<T>{pv.r / den, -pv.i / den} : cx<T>{0, 0};
+    __syncthreads();
+    for (int cc = threadIdx.x; cc < w; cc += blockDim.x) M[col * w + cc] = M[col * w + cc] * inv;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      fac_r[r] = M[r * w + col].r;
+      fac_i[r] = M[r * w + col].i;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
+      const int r = e / w, cc = e % w;
+      if (r != col) {
+        const cx<T> f{fac_r[r], fac_i[r]};
+        M[r * w + cc] = M[r * w + cc] - f * M[col * w + cc];
+      }
+    }
+    __syncthreads();
+  }
+  cx<T>* out = reinterpret_cast<cx<T>*>(Dinv) + (long)k * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int cc = e / n, r = e % n;  // column-major output
+    out[(long)cc * n + r] = M[r * w + n + cc];
+  }
+}
+
+template <typename T>
+void launch_oe_invert(const T* Dc, T* Dinv, const OEGeom& oe, double mu_c, int* err, cudaStream_t st) {
+  const int n = 2 * oe.nv;
+  const size_t smem = (size_t)n * 2 * n * sizeof(cx<T>);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_oe_invert<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_oe_invert<T><<<oe.nhalf, 256, smem, st>>>(Dc, Dinv, oe, (T)mu_c, err);
+}
+
+// Generic odd-even stencil piece on sites of one parity (compact index k):
+//   acc = pre + sgn * sum_{t=1..8} B_t(site) src(nb_t(site))   [src compact, other parity]
+//   out = post ? Dinv(k) acc : acc
+// pre: 0 (mode 0), (self + i mu_c G5c) v(site) with v compact (mode 1), or
+// b(site) with b a full coarse vector (mode 2).
+template <typename T>
+struct OEArgs {
+  const T* Dc;
+  const T* Dinv;
+  const T* src;   // compact, other parity
+  const T* pre;   // mode 1: compact same parity; mode 2: full vector
+  T* out;         // compact (or full when full_out)
+  OEGeom oe;
+  T mu_c;
+  T sgn;
+  int mode;
+  int odd;        // target parity
+  int post;       // multiply by Dinv (odd targets only)
+  int full_out;   // write into a full coarse vector at the site
+};
+
+template <typename T>
+__global__ void k_oe_stencil(OEArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nv = a.oe.nv, n = 2 * nv;
+  cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);  // [9][n]
+  cx<T>* accs = part + 9 * n;                          // [n]
+  const int k = blockIdx.x;
+  const int site = a.odd ? a.oe.odd_site[k] : a.oe.even_site[k];
+  const int row = threadIdx.x % n, t = threadIdx.x / n;
+  const cx<T>* B = reinterpret_cast<const cx<T>*>(a.Dc) + (long)site * 9 * n * n;
+  if (t < 9) {
+    cx<T> acc{0, 0};
+    if (t == 0) {
+      if (a.mode == 1) {
+        const cx<T>* v = reinterpret_cast<const cx<T>*>(a.pre) + (long)k * n;
+        for (int col = 0; col < n; ++col) cfma(acc, B[(long)col * n + row], v[col]);
+        const cx<T> x = v[row];
+        const T sg = row < nv ? -a.mu_c : a.mu_c;
+        acc.r -= sg * x.i;
+        acc.i += sg * x.r;
+      } else if (a.mode == 2) {
+        acc = reinterpret_cast<const cx<T>*>(a.pre)[(long)site * n + row];
+      }
+    } else {
+      const int nb = coarse_nb(a.oe.gc, site, t);
+      const cx<T>* src = reinterpret_cast<const cx<T>*>(a.src) + (long)a.oe.cidx[nb] * n;
+      cx<T> h{0, 0};
+      const cx<T>* Bt = B + (long)t * n * n;
+      for (int col = 0; col < n; ++col) cfma(h, Bt[(long)col * n + row], src[col]);
+      acc = a.sgn * h;
+    }
+    part[t * n + row] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    cx<T> acc = part[row];
+    for (int q = 1; q < 9; ++q) acc = acc + part[q * n + row];
+    accs[row] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    cx<T> res = accs[row];
+    if (a.post) {
+      const cx<T>* Di = reinterpret_cast<const cx<T>*>(a.Dinv) + (long)k * n * n;
+      res = cx<T>{0, 0};
+      for (int col = 0; col < n; ++col) cfma(res, Di[(long)col * n + row], accs[col]);
+    }
+    cx<T>* out = reinterpret_cast<cx<T>*>(a.out);
+    if (a.full_out)
+      out[(long)site * n + row] = res;
+    else
+      out[(long)k * n + row] = res;
+  }
+}
+
+template <typename T>
+static void launch_oe_stencil(const OEArgs<T>& a, cudaStream_t st) {
+  const int n = 2 * a.oe.nv;
+  const int threads = (9 * n + 31) / 32 * 32;
+  k_oe_stencil<T><<<a.oe.nhalf, threads, 10 * n * sizeof(cx<T>), st>>>(a);
+}
+
+template <typename T>
+void launch_oe_hop_inv(const T* Dc, const T* Dinv, const T* ve, T* uo, const OEGeom& oe, cudaStream_t st) {
+  OEArgs<T> a{Dc, Dinv, ve, nullptr, uo, oe, T(0), T(1), 0, 1, 1, 0};
+  launch_oe_stencil(a, st);
+}
+template <typename T>
+void launch_oe_even(const T* Dc, const T* ve, const T* uo, T* ye, const OEGeom& oe, double mu_c, int diag,
+                    cudaStream_t st) {
+  OEArgs<T> a{Dc, nullptr, uo, ve, ye, oe, (T)mu_c, T(-1), diag ? 1 : 0, 0, 0, 0};
+  launch_oe_stencil(a, st);
+}
+template <typename T>
+void launch_oe_rhs(const T* Dc, const T* b, const T* to, T* bh, const OEGeom& oe, cudaStream_t st) {
+  OEArgs<T> a{Dc, nullptr, to, b, bh, oe, T(0), T(-1), 2, 0, 0, 0};
+  launch_oe_stencil(a, st);
+}
+
+// t_o = Dinv b_o  (b full); CTA per odd site, thread per row
+template <typename T>
+__global__ void k_oe_inv_odd(const T* __restrict__ Dinv, const T* __restrict__ b, T* __restrict__ to, OEGeom oe) {
+  const int n = 2 * oe.nv;
+  const int k = blockIdx.x, row = threadIdx.x;
+  if (row >= n) return;
+  const int site = oe.odd_site[k];
+  const cx<T>* bb = reinterpret_cast<const cx<T>*>(b) + (long)site * n;
+  const cx<T>* Di = reinterpret_cast<const cx<T>*>(Dinv) + (long)k * n * n;
+  cx<T> acc{0, 0};
+  for (int col = 0; col < n; ++col) cfma(acc, Di[(long)col * n + row], bb[col]);
+  reinterpret_cast<cx<T>*>(to)[(long)k * n + row] = acc;
+}
+
+template <typename T>
+void launch_oe_inv_odd(const T* Dinv, const T* b, T* to, const OEGeom& oe, cudaStream_t st) {
+  const int n = 2 * oe.nv;
+  k_oe_inv_odd<T><<<oe.nhalf, (n + 31) / 32 * 32, 0, st>>>(Dinv, b, to, oe);
+}
+
+// scatter the compact even solution into the full vector
+template <typename T>
+__global__ void k_oe_scatter_even(const T* __restrict__ xe, T* __restrict__ x, OEGeom oe) {
+  const int n = 2 * oe.nv;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)oe.nhalf * n) return;
+  const int k = (int)(e / n), row = (int)(e % n);
+  reinterpret_cast<cx<T>*>(x)[(long)oe.even_site[k] * n + row] = reinterpret_cast<const cx<T>*>(xe)[e];
+}
+
+template <typename T>
+void launch_oe_reconstruct(const T* Dc, const T* Dinv, const T* b, const T* xe, T* x, const OEGeom& oe,
+                           cudaStream_t st) {
+  const int n = 2 * oe.nv;
+  const long tot = (long)oe.nhalf * n;
+  k_oe_scatter_even<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(xe, x, oe);
+  OEArgs<T> a{Dc, Dinv, xe, b, x, oe, T(0), T(-1), 2, 1, 1, 1};
+  launch_oe_stencil(a, st);
+}
+
+#define TM_INST(T)                                                                                               \
+  template void launch_orthonormalise<T>(T*, const AggGeom&, int*, cudaStream_t);                              \
+  template void launch_restrict<T>(const T*, const T*, T*, const AggGeom&, int, cudaStream_t);                 \
+  template void launch_prolong<T>(const T*, const T*, T*, const AggGeom&, int, bool, cudaStream_t);            \
+  template void launch_coarse_build<T>(const T*, const T*, const T*, T*, const AggGeom&, double, cudaStream_t); \
+  template void launch_coarse_apply<T>(const T*, const T*, T*, const Lat&, int, double, int, cudaStream_t);    \
+  template void launch_oe_invert<T>(const T*, T*, const OEGeom&, double, int*, cudaStream_t);                  \
+  template void launch_oe_hop_inv<T>(const T*, const T*, const T*, T*, const OEGeom&, cudaStream_t);           \
+  template void launch_oe_even<T>(const T*, const T*, const T*, T*, const OEGeom&, double, int, cudaStream_t); \
+  template void launch_oe_inv_odd<T>(const T*, const T*, T*, const OEGeom&, cudaStream_t);                     \
+  template void launch_oe_rhs<T>(const T*, const T*, const T*, T*, const OEGeom&, cudaStream_t);               \
+  template void launch_oe_reconstruct<T>(const T*, const T*, const T*, const T*, T*, const OEGeom&, cudaStream_t);
+TM_INST(double)
+TM_INST(float)
+#undef TM_INST
+
+}  // namespace tmamg

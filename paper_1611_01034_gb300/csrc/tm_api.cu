@@ -1,0 +1,1038 @@
+// C ABI and host orchestration of the twisted-mass DD-alphaAMG solver:
+// FGMRES (FP64) preconditioned by the K-cycle of eq. (1) (SAP smoother,
+// restriction, odd-even GMRES on D_c(delta mu), prolongation), the adaptive
+// setup, and the field-level entry points.  All arithmetic on vectors runs
+// in the kernels of dirac.cu, sap.cu, coarse.cu and blas.cu; the host only
+// sequences launches and solves the small Hessenberg least-squares problems.
+#include "tm.h"
+#include "tm_kernels.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <type_traits>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace tmamg;
+
+namespace {
+
+struct TmError {
+  tm_status s;
+  std::string m;
+};
+
+[[noreturn]] void raise(tm_status s, const std::string& m) { throw TmError{s, m}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    raise(e == cudaErrorMemoryAllocation ? TM_ERR_OOM : TM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+#define CK(x) ck((x), #x)
+#define CKL() ck(cudaGetLastError(), "kernel launch")
+
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct tm_handle {
+  tm_params p;
+  cudaStream_t st = nullptr;
+  Lat g{}, gc{};
+  SapGeom sg{};
+  AggGeom ag{};
+  OEGeom oe{};
+  int n = 0;       // 2 Nv
+  int nhalf = 0;   // coarse sites per parity
+  int* d_err = nullptr;
+  double* g64 = nullptr;
+  float* g32 = nullptr;
+  double* c64 = nullptr;
+  float* c32 = nullptr;
+  void* tv = nullptr;
+  void* P = nullptr;
+  void* Dc = nullptr;
+  void* Dinv = nullptr;
+  int* d_even = nullptr;
+  int* d_odd = nullptr;
+  int* d_cidx = nullptr;
+  double* scratch = nullptr;  // reduction partials
+  double* dsmall = nullptr;   // small device results
+  double* hsmall = nullptr;   // pinned host mirror
+  std::map<std::string, Buf> work;
+  bool gauge_ok = false, setup_ok = false;
+  std::string err;
+  long long coarse_iters = 0;
+  int kcycles = 0;
+};
+
+namespace {
+
+constexpr int kScratchBlocks = kReduceBlocks;
+constexpr int kMaxDots = 128;
+constexpr int kSmall = 4096;
+
+size_t csize(int prec) { return prec == TM_F64 ? sizeof(double) : sizeof(float); }
+
+void* dalloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) return nullptr;
+  ck(cudaMalloc(&p, bytes), "cudaMalloc");
+  return p;
+}
+
+// named, lazily grown device work buffer
+template <typename T>
+T* W(tm_handle* h, const std::string& name, size_t count) {
+  Buf& b = h->work[name];
+  const size_t bytes = count * sizeof(T);
+  if (b.n < bytes) {
+    if (b.p) CK(cudaFree(b.p));
+    b.p = nullptr;
+    b.n = 0;
+    b.p = dalloc(bytes);
+    b.n = bytes;
+  }
+  return static_cast<T*>(b.p);
+}
+
+void sync(tm_handle* h) { CK(cudaStreamSynchronize(h->st)); }
+
+void check_flags(tm_handle* h) {
+  int f = 0;
+  CK(cudaMemcpyAsync(&f, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  sync(h);
+  if (f) {
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
+    if (f & ERRF_NOT_SU3) raise(TM_ERR_NOT_SU3, "gauge link not in SU(3) within 1e-10");
+    if (f & ERRF_RANK) raise(TM_ERR_ARG, "test vectors are rank deficient on an aggregate");
+    if (f & ERRF_SINGULAR) raise(TM_ERR_ARG, "singular coarse self block");
+    raise(TM_ERR_NONFINITE, "non-finite value");
+  }
+}
+
+template <typename T>
+const T* gaugeT(tm_handle* h);
+template <>
+const double* gaugeT<double>(tm_handle* h) { return h->g64; }
+template <>
+const float* gaugeT<float>(tm_handle* h) { return h->g32; }
+template <typename T>
+const T* cloverT(tm_handle* h);
+template <>
+const double* cloverT<double>(tm_handle* h) { return h->c64; }
+template <>
+const float* cloverT<float>(tm_handle* h) { return h->c32; }
+
+long fine_reals(tm_handle* h) { return (long)NR_SPINOR * h->g.V; }
+long coarse_cx(tm_handle* h) { return (long)h->gc.V * h->n; }
+
+double mu_c(tm_handle* h) { return h->p.delta * h->p.mu; }
+
+// ---------------------------------------------------------------------------
+// fine operator pieces
+// ---------------------------------------------------------------------------
+template <typename T>
+void dslash(tm_handle* h, const T* in, T* out, const T* b, int nrhs) {
+  launch_dslash<T>(gaugeT<T>(h), cloverT<T>(h), in, out, b, h->g, h->p.mu, h->p.bc_t, nrhs, h->st);
+  CKL();
+}
+
+template <typename T>
+void sap_sweeps(tm_handle* h, const T* b, T* x, int sweeps, int nrhs) {
+  for (int s = 0; s < sweeps; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      launch_sap_colour<T>(gaugeT<T>(h), cloverT<T>(h), b, x, h->sg, h->p.mu, h->p.bc_t, h->p.mr_iters, colour, nrhs,
+                           h->st);
+      CKL();
+    }
+}
+
+// ||x_r||^2 for nrhs vectors -> host
+template <typename T>
+std::vector<double> norms2(tm_handle* h, const T* x, long ncx, int nrhs) {
+  launch_norm2<T>(x, ncx, nrhs, h->dsmall, h->scratch, kScratchBlocks, h->st);
+  CKL();
+  CK(cudaMemcpyAsync(h->hsmall, h->dsmall, nrhs * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  sync(h);
+  return std::vector<double>(h->hsmall, h->hsmall + nrhs);
+}
+
+// ---------------------------------------------------------------------------
+// restarted (flexible) GMRES, CGS2 Arnoldi, Givens on the host
+//   A(const T* in, T* out)   operator on basis-type vectors (true residuals)
+//   AZ(const TZ* z, T* out)  operator on preconditioned vectors (flexible)
+//   M(const T* v, TZ* z)     preconditioner (flexible)
+// ---------------------------------------------------------------------------
+struct KrylovOut {
+  int iters = 0;
+  int restarts = 0;
+  double relres = 0;
+  bool converged = false;
+};
+
+void givens(std::complex<double> a, double b, double& c, std::complex<double>& s, std::complex<double>& rho) {
+  if (b == 0) {
+    c = 1;
+    s = 0;
+    rho = a;
+    return;
+  }
+  if (std::abs(a) == 0) {
+    c = 0;
+    s = 1;
+    rho = b;
+    return;
+  }
+  const double nu = std::hypot(std::abs(a), b);
+  c = std::abs(a) / nu;
+  const std::complex<double> ph = a / std::abs(a);
+  s = ph * b / nu;  // conj(b) = b (real)
+  rho = ph * nu;
+}
+
+template <typename T, typename TZ, typename FA, typename FAZ, typename FM>
+KrylovOut krylov(tm_handle* h, const std::string& tag, FA A, FAZ AZ, FM M, bool flexible, const T* b, T* x,
+                 bool x0, long ncx, double tol, int m, int maxit) {
+  using cd = std::complex<double>;
+  KrylovOut out;
+  T* Vb = W<T>(h, tag + "V", (size_t)(m + 1) * 2 * ncx);
+  T* w = W<T>(h, tag + "w", (size_t)2 * ncx);
+  TZ* Z = flexible ? W<TZ>(h, tag + "Z", (size_t)m * 2 * ncx) : nullptr;
+  const long ld = 2 * ncx;
+  const double bnorm = std::sqrt(norms2<T>(h, b, ncx, 1)[0]);
+  if (!std::isfinite(bnorm)) raise(TM_ERR_NONFINITE, "non-finite right-hand side");
+  if (!x0) {
+    launch_zero<T>(x, 2 * ncx, h->st);
+    CKL();
+  }
+  if (bnorm == 0) {
+    launch_zero<T>(x, 2 * ncx, h->st);
+    CKL();
+    out.converged = true;
+    return out;
+  }
+  // r = b - A x
+  auto residual = [&](T* r) {
+    if (x0 || out.iters > 0) {
+      A(x, w);
+      CK(cudaMemcpyAsync(r, b, 2 * ncx * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+      launch_caxpby<T>(-1, 0, w, 1, 0, r, ncx, h->st);
+      CKL();
+    } else {
+      CK(cudaMemcpyAsync(r, b, 2 * ncx * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+    }
+    return std::sqrt(norms2<T>(h, r, ncx, 1)[0]);
+  };
+  double beta = residual(Vb);
+  std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m), y(m);
+  std::vector<double> cs(m);
+  while (beta > tol * bnorm && out.iters < maxit) {
+    if (!std::isfinite(beta)) raise(TM_ERR_NONFINITE, "non-finite residual");
+    launch_caxpby<T>(1.0 / beta, 0, Vb, 0, 0, Vb, ncx, h->st);
+    CKL();
+    std::fill(g.begin(), g.end(), cd(0));
+    g[0] = beta;
+    int k = 0;
+    while (k < m) {
+      T* vk = Vb + (long)k * ld;
+      if (flexible) {
+        TZ* zk = Z + (long)k * ld;
+        M(vk, zk);
+        AZ(zk, w);
+      } else {
+        A(vk, w);
+      }
+      // CGS2 against V_0..V_k
+      double* d1 = h->dsmall;
+      double* d2 = h->dsmall + 2 * kMaxDots;
+      double* dn = h->dsmall + 4 * kMaxDots;
+      launch_multidot<T>(Vb, ld, k + 1, w, ncx, d1, h->scratch, kScratchBlocks, h->st);
+      CKL();
+      launch_multi_caxpy<T>(Vb, ld, k + 1, d1, 1.0, w, ncx, h->st);
+      CKL();
+      launch_multidot<T>(Vb, ld, k + 1, w, ncx, d2, h->scratch, kScratchBlocks, h->st);
+      CKL();
+      launch_multi_caxpy<T>(Vb, ld, k + 1, d2, 1.0, w, ncx, h->st);
+      CKL();
+      launch_norm2<T>(w, ncx, 1, dn, h->scratch, kScratchBlocks, h->st);
+      CKL();
+      CK(cudaMemcpyAsync(Vb + (long)(k + 1) * ld, w, 2 * ncx * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+      launch_scale<T>(Vb + (long)(k + 1) * ld, ncx, 1, dn, true, h->st);
+      CKL();
+      CK(cudaMemcpyAsync(h->hsmall, h->dsmall, (4 * kMaxDots + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      sync(h);
+      const double hn = std::sqrt(h->hsmall[4 * kMaxDots]);
+      if (!std::isfinite(hn)) raise(TM_ERR_NONFINITE, "non-finite Arnoldi vector");
+      std::vector<cd> col(m + 1, cd(0));
+      for (int j = 0; j <= k; ++j)
+        col[j] = cd(h->hsmall[2 * j] + h->hsmall[2 * kMaxDots + 2 * j],
+                    h->hsmall[2 * j + 1] + h->hsmall[2 * kMaxDots + 2 * j + 1]);
+      col[k + 1] = hn;
+      for (int j = 0; j < k; ++j) {
+        const cd t = cs[j] * col[j] + sn[j] * col[j + 1];
+        col[j + 1] = -std::conj(sn[j]) * col[j] + cs[j] * col[j + 1];
+        col[j] = t;
+      }
+      double c;
+      cd s, rho;
+      givens(col[k], hn, c, s, rho);
+      cs[k] = c;
+      sn[k] = s;
+      col[k] = rho;
+      col[k + 1] = 0;
+      for (int j = 0; j <= m; ++j) H[(size_t)j * m + k] = col[j];
+      g[k + 1] = -std::conj(s) * g[k];
+      g[k] = c * g[k];
+      ++out.iters;
+      ++k;
+      if (hn == 0 || std::abs(g[k]) <= tol * bnorm || out.iters >= maxit) break;
+    }
+    // back substitution R y = g
+    for (int i = k - 1; i >= 0; --i) {
+      cd acc = g[i];
+      for (int j = i + 1; j < k; ++j) acc -= H[(size_t)i * m + j] * y[j];
+      y[i] = acc / H[(size_t)i * m + i];
+    }
+    for (int i = 0; i < k; ++i) {
+      h->hsmall[2 * i] = y[i].real();
+      h->hsmall[2 * i + 1] = y[i].imag();
+    }
+    double* dy = h->dsmall + 6 * kMaxDots;
+    CK(cudaMemcpyAsync(dy, h->hsmall, 2 * k * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    if (flexible)
+      launch_lincomb<TZ, T>(Z, ld, k, dy, x, ncx, h->st);
+    else
+      launch_lincomb<T, T>(Vb, ld, k, dy, x, ncx, h->st);
+    CKL();
+    ++out.restarts;
+    beta = residual(Vb);
+  }
+  out.relres = beta / bnorm;
+  out.converged = beta <= tol * bnorm;
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// coarse level
+// ---------------------------------------------------------------------------
+template <typename T>
+void build_coarse(tm_handle* h) {
+  T* P = static_cast<T*>(h->P);
+  launch_orthonormalise<T>(P, h->ag, h->d_err, h->st);
+  CKL();
+  launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, static_cast<T*>(h->Dc), h->ag, h->p.bc_t, h->st);
+  CKL();
+  launch_oe_invert<T>(static_cast<T*>(h->Dc), static_cast<T*>(h->Dinv), h->oe, mu_c(h), h->d_err, h->st);
+  CKL();
+}
+
+// odd-even GMRES on D_c(delta mu) x = b (full coarse vectors, one rhs)
+template <typename T>
+KrylovOut coarse_solve(tm_handle* h, const T* b, T* x, double tol, int maxit) {
+  const T* Dc = static_cast<const T*>(h->Dc);
+  const T* Di = static_cast<const T*>(h->Dinv);
+  const long nc = (long)h->nhalf * h->n;  // complex per parity
+  T* to = W<T>(h, "c_to", 2 * nc);
+  T* bh = W<T>(h, "c_bh", 2 * nc);
+  T* xe = W<T>(h, "c_xe", 2 * nc);
+  T* uo = W<T>(h, "c_uo", 2 * nc);
+  launch_oe_inv_odd<T>(Di, b, to, h->oe, h->st);
+  CKL();
+  launch_oe_rhs<T>(Dc, b, to, bh, h->oe, h->st);
+  CKL();
+  const double mc = mu_c(h);
+  auto S = [&](const T* ve, T* ye) {
+    launch_oe_hop_inv<T>(Dc, Di, ve, uo, h->oe, h->st);
+    CKL();
+    launch_oe_even<T>(Dc, ve, uo, ye, h->oe, mc, 1, h->st);
+    CKL();
+  };
+  auto none = [](const T*, T*) {};
+  KrylovOut r = krylov<T, T>(h, "cg", S, S, none, false, bh, xe, false, nc, tol, h->p.coarse_restart, maxit);
+  launch_oe_reconstruct<T>(Dc, Di, b, xe, x, h->oe, h->st);
+  CKL();
+  h->coarse_iters += r.iters;
+  return r;
+}
+
+// z = B(v), eq. (1), nrhs fine fields in T
+template <typename T>
+void kcycle(tm_handle* h, const T* v, T* z, int nrhs) {
+  const long fr = fine_reals(h);
+  launch_zero<T>(z, fr * nrhs, h->st);
+  CKL();
+  sap_sweeps<T>(h, v, z, h->p.pre_smooth, nrhs);
+  const T* r = v;
+  if (h->p.pre_smooth > 0) {
+    T* rr = W<T>(h, "k_r", fr * nrhs);
+    dslash<T>(h, z, rr, v, nrhs);
+    r = rr;
+  }
+  const long cc = coarse_cx(h);
+  T* rc = W<T>(h, "k_rc", 2 * cc * nrhs);
+  T* ec = W<T>(h, "k_ec", 2 * cc * nrhs);
+  launch_restrict<T>(static_cast<const T*>(h->P), r, rc, h->ag, nrhs, h->st);
+  CKL();
+  for (int i = 0; i < nrhs; ++i)
+    coarse_solve<T>(h, rc + 2 * cc * i, ec + 2 * cc * i, h->p.coarse_tol, h->p.coarse_maxit);
+  launch_prolong<T>(static_cast<const T*>(h->P), ec, z, h->ag, nrhs, true, h->st);
+  CKL();
+  sap_sweeps<T>(h, v, z, h->p.post_smooth, nrhs);
+  h->kcycles += nrhs;
+}
+
+template <typename T>
+void normalise_fields(tm_handle* h, T* f, int nrhs) {
+  const long fr = fine_reals(h);
+  launch_norm2<T>(f, fr / 2, nrhs, h->dsmall, h->scratch, kScratchBlocks, h->st);
+  CKL();
+  launch_scale<T>(f, fr / 2, nrhs, h->dsmall, true, h->st);
+  CKL();
+}
+
+template <typename T>
+void setup_impl(tm_handle* h, const double* tv_dev, bool adaptive) {
+  const int nv = h->p.nv;
+  const long fr = fine_reals(h);
+  T* tv = static_cast<T*>(h->tv);
+  T* P = static_cast<T*>(h->P);
+  launch_pack_spinor<T>(tv_dev, tv, h->g, nv, h->st);
+  CKL();
+  if (adaptive) {
+    sap_sweeps<T>(h, nullptr, tv, h->p.init_sweeps, nv);
+    normalise_fields<T>(h, tv, nv);
+  }
+  CK(cudaMemcpyAsync(P, tv, fr * nv * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+  build_coarse<T>(h);
+  check_flags(h);
+  if (adaptive) {
+    T* z = W<T>(h, "setup_z", fr * nv);
+    for (int it = 0; it < h->p.setup_iters; ++it) {
+      kcycle<T>(h, tv, z, nv);
+      CK(cudaMemcpyAsync(tv, z, fr * nv * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+      normalise_fields<T>(h, tv, nv);
+      CK(cudaMemcpyAsync(P, tv, fr * nv * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+      build_coarse<T>(h);
+      check_flags(h);
+    }
+  }
+  sync(h);
+}
+
+// FGMRES in FP64 preconditioned by the K-cycle in T; b, x packed FP64 fields
+template <typename T>
+KrylovOut solve_one(tm_handle* h, const double* b, double* x, double tol) {
+  const long fr = fine_reals(h);
+  double* zt = W<double>(h, "s_z64", fr);
+  T* vt = std::is_same<T, double>::value ? nullptr : W<T>(h, "s_vT", fr);
+  auto A = [&](const double* in, double* out) { dslash<double>(h, in, out, nullptr, 1); };
+  auto AZ = [&](const T* z, double* out) {
+    if constexpr (std::is_same<T, double>::value) {
+      dslash<double>(h, z, out, nullptr, 1);
+    } else {
+      launch_convert<T, double>(z, zt, fr, h->st);
+      CKL();
+      dslash<double>(h, zt, out, nullptr, 1);
+    }
+  };
+  auto M = [&](const double* v, T* z) {
+    if constexpr (std::is_same<T, double>::value) {
+      kcycle<double>(h, v, z, 1);
+    } else {
+      launch_convert<double, T>(v, vt, fr, h->st);
+      CKL();
+      kcycle<T>(h, vt, z, 1);
+    }
+  };
+  return krylov<double, T>(h, "fg", A, AZ, M, true, b, x, true, fr / 2, tol, h->p.restart, h->p.maxit);
+}
+
+// stage a natural (host or device) array of `bytes` on the device
+const double* stage_in(tm_handle* h, const double* src, size_t bytes, const char* name) {
+  if (is_device_ptr(src)) return src;
+  double* d = W<double>(h, name, bytes / sizeof(double));
+  CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, h->st));
+  return d;
+}
+
+void validate(const tm_params* p) {
+  auto bad = [](const std::string& m) { raise(TM_ERR_ARG, m); };
+  for (int d = 0; d < 4; ++d) {
+    if (p->L[d] < 2) bad("lattice extents must be >= 2");
+    if (p->agg[d] < 1 || p->L[d] % p->agg[d]) bad("lattice not divisible by the aggregate");
+    if (p->sap_block[d] < 1 || p->L[d] % p->sap_block[d]) bad("lattice not divisible by the SAP block");
+    const int nb = p->L[d] / p->sap_block[d];
+    if (nb < 2 || nb % 2) bad("SAP block count per dimension must be even and >= 2");
+    const int nc = p->L[d] / p->agg[d];
+    if (nc < 2 || nc % 2) bad("coarse extents must be even and >= 2 (odd-even coarse solve)");
+  }
+  const long asites = (long)p->agg[0] * p->agg[1] * p->agg[2] * p->agg[3];
+  const long bsites = (long)p->sap_block[0] * p->sap_block[1] * p->sap_block[2] * p->sap_block[3];
+  if (asites > 1024) bad("aggregate volume must be <= 1024");
+  if (bsites > 1024) bad("SAP block volume must be <= 1024");
+  if (p->nv < 1 || p->nv > 28) bad("nv must be in 1..28");
+  if (p->mr_iters < 0 || p->pre_smooth < 0 || p->post_smooth < 0 || p->init_sweeps < 0 || p->setup_iters < 0)
+    bad("negative iteration count");
+  if (p->restart < 1 || p->restart > kMaxDots - 2) bad("restart must be in 1..126");
+  if (p->coarse_restart < 1 || p->coarse_restart > kMaxDots - 2) bad("coarse_restart must be in 1..126");
+  if (p->maxit < 1 || p->coarse_maxit < 1) bad("maxit must be >= 1");
+  if (p->cycle_prec != TM_F64 && p->cycle_prec != TM_F32) bad("cycle_prec must be TM_F64 or TM_F32");
+  if (p->bc_t != 1.0 && p->bc_t != -1.0) bad("bc_t must be +1 or -1");
+  if (!(p->delta >= 1.0)) bad("delta must be >= 1");
+  if (p->max_rhs < 1) bad("max_rhs must be >= 1");
+  const double lv = (double)p->L[0] * p->L[1] * p->L[2] * p->L[3];
+  if (lv * 24.0 * p->max_rhs > 4.0e9 || lv * 24.0 * p->nv > 4.0e9) bad("lattice too large for 32-bit site indexing");
+}
+
+template <typename T>
+void unpack_fine(tm_handle* h, const void* f, double* nat, int nrhs) {
+  launch_unpack_spinor<T>(static_cast<const T*>(f), nat, h->g, nrhs, h->st);
+  CKL();
+}
+
+}  // namespace
+
+#define API_BEGIN try {
+#define API_END                                  \
+  }                                              \
+  catch (const TmError& e) {                     \
+    if (h) h->err = e.m;                         \
+    return e.s;                                  \
+  }                                              \
+  catch (const std::exception& e) {              \
+    if (h) h->err = e.what();                    \
+    return TM_ERR_CUDA;                          \
+  }                                              \
+  if (h) h->err.clear();                         \
+  return TM_OK;
+
+extern "C" {
+
+void tm_params_default(tm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->bc_t = -1;
+  p->delta = 1;
+  p->nv = 20;
+  for (int d = 0; d < 4; ++d) p->agg[d] = p->sap_block[d] = 4;
+  p->mr_iters = 4;
+  p->pre_smooth = 0;
+  p->post_smooth = 4;
+  p->init_sweeps = 3;
+  p->setup_iters = 3;
+  p->coarse_tol = 5e-2;
+  p->coarse_restart = 30;
+  p->coarse_maxit = 200;
+  p->restart = 25;
+  p->maxit = 1000;
+  p->cycle_prec = TM_F32;
+  p->max_rhs = 1;
+}
+
+const char* tm_status_string(int s) {
+  switch (s) {
+    case TM_OK: return "ok";
+    case TM_ERR_ARG: return "invalid argument";
+    case TM_ERR_CUDA: return "CUDA error";
+    case TM_ERR_OOM: return "out of device memory";
+    case TM_ERR_NOT_CONVERGED: return "not converged";
+    case TM_ERR_TIMEOUT: return "device wait timed out";
+    case TM_ERR_NOT_SU3: return "gauge link not in SU(3)";
+    case TM_ERR_NONFINITE: return "non-finite value";
+    case TM_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* tm_last_error(const tm_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+void tm_destroy(tm_handle* h) {
+  if (!h) return;
+  for (auto& kv : h->work)
+    if (kv.second.p) cudaFree(kv.second.p);
+  void* ptrs[] = {h->d_err, h->g64, h->g32, h->c64, h->c32, h->tv, h->P, h->Dc, h->Dinv,
+                  h->d_even, h->d_odd, h->d_cidx, h->scratch, h->dsmall};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (h->hsmall) cudaFreeHost(h->hsmall);
+  delete h;
+}
+
+tm_status tm_create(tm_handle** out, const tm_params* p, void* stream) {
+  tm_handle* h = nullptr;
+  if (!out || !p) return TM_ERR_ARG;
+  *out = nullptr;
+  try {
+    validate(p);
+    h = new tm_handle();
+    h->p = *p;
+    h->st = static_cast<cudaStream_t>(stream);
+    h->g = make_lat(p->L);
+    int Lc[4];
+    for (int d = 0; d < 4; ++d) Lc[d] = p->L[d] / p->agg[d];
+    h->gc = make_lat(Lc);
+    h->n = 2 * p->nv;
+    h->nhalf = h->gc.V / 2;
+    h->sg.g = h->g;
+    h->sg.bsites = 1;
+    for (int d = 0; d < 4; ++d) {
+      h->sg.blk[d] = p->sap_block[d];
+      h->sg.nb[d] = p->L[d] / p->sap_block[d];
+      h->sg.bsites *= p->sap_block[d];
+    }
+    h->ag.g = h->g;
+    h->ag.gc = h->gc;
+    h->ag.asites = 1;
+    h->ag.nv = p->nv;
+    for (int d = 0; d < 4; ++d) {
+      h->ag.agg[d] = p->agg[d];
+      h->ag.asites *= p->agg[d];
+    }
+    // odd-even index maps of the coarse lattice
+    std::vector<int> ev, od, cidx(h->gc.V);
+    for (int a = 0; a < h->gc.V; ++a) {
+      int c[4];
+      site_coords(h->gc, a, c);
+      if ((c[0] + c[1] + c[2] + c[3]) % 2 == 0) {
+        cidx[a] = (int)ev.size();
+        ev.push_back(a);
+      } else {
+        cidx[a] = (int)od.size();
+        od.push_back(a);
+      }
+    }
+    h->d_even = static_cast<int*>(dalloc(ev.size() * sizeof(int)));
+    h->d_odd = static_cast<int*>(dalloc(od.size() * sizeof(int)));
+    h->d_cidx = static_cast<int*>(dalloc(cidx.size() * sizeof(int)));
+    CK(cudaMemcpy(h->d_even, ev.data(), ev.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_odd, od.data(), od.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_cidx, cidx.data(), cidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    h->oe.gc = h->gc;
+    h->oe.nv = p->nv;
+    h->oe.nhalf = h->nhalf;
+    h->oe.even_site = h->d_even;
+    h->oe.odd_site = h->d_odd;
+    h->oe.cidx = h->d_cidx;
+
+    const long V = h->g.V;
+    h->d_err = static_cast<int*>(dalloc(sizeof(int)));
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    h->g64 = static_cast<double*>(dalloc(4L * NR_LINK * V * sizeof(double)));
+    h->g32 = static_cast<float*>(dalloc(4L * NR_LINK * V * sizeof(float)));
+    h->c64 = static_cast<double*>(dalloc((long)NR_CLOVER * V * sizeof(double)));
+    h->c32 = static_cast<float*>(dalloc((long)NR_CLOVER * V * sizeof(float)));
+    const size_t cs = csize(p->cycle_prec);
+    h->tv = dalloc((size_t)p->nv * NR_SPINOR * V * cs);
+    h->P = dalloc((size_t)p->nv * NR_SPINOR * V * cs);
+    h->Dc = dalloc((size_t)h->gc.V * 9 * h->n * h->n * 2 * cs);
+    h->Dinv = dalloc((size_t)h->nhalf * h->n * h->n * 2 * cs);
+    h->scratch = static_cast<double*>(dalloc((size_t)kScratchBlocks * kMaxDots * 2 * sizeof(double)));
+    h->dsmall = static_cast<double*>(dalloc(kSmall * sizeof(double)));
+    CK(cudaMallocHost(&h->hsmall, kSmall * sizeof(double)));
+    *out = h;
+  } catch (const TmError& e) {
+    if (h) tm_destroy(h);
+    return e.s;
+  } catch (...) {
+    if (h) tm_destroy(h);
+    return TM_ERR_OOM;
+  }
+  return TM_OK;
+}
+
+tm_status tm_load_gauge(tm_handle* h, const double* gauge) {
+  if (!h || !gauge) return TM_ERR_ARG;
+  API_BEGIN
+  const size_t bytes = (size_t)h->g.V * 4 * 9 * 2 * sizeof(double);
+  const double* gd = stage_in(h, gauge, bytes, "stage_gauge");
+  launch_pack_gauge(gd, h->g64, h->g32, h->g, 1e-10, h->d_err, h->st);
+  CKL();
+  launch_clover(gd, h->c64, h->c32, h->g, h->p.m0, h->p.c_sw, h->st);
+  CKL();
+  h->gauge_ok = false;
+  h->setup_ok = false;
+  check_flags(h);
+  h->gauge_ok = true;
+  API_END
+}
+
+static tm_status setup_common(tm_handle* h, const double* tv, bool adaptive) {
+  if (!h || !tv) return TM_ERR_ARG;
+  API_BEGIN
+  if (!h->gauge_ok) raise(TM_ERR_STATE, "tm_load_gauge must come first");
+  h->setup_ok = false;
+  const size_t bytes = (size_t)h->p.nv * h->g.V * 12 * 2 * sizeof(double);
+  const double* d = stage_in(h, tv, bytes, "stage_tv");
+  h->coarse_iters = 0;
+  h->kcycles = 0;
+  if (h->p.cycle_prec == TM_F64)
+    setup_impl<double>(h, d, adaptive);
+  else
+    setup_impl<float>(h, d, adaptive);
+  h->setup_ok = true;
+  API_END
+}
+
+tm_status tm_setup(tm_handle* h, const double* test_vectors) { return setup_common(h, test_vectors, true); }
+tm_status tm_setup_from_vectors(tm_handle* h, const double* test_vectors) {
+  return setup_common(h, test_vectors, false);
+}
+
+tm_status tm_set_mu(tm_handle* h, double mu, double delta) {
+  if (!h) return TM_ERR_ARG;
+  API_BEGIN
+  if (!(delta >= 1.0) || !std::isfinite(mu)) raise(TM_ERR_ARG, "need finite mu and delta >= 1");
+  h->p.mu = mu;
+  h->p.delta = delta;
+  if (h->setup_ok) {
+    if (h->p.cycle_prec == TM_F64)
+      launch_oe_invert<double>(static_cast<double*>(h->Dc), static_cast<double*>(h->Dinv), h->oe, mu_c(h), h->d_err,
+                               h->st);
+    else
+      launch_oe_invert<float>(static_cast<float*>(h->Dc), static_cast<float*>(h->Dinv), h->oe, mu_c(h), h->d_err,
+                              h->st);
+    CKL();
+    check_flags(h);
+  }
+  API_END
+}
+
+tm_status tm_solve(tm_handle* h, const double* b, double* x, int nrhs, double tol, tm_solve_info* info) {
+  if (!h || !b || !x || nrhs < 1 || !(tol > 0)) return TM_ERR_ARG;
+  tm_solve_info loc{};
+  loc.converged = 1;
+  tm_status st = TM_OK;
+  try {
+    if (!h->setup_ok) raise(TM_ERR_STATE, "tm_setup must come first");
+    const long V = h->g.V;
+    const size_t one = (size_t)V * 12 * 2 * sizeof(double);
+    const bool xdev = is_device_ptr(x);
+    const double* bd = stage_in(h, b, one * nrhs, "stage_b");
+    double* xd = xdev ? x : W<double>(h, "stage_x", one * nrhs / sizeof(double));
+    if (!xdev) CK(cudaMemcpyAsync(xd, x, one * nrhs, cudaMemcpyHostToDevice, h->st));
+    const long fr = fine_reals(h);
+    double* bf = W<double>(h, "s_b", fr);
+    double* xf = W<double>(h, "s_x", fr);
+    h->coarse_iters = 0;
+    h->kcycles = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      launch_pack_spinor<double>(bd + (size_t)r * V * 24, bf, h->g, 1, h->st);
+      CKL();
+      launch_pack_spinor<double>(xd + (size_t)r * V * 24, xf, h->g, 1, h->st);
+      CKL();
+      KrylovOut k = h->p.cycle_prec == TM_F64 ? solve_one<double>(h, bf, xf, tol) : solve_one<float>(h, bf, xf, tol);
+      launch_unpack_spinor<double>(xf, xd + (size_t)r * V * 24, h->g, 1, h->st);
+      CKL();
+      loc.iters += k.iters;
+      loc.restarts += k.restarts;
+      loc.true_relres = std::max(loc.true_relres, k.relres);
+      if (!k.converged) loc.converged = 0;
+    }
+    if (!xdev) CK(cudaMemcpyAsync(x, xd, one * nrhs, cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    loc.coarse_iters = h->coarse_iters;
+    loc.kcycles = h->kcycles;
+    if (!loc.converged) {
+      h->err = "solver reached maxit";
+      st = TM_ERR_NOT_CONVERGED;
+    } else {
+      h->err.clear();
+    }
+  } catch (const TmError& e) {
+    h->err = e.m;
+    st = e.s;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    st = TM_ERR_CUDA;
+  }
+  if (info) *info = loc;
+  return st;
+}
+
+size_t tm_field_bytes(const tm_handle* h, int level, int prec, int nrhs) {
+  if (!h || nrhs < 1 || (prec != TM_F64 && prec != TM_F32)) return 0;
+  if (level == 0) return (size_t)nrhs * NR_SPINOR * h->g.V * csize(prec);
+  if (level == 1) return (size_t)nrhs * h->gc.V * h->n * 2 * csize(prec);
+  return 0;
+}
+
+static void need_dev(const void* p, const char* what) {
+  if (!is_device_ptr(p)) raise(TM_ERR_ARG, std::string(what) + " must be a device pointer");
+}
+
+tm_status tm_pack(tm_handle* h, int level, int prec, const double* natural, void* field, int nrhs) {
+  if (!h || !natural || !field || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  need_dev(natural, "natural");
+  need_dev(field, "field");
+  if (level == 0) {
+    if (prec == TM_F64)
+      launch_pack_spinor<double>(natural, static_cast<double*>(field), h->g, nrhs, h->st);
+    else if (prec == TM_F32)
+      launch_pack_spinor<float>(natural, static_cast<float*>(field), h->g, nrhs, h->st);
+    else
+      raise(TM_ERR_ARG, "bad precision");
+  } else if (level == 1) {
+    const long nre = (long)nrhs * h->gc.V * h->n * 2;
+    if (prec == TM_F64)
+      launch_convert<double, double>(natural, static_cast<double*>(field), nre, h->st);
+    else if (prec == TM_F32)
+      launch_convert<double, float>(natural, static_cast<float*>(field), nre, h->st);
+    else
+      raise(TM_ERR_ARG, "bad precision");
+  } else {
+    raise(TM_ERR_ARG, "level must be 0 or 1");
+  }
+  CKL();
+  API_END
+}
+
+tm_status tm_unpack(tm_handle* h, int level, int prec, const void* field, double* natural, int nrhs) {
+  if (!h || !natural || !field || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  need_dev(natural, "natural");
+  need_dev(field, "field");
+  if (level == 0) {
+    if (prec == TM_F64)
+      unpack_fine<double>(h, field, natural, nrhs);
+    else if (prec == TM_F32)
+      unpack_fine<float>(h, field, natural, nrhs);
+    else
+      raise(TM_ERR_ARG, "bad precision");
+  } else if (level == 1) {
+    const long nre = (long)nrhs * h->gc.V * h->n * 2;
+    if (prec == TM_F64)
+      launch_convert<double, double>(static_cast<const double*>(field), natural, nre, h->st);
+    else if (prec == TM_F32)
+      launch_convert<float, double>(static_cast<const float*>(field), natural, nre, h->st);
+    else
+      raise(TM_ERR_ARG, "bad precision");
+    CKL();
+  } else {
+    raise(TM_ERR_ARG, "level must be 0 or 1");
+  }
+  API_END
+}
+
+static void need_cycle_prec(tm_handle* h, int prec) {
+  if (prec != h->p.cycle_prec) raise(TM_ERR_ARG, "prec must equal the handle's cycle_prec for this call");
+  if (!h->setup_ok) raise(TM_ERR_STATE, "needs a setup");
+}
+
+tm_status tm_apply(tm_handle* h, int level, int prec, const void* in, void* out, int nrhs) {
+  if (!h || !in || !out || in == out || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  if (nrhs > h->p.max_rhs) raise(TM_ERR_ARG, "nrhs > max_rhs");
+  if (level == 0) {
+    if (!h->gauge_ok) raise(TM_ERR_STATE, "no gauge field");
+    if (prec == TM_F64)
+      dslash<double>(h, static_cast<const double*>(in), static_cast<double*>(out), nullptr, nrhs);
+    else if (prec == TM_F32)
+      dslash<float>(h, static_cast<const float*>(in), static_cast<float*>(out), nullptr, nrhs);
+    else
+      raise(TM_ERR_ARG, "bad precision");
+  } else if (level == 1) {
+    need_cycle_prec(h, prec);
+    if (prec == TM_F64)
+      launch_coarse_apply<double>(static_cast<const double*>(h->Dc), static_cast<const double*>(in),
+                                  static_cast<double*>(out), h->gc, h->p.nv, mu_c(h), nrhs, h->st);
+    else
+      launch_coarse_apply<float>(static_cast<const float*>(h->Dc), static_cast<const float*>(in),
+                                 static_cast<float*>(out), h->gc, h->p.nv, mu_c(h), nrhs, h->st);
+    CKL();
+  } else {
+    raise(TM_ERR_ARG, "level must be 0 or 1");
+  }
+  API_END
+}
+
+tm_status tm_sap(tm_handle* h, int prec, const void* b, void* x, int sweeps, int nrhs) {
+  if (!h || !x || sweeps < 0 || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  if (!h->gauge_ok) raise(TM_ERR_STATE, "no gauge field");
+  if (prec == TM_F64)
+    sap_sweeps<double>(h, static_cast<const double*>(b), static_cast<double*>(x), sweeps, nrhs);
+  else if (prec == TM_F32)
+    sap_sweeps<float>(h, static_cast<const float*>(b), static_cast<float*>(x), sweeps, nrhs);
+  else
+    raise(TM_ERR_ARG, "bad precision");
+  API_END
+}
+
+tm_status tm_restrict(tm_handle* h, int prec, const void* fine, void* coarse, int nrhs) {
+  if (!h || !fine || !coarse || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  need_cycle_prec(h, prec);
+  if (prec == TM_F64)
+    launch_restrict<double>(static_cast<const double*>(h->P), static_cast<const double*>(fine),
+                            static_cast<double*>(coarse), h->ag, nrhs, h->st);
+  else
+    launch_restrict<float>(static_cast<const float*>(h->P), static_cast<const float*>(fine),
+                           static_cast<float*>(coarse), h->ag, nrhs, h->st);
+  CKL();
+  API_END
+}
+
+tm_status tm_prolong(tm_handle* h, int prec, const void* coarse, void* fine, int nrhs, int accumulate) {
+  if (!h || !fine || !coarse || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  need_cycle_prec(h, prec);
+  if (prec == TM_F64)
+    launch_prolong<double>(static_cast<const double*>(h->P), static_cast<const double*>(coarse),
+                           static_cast<double*>(fine), h->ag, nrhs, accumulate != 0, h->st);
+  else
+    launch_prolong<float>(static_cast<const float*>(h->P), static_cast<const float*>(coarse),
+                          static_cast<float*>(fine), h->ag, nrhs, accumulate != 0, h->st);
+  CKL();
+  API_END
+}
+
+tm_status tm_coarse_solve(tm_handle* h, int prec, const void* b, void* x, double tol, int maxit, int* iters) {
+  if (!h || !b || !x || maxit < 1 || tol < 0) return TM_ERR_ARG;
+  API_BEGIN
+  need_cycle_prec(h, prec);
+  KrylovOut r;
+  if (prec == TM_F64)
+    r = coarse_solve<double>(h, static_cast<const double*>(b), static_cast<double*>(x), tol, maxit);
+  else
+    r = coarse_solve<float>(h, static_cast<const float*>(b), static_cast<float*>(x), tol, maxit);
+  sync(h);
+  if (iters) *iters = r.iters;
+  API_END
+}
+
+tm_status tm_kcycle(tm_handle* h, int prec, const void* v, void* z, int nrhs) {
+  if (!h || !v || !z || v == z || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  need_cycle_prec(h, prec);
+  if (prec == TM_F64)
+    kcycle<double>(h, static_cast<const double*>(v), static_cast<double*>(z), nrhs);
+  else
+    kcycle<float>(h, static_cast<const float*>(v), static_cast<float*>(z), nrhs);
+  API_END
+}
+
+tm_status tm_synchronize(tm_handle* h) {
+  if (!h) return TM_ERR_ARG;
+  API_BEGIN
+  sync(h);
+  check_flags(h);
+  API_END
+}
+
+tm_status tm_export(tm_handle* h, int what, double* out, size_t bytes) {
+  if (!h || !out) return TM_ERR_ARG;
+  API_BEGIN
+  const long V = h->g.V;
+  const int nv = h->p.nv, n = h->n;
+  std::vector<double> host;
+  if (what == TM_EXPORT_P || what == TM_EXPORT_TV) {
+    if (!h->setup_ok) raise(TM_ERR_STATE, "needs a setup");
+    const size_t one = (size_t)V * 24;
+    double* nat = W<double>(h, "exp_nat", one * nv);
+    const void* src = what == TM_EXPORT_P ? h->P : h->tv;
+    if (h->p.cycle_prec == TM_F64)
+      unpack_fine<double>(h, src, nat, nv);
+    else
+      unpack_fine<float>(h, src, nat, nv);
+    std::vector<double> tmp(one * nv);
+    CK(cudaMemcpyAsync(tmp.data(), nat, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    if (what == TM_EXPORT_TV) {
+      host.swap(tmp);
+    } else {
+      host.assign(one * n, 0.0);
+      for (int chi = 0; chi < 2; ++chi)
+        for (int i = 0; i < nv; ++i) {
+          double* col = host.data() + (size_t)(chi * nv + i) * one;
+          const double* f = tmp.data() + (size_t)i * one;
+          for (long s = 0; s < V; ++s)
+            for (int k = 0; k < 12; ++k)
+              if (k / 6 == chi) {
+                col[(s * 12 + k) * 2] = f[(s * 12 + k) * 2];
+                col[(s * 12 + k) * 2 + 1] = f[(s * 12 + k) * 2 + 1];
+              }
+        }
+    }
+  } else if (what == TM_EXPORT_DC) {
+    if (!h->setup_ok) raise(TM_ERR_STATE, "needs a setup");
+    const size_t cnt = (size_t)h->gc.V * 9 * n * n;
+    std::vector<double> raw(cnt * 2);
+    if (h->p.cycle_prec == TM_F64) {
+      CK(cudaMemcpyAsync(raw.data(), h->Dc, cnt * 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      sync(h);
+    } else {
+      std::vector<float> rf(cnt * 2);
+      CK(cudaMemcpyAsync(rf.data(), h->Dc, cnt * 2 * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+      sync(h);
+      for (size_t i = 0; i < rf.size(); ++i) raw[i] = rf[i];
+    }
+    host.assign(cnt * 2, 0.0);
+    for (size_t blk = 0; blk < (size_t)h->gc.V * 9; ++blk)
+      for (int col = 0; col < n; ++col)
+        for (int row = 0; row < n; ++row) {
+          const size_t s = (blk * n + col) * n + row, d = (blk * n + row) * n + col;
+          host[2 * d] = raw[2 * s];
+          host[2 * d + 1] = raw[2 * s + 1];
+        }
+  } else if (what == TM_EXPORT_CLOVER) {
+    if (!h->gauge_ok) raise(TM_ERR_STATE, "no gauge field");
+    std::vector<double> raw((size_t)NR_CLOVER * V);
+    CK(cudaMemcpyAsync(raw.data(), h->c64, raw.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    host.assign((size_t)V * 2 * 36 * 2, 0.0);
+    for (long s = 0; s < V; ++s)
+      for (int hb = 0; hb < 2; ++hb) {
+        double pk[36];
+        for (int k = 0; k < 36; ++k) {
+          const long r = 36L * hb + k;  // real index within the site
+          pk[k] = raw[(size_t)(r / 2) * V * 2 + s * 2 + (r % 2)];
+        }
+        double* M = host.data() + ((size_t)s * 2 + hb) * 72;
+        for (int i = 0; i < 6; ++i) {
+          M[(i * 6 + i) * 2] = pk[i];
+          M[(i * 6 + i) * 2 + 1] = 0;
+        }
+        int k = 6;
+        for (int i = 0; i < 6; ++i)
+          for (int j = i + 1; j < 6; ++j) {
+            M[(i * 6 + j) * 2] = pk[k];
+            M[(i * 6 + j) * 2 + 1] = pk[k + 1];
+            M[(j * 6 + i) * 2] = pk[k];
+            M[(j * 6 + i) * 2 + 1] = -pk[k + 1];
+            k += 2;
+          }
+      }
+  } else {
+    raise(TM_ERR_ARG, "unknown export");
+  }
+  if (bytes < host.size() * sizeof(double)) raise(TM_ERR_ARG, "export buffer too small");
+  if (is_device_ptr(out)) {
+    CK(cudaMemcpyAsync(out, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    sync(h);
+  } else {
+    std::memcpy(out, host.data(), host.size() * sizeof(double));
+  }
+  API_END
+}
+
+}  // extern "C"

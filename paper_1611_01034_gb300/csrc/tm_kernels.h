@@ -1,0 +1,126 @@
+// Host-side launchers of the library's kernels (internal, C++ linkage).
+// Every launcher enqueues on the given stream and returns immediately.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "tm_internal.cuh"
+
+namespace tmamg {
+
+// ---- fine fields (dirac.cu) ----------------------------------------------
+// natural layout: [rhs][V][4 spin][3 colour] complex128, interleaved re/im
+template <typename T>
+void launch_pack_spinor(const double* nat, T* field, const Lat& g, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_unpack_spinor(const T* field, double* nat, const Lat& g, int nrhs, cudaStream_t st);
+// natural gauge [V][4][3][3] complex128 -> packed FP64 and FP32 links, SU(3) check
+void launch_pack_gauge(const double* nat, double* g64, float* g32, const Lat& g, double tol,
+                       int* err, cudaStream_t st);
+// clover blocks (m0 + 4 included, mu-free) from the natural gauge field
+void launch_clover(const double* nat, double* c64, float* c32, const Lat& g, double m0, double c_sw,
+                   cudaStream_t st);
+// out = D(mu) in (res == nullptr) or out = b - D(mu) in
+template <typename T>
+void launch_dslash(const T* gauge, const T* clover, const T* in, T* out, const T* b, const Lat& g,
+                   double mu, double bc_t, int nrhs, cudaStream_t st);
+
+// ---- SAP (sap.cu) ------------------------------------------------------------
+struct SapGeom {
+  Lat g;
+  int blk[4];   // block dims
+  int nb[4];    // blocks per dimension (all even)
+  int bsites;   // sites per block
+};
+// one colour of one sweep on D x = b (b may be null: b = 0)
+template <typename T>
+void launch_sap_colour(const T* gauge, const T* clover, const T* b, T* x, const SapGeom& sg,
+                       double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st);
+
+// ---- aggregation and coarse operator (coarse.cu) ---------------------------
+struct AggGeom {
+  Lat g;        // fine lattice
+  Lat gc;       // coarse lattice
+  int agg[4];
+  int asites;   // sites per aggregate
+  int nv;       // test vectors
+};
+// P <- per (aggregate, chirality) CGS2 orthonormalisation of the Nv fields in P (in place)
+template <typename T>
+void launch_orthonormalise(T* P, const AggGeom& ag, int* err, cudaStream_t st);
+// coarse[rhs][Vc][2Nv] = P^dagger fine
+template <typename T>
+void launch_restrict(const T* P, const T* fine, T* coarse, const AggGeom& ag, int nrhs, cudaStream_t st);
+// fine = (accumulate ? fine : 0) + P coarse
+template <typename T>
+void launch_prolong(const T* P, const T* coarse, T* fine, const AggGeom& ag, int nrhs, bool accumulate,
+                    cudaStream_t st);
+// Dc blocks [Vc][9][2Nv col][2Nv row] = local Galerkin projection (mu-free)
+template <typename T>
+void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, const AggGeom& ag,
+                         double bc_t, cudaStream_t st);
+// y = D_c(mu_c) v on the full coarse lattice
+template <typename T>
+void launch_coarse_apply(const T* Dc, const T* v, T* y, const Lat& gc, int nv, double mu_c, int nrhs,
+                         cudaStream_t st);
+
+// odd-even on the coarse lattice
+struct OEGeom {
+  Lat gc;
+  int nv;
+  int nhalf;            // Vc / 2
+  const int* even_site; // compact even index -> site
+  const int* odd_site;  // compact odd index -> site
+  const int* cidx;      // site -> compact index within its parity
+};
+// Dinv[odd k] = (self block + i mu_c Gamma5_c)^-1, Gauss-Jordan with partial pivoting
+template <typename T>
+void launch_oe_invert(const T* Dc, T* Dinv, const OEGeom& oe, double mu_c, int* err, cudaStream_t st);
+// u_o = Dinv (D_oe v_e)   (v_e compact even, u_o compact odd)
+template <typename T>
+void launch_oe_hop_inv(const T* Dc, const T* Dinv, const T* ve, T* uo, const OEGeom& oe, cudaStream_t st);
+// y_e = alpha_d (self + i mu_c G5c) v_e - D_eo u_o  (alpha_d in {0,1})
+template <typename T>
+void launch_oe_even(const T* Dc, const T* ve, const T* uo, T* ye, const OEGeom& oe, double mu_c,
+                    int diag, cudaStream_t st);
+// t_o = Dinv b_o   (b full coarse vector; reads its odd sites)
+template <typename T>
+void launch_oe_inv_odd(const T* Dinv, const T* b, T* to, const OEGeom& oe, cudaStream_t st);
+// bhat_e = b_e - D_eo t_o
+template <typename T>
+void launch_oe_rhs(const T* Dc, const T* b, const T* to, T* bh, const OEGeom& oe, cudaStream_t st);
+// x(full) from x_e: x_o = Dinv (b_o - D_oe x_e)
+template <typename T>
+void launch_oe_reconstruct(const T* Dc, const T* Dinv, const T* b, const T* xe, T* x, const OEGeom& oe,
+                           cudaStream_t st);
+
+// ---- level-1 vectors (blas.cu) ----------------------------------------------
+// all BLAS works on flat arrays of n complex numbers stored as (re, im) pairs
+template <typename Ti, typename To>
+void launch_convert(const Ti* in, To* out, long n_reals, cudaStream_t st);
+template <typename T>
+void launch_zero(T* x, long n_reals, cudaStream_t st);
+// y = a x + b y  (complex a, b as double pairs)
+template <typename T>
+void launch_caxpby(double ar, double ai, const T* x, double br, double bi, T* y, long ncx, cudaStream_t st);
+// out[j] = sum conj(X_j) y for j < k; X_j = X + j * ldx (reals); results as double2 into dev_out
+template <typename T>
+void launch_multidot(const T* X, long ldx, int k, const T* y, long ncx, double* dev_out, double* scratch,
+                     int nscratch_blocks, cudaStream_t st);
+// y -= sum_j c_j X_j   (c on device, double2[k])
+template <typename T>
+void launch_multi_caxpy(const T* X, long ldx, int k, const double* c, double sign, T* y, long ncx,
+                        cudaStream_t st);
+// y += sum_j c_j X_j with X of type Tx and y of type Ty (c on device)
+template <typename Tx, typename Ty>
+void launch_lincomb(const Tx* X, long ldx, int k, const double* c, Ty* y, long ncx, cudaStream_t st);
+// dev_out[r] = ||x_r||^2 for nrhs vectors of ncx complex each
+template <typename T>
+void launch_norm2(const T* x, long ncx, int nrhs, double* dev_out, double* scratch, int nscratch_blocks,
+                  cudaStream_t st);
+// x_r *= s_r (s on device, double[nrhs], scale = 1 / sqrt(s_r) if inv_sqrt)
+template <typename T>
+void launch_scale(T* x, long ncx, int nrhs, const double* s, bool inv_sqrt, cudaStream_t st);
+
+constexpr int kReduceBlocks = 304;  // 2 x 152 SMs
+
+}  // namespace tmamg

@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+The library must build for sm_103a, load, and export every entry point that
+``include/tm.h`` declares; parameter validation runs before any device call,
+so invalid parameters are rejected with TM_ERR_ARG even without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tm_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1611_01034_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_declares_exactly_the_header():
+    from paper_1611_01034_gb300._binding import exported_symbols
+    assert sorted(exported_symbols()) == _declared()
+
+
+def test_defaults_and_status_strings(lib):
+    import paper_1611_01034_gb300 as tm
+    p = tm.tm_params_default()
+    assert p.nv == 20 and list(p.agg) == [4, 4, 4, 4] and p.bc_t == -1.0
+    assert p.cycle_prec == tm.TM_F32 and p.delta == 1.0
+    assert tm.tm_status_string(tm.TM_ERR_NOT_CONVERGED) == "not converged"
+    assert tm.tm_status_string(12345) == "unknown status"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(L=(4, 4, 4, 6), agg=(4, 4, 4, 4)),              # not divisible
+    dict(L=(8, 8, 8, 12), agg=(2, 2, 2, 4)),             # odd coarse extent (3)
+    dict(L=(8, 8, 8, 8), sap_block=(8, 4, 4, 4)),        # one SAP block in T
+    dict(L=(8, 8, 8, 8), nv=40),                          # too many test vectors
+    dict(L=(8, 8, 8, 8), delta=0.5),                      # delta < 1
+    dict(L=(8, 8, 8, 8), cycle_prec=7),
+    dict(L=(8, 8, 8, 8), bc_t=0.3),
+    dict(L=(32, 32, 32, 32), agg=(8, 8, 8, 4)),          # aggregate volume > 1024
+])
+def test_invalid_parameters_rejected_before_any_device_call(lib, bad):
+    import paper_1611_01034_gb300 as tm
+    kw = dict(L=(8, 8, 8, 8), agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), nv=8)
+    kw.update(bad)
+    with pytest.raises(tm.TMError) as e:
+        tm.tm_create(tm.params(**kw))
+    assert e.value.status == tm.TM_ERR_ARG
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    import paper_1611_01034_gb300 as tm
+    L = tm.lib()
+    assert L.tm_solve(None, None, None, 1, 1e-10, None) == tm.TM_ERR_ARG
+    assert L.tm_apply(None, 0, 0, None, None, 1) == tm.TM_ERR_ARG
+    assert L.tm_synchronize(None) == tm.TM_ERR_ARG
+    L.tm_destroy(None)

@@ -1,0 +1,248 @@
+"""GPU parity: every step of the hot path through the C ABI against the oracle.
+
+Tolerances (relative L2): FP64 single operator applies <= 1e-12; FP64
+composite fixed-count applications (SAP sweeps, coarse GMRES with a fixed
+step count, one K-cycle) <= 1e-10; FP32 single applies <= 5e-6 (24-bit
+mantissa, sums of <= 100 terms).  Shapes cover the 4^4 configuration, a
+ragged 4x6x4x10 lattice (960 sites: the last 128-thread CTA is partial;
+60-site aggregates and SAP blocks leave idle lanes in every warp) and 8^4.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle.dirac import Operator, clover_blocks
+from oracle.sap import SAP
+from oracle.coarse import Interpolation, CoarseOperator, OddEvenCoarse
+from oracle.krylov import gmres
+from oracle.amg import TwoLevel, AMGParams
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1611_01034_gb300 as tm  # noqa: E402
+from tests.gpu_helpers import GPU, rel  # noqa: E402
+
+F64, F32 = tm.TM_F64, tm.TM_F32
+
+KAPPA1 = 0.13
+CASES = {
+    # name: (L, eps, seed, m0, c_sw, mu, delta, nv, agg/sap block)
+    "c1_4x4x4x4": ((4, 4, 4, 4), 0.3, 1, 1 / (2 * KAPPA1) - 4, 1.0, 0.01, 1.0, 8, (2, 2, 2, 2)),
+    "ragged_4x6x4x10": ((4, 6, 4, 10), 0.5, 3, -0.3, 1.5, 0.02, 3.0, 6, (2, 3, 2, 5)),
+    "8x8x8x8": ((8, 8, 8, 8), 0.5, 5, -0.4, 1.5, 0.005, 5.0, 8, (4, 4, 4, 4)),
+}
+
+
+def _case(name, prec=F64, **over):
+    L, eps, seed, m0, csw, mu, delta, nv, blk = CASES[name]
+    U = inputs.gauge_field(L, eps, seed)
+    kw = dict(m0=m0, c_sw=csw, mu=mu, delta=delta, nv=nv, agg=blk, sap_block=blk, cycle_prec=prec,
+              max_rhs=4)
+    kw.update(over)
+    g = GPU(U, **kw)
+    op = Operator(U, m0, csw, mu)
+    return U, g, op, seed
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_clover_matches_oracle(name):
+    U, g, op, _ = _case(name)
+    assert rel(g.clover(), clover_blocks(op.A)) <= 1e-13
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-12), (F32, 5e-6)])
+def test_dirac_apply(name, prec, tol):
+    U, g, op, seed = _case(name)
+    psi = inputs.gaussian_spinor(g.L, seed + 1000, nrhs=3)
+    got = g.apply_fine(psi, prec, nrhs=3)
+    assert rel(got, op.apply(psi)) <= tol
+    for r in range(3):
+        assert rel(got[r], op.apply(psi[r])) <= tol
+
+
+def test_dirac_periodic_and_free_field():
+    L = (4, 6, 4, 10)
+    U = inputs.unit_gauge(L)
+    g = GPU(U, m0=-0.2, c_sw=1.1, mu=0.3, nv=4, agg=(2, 3, 2, 5), sap_block=(2, 3, 2, 5), bc_t=1.0,
+            cycle_prec=F64)
+    op = Operator(U, -0.2, 1.1, 0.3, bc_t=1.0)
+    psi = inputs.gaussian_spinor(L, 7)
+    assert rel(g.apply_fine(psi, F64), op.apply(psi)) <= 1e-13
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-10), (F32, 5e-5)])
+def test_sap_sweeps(name, prec, tol):
+    U, g, op, seed = _case(name)
+    blk = CASES[name][8]
+    sap = SAP(op, blk, n_mr=4)
+    b = inputs.gaussian_spinor(g.L, seed + 11)
+    x0 = 0.1 * inputs.gaussian_spinor(g.L, seed + 12)
+    expect = sap.smooth(b, x0, 2)
+    got = g.sap(b, x0, 2, prec)
+    assert rel(got, expect) <= tol
+    # homogeneous system (b = 0), as in the setup's initial smoothing
+    expect0 = sap.smooth(np.zeros_like(b), x0, 1)
+    got0 = g.sap(None, x0, 1, prec)
+    assert rel(got0, expect0) <= tol
+
+
+def _from_vectors(name, prec=F64):
+    U, g, op, seed = _case(name, prec)
+    tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+    tm.tm_setup_from_vectors(g.h, tv)
+    P = Interpolation(tv, g.p.agg)
+    Dc = CoarseOperator.build(op, P, mu_c=g.p.delta * g.p.mu)
+    return g, op, P, Dc, seed
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_interpolation_and_coarse_operator(name):
+    g, op, P, Dc, _ = _from_vectors(name)
+    assert rel(g.P_columns(), P.columns()) <= 1e-12
+    assert rel(g.Dc_blocks(), Dc.blocks) <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-12), (F32, 5e-6)])
+def test_restrict_prolong_coarse_apply(name, prec, tol):
+    g, op, P, Dc, seed = _from_vectors(name, prec)
+    psi = inputs.gaussian_spinor(g.L, seed + 21, nrhs=2)
+    fi = g.pack(0, prec, psi, 2)
+    fc = g.field(1, prec, 2)
+    tm.tm_restrict(g.h, prec, fi, fc, 2)
+    rc = g.unpack(1, prec, fc, g.coarse_shape(2), 2)
+    assert rel(rc, P.restrict(psi)) <= tol
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(g.coarse_shape(2)) + 1j * rng.standard_normal(g.coarse_shape(2))
+    fv = g.pack(1, prec, v, 2)
+    fo = g.pack(0, prec, psi, 2)
+    tm.tm_prolong(g.h, prec, fv, fo, 2, 1)
+    assert rel(g.unpack(0, prec, fo, psi.shape, 2), psi + P.prolong(v)) <= tol
+    tm.tm_prolong(g.h, prec, fv, fo, 2, 0)
+    assert rel(g.unpack(0, prec, fo, psi.shape, 2), P.prolong(v)) <= tol
+    fy = g.field(1, prec, 2)
+    tm.tm_apply(g.h, 1, prec, fv, fy, 2)
+    assert rel(g.unpack(1, prec, fy, v.shape, 2), Dc.apply(v)) <= tol
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coarse_solve_fixed_steps(name):
+    g, op, P, Dc, seed = _from_vectors(name)
+    rng = np.random.default_rng(seed + 3)
+    b = rng.standard_normal(g.coarse_shape()) + 1j * rng.standard_normal(g.coarse_shape())
+    oe = OddEvenCoarse(Dc)
+    for steps in (1, 7, 45):
+        res = gmres(oe.schur, oe.reduced_rhs(b), tol=0.0, restart=g.p.coarse_restart, maxit=steps)
+        expect = oe.reconstruct(b, res.x)
+        fb = g.pack(1, F64, b)
+        fx = g.field(1, F64)
+        it = tm.tm_coarse_solve(g.h, F64, fb, fx, 0.0, steps)
+        assert it == steps == res.iters
+        assert rel(g.unpack(1, F64, fx, b.shape), expect) <= 1e-10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coarse_solve_to_tolerance(name):
+    g, op, P, Dc, seed = _from_vectors(name)
+    rng = np.random.default_rng(seed + 4)
+    b = rng.standard_normal(g.coarse_shape()) + 1j * rng.standard_normal(g.coarse_shape())
+    fb = g.pack(1, F64, b)
+    fx = g.field(1, F64)
+    tm.tm_coarse_solve(g.h, F64, fb, fx, 1e-11, 400)
+    x = g.unpack(1, F64, fx, b.shape)
+    assert np.linalg.norm(Dc.apply(x) - b) / np.linalg.norm(b) <= 1e-9
+
+
+def _oracle_two_level(g, U, name, **over):
+    L, eps, seed, m0, csw, mu, delta, nv, blk = CASES[name]
+    prm = AMGParams(m0=m0, c_sw=csw, mu=mu, delta=delta, nv=nv, agg=blk, sap_block=blk,
+                    mr_iters=g.p.mr_iters, pre_smooth=g.p.pre_smooth, post_smooth=g.p.post_smooth,
+                    init_sweeps=g.p.init_sweeps, setup_iters=g.p.setup_iters,
+                    coarse_tol=g.p.coarse_tol, coarse_restart=g.p.coarse_restart,
+                    coarse_maxit=g.p.coarse_maxit, restart=g.p.restart, maxit=g.p.maxit)
+    for k, v in over.items():
+        setattr(prm, k, v)
+    return TwoLevel(U, prm)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("pre", [0, 1])
+def test_kcycle_fixed_coarse_steps(name, pre):
+    U, g, op, seed = _case(name, F64, coarse_tol=0.0, coarse_maxit=9, pre_smooth=pre, post_smooth=2)
+    tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+    tm.tm_setup_from_vectors(g.h, tv)
+    tl = _oracle_two_level(g, U, name)
+    tl.build_coarse(tv)
+    v = inputs.gaussian_spinor(g.L, seed + 31, nrhs=2)
+    fv = g.pack(0, F64, v, 2)
+    fz = g.field(0, F64, 2)
+    tm.tm_kcycle(g.h, F64, fv, fz, 2)
+    got = g.unpack(0, F64, fz, v.shape, 2)
+    for r in range(2):
+        assert rel(got[r], tl.kcycle(v[r])) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["c1_4x4x4x4", "ragged_4x6x4x10"])
+def test_adaptive_setup_matches_oracle(name):
+    U, g, op, seed = _case(name, F64, setup_iters=1)
+    tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+    tm.tm_setup(g.h, tv)
+    tl = _oracle_two_level(g, U, name)
+    tl.setup(tv)
+    assert rel(g.export(tm.TM_EXPORT_TV, (g.nv,) + g.L + (4, 3)), tl.test_vectors) <= 1e-9
+    assert rel(g.P_columns(), tl.P.columns()) <= 1e-9
+    assert rel(g.Dc_blocks(), tl.Dc.blocks) <= 1e-9
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_solve_true_residual(name, prec):
+    U, g, op, seed = _case(name, prec, setup_iters=2)
+    tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+    tm.tm_setup(g.h, tv)
+    b = inputs.gaussian_spinor(g.L, seed + 1000, nrhs=2)
+    x = np.zeros_like(b)
+    st, info = tm.tm_solve(g.h, b, x, 2, 1e-10)
+    assert st == tm.TM_OK and info.converged
+    for r in range(2):
+        assert np.linalg.norm(b[r] - op.apply(x[r])) / np.linalg.norm(b[r]) <= 1e-10
+    assert info.true_relres <= 1e-10
+
+
+def test_solve_iterations_match_oracle_fp64():
+    name = "c1_4x4x4x4"
+    U, g, op, seed = _case(name, F64, setup_iters=2)
+    tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+    tm.tm_setup(g.h, tv)
+    tl = _oracle_two_level(g, U, name)
+    tl.setup(tv)
+    b = inputs.gaussian_spinor(g.L, seed + 1000)
+    res = tl.solve(b, tol=1e-10)
+    x = np.zeros_like(b)
+    st, info = tm.tm_solve(g.h, b, x, 1, 1e-10)
+    assert st == tm.TM_OK
+    assert abs(info.iters - res.iters) <= max(1, int(0.1 * res.iters))
+    assert rel(x, res.x) <= 1e-8
+
+
+def test_device_pointers_and_mu_change():
+    name = "8x8x8x8"
+    U, g, op, seed = _case(name, F32, setup_iters=1)
+    tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+    from tests.gpu_helpers import dev, host
+    tm.tm_setup(g.h, dev(tv))
+    b = inputs.gaussian_spinor(g.L, seed + 1000)
+    for mu in (op.mu, -op.mu):  # one setup serves D(+mu) and D(-mu)
+        tm.tm_set_mu(g.h, mu, g.p.delta)
+        xd = dev(np.zeros_like(b))
+        st, info = tm.tm_solve(g.h, dev(b), xd, 1, 1e-10)
+        assert st == tm.TM_OK
+        x = host(xd)
+        opm = op.with_mu(mu)
+        assert np.linalg.norm(b - opm.apply(x)) / np.linalg.norm(b) <= 1e-10
