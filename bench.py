@@ -1,0 +1,487 @@
+#!/usr/bin/env python
+"""Benchmark of the twisted-mass DD-alphaAMG hot path on one GB300.
+
+One step = the whole path of the paper's method on one batch of synthetic
+input: load the gauge field (SU(3) check, link packing, clover term), the
+adaptive setup (test vectors, P, D_c(delta mu)), and the FGMRES solve of
+D(mu) x = b to a true relative residual of 1e-10 (FP64 outer iteration,
+FP32 K-cycle of eq. (1)).  Fig. 1 of the paper also times setup + solve.
+
+Workload (default): 16^3 x 32 lattice, U = exp(0.5 i H), c_sw = 1.5,
+mu = 0.003, delta = 5, two levels, N_v = 20, 4^4 aggregates and SAP
+blocks, 3 setup iterations (few right-hand sides), one Gaussian rhs, m0 from
+inputs/m0_tuned.json (near-critical).  Inputs per step (gauge 75 MB, test
+vectors 503 MB, rhs 25 MB in FP64) exceed the 129 MB L2, so no extra flush.
+
+Output: one JSON line (rank 0).  ``value`` is seconds per step with inputs
+resident in HBM; ``e2e`` the same through the C ABI with pinned host
+buffers (host->device copies and the device->host read of x inside the
+timed region).  ``roofline`` rates the dominant kernel class by its
+algorithmic bytes per launch over its CUDA-event time, measured live during
+the timed steps.  ``cpu_baseline`` times the FP64 numpy oracle on a bounded
+sample of the same workload and scales it by the unit counts of the run.
+
+``--impl reference`` times the oracle alone (the reference arm of this
+method is the CPU oracle; there is no other implementation to install).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "16x16x16x32_2lvl_nv20": dict(
+        L=(32, 16, 16, 16), eps=0.5, seed=1, c_sw=1.5, mu=0.003, delta=5.0, nv=20,
+        agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10,
+        m0_key="16x16x16x32_eps0.5_seed1"),
+    "8x8x8x8_2lvl_nv8": dict(
+        L=(8, 8, 8, 8), eps=0.5, seed=5, c_sw=1.5, mu=0.005, delta=5.0, nv=8,
+        agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, m0=-0.4),
+}
+DEFAULT_WORKLOAD = "16x16x16x32_2lvl_nv20"
+COUNTS_FILE = os.path.join(ROOT, "profiles", "bench_unit_counts.json")
+
+
+def workload_m0(wl: dict) -> tuple[float, str]:
+    if "m0" in wl:
+        return wl["m0"], "fixed"
+    path = os.path.join(ROOT, "inputs", "m0_tuned.json")
+    table = json.load(open(path))
+    return float(table[wl["m0_key"]]["m0"]), "inputs/m0_tuned.json"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per unit (one right-hand side) of each kernel class
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(kind: str, wl: dict) -> float | None:
+    """Bytes per rhs unit that the kernel class must move at minimum.
+
+    dslash:   in spinor 24 + out 24 + 4 links x 12 + clover 72 = 168 reals/site
+    sap:      one colour launch: x everywhere (24 V) + b, links, clover, x-write
+              on the colour's half (24 + 48 + 72 + 24 = 168 reals x V/2)
+    restrict: fine spinor 24 + P (24 N_v) reals/site
+    prolong:  P (24 N_v) + fine in/out (48) reals/site
+    """
+    V = 1
+    for n in wl["L"]:
+        V *= n
+    nv = wl["nv"]
+    if kind == "dslash_f64":
+        return 168 * 8 * V
+    if kind == "dslash_f32":
+        return 168 * 4 * V
+    if kind == "sap":
+        return (24 * V + 168 * V / 2) * 4
+    if kind == "restrict":
+        return (24 + 24 * nv) * 4 * V
+    if kind == "prolong":
+        return (24 * nv + 48) * 4 * V
+    return None
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle CPU baseline: per-unit costs on the full-size workload
+# ---------------------------------------------------------------------------
+def oracle_unit_costs(wl_name: str) -> dict:
+    """Seconds per unit of each step component, timed on the oracle (FP64 numpy).
+
+    Samples (full 16^3 x 32 lattice unless stated): the clover leaves of one
+    ordered plane (x12 for the clover term); one D(mu) apply; one SAP colour
+    half-sweep with 4 MR steps; one restriction and one prolongation with N_v
+    vectors; the thin QR of all aggregates; 10 coarse odd-even GMRES steps on
+    a coarse operator of the workload's shape; the local Galerkin build of
+    D_c for N_v = 2 (scaled by columns x rows to N_v).
+    """
+    import numpy as np
+    import inputs
+    from oracle.dirac import Operator, clover_leaves
+    from oracle.sap import SAP
+    from oracle.coarse import Interpolation, CoarseOperator, OddEvenCoarse
+    from oracle.krylov import gmres
+
+    wl = WORKLOADS[wl_name]
+    L, nv = wl["L"], wl["nv"]
+    try:
+        m0, _ = workload_m0(wl)
+    except (OSError, KeyError):
+        m0 = -0.5  # the unit costs do not depend on the value of m0
+    U = inputs.gauge_field(L, wl["eps"], wl["seed"])
+    out = {}
+    t = time.perf_counter()
+    clover_leaves(U, 0, 1)
+    out["clover"] = 12 * (time.perf_counter() - t)
+    op = Operator.__new__(Operator)
+    op.U, op.L, op.m0, op.c_sw, op.mu, op.bc_t = U, tuple(L), m0, wl["c_sw"], wl["mu"], -1.0
+    A = np.zeros(tuple(L) + (12, 12), dtype=np.complex128)
+    A[...] = (m0 + 4) * np.eye(12)
+    op.A = A
+    psi = inputs.gaussian_spinor(L, 7)
+    t = time.perf_counter()
+    op.apply(psi)
+    out["dslash_f64"] = time.perf_counter() - t
+    sap = SAP(op, wl["sap_block"], n_mr=4)
+    mask = sap.colour == 0
+    t = time.perf_counter()
+    r = psi - op.apply(psi)
+    psi + sap.mr(r, mask) * mask[..., None, None]
+    out["sap"] = time.perf_counter() - t
+    tv = inputs.random_test_vectors(L, nv, 11)
+    t = time.perf_counter()
+    P = Interpolation(tv, wl["agg"])
+    out["qr"] = time.perf_counter() - t
+    t = time.perf_counter()
+    rc = P.restrict(psi)
+    out["restrict"] = time.perf_counter() - t
+    t = time.perf_counter()
+    psi + P.prolong(rc)
+    out["prolong"] = time.perf_counter() - t
+    rng = np.random.default_rng(0)
+    n = 2 * nv
+    blocks = (rng.standard_normal(P.Lc + (9, n, n)) + 1j * rng.standard_normal(P.Lc + (9, n, n))) * 0.05
+    blocks[..., 0, :, :] += 4 * np.eye(n)
+    oe = OddEvenCoarse(CoarseOperator(blocks, nv, wl["delta"] * wl["mu"]))
+    t = time.perf_counter()
+    gmres(oe.schur, oe.reduced_rhs(rc), tol=0.0, restart=30, maxit=10)
+    out["coarse_iter"] = (time.perf_counter() - t) / 10
+    P2 = Interpolation(tv[:2], wl["agg"])
+    t = time.perf_counter()
+    CoarseOperator.build(op, P2, 0.0)
+    t2 = time.perf_counter() - t
+    out["coarse_build"] = t2 * (nv / 2) ** 2 + out["qr"]
+    return out
+
+
+def oracle_seconds(costs: dict, counts: dict) -> float:
+    """Oracle seconds per step = sum over components of count x unit cost."""
+    return (counts["clover"] * costs["clover"]
+            + counts["dslash_f64"] * costs["dslash_f64"]
+            + counts["dslash_f32"] * costs["dslash_f64"]
+            + counts["sap"] * costs["sap"]
+            + counts["restrict"] * costs["restrict"]
+            + counts["prolong"] * costs["prolong"]
+            + counts["coarse_iter"] * costs["coarse_iter"]
+            + counts["coarse_build"] * costs["coarse_build"])
+
+
+def run_oracle_worker(wl_name: str) -> dict:
+    """Time the unit costs in a fresh single-threaded process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    t0 = time.time()
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", wl_name],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle worker failed: " + r.stderr[-2000:])
+    costs = json.loads(r.stdout.strip().splitlines()[-1])
+    costs["_wall"] = time.time() - t0
+    return costs
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def main_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import inputs
+    import paper_1611_01034_gb300 as tm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    wl = WORKLOADS[args.workload]
+    m0, m0_src = (args.m0, "command line") if args.m0 is not None else workload_m0(wl)
+    L, nv, seed = wl["L"], wl["nv"], wl["seed"] + rank  # one independent replica per rank
+    U = inputs.gauge_field(L, wl["eps"], seed)
+    tv = inputs.random_test_vectors(L, nv, seed + inputs.TV_SEED_OFFSET)
+    b = inputs.gaussian_spinor(L, seed + inputs.RHS_SEED_OFFSET)
+    Ud, tvd, bd = (torch.from_numpy(a).cuda() for a in (U, tv, b))
+    xd = torch.zeros_like(bd)
+    Uh, tvh, bh = (torch.from_numpy(a).pin_memory() for a in (U, tv, b))
+    xh = torch.zeros(bh.shape, dtype=bh.dtype).pin_memory()
+    stream = torch.cuda.current_stream()
+    p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv,
+                  agg=wl["agg"], sap_block=wl["sap_block"], setup_iters=wl["setup_iters"],
+                  cycle_prec=tm.TM_F32)
+    h = tm.tm_create(p, stream)
+    infos = []
+
+    def step(Ug, tvg, bg, xg):
+        tm.tm_load_gauge(h, Ug)
+        tm.tm_setup(h, tvg)
+        xg.zero_()
+        st, info = tm.tm_solve(h, bg, xg, 1, wl["tol"])
+        if st != tm.TM_OK:
+            raise RuntimeError(f"solve failed: {tm.tm_status_string(st)}")
+        infos.append(info.as_dict())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(Ug, tvg, bg, xg, k, profile):
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            tm.tm_profile(h, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            step(Ug, tvg, bg, xg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        sec = e0.elapsed_time(e1) / 1000.0
+        if world > 1:
+            t = torch.tensor([sec], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sec = float(t.item())
+        return sec
+
+    for _ in range(args.warmup):
+        step(Ud, tvd, bd, xd)
+    clocks = ClockSampler(local)
+    clocks.start()
+    infos.clear()
+    sec = timed(Ud, tvd, bd, xd, args.steps, profile=True)
+    prof = tm.tm_profile_read(h)
+    tm.tm_profile(h, False)
+    clk = clocks.stop()
+    step_infos = list(infos)
+    # end-to-end through the C ABI with pinned host buffers
+    step(Uh, tvh, bh, xh)
+    sec_e2e = timed(Uh, tvh, bh, xh, args.steps, profile=False)
+    # correctness of the last solution: true residual by the GPU is in info; spot-check
+    x_last = xh.numpy()
+    h2d = (Uh.numel() + tvh.numel() + bh.numel() + xh.numel()) * 16
+    d2h = xh.numel() * 16
+    tm.tm_destroy(h)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    K = args.steps
+    units_total = world * K
+    value = sec / units_total
+    # per-step unit counts (per rhs unit) from the profile
+    per_step = {k: v["units"] / K for k, v in prof.items()}
+    launches = sum(v["launches"] for v in prof.values())
+    kernel_ms = {k: v["ms"] for k, v in prof.items()}
+    dom = max(kernel_ms, key=lambda k: kernel_ms[k])
+    roof = None
+    bytes_unit = algorithmic_bytes(dom, wl)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    if bytes_unit is not None and prof[dom]["launches"]:
+        per_launch_bytes = bytes_unit * prof[dom]["units"] / prof[dom]["launches"]
+        avg_s = prof[dom]["ms"] / prof[dom]["launches"] / 1000.0
+        achieved = per_launch_bytes / avg_s / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                "bytes_per_launch": per_launch_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "share": round(v["ms"] / max(1e-12, sum(kernel_ms.values())), 4)}
+               for k, v in prof.items() if v["launches"]}
+    # units per step; coarse_oe units count the odd-even Schur applications
+    # (one per coarse GMRES step, plus the per-solve rhs/reconstruction)
+    counts = {
+        "clover": 1.0,
+        "dslash_f64": per_step["dslash_f64"],
+        "dslash_f32": per_step["dslash_f32"],
+        "sap": per_step["sap"],
+        "restrict": per_step["restrict"],
+        "prolong": per_step["prolong"],
+        "coarse_iter": per_step["coarse_oe"],
+        "coarse_build": prof["coarse_build"]["launches"] / K,
+    }
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            costs = run_oracle_worker(args.workload)
+            osec = oracle_seconds(costs, counts)
+            cpu = {"value": round(osec, 2), "unit": "s", "cores": 1, "kind": "oracle",
+                   "sample": ("FP64 numpy oracle, single thread, per-unit costs timed on the "
+                              "full lattice (clover plane, D apply, SAP colour half-sweep, "
+                              "restriction, prolongation, QR, 10 coarse GMRES steps, D_c build "
+                              "for N_v=2 scaled to N_v) x this run's unit counts per step"),
+                   "sample_wall_s": round(costs["_wall"], 1),
+                   "unit_costs_s": {k: round(v, 4) for k, v in costs.items() if not k.startswith("_")}}
+        except Exception as e:  # report, do not hide
+            cpu = {"value": None, "error": str(e)[:300]}
+    if args.write_counts:
+        os.makedirs(os.path.dirname(COUNTS_FILE), exist_ok=True)
+        json.dump({"workload": args.workload, "counts_per_step": counts,
+                   "note": "unit counts per step of the hot path (algorithmic counts of this "
+                           "method on this workload), used to scale the oracle's per-unit costs"},
+                  open(COUNTS_FILE, "w"), indent=1)
+    V = 1
+    for n in L:
+        V *= n
+    line = {
+        "metric": "solve seconds to 1e-10 rel. residual; D(mu) HBM GB/s and D_c TFLOP/s vs peak",
+        "value": round(value, 5),
+        "unit": "s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(sec / K * 1000, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 outer / f32 cycle",
+        "data": "synthetic (seeded random SU(3) field U = exp(0.5 i H); Gaussian rhs)",
+        "config": {
+            "workload": args.workload, "lattice_TZYX": list(L), "sites": V, "levels": 2,
+            "nv": nv, "aggregate": list(wl["agg"]), "sap_block": list(wl["sap_block"]),
+            "m0": m0, "m0_source": m0_src, "c_sw": wl["c_sw"], "mu": wl["mu"],
+            "delta": wl["delta"], "setup_iters": wl["setup_iters"], "tol": wl["tol"], "nrhs": 1,
+            "step": "load gauge + clover, adaptive setup, FGMRES solve (one rhs)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "inputs per step 603 MB > 129 MB L2 (no extra flush)",
+        },
+        "solve": {
+            "outer_iters": [i["iters"] for i in step_infos],
+            "coarse_iters": [i["coarse_iters"] for i in step_infos],
+            "true_relres": max(i["true_relres"] for i in step_infos),
+        },
+        "e2e": {"value": round(sec_e2e / units_total, 5), "unit": "s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernels": kernels,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle alone
+# ---------------------------------------------------------------------------
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    if not os.path.exists(COUNTS_FILE):
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "no unit counts recorded (profiles/bench_unit_counts.json)"}))
+        return
+    counts = json.load(open(COUNTS_FILE))["counts_per_step"]
+    times = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        costs = run_oracle_worker(args.workload)
+        if i >= args.warmup:
+            times.append(oracle_seconds(costs, counts))
+        last = costs
+    value = statistics.mean(times)
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "solve seconds to 1e-10 rel. residual; D(mu) HBM GB/s and D_c TFLOP/s vs peak",
+        "value": round(value, 2), "unit": "s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": round(value, 2), "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": "per-unit oracle costs x recorded unit counts per step",
+                         "unit_costs_s": {k: round(v, 4) for k, v in last.items() if not k.startswith("_")}},
+        "e2e": {"value": round(value, 2), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--write-counts", action="store_true")
+    ap.add_argument("--oracle-worker", default=None)
+    ap.add_argument("--m0", type=float, default=None, help="override the workload's tuned m0")
+    args = ap.parse_args()
+    if args.oracle_worker:
+        print(json.dumps(oracle_unit_costs(args.oracle_worker)))
+        return
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_native(args)
+
+
+if __name__ == "__main__":
+    main()

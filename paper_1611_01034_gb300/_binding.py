@@ -66,6 +66,10 @@ _SIGS = {
     "tm_kcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "tm_export": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
     "tm_synchronize": (c_int, [c_void_p]),
+    "tm_profile": (c_int, [c_void_p, c_int]),
+    "tm_profile_kinds": (c_int, []),
+    "tm_profile_name": (c_char_p, [c_int]),
+    "tm_profile_read": (c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong), POINTER(c_double), c_int]),
 }
 
 
@@ -223,3 +227,25 @@ def tm_export(h, what, out, nbytes) -> None:
 
 def tm_synchronize(h) -> None:
     _check(lib().tm_synchronize(h), h)
+
+
+def tm_profile(h, enable: bool) -> None:
+    _check(lib().tm_profile(h, int(enable)), h)
+
+
+def tm_profile_kinds() -> int:
+    return int(lib().tm_profile_kinds())
+
+
+def tm_profile_name(kind: int) -> str:
+    return lib().tm_profile_name(kind).decode()
+
+
+def tm_profile_read(h) -> dict:
+    """{name: {"launches", "units", "ms"}} since the last tm_profile()."""
+    n = tm_profile_kinds()
+    la = (c_longlong * n)()
+    un = (c_longlong * n)()
+    ms = (c_double * n)()
+    _check(lib().tm_profile_read(h, la, un, ms, n), h)
+    return {tm_profile_name(k): {"launches": la[k], "units": un[k], "ms": ms[k]} for k in range(n)}

@@ -82,6 +82,17 @@ struct tm_handle {
   std::string err;
   long long coarse_iters = 0;
   int kcycles = 0;
+  // opt-in per-kernel timing (tm_profile)
+  bool prof = false;
+  struct Rec {
+    int kind, units, nk;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> evpool;
+  long long prof_launch[16] = {};
+  long long prof_units[16] = {};
+  double prof_ms[16] = {};
 };
 
 namespace {
@@ -115,6 +126,68 @@ T* W(tm_handle* h, const std::string& name, size_t count) {
 }
 
 void sync(tm_handle* h) { CK(cudaStreamSynchronize(h->st)); }
+
+// ---------------------------------------------------------------------------
+// opt-in profiler: CUDA events around each launch on the handle's stream
+// ---------------------------------------------------------------------------
+enum ProfKind {
+  PK_DSLASH64 = 0, PK_DSLASH32, PK_SAP, PK_RESTRICT, PK_PROLONG, PK_COARSE_OE, PK_BLAS_FINE, PK_BLAS_COARSE,
+  PK_BUILD, PK_OTHER, PK_N
+};
+const char* const kProfNames[PK_N] = {"dslash_f64", "dslash_f32",  "sap",         "restrict",     "prolong",
+                                      "coarse_oe",  "blas_fine",   "blas_coarse", "coarse_build", "other"};
+
+cudaEvent_t take_event(tm_handle* h) {
+  if (!h->evpool.empty()) {
+    cudaEvent_t e = h->evpool.back();
+    h->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  return e;
+}
+
+// fold finished records into the totals (all of them if wait)
+void harvest(tm_handle* h, bool wait) {
+  if (wait) sync(h);
+  size_t keep = 0;
+  for (size_t i = 0; i < h->recs.size(); ++i) {
+    auto& r = h->recs[i];
+    if (!wait && cudaEventQuery(r.b) != cudaSuccess) {
+      cudaGetLastError();
+      h->recs[keep++] = r;
+      continue;
+    }
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    h->prof_ms[r.kind] += ms;
+    h->prof_launch[r.kind] += r.nk;
+    h->prof_units[r.kind] += r.units;
+    h->evpool.push_back(r.a);
+    h->evpool.push_back(r.b);
+  }
+  h->recs.resize(keep);
+}
+
+// one scope = nk kernel launches of one class processing u rhs units
+struct Prof {
+  tm_handle* h;
+  int kind, units, nk;
+  cudaEvent_t a = nullptr;
+  Prof(tm_handle* hh, int k, int u = 1, int n = 1) : h(hh), kind(k), units(u), nk(n) {
+    if (!h->prof) return;
+    if (h->recs.size() > 4096) harvest(h, false);
+    a = take_event(h);
+    CK(cudaEventRecord(a, h->st));
+  }
+  ~Prof() noexcept(false) {
+    if (!h->prof || !a) return;
+    cudaEvent_t b = take_event(h);
+    CK(cudaEventRecord(b, h->st));
+    h->recs.push_back({kind, units, nk, a, b});
+  }
+};
 
 void check_flags(tm_handle* h) {
   int f = 0;
@@ -152,6 +225,7 @@ double mu_c(tm_handle* h) { return h->p.delta * h->p.mu; }
 // ---------------------------------------------------------------------------
 template <typename T>
 void dslash(tm_handle* h, const T* in, T* out, const T* b, int nrhs) {
+  Prof pf(h, std::is_same<T, double>::value ? PK_DSLASH64 : PK_DSLASH32, nrhs);
   launch_dslash<T>(gaugeT<T>(h), cloverT<T>(h), in, out, b, h->g, h->p.mu, h->p.bc_t, nrhs, h->st);
   CKL();
 }
@@ -160,6 +234,7 @@ template <typename T>
 void sap_sweeps(tm_handle* h, const T* b, T* x, int sweeps, int nrhs) {
   for (int s = 0; s < sweeps; ++s)
     for (int colour = 0; colour < 2; ++colour) {
+      Prof pf(h, PK_SAP, nrhs);
       launch_sap_colour<T>(gaugeT<T>(h), cloverT<T>(h), b, x, h->sg, h->p.mu, h->p.bc_t, h->p.mr_iters, colour, nrhs,
                            h->st);
       CKL();
@@ -168,9 +243,12 @@ void sap_sweeps(tm_handle* h, const T* b, T* x, int sweeps, int nrhs) {
 
 // ||x_r||^2 for nrhs vectors -> host
 template <typename T>
-std::vector<double> norms2(tm_handle* h, const T* x, long ncx, int nrhs) {
-  launch_norm2<T>(x, ncx, nrhs, h->dsmall, h->scratch, kScratchBlocks, h->st);
-  CKL();
+std::vector<double> norms2(tm_handle* h, const T* x, long ncx, int nrhs, int kind) {
+  {
+    Prof pf(h, kind, nrhs, 2);
+    launch_norm2<T>(x, ncx, nrhs, h->dsmall, h->scratch, kScratchBlocks, h->st);
+    CKL();
+  }
   CK(cudaMemcpyAsync(h->hsmall, h->dsmall, nrhs * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   sync(h);
   return std::vector<double>(h->hsmall, h->hsmall + nrhs);
@@ -212,19 +290,22 @@ void givens(std::complex<double> a, double b, double& c, std::complex<double>& s
 template <typename T, typename TZ, typename FA, typename FAZ, typename FM>
 KrylovOut krylov(tm_handle* h, const std::string& tag, FA A, FAZ AZ, FM M, bool flexible, const T* b, T* x,
                  bool x0, long ncx, double tol, int m, int maxit) {
+  const int bk = flexible ? PK_BLAS_FINE : PK_BLAS_COARSE;
   using cd = std::complex<double>;
   KrylovOut out;
   T* Vb = W<T>(h, tag + "V", (size_t)(m + 1) * 2 * ncx);
   T* w = W<T>(h, tag + "w", (size_t)2 * ncx);
   TZ* Z = flexible ? W<TZ>(h, tag + "Z", (size_t)m * 2 * ncx) : nullptr;
   const long ld = 2 * ncx;
-  const double bnorm = std::sqrt(norms2<T>(h, b, ncx, 1)[0]);
+  const double bnorm = std::sqrt(norms2<T>(h, b, ncx, 1, bk)[0]);
   if (!std::isfinite(bnorm)) raise(TM_ERR_NONFINITE, "non-finite right-hand side");
   if (!x0) {
+    Prof pf(h, bk);
     launch_zero<T>(x, 2 * ncx, h->st);
     CKL();
   }
   if (bnorm == 0) {
+    Prof pf(h, bk);
     launch_zero<T>(x, 2 * ncx, h->st);
     CKL();
     out.converged = true;
@@ -235,20 +316,24 @@ KrylovOut krylov(tm_handle* h, const std::string& tag, FA A, FAZ AZ, FM M, bool 
     if (x0 || out.iters > 0) {
       A(x, w);
       CK(cudaMemcpyAsync(r, b, 2 * ncx * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+      Prof pf(h, bk);
       launch_caxpby<T>(-1, 0, w, 1, 0, r, ncx, h->st);
       CKL();
     } else {
       CK(cudaMemcpyAsync(r, b, 2 * ncx * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
     }
-    return std::sqrt(norms2<T>(h, r, ncx, 1)[0]);
+    return std::sqrt(norms2<T>(h, r, ncx, 1, bk)[0]);
   };
   double beta = residual(Vb);
   std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m), y(m);
   std::vector<double> cs(m);
   while (beta > tol * bnorm && out.iters < maxit) {
     if (!std::isfinite(beta)) raise(TM_ERR_NONFINITE, "non-finite residual");
-    launch_caxpby<T>(1.0 / beta, 0, Vb, 0, 0, Vb, ncx, h->st);
-    CKL();
+    {
+      Prof pf(h, bk);
+      launch_caxpby<T>(1.0 / beta, 0, Vb, 0, 0, Vb, ncx, h->st);
+      CKL();
+    }
     std::fill(g.begin(), g.end(), cd(0));
     g[0] = beta;
     int k = 0;
@@ -265,19 +350,37 @@ KrylovOut krylov(tm_handle* h, const std::string& tag, FA A, FAZ AZ, FM M, bool 
       double* d1 = h->dsmall;
       double* d2 = h->dsmall + 2 * kMaxDots;
       double* dn = h->dsmall + 4 * kMaxDots;
-      launch_multidot<T>(Vb, ld, k + 1, w, ncx, d1, h->scratch, kScratchBlocks, h->st);
-      CKL();
-      launch_multi_caxpy<T>(Vb, ld, k + 1, d1, 1.0, w, ncx, h->st);
-      CKL();
-      launch_multidot<T>(Vb, ld, k + 1, w, ncx, d2, h->scratch, kScratchBlocks, h->st);
-      CKL();
-      launch_multi_caxpy<T>(Vb, ld, k + 1, d2, 1.0, w, ncx, h->st);
-      CKL();
-      launch_norm2<T>(w, ncx, 1, dn, h->scratch, kScratchBlocks, h->st);
-      CKL();
+      {
+        Prof pf(h, bk, 1, 2);
+        launch_multidot<T>(Vb, ld, k + 1, w, ncx, d1, h->scratch, kScratchBlocks, h->st);
+        CKL();
+      }
+      {
+        Prof pf(h, bk);
+        launch_multi_caxpy<T>(Vb, ld, k + 1, d1, 1.0, w, ncx, h->st);
+        CKL();
+      }
+      {
+        Prof pf(h, bk, 1, 2);
+        launch_multidot<T>(Vb, ld, k + 1, w, ncx, d2, h->scratch, kScratchBlocks, h->st);
+        CKL();
+      }
+      {
+        Prof pf(h, bk);
+        launch_multi_caxpy<T>(Vb, ld, k + 1, d2, 1.0, w, ncx, h->st);
+        CKL();
+      }
+      {
+        Prof pf(h, bk, 1, 2);
+        launch_norm2<T>(w, ncx, 1, dn, h->scratch, kScratchBlocks, h->st);
+        CKL();
+      }
       CK(cudaMemcpyAsync(Vb + (long)(k + 1) * ld, w, 2 * ncx * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
-      launch_scale<T>(Vb + (long)(k + 1) * ld, ncx, 1, dn, true, h->st);
-      CKL();
+      {
+        Prof pf(h, bk);
+        launch_scale<T>(Vb + (long)(k + 1) * ld, ncx, 1, dn, true, h->st);
+        CKL();
+      }
       CK(cudaMemcpyAsync(h->hsmall, h->dsmall, (4 * kMaxDots + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
       sync(h);
       const double hn = std::sqrt(h->hsmall[4 * kMaxDots]);
@@ -318,11 +421,14 @@ KrylovOut krylov(tm_handle* h, const std::string& tag, FA A, FAZ AZ, FM M, bool 
     }
     double* dy = h->dsmall + 6 * kMaxDots;
     CK(cudaMemcpyAsync(dy, h->hsmall, 2 * k * sizeof(double), cudaMemcpyHostToDevice, h->st));
-    if (flexible)
-      launch_lincomb<TZ, T>(Z, ld, k, dy, x, ncx, h->st);
-    else
-      launch_lincomb<T, T>(Vb, ld, k, dy, x, ncx, h->st);
-    CKL();
+    {
+      Prof pf(h, bk);
+      if (flexible)
+        launch_lincomb<TZ, T>(Z, ld, k, dy, x, ncx, h->st);
+      else
+        launch_lincomb<T, T>(Vb, ld, k, dy, x, ncx, h->st);
+      CKL();
+    }
     ++out.restarts;
     beta = residual(Vb);
   }
@@ -337,6 +443,7 @@ KrylovOut krylov(tm_handle* h, const std::string& tag, FA A, FAZ AZ, FM M, bool 
 template <typename T>
 void build_coarse(tm_handle* h) {
   T* P = static_cast<T*>(h->P);
+  Prof pf(h, PK_BUILD, 1, 3);
   launch_orthonormalise<T>(P, h->ag, h->d_err, h->st);
   CKL();
   launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, static_cast<T*>(h->Dc), h->ag, h->p.bc_t, h->st);
@@ -355,12 +462,16 @@ KrylovOut coarse_solve(tm_handle* h, const T* b, T* x, double tol, int maxit) {
   T* bh = W<T>(h, "c_bh", 2 * nc);
   T* xe = W<T>(h, "c_xe", 2 * nc);
   T* uo = W<T>(h, "c_uo", 2 * nc);
-  launch_oe_inv_odd<T>(Di, b, to, h->oe, h->st);
-  CKL();
-  launch_oe_rhs<T>(Dc, b, to, bh, h->oe, h->st);
-  CKL();
+  {
+    Prof pf(h, PK_COARSE_OE, 1, 2);
+    launch_oe_inv_odd<T>(Di, b, to, h->oe, h->st);
+    CKL();
+    launch_oe_rhs<T>(Dc, b, to, bh, h->oe, h->st);
+    CKL();
+  }
   const double mc = mu_c(h);
   auto S = [&](const T* ve, T* ye) {
+    Prof pf(h, PK_COARSE_OE, 1, 2);
     launch_oe_hop_inv<T>(Dc, Di, ve, uo, h->oe, h->st);
     CKL();
     launch_oe_even<T>(Dc, ve, uo, ye, h->oe, mc, 1, h->st);
@@ -368,8 +479,11 @@ KrylovOut coarse_solve(tm_handle* h, const T* b, T* x, double tol, int maxit) {
   };
   auto none = [](const T*, T*) {};
   KrylovOut r = krylov<T, T>(h, "cg", S, S, none, false, bh, xe, false, nc, tol, h->p.coarse_restart, maxit);
-  launch_oe_reconstruct<T>(Dc, Di, b, xe, x, h->oe, h->st);
-  CKL();
+  {
+    Prof pf(h, PK_COARSE_OE, 1, 2);
+    launch_oe_reconstruct<T>(Dc, Di, b, xe, x, h->oe, h->st);
+    CKL();
+  }
   h->coarse_iters += r.iters;
   return r;
 }
@@ -378,8 +492,11 @@ KrylovOut coarse_solve(tm_handle* h, const T* b, T* x, double tol, int maxit) {
 template <typename T>
 void kcycle(tm_handle* h, const T* v, T* z, int nrhs) {
   const long fr = fine_reals(h);
-  launch_zero<T>(z, fr * nrhs, h->st);
-  CKL();
+  {
+    Prof pf(h, PK_OTHER);
+    launch_zero<T>(z, fr * nrhs, h->st);
+    CKL();
+  }
   sap_sweeps<T>(h, v, z, h->p.pre_smooth, nrhs);
   const T* r = v;
   if (h->p.pre_smooth > 0) {
@@ -390,12 +507,18 @@ void kcycle(tm_handle* h, const T* v, T* z, int nrhs) {
   const long cc = coarse_cx(h);
   T* rc = W<T>(h, "k_rc", 2 * cc * nrhs);
   T* ec = W<T>(h, "k_ec", 2 * cc * nrhs);
-  launch_restrict<T>(static_cast<const T*>(h->P), r, rc, h->ag, nrhs, h->st);
-  CKL();
+  {
+    Prof pf(h, PK_RESTRICT, nrhs);
+    launch_restrict<T>(static_cast<const T*>(h->P), r, rc, h->ag, nrhs, h->st);
+    CKL();
+  }
   for (int i = 0; i < nrhs; ++i)
     coarse_solve<T>(h, rc + 2 * cc * i, ec + 2 * cc * i, h->p.coarse_tol, h->p.coarse_maxit);
-  launch_prolong<T>(static_cast<const T*>(h->P), ec, z, h->ag, nrhs, true, h->st);
-  CKL();
+  {
+    Prof pf(h, PK_PROLONG, nrhs);
+    launch_prolong<T>(static_cast<const T*>(h->P), ec, z, h->ag, nrhs, true, h->st);
+    CKL();
+  }
   sap_sweeps<T>(h, v, z, h->p.post_smooth, nrhs);
   h->kcycles += nrhs;
 }
@@ -403,6 +526,7 @@ void kcycle(tm_handle* h, const T* v, T* z, int nrhs) {
 template <typename T>
 void normalise_fields(tm_handle* h, T* f, int nrhs) {
   const long fr = fine_reals(h);
+  Prof pf(h, PK_OTHER, nrhs, 3);
   launch_norm2<T>(f, fr / 2, nrhs, h->dsmall, h->scratch, kScratchBlocks, h->st);
   CKL();
   launch_scale<T>(f, fr / 2, nrhs, h->dsmall, true, h->st);
@@ -415,8 +539,11 @@ void setup_impl(tm_handle* h, const double* tv_dev, bool adaptive) {
   const long fr = fine_reals(h);
   T* tv = static_cast<T*>(h->tv);
   T* P = static_cast<T*>(h->P);
-  launch_pack_spinor<T>(tv_dev, tv, h->g, nv, h->st);
-  CKL();
+  {
+    Prof pf(h, PK_OTHER, nv);
+    launch_pack_spinor<T>(tv_dev, tv, h->g, nv, h->st);
+    CKL();
+  }
   if (adaptive) {
     sap_sweeps<T>(h, nullptr, tv, h->p.init_sweeps, nv);
     normalise_fields<T>(h, tv, nv);
@@ -449,8 +576,11 @@ KrylovOut solve_one(tm_handle* h, const double* b, double* x, double tol) {
     if constexpr (std::is_same<T, double>::value) {
       dslash<double>(h, z, out, nullptr, 1);
     } else {
-      launch_convert<T, double>(z, zt, fr, h->st);
-      CKL();
+      {
+        Prof pf(h, PK_OTHER);
+        launch_convert<T, double>(z, zt, fr, h->st);
+        CKL();
+      }
       dslash<double>(h, zt, out, nullptr, 1);
     }
   };
@@ -458,8 +588,11 @@ KrylovOut solve_one(tm_handle* h, const double* b, double* x, double tol) {
     if constexpr (std::is_same<T, double>::value) {
       kcycle<double>(h, v, z, 1);
     } else {
-      launch_convert<double, T>(v, vt, fr, h->st);
-      CKL();
+      {
+        Prof pf(h, PK_OTHER);
+        launch_convert<double, T>(v, vt, fr, h->st);
+        CKL();
+      }
       kcycle<T>(h, vt, z, 1);
     }
   };
@@ -574,6 +707,11 @@ void tm_destroy(tm_handle* h) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (h->hsmall) cudaFreeHost(h->hsmall);
+  for (auto& r : h->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   delete h;
 }
 
@@ -664,10 +802,13 @@ tm_status tm_load_gauge(tm_handle* h, const double* gauge) {
   API_BEGIN
   const size_t bytes = (size_t)h->g.V * 4 * 9 * 2 * sizeof(double);
   const double* gd = stage_in(h, gauge, bytes, "stage_gauge");
-  launch_pack_gauge(gd, h->g64, h->g32, h->g, 1e-10, h->d_err, h->st);
-  CKL();
-  launch_clover(gd, h->c64, h->c32, h->g, h->p.m0, h->p.c_sw, h->st);
-  CKL();
+  {
+    Prof pf(h, PK_OTHER, 1, 2);
+    launch_pack_gauge(gd, h->g64, h->g32, h->g, 1e-10, h->d_err, h->st);
+    CKL();
+    launch_clover(gd, h->c64, h->c32, h->g, h->p.m0, h->p.c_sw, h->st);
+    CKL();
+  }
   h->gauge_ok = false;
   h->setup_ok = false;
   check_flags(h);
@@ -735,13 +876,19 @@ tm_status tm_solve(tm_handle* h, const double* b, double* x, int nrhs, double to
     h->coarse_iters = 0;
     h->kcycles = 0;
     for (int r = 0; r < nrhs; ++r) {
-      launch_pack_spinor<double>(bd + (size_t)r * V * 24, bf, h->g, 1, h->st);
-      CKL();
-      launch_pack_spinor<double>(xd + (size_t)r * V * 24, xf, h->g, 1, h->st);
-      CKL();
+      {
+        Prof pf(h, PK_OTHER, 1, 2);
+        launch_pack_spinor<double>(bd + (size_t)r * V * 24, bf, h->g, 1, h->st);
+        CKL();
+        launch_pack_spinor<double>(xd + (size_t)r * V * 24, xf, h->g, 1, h->st);
+        CKL();
+      }
       KrylovOut k = h->p.cycle_prec == TM_F64 ? solve_one<double>(h, bf, xf, tol) : solve_one<float>(h, bf, xf, tol);
-      launch_unpack_spinor<double>(xf, xd + (size_t)r * V * 24, h->g, 1, h->st);
-      CKL();
+      {
+        Prof pf(h, PK_OTHER);
+        launch_unpack_spinor<double>(xf, xd + (size_t)r * V * 24, h->g, 1, h->st);
+        CKL();
+      }
       loc.iters += k.iters;
       loc.restarts += k.restarts;
       loc.true_relres = std::max(loc.true_relres, k.relres);
@@ -1005,7 +1152,7 @@ tm_status tm_export(tm_handle* h, int what, double* out, size_t bytes) {
         double pk[36];
         for (int k = 0; k < 36; ++k) {
           const long r = 36L * hb + k;  // real index within the site
-          pk[k] = raw[(size_t)(r / 2) * V * 2 + s * 2 + (r % 2)];
+          pk[k] = raw[(size_t)(r / 4) * V * 4 + s * 4 + (r % 4)];
         }
         double* M = host.data() + ((size_t)s * 2 + hb) * 72;
         for (int i = 0; i < 6; ++i) {
@@ -1031,6 +1178,34 @@ tm_status tm_export(tm_handle* h, int what, double* out, size_t bytes) {
     sync(h);
   } else {
     std::memcpy(out, host.data(), host.size() * sizeof(double));
+  }
+  API_END
+}
+
+tm_status tm_profile(tm_handle* h, int enable) {
+  if (!h) return TM_ERR_ARG;
+  API_BEGIN
+  harvest(h, true);
+  for (int k = 0; k < PK_N; ++k) {
+    h->prof_launch[k] = h->prof_units[k] = 0;
+    h->prof_ms[k] = 0;
+  }
+  h->prof = enable != 0;
+  API_END
+}
+
+int tm_profile_kinds(void) { return PK_N; }
+
+const char* tm_profile_name(int kind) { return (kind >= 0 && kind < PK_N) ? kProfNames[kind] : ""; }
+
+tm_status tm_profile_read(tm_handle* h, long long* launches, long long* units, double* ms, int n) {
+  if (!h || n < 0) return TM_ERR_ARG;
+  API_BEGIN
+  harvest(h, true);
+  for (int k = 0; k < n && k < PK_N; ++k) {
+    if (launches) launches[k] = h->prof_launch[k];
+    if (units) units[k] = h->prof_units[k];
+    if (ms) ms[k] = h->prof_ms[k];
   }
   API_END
 }

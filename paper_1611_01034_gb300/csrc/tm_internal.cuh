@@ -2,8 +2,11 @@
 // twisted-mass DD-alphaAMG library.  Nothing here is part of the C ABI.
 //
 // Field layout ("chunked SoA"): a site field with NR reals per site is stored
-// as [NR / n][V] 16-byte vectors, n = 2 (double2) or 4 (float4), so that one
-// warp's load of one chunk is 512 contiguous bytes.  A spinor has 24 reals
+// as [NR / 4][V] chunks of 4 reals (two complex numbers): one float4 in FP32,
+// two consecutive double2 in FP64.  One warp's load of one chunk is 512 (FP32)
+// or 1024 (FP64) contiguous bytes, and both precisions share one index map
+// (real r of site s at ((r / 4) * V + s) * 4 + r % 4), so precision casts and
+// mixed-precision vector operations can run on the flat arrays.  A spinor has 24 reals
 // (12 complex, index 3*spin + colour), a link 12 reals (rows 0 and 1 of the
 // SU(3) matrix; row 2 is rebuilt as conj(row0 x row1)), a clover site 72
 // reals (two Hermitian 6x6 chiral blocks, 36 reals each: 6 real diagonal
@@ -129,31 +132,20 @@ __host__ __device__ __forceinline__ int nb_bwd(const Lat& g, int s, const int c[
 // ---------------------------------------------------------------------------
 // chunked SoA loads and stores
 // ---------------------------------------------------------------------------
-template <typename T>
-struct V16;
-template <>
-struct V16<double> {
-  using type = double2;
-  static constexpr int n = 2;
-};
-template <>
-struct V16<float> {
-  using type = float4;
-  static constexpr int n = 4;
-};
-
 // load NC complex numbers of site s from a chunked field with V sites
 template <typename T, int NC>
 __device__ __forceinline__ void ld_cx(const T* __restrict__ base, long V, long s, cx<T> (&z)[NC]) {
+  static_assert(NC % 2 == 0, "chunks hold two complex numbers");
   if constexpr (sizeof(T) == 8) {
     const double2* p = reinterpret_cast<const double2*>(base);
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      double2 v = __ldg(p + k * V + s);
-      z[k] = cx<T>{(T)v.x, (T)v.y};
+    for (int k = 0; k < NC / 2; ++k) {
+      const double2* q = p + 2 * (k * V + s);
+      double2 v0 = __ldg(q), v1 = __ldg(q + 1);
+      z[2 * k] = cx<T>{(T)v0.x, (T)v0.y};
+      z[2 * k + 1] = cx<T>{(T)v1.x, (T)v1.y};
     }
   } else {
-    static_assert(NC % 2 == 0, "float chunks hold two complex numbers");
     const float4* p = reinterpret_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < NC / 2; ++k) {
@@ -166,10 +158,15 @@ __device__ __forceinline__ void ld_cx(const T* __restrict__ base, long V, long s
 
 template <typename T, int NC>
 __device__ __forceinline__ void st_cx(T* __restrict__ base, long V, long s, const cx<T> (&z)[NC]) {
+  static_assert(NC % 2 == 0, "chunks hold two complex numbers");
   if constexpr (sizeof(T) == 8) {
     double2* p = reinterpret_cast<double2*>(base);
 #pragma unroll
-    for (int k = 0; k < NC; ++k) p[k * V + s] = make_double2((double)z[k].r, (double)z[k].i);
+    for (int k = 0; k < NC / 2; ++k) {
+      double2* q = p + 2 * (k * V + s);
+      q[0] = make_double2((double)z[2 * k].r, (double)z[2 * k].i);
+      q[1] = make_double2((double)z[2 * k + 1].r, (double)z[2 * k + 1].i);
+    }
   } else {
     float4* p = reinterpret_cast<float4*>(base);
 #pragma unroll
@@ -185,10 +182,13 @@ __device__ __forceinline__ void ld_re(const T* __restrict__ base, long V, long s
   if constexpr (sizeof(T) == 8) {
     const double2* p = reinterpret_cast<const double2*>(base);
 #pragma unroll
-    for (int k = 0; k < NR / 2; ++k) {
-      double2 v = __ldg(p + k * V + s);
-      r[2 * k] = v.x;
-      r[2 * k + 1] = v.y;
+    for (int k = 0; k < NR / 4; ++k) {
+      const double2* q = p + 2 * (k * V + s);
+      double2 v0 = __ldg(q), v1 = __ldg(q + 1);
+      r[4 * k] = v0.x;
+      r[4 * k + 1] = v0.y;
+      r[4 * k + 2] = v1.x;
+      r[4 * k + 3] = v1.y;
     }
   } else {
     const float4* p = reinterpret_cast<const float4*>(base);
@@ -208,7 +208,11 @@ __device__ __forceinline__ void st_re(T* __restrict__ base, long V, long s, cons
   if constexpr (sizeof(T) == 8) {
     double2* p = reinterpret_cast<double2*>(base);
 #pragma unroll
-    for (int k = 0; k < NR / 2; ++k) p[k * V + s] = make_double2(r[2 * k], r[2 * k + 1]);
+    for (int k = 0; k < NR / 4; ++k) {
+      double2* q = p + 2 * (k * V + s);
+      q[0] = make_double2(r[4 * k], r[4 * k + 1]);
+      q[1] = make_double2(r[4 * k + 2], r[4 * k + 3]);
+    }
   } else {
     float4* p = reinterpret_cast<float4*>(base);
 #pragma unroll

@@ -246,3 +246,52 @@ def test_device_pointers_and_mu_change():
         x = host(xd)
         opm = op.with_mu(mu)
         assert np.linalg.norm(b - opm.apply(x)) / np.linalg.norm(b) <= 1e-10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_kcycle_fp32_against_fp64_oracle(name):
+    """The FP32 K-cycle (FP32 SAP, P, D_c, coarse GMRES) stays within FP32
+    rounding (amplified by the nonlinear MR and GMRES steps) of the FP64
+    oracle; the input arrives as an FP64 field, as in the solve."""
+    U, g, op, seed = _case(name, F32, coarse_tol=0.0, coarse_maxit=9, post_smooth=2)
+    tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+    tm.tm_setup_from_vectors(g.h, tv)
+    tl = _oracle_two_level(g, U, name)
+    tl.build_coarse(tv)
+    v = inputs.gaussian_spinor(g.L, seed + 31)
+    fv = g.pack(0, F32, v)
+    fz = g.field(0, F32)
+    tm.tm_kcycle(g.h, F32, fv, fz, 1)
+    assert rel(g.unpack(0, F32, fz, v.shape), tl.kcycle(v)) <= 1e-4
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coarse_solve_fp32_fixed_steps(name):
+    g, op, P, Dc, seed = _from_vectors(name, F32)
+    rng = np.random.default_rng(seed + 3)
+    b = rng.standard_normal(g.coarse_shape()) + 1j * rng.standard_normal(g.coarse_shape())
+    oe = OddEvenCoarse(Dc)
+    res = gmres(oe.schur, oe.reduced_rhs(b), tol=0.0, restart=g.p.coarse_restart, maxit=12)
+    fb = g.pack(1, F32, b)
+    fx = g.field(1, F32)
+    assert tm.tm_coarse_solve(g.h, F32, fb, fx, 0.0, 12) == 12
+    assert rel(g.unpack(1, F32, fx, b.shape), oe.reconstruct(b, res.x)) <= 1e-4
+
+
+def test_mixed_precision_cycle_iterations():
+    """FP32 cycle inside FP64 FGMRES needs about as many outer steps as the FP64 cycle."""
+    L = (8, 8, 8, 8)
+    U = inputs.gauge_field(L, 0.5, 5)
+    b = inputs.gaussian_spinor(L, 1005)
+    tv = inputs.random_test_vectors(L, 8, 2005)
+    iters = {}
+    for prec in (F64, F32):
+        g = GPU(U, m0=-0.4, c_sw=1.5, mu=0.005, delta=5.0, nv=8, agg=(4, 4, 4, 4),
+                sap_block=(4, 4, 4, 4), setup_iters=3, cycle_prec=prec)
+        tm.tm_setup(g.h, tv)
+        x = np.zeros_like(b)
+        st, info = tm.tm_solve(g.h, b, x, 1, 1e-10)
+        assert st == tm.TM_OK
+        iters[prec] = info.iters
+        g.close()
+    assert iters[F32] <= 1.25 * iters[F64] + 2, iters
