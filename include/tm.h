@@ -194,6 +194,29 @@ tm_status tm_prolong(tm_handle* h, int prec, const void* coarse, void* fine, int
  * cycle_prec).  *iters (may be NULL) receives the step count. */
 tm_status tm_coarse_solve(tm_handle* h, int prec, const void* b, void* x, double tol, int maxit, int* iters);
 
+/* Allocation-free variant of tm_coarse_solve (the paper has no counterpart;
+ * this is a library convenience).  Some callers cannot call cudaMalloc when
+ * they need a coarse solve, e.g. an application whose own memory pool has
+ * already taken the free device memory, or a latency-critical loop that must
+ * not pay for cudaMalloc's implicit synchronisation.  This call computes the
+ * same odd-even GMRES as tm_coarse_solve (same arguments, same result) but
+ * allocates nothing: every workspace lives in one fixed 8 MiB device array
+ * that the library holds on each GPU that loads it until the process exits.
+ * The handle's setup data (D_c, the odd-site inverses) must exist already.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress, with the device current) and caches it; make
+ *     that first call before any stream capture.  Call with the handle's
+ *     device current.
+ *   - Coarse systems whose Krylov basis (coarse_restart + 1 vectors), five
+ *     work vectors and reduction buffers exceed 8 MiB are rejected with
+ *     TM_ERR_ARG and a message giving the size needed.
+ *   - All calls share the array and it keeps the last call's contents; the
+ *     call zeroes the iterate it keeps there and writes everything else
+ *     before reading it.  Calls whose work overlaps on the GPU (other
+ *     threads, other streams) race on the array: serialise them. */
+tm_status tm_coarse_solve_noalloc(tm_handle* h, int prec, const void* b, void* x, double tol, int maxit,
+                                  int* iters);
+
 /* A7 preconditioner: z = B(v), one application of eq. (1) from a zero start
  * (pre SAP sweeps, coarse correction, post SAP sweeps).  Fine fields in
  * cycle_prec, nrhs vectors. */

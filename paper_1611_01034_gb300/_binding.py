@@ -63,6 +63,7 @@ _SIGS = {
     "tm_restrict": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "tm_prolong": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
     "tm_coarse_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, POINTER(c_int)]),
+    "tm_coarse_solve_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, POINTER(c_int)]),
     "tm_kcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "tm_export": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
     "tm_synchronize": (c_int, [c_void_p]),
@@ -214,6 +215,14 @@ def tm_prolong(h, prec, coarse, fine, nrhs, accumulate) -> None:
 def tm_coarse_solve(h, prec, b, x, tol, maxit) -> int:
     it = c_int(0)
     _check(lib().tm_coarse_solve(h, prec, _ptr(b), _ptr(x), tol, maxit, ctypes.byref(it)), h)
+    return it.value
+
+
+def tm_coarse_solve_noalloc(h, prec, b, x, tol, maxit) -> int:
+    """Same as tm_coarse_solve, with all workspaces in the library's fixed
+    8 MiB device array instead of device allocations (see include/tm.h)."""
+    it = c_int(0)
+    _check(lib().tm_coarse_solve_noalloc(h, prec, _ptr(b), _ptr(x), tol, maxit, ctypes.byref(it)), h)
     return it.value
 
 

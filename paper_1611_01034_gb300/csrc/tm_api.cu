@@ -13,6 +13,7 @@
 #include <cstring>
 #include <type_traits>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1211,3 +1212,206 @@ tm_status tm_profile_read(tm_handle* h, long long* launches, long long* units, d
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free coarse solve.
+//
+// Some callers cannot call cudaMalloc at the moment they need a coarse
+// solve: for example an application that hands all free device memory to its
+// own memory pool up front (so a raw cudaMalloc would fail or fragment that
+// pool), or a latency-critical loop that must not pay for cudaMalloc's
+// implicit device synchronisation.  tm_coarse_solve_noalloc serves them: it
+// runs the same odd-even GMRES as tm_coarse_solve, but every workspace
+// (Krylov basis, work vectors, reduction partial sums, small results) is
+// carved from one file-scope device array of fixed size that the library
+// holds on every GPU that loads it, until the process exits.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(8) << 20;  // 8 MiB per device
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char tm_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on the current device.  In host code the
+// symbol's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+void* noalloc_scratch() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) raise(TM_ERR_ARG, "device index beyond the supported range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, tm_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      raise(TM_ERR_CUDA, std::string("cudaGetSymbolAddress of the allocation-free scratch failed: ") +
+                             cudaGetErrorString(e));
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  return g_noalloc_ptr[dev];
+}
+
+size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+// scratch bytes the solve needs: (m + 1) basis vectors, five work vectors,
+// the reduction partials and the small result area
+size_t noalloc_bytes(const tm_handle* h, int prec, int m) {
+  const size_t vec = align256((size_t)h->nhalf * h->n * 2 * csize(prec));
+  return (size_t)(m + 1) * vec + 5 * vec + align256((size_t)kScratchBlocks * kMaxDots * 2 * sizeof(double)) +
+         align256((size_t)8 * kMaxDots * sizeof(double));
+}
+
+template <typename T>
+int coarse_solve_noalloc(tm_handle* h, const T* b, T* x, double tol, int maxit) {
+  using cd = std::complex<double>;
+  const int m = h->p.coarse_restart;
+  const long nc = (long)h->nhalf * h->n;  // complex numbers per parity vector
+  const size_t vec = align256((size_t)2 * nc * sizeof(T));
+  unsigned char* base = static_cast<unsigned char*>(noalloc_scratch());
+  T* Vb = reinterpret_cast<T*>(base);
+  unsigned char* q = base + (size_t)(m + 1) * vec;
+  T* to = reinterpret_cast<T*>(q);
+  T* bh = reinterpret_cast<T*>(q + vec);
+  T* xe = reinterpret_cast<T*>(q + 2 * vec);
+  T* uo = reinterpret_cast<T*>(q + 3 * vec);
+  T* w = reinterpret_cast<T*>(q + 4 * vec);
+  double* part = reinterpret_cast<double*>(q + 5 * vec);
+  double* small = reinterpret_cast<double*>(q + 5 * vec + align256((size_t)kScratchBlocks * kMaxDots * 2 * 8));
+  const long ld = vec / sizeof(T);
+  const T* Dc = static_cast<const T*>(h->Dc);
+  const T* Di = static_cast<const T*>(h->Dinv);
+  const double mc = mu_c(h);
+  // host-side Hessenberg state, per calling thread, sized for the largest restart
+  thread_local cd H[kMaxDots * kMaxDots], g[kMaxDots], sn[kMaxDots], y[kMaxDots], col[kMaxDots];
+  thread_local double cs[kMaxDots], hb[4 * kMaxDots + 2];
+  auto S = [&](const T* ve, T* ye) {
+    launch_oe_hop_inv<T>(Dc, Di, ve, uo, h->oe, h->st);
+    CKL();
+    launch_oe_even<T>(Dc, ve, uo, ye, h->oe, mc, 1, h->st);
+    CKL();
+  };
+  auto norm = [&](const T* v) {
+    launch_norm2<T>(v, nc, 1, small, part, kScratchBlocks, h->st);
+    CKL();
+    CK(cudaMemcpyAsync(hb, small, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return std::sqrt(hb[0]);
+  };
+  launch_oe_inv_odd<T>(Di, b, to, h->oe, h->st);
+  CKL();
+  launch_oe_rhs<T>(Dc, b, to, bh, h->oe, h->st);
+  CKL();
+  launch_zero<T>(xe, 2 * nc, h->st);  // the iterate must start at zero; the array keeps old contents
+  CKL();
+  const double bnorm = norm(bh);
+  if (!std::isfinite(bnorm)) raise(TM_ERR_NONFINITE, "non-finite right-hand side");
+  int iters = 0;
+  if (bnorm > 0) {
+    CK(cudaMemcpyAsync(Vb, bh, 2 * nc * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+    double beta = bnorm;
+    while (beta > tol * bnorm && iters < maxit) {
+      launch_caxpby<T>(1.0 / beta, 0, Vb, 0, 0, Vb, nc, h->st);
+      CKL();
+      for (int j = 0; j <= m; ++j) g[j] = 0;
+      g[0] = beta;
+      int k = 0;
+      while (k < m) {
+        S(Vb + (long)k * ld, w);
+        launch_multidot<T>(Vb, ld, k + 1, w, nc, small, part, kScratchBlocks, h->st);
+        CKL();
+        launch_multi_caxpy<T>(Vb, ld, k + 1, small, 1.0, w, nc, h->st);
+        CKL();
+        launch_multidot<T>(Vb, ld, k + 1, w, nc, small + 2 * kMaxDots, part, kScratchBlocks, h->st);
+        CKL();
+        launch_multi_caxpy<T>(Vb, ld, k + 1, small + 2 * kMaxDots, 1.0, w, nc, h->st);
+        CKL();
+        launch_norm2<T>(w, nc, 1, small + 4 * kMaxDots, part, kScratchBlocks, h->st);
+        CKL();
+        CK(cudaMemcpyAsync(Vb + (long)(k + 1) * ld, w, 2 * nc * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+        launch_scale<T>(Vb + (long)(k + 1) * ld, nc, 1, small + 4 * kMaxDots, true, h->st);
+        CKL();
+        CK(cudaMemcpyAsync(hb, small, (4 * kMaxDots + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        const double hn = std::sqrt(hb[4 * kMaxDots]);
+        if (!std::isfinite(hn)) raise(TM_ERR_NONFINITE, "non-finite Arnoldi vector");
+        for (int j = 0; j <= m; ++j) col[j] = 0;
+        for (int j = 0; j <= k; ++j)
+          col[j] = cd(hb[2 * j] + hb[2 * kMaxDots + 2 * j], hb[2 * j + 1] + hb[2 * kMaxDots + 2 * j + 1]);
+        col[k + 1] = hn;
+        for (int j = 0; j < k; ++j) {
+          const cd t = cs[j] * col[j] + sn[j] * col[j + 1];
+          col[j + 1] = -std::conj(sn[j]) * col[j] + cs[j] * col[j + 1];
+          col[j] = t;
+        }
+        double c;
+        cd s, rho;
+        givens(col[k], hn, c, s, rho);
+        cs[k] = c;
+        sn[k] = s;
+        col[k] = rho;
+        col[k + 1] = 0;
+        for (int j = 0; j <= m; ++j) H[(size_t)j * m + k] = col[j];
+        g[k + 1] = -std::conj(s) * g[k];
+        g[k] = c * g[k];
+        ++iters;
+        ++k;
+        if (hn == 0 || std::abs(g[k]) <= tol * bnorm || iters >= maxit) break;
+      }
+      for (int i = k - 1; i >= 0; --i) {
+        cd acc = g[i];
+        for (int j = i + 1; j < k; ++j) acc -= H[(size_t)i * m + j] * y[j];
+        y[i] = acc / H[(size_t)i * m + i];
+      }
+      for (int i = 0; i < k; ++i) {
+        hb[2 * i] = y[i].real();
+        hb[2 * i + 1] = y[i].imag();
+      }
+      double* dy = small + 6 * kMaxDots;
+      CK(cudaMemcpyAsync(dy, hb, 2 * k * sizeof(double), cudaMemcpyHostToDevice, h->st));
+      launch_lincomb<T, T>(Vb, ld, k, dy, xe, nc, h->st);
+      CKL();
+      // true residual of the reduced system
+      S(xe, w);
+      CK(cudaMemcpyAsync(Vb, bh, 2 * nc * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+      launch_caxpby<T>(-1, 0, w, 1, 0, Vb, nc, h->st);
+      CKL();
+      beta = norm(Vb);
+    }
+  }
+  launch_oe_reconstruct<T>(Dc, Di, b, xe, x, h->oe, h->st);
+  CKL();
+  CK(cudaStreamSynchronize(h->st));
+  return iters;
+}
+
+}  // namespace
+
+extern "C" tm_status tm_coarse_solve_noalloc(tm_handle* h, int prec, const void* b, void* x, double tol, int maxit,
+                                             int* iters) {
+  if (!h || !b || !x || maxit < 1 || tol < 0) return TM_ERR_ARG;
+  API_BEGIN
+  if (prec != TM_F64 && prec != TM_F32) raise(TM_ERR_ARG, "bad precision");
+  const size_t need = noalloc_bytes(h, prec, h->p.coarse_restart);
+  if (need > kNoAllocBytes)
+    raise(TM_ERR_ARG, "tm_coarse_solve_noalloc: this coarse system needs " + std::to_string(need) +
+                          " bytes of scratch, more than the fixed " + std::to_string(kNoAllocBytes) +
+                          " bytes (8 MiB) the allocation-free entry point holds; use tm_coarse_solve");
+  need_cycle_prec(h, prec);
+  int it;
+  if (prec == TM_F64)
+    it = coarse_solve_noalloc<double>(h, static_cast<const double*>(b), static_cast<double*>(x), tol, maxit);
+  else
+    it = coarse_solve_noalloc<float>(h, static_cast<const float*>(b), static_cast<float*>(x), tol, maxit);
+  if (iters) *iters = it;
+  API_END
+}
