@@ -6,11 +6,13 @@ writes ``inputs/m0_tuned.json``, the m0 values the synthetic workloads use.
 The workloads ask for "m0 fixed per seed so that the smallest singular value
 of D_W is about 1e-3" (the paper's ensembles are tuned to the physical point,
 Sec. 1; the synthetic stand-ins are not).  D_W(m0) = D_W(0) + m0, so its
-eigenvalues move rigidly with m0.  Reading used here: take the leftmost real
-eigenvalue lambda_r of D_W(0) (real eigenvalues come from Gamma5-hermiticity)
-and set m0 = target - lambda_r, so that D_W(m0) has the real eigenvalue
-``target``.  With v its eigenvector, sigma_min(D_W) <= ||D_W v|| / ||v|| =
-target, so the tuned operator is at least as close to singular as asked.
+eigenvalues move rigidly with m0.  Reading used here: find the eigenvalues
+of D_W(0) with the smallest real part and set m0 = target - Re(lambda_left),
+so that the spectrum of D_W(m0) just touches Re = target from the right (the
+onset of eigenvalues with negative real part, i.e. the critical edge).  With
+v the eigenvector of lambda_left, sigma_min(D_W) <= |lambda_left(m0)|; when the
+field has a real eigenvalue at its left edge this bound equals the target,
+otherwise it is the edge pair's modulus, which the output records.
 
 D_W(0) is assembled as a sparse matrix (the same conventions as
 :class:`oracle.dirac.Operator`, checked against it by
@@ -74,27 +76,27 @@ def sparse_dirac(U: np.ndarray, m0: float, c_sw: float, bc_t: float = -1.0) -> s
     return sp.csr_matrix((v, (r, c)), shape=(12 * V, 12 * V))
 
 
-def leftmost_real_eigenvalue(D: sp.spmatrix, k: int = 8, ncv: int = 80, tol: float = 1e-8,
-                             imag_tol: float = 1e-6, seed: int = 0):
-    """Eigenvalues of smallest real part (ARPACK), and the leftmost real one."""
+def leftmost_eigenvalues(D: sp.spmatrix, k: int = 16, ncv: int = 120, tol: float = 1e-7,
+                         seed: int = 0) -> np.ndarray:
+    """The k eigenvalues of smallest real part (ARPACK), sorted by real part."""
     rng = np.random.default_rng(seed)
     v0 = rng.standard_normal(D.shape[0]) + 1j * rng.standard_normal(D.shape[0])
     ev = spla.eigs(D, k=k, which="SR", ncv=ncv, tol=tol, v0=v0, return_eigenvectors=False,
                    maxiter=100000)
-    ev = ev[np.argsort(ev.real)]
-    real = ev[np.abs(ev.imag) < imag_tol]
-    lam = float(real[0].real) if real.size else None
-    return lam, ev
+    return ev[np.argsort(ev.real)]
 
 
-def tune_m0(U: np.ndarray, c_sw: float, target: float = 1e-3, bc_t: float = -1.0) -> dict:
+def tune_m0(U: np.ndarray, c_sw: float, target: float = 1e-3, bc_t: float = -1.0, **kw) -> dict:
     D0 = sparse_dirac(U, 0.0, c_sw, bc_t)
     t0 = time.time()
-    lam, ev = leftmost_real_eigenvalue(D0)
-    if lam is None:
-        raise RuntimeError("no real eigenvalue among the leftmost ones; raise k")
-    return {"m0": target - lam, "lambda_r": lam, "target": target,
-            "leftmost": [[float(e.real), float(e.imag)] for e in ev],
+    ev = leftmost_eigenvalues(D0, **kw)
+    lam = ev[0]
+    real = ev[np.abs(ev.imag) < 1e-6]
+    m0 = target - float(lam.real)
+    return {"m0": m0, "lambda_left": [float(lam.real), float(lam.imag)],
+            "sigma_min_bound": float(abs(complex(target, lam.imag))),
+            "real_eigenvalue_at_edge": bool(real.size and abs(real[0].real - lam.real) < 1e-6),
+            "target": target, "leftmost": [[float(e.real), float(e.imag)] for e in ev],
             "seconds": time.time() - t0}
 
 
