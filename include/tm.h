@@ -230,14 +230,15 @@ tm_status tm_export(tm_handle* h, int what, double* out, size_t bytes);
  * kernel errors. */
 tm_status tm_synchronize(tm_handle* h);
 
-/* Opt-in per-kernel timing.  With enable = 1 every kernel launch the handle
- * makes is bracketed by a pair of CUDA events recorded on its stream and
- * attributed to one of tm_profile_kinds() classes (named by
- * tm_profile_name: dslash_f64, dslash_f32, sap, restrict, prolong,
- * coarse_oe, blas_fine, blas_coarse, coarse_build, other).  tm_profile
- * resets the totals; tm_profile_read waits for the stream and copies, per
- * class, the number of launches, the number of right-hand-side units they
- * processed and the summed event time in milliseconds (arrays of n; any may
+/* Opt-in per-kernel accounting.  Kernel launches fall into
+ * tm_profile_kinds() classes (named by tm_profile_name: dslash_f64,
+ * dslash_f32, sap, restrict, prolong, coarse_oe, blas_fine, blas_coarse,
+ * coarse_build, other).  With enable != 0 every launch is counted (launches
+ * and right-hand-side units) and the launches of class k are also bracketed
+ * by a pair of CUDA events on the handle's stream when bit k of enable is set
+ * (enable = -1 times every class).  tm_profile resets the totals;
+ * tm_profile_read waits for the stream and copies, per class, the launches,
+ * the units and the summed event time in milliseconds (arrays of n; any may
  * be NULL).  Not part of the method: measurement only. */
 tm_status tm_profile(tm_handle* h, int enable);
 int tm_profile_kinds(void);

@@ -238,8 +238,10 @@ def tm_synchronize(h) -> None:
     _check(lib().tm_synchronize(h), h)
 
 
-def tm_profile(h, enable: bool) -> None:
-    _check(lib().tm_profile(h, int(enable)), h)
+def tm_profile(h, enable) -> None:
+    """enable: False/0 off, True/-1 time every class, or a bit mask of classes to time."""
+    mask = -1 if enable is True else int(enable)
+    _check(lib().tm_profile(h, mask), h)
 
 
 def tm_profile_kinds() -> int:

@@ -2,8 +2,10 @@
 // GMRES on the coarsest level): casts, axpby, linear combinations, and
 // inner products reduced deterministically in two stages (per-CTA partial
 // sums into a scratch array, then one CTA per result in fixed order).
-// Vectors are flat arrays of complex numbers stored as (re, im) pairs; the
-// inner products accumulate in FP64 whatever the storage precision.
+// Vectors are flat arrays of complex numbers stored as (re, im) pairs.  Inner
+// products accumulate in the storage precision within a CTA (FP32 sums for
+// FP32 fields: FP64 arithmetic is a small fraction of FP32 throughput on this
+// GPU) and combine the per-CTA partial sums in FP64.
 #include "tm_kernels.h"
 
 namespace tmamg {
@@ -52,9 +54,9 @@ void launch_caxpby(double ar, double ai, const T* x, double br, double bi, T* y,
 template <typename T>
 __global__ void k_multidot_partial(const T* __restrict__ X, long ldx, int k, const T* __restrict__ y, long ncx,
                                    double* __restrict__ part) {
-  __shared__ double red[32 * 16];
+  __shared__ T red[32 * 16];
   const int j0 = blockIdx.y * 8;
-  double d[16];
+  T d[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) d[m] = 0;
   const cx<T>* yy = reinterpret_cast<const cx<T>*>(y);
@@ -64,15 +66,15 @@ __global__ void k_multidot_partial(const T* __restrict__ X, long ldx, int k, con
     for (int jj = 0; jj < 8; ++jj) {
       if (j0 + jj < k) {
         const cx<T> xv = reinterpret_cast<const cx<T>*>(X + (long)(j0 + jj) * ldx)[i];
-        d[2 * jj] += (double)xv.r * yv.r + (double)xv.i * yv.i;
-        d[2 * jj + 1] += (double)xv.r * yv.i - (double)xv.i * yv.r;
+        d[2 * jj] += xv.r * yv.r + xv.i * yv.i;
+        d[2 * jj + 1] += xv.r * yv.i - xv.i * yv.r;
       }
     }
   }
-  block_allreduce<double, 16>(d, red);
+  block_allreduce<T, 16>(d, red);
   if (threadIdx.x < 16) {
     const int jj = threadIdx.x >> 1;
-    if (j0 + jj < k) part[((long)(j0 + jj) * gridDim.x + blockIdx.x) * 2 + (threadIdx.x & 1)] = d[threadIdx.x];
+    if (j0 + jj < k) part[((long)(j0 + jj) * gridDim.x + blockIdx.x) * 2 + (threadIdx.x & 1)] = (double)d[threadIdx.x];
   }
 }
 
@@ -105,16 +107,16 @@ void launch_multidot(const T* X, long ldx, int k, const T* y, long ncx, double* 
 // ---- norms of nrhs vectors ----------------------------------------------------
 template <typename T>
 __global__ void k_norm2_partial(const T* __restrict__ x, long ncx, double* __restrict__ part) {
-  __shared__ double red[32 * 2];
+  __shared__ T red[32 * 2];
   const int r = blockIdx.y;
   const cx<T>* xx = reinterpret_cast<const cx<T>*>(x) + (long)r * ncx;
-  double d[2] = {0, 0};
+  T d[2] = {0, 0};
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
     const cx<T> v = xx[i];
-    d[0] += (double)v.r * v.r + (double)v.i * v.i;
+    d[0] += v.r * v.r + v.i * v.i;
   }
-  block_allreduce<double, 2>(d, red);
-  if (threadIdx.x < 2) part[((long)r * gridDim.x + blockIdx.x) * 2 + threadIdx.x] = d[threadIdx.x];
+  block_allreduce<T, 2>(d, red);
+  if (threadIdx.x < 2) part[((long)r * gridDim.x + blockIdx.x) * 2 + threadIdx.x] = (double)d[threadIdx.x];
 }
 
 __global__ void k_reduce_norm(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
@@ -194,6 +196,215 @@ void launch_scale(T* x, long ncx, int nrhs, const double* s, bool inv_sqrt, cuda
   dim3 grid(grid_for(2 * ncx), nrhs);
   k_scale<T><<<grid, 256, 0, st>>>(x, ncx, s, inv_sqrt ? 1 : 0);
 }
+
+// ===========================================================================
+// batched variants over right-hand sides (blockIdx.y or .z = rhs); each rhs
+// uses the same grid decomposition as the single-rhs kernels above, so the
+// per-rhs arithmetic is the same; masked (finished) right-hand sides skip.
+// ===========================================================================
+static inline int dot_grid(long ncx) {
+  int G = grid_for(ncx);
+  return G > kReduceBlocks ? kReduceBlocks : G;
+}
+
+long multidot_scratch_doubles(long ncx, int k, int nrhs) { return 2L * dot_grid(ncx) * k * nrhs; }
+
+template <typename T>
+__global__ void k_multidot_partial_b(const T* __restrict__ X, long xstr, long ldx, int k, const T* __restrict__ y,
+                                     long ystr, long ncx, double* __restrict__ part, const int* __restrict__ active) {
+  __shared__ T red[32 * 16];
+  const int r = blockIdx.z;
+  if (active && !active[r]) return;
+  const int j0 = blockIdx.y * 8;
+  T d[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) d[m] = 0;
+  const cx<T>* yy = reinterpret_cast<const cx<T>*>(y + r * ystr);
+  const T* Xr = X + r * xstr;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
+    const cx<T> yv = yy[i];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      if (j0 + jj < k) {
+        const cx<T> xv = reinterpret_cast<const cx<T>*>(Xr + (long)(j0 + jj) * ldx)[i];
+        d[2 * jj] += xv.r * yv.r + xv.i * yv.i;
+        d[2 * jj + 1] += xv.r * yv.i - xv.i * yv.r;
+      }
+    }
+  }
+  block_allreduce<T, 16>(d, red);
+  if (threadIdx.x < 16) {
+    const int jj = threadIdx.x >> 1;
+    if (j0 + jj < k)
+      part[(((long)r * k + j0 + jj) * gridDim.x + blockIdx.x) * 2 + (threadIdx.x & 1)] = (double)d[threadIdx.x];
+  }
+}
+
+__global__ void k_reduce_partials_b(const double* __restrict__ part, int nblocks, int k, double* __restrict__ out,
+                                    long ostr, const int* __restrict__ active) {
+  __shared__ double red[32 * 2];
+  const int j = blockIdx.x, r = blockIdx.y;
+  if (active && !active[r]) return;
+  double d[2] = {0, 0};
+  const double* p = part + ((long)r * k + j) * nblocks * 2;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    d[0] += p[2 * b];
+    d[1] += p[2 * b + 1];
+  }
+  block_allreduce<double, 2>(d, red);
+  if (threadIdx.x == 0) {
+    out[r * ostr + 2 * j] = d[0];
+    out[r * ostr + 2 * j + 1] = d[1];
+  }
+}
+
+template <typename T>
+void launch_multidot_b(const T* X, long xstr, long ldx, int k, const T* y, long ystr, long ncx, double* out, long ostr,
+                       double* scratch, int nrhs, const int* active, cudaStream_t st) {
+  const int G = dot_grid(ncx);
+  dim3 grid(G, (k + 7) / 8, nrhs);
+  k_multidot_partial_b<T><<<grid, 256, 0, st>>>(X, xstr, ldx, k, y, ystr, ncx, scratch, active);
+  dim3 g2(k, nrhs);
+  k_reduce_partials_b<<<g2, 256, 0, st>>>(scratch, G, k, out, ostr, active);
+}
+
+template <typename T>
+__global__ void k_norm2_partial_b(const T* __restrict__ y, long ystr, long ncx, double* __restrict__ part,
+                                  const int* __restrict__ active) {
+  __shared__ T red[32 * 2];
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const cx<T>* yy = reinterpret_cast<const cx<T>*>(y + r * ystr);
+  T d[2] = {0, 0};
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
+    const cx<T> v = yy[i];
+    d[0] += v.r * v.r + v.i * v.i;
+  }
+  block_allreduce<T, 2>(d, red);
+  if (threadIdx.x < 2) part[((long)r * gridDim.x + blockIdx.x) * 2 + threadIdx.x] = (double)d[threadIdx.x];
+}
+
+__global__ void k_reduce_norm_b(const double* __restrict__ part, int nblocks, double* __restrict__ out,
+                                const int* __restrict__ active) {
+  __shared__ double red[32];
+  const int r = blockIdx.x;
+  if (active && !active[r]) return;
+  double d[1] = {0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) d[0] += part[((long)r * nblocks + b) * 2];
+  block_allreduce<double, 1>(d, red);
+  if (threadIdx.x == 0) out[r] = d[0];
+}
+
+template <typename T>
+void launch_norm2_b(const T* y, long ystr, long ncx, double* out, double* scratch, int nrhs, const int* active,
+                    cudaStream_t st) {
+  const int G = dot_grid(ncx);
+  dim3 grid(G, nrhs);
+  k_norm2_partial_b<T><<<grid, 256, 0, st>>>(y, ystr, ncx, scratch, active);
+  k_reduce_norm_b<<<nrhs, 256, 0, st>>>(scratch, G, out, active);
+}
+
+template <typename T>
+__global__ void k_multi_caxpy_b(const T* __restrict__ X, long xstr, long ldx, int k, const double* __restrict__ c,
+                                long cstr, T* __restrict__ y, long ystr, long ncx, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  cx<T>* yy = reinterpret_cast<cx<T>*>(y + r * ystr);
+  const T* Xr = X + r * xstr;
+  const double* cr = c + r * cstr;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
+    cx<T> acc = yy[i];
+    for (int j = 0; j < k; ++j) {
+      const cx<T> cj{(T)cr[2 * j], (T)cr[2 * j + 1]};
+      acc = acc - cj * reinterpret_cast<const cx<T>*>(Xr + (long)j * ldx)[i];
+    }
+    yy[i] = acc;
+  }
+}
+template <typename T>
+void launch_multi_caxpy_b(const T* X, long xstr, long ldx, int k, const double* c, long cstr, T* y, long ystr, long ncx,
+                          int nrhs, const int* active, cudaStream_t st) {
+  dim3 grid(grid_for(ncx), nrhs);
+  k_multi_caxpy_b<T><<<grid, 256, 0, st>>>(X, xstr, ldx, k, c, cstr, y, ystr, ncx, active);
+}
+
+template <typename T>
+__global__ void k_lincomb_b(const T* __restrict__ X, long xstr, long ldx, int k, const double* __restrict__ c,
+                            long cstr, T* __restrict__ y, long ystr, long ncx, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  if (active) k = min(k, active[r]);  // active[r] = number of terms for rhs r
+  cx<T>* yy = reinterpret_cast<cx<T>*>(y + r * ystr);
+  const T* Xr = X + r * xstr;
+  const double* cr = c + r * cstr;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
+    cx<T> acc = yy[i];
+    for (int j = 0; j < k; ++j) {
+      const cx<T> cj{(T)cr[2 * j], (T)cr[2 * j + 1]};
+      cfma(acc, cj, reinterpret_cast<const cx<T>*>(Xr + (long)j * ldx)[i]);
+    }
+    yy[i] = acc;
+  }
+}
+template <typename T>
+void launch_lincomb_b(const T* X, long xstr, long ldx, int k, const double* c, long cstr, T* y, long ystr, long ncx,
+                      int nrhs, const int* active, cudaStream_t st) {
+  dim3 grid(grid_for(ncx), nrhs);
+  k_lincomb_b<T><<<grid, 256, 0, st>>>(X, xstr, ldx, k, c, cstr, y, ystr, ncx, active);
+}
+
+template <typename T>
+__global__ void k_scale_copy_b(const T* __restrict__ src, long sstr, T* __restrict__ dst, long dstr,
+                               const double* __restrict__ s, long ncx, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  T f = T(1);
+  if (s) {
+    const double sc = s[r];
+    f = (T)(sc > 0 ? 1.0 / sqrt(sc) : 0.0);
+  }
+  const T* a = src + r * sstr;
+  T* b = dst + r * dstr;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * ncx; i += (long)gridDim.x * blockDim.x)
+    b[i] = s ? a[i] * f : a[i];
+}
+template <typename T>
+void launch_scale_copy_b(const T* src, long sstr, T* dst, long dstr, const double* s, long ncx, int nrhs,
+                         const int* active, cudaStream_t st) {
+  dim3 grid(grid_for(2 * ncx), nrhs);
+  k_scale_copy_b<T><<<grid, 256, 0, st>>>(src, sstr, dst, dstr, s, ncx, active);
+}
+
+template <typename T>
+__global__ void k_sub_b(const T* __restrict__ x, long xstr, T* __restrict__ y, long ystr, long ncx,
+                        const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const T* a = x + r * xstr;
+  T* b = y + r * ystr;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * ncx; i += (long)gridDim.x * blockDim.x)
+    b[i] = a[i] - b[i];
+}
+template <typename T>
+void launch_sub_b(const T* x, long xstr, T* y, long ystr, long ncx, int nrhs, const int* active, cudaStream_t st) {
+  dim3 grid(grid_for(2 * ncx), nrhs);
+  k_sub_b<T><<<grid, 256, 0, st>>>(x, xstr, y, ystr, ncx, active);
+}
+
+#define TM_INST_B(T)                                                                                              \
+  template void launch_multidot_b<T>(const T*, long, long, int, const T*, long, long, double*, long, double*, int, \
+                                     const int*, cudaStream_t);                                                   \
+  template void launch_multi_caxpy_b<T>(const T*, long, long, int, const double*, long, T*, long, long, int,      \
+                                        const int*, cudaStream_t);                                                \
+  template void launch_lincomb_b<T>(const T*, long, long, int, const double*, long, T*, long, long, int,          \
+                                    const int*, cudaStream_t);                                                    \
+  template void launch_norm2_b<T>(const T*, long, long, double*, double*, int, const int*, cudaStream_t);         \
+  template void launch_scale_copy_b<T>(const T*, long, T*, long, const double*, long, int, const int*,            \
+                                       cudaStream_t);                                                             \
+  template void launch_sub_b<T>(const T*, long, T*, long, long, int, const int*, cudaStream_t);
+TM_INST_B(double)
+TM_INST_B(float)
+#undef TM_INST_B
 
 #define TM_INST(T)                                                                                    \
   template void launch_zero<T>(T*, long, cudaStream_t);                                               \

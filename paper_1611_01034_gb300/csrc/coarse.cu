@@ -44,7 +44,7 @@ __device__ __forceinline__ int coarse_of(const AggGeom& ag, const int c[4]) {
 // ===========================================================================
 template <typename T>
 __global__ void k_orthonormalise(T* P, AggGeom ag, int* err) {
-  __shared__ double red[32 * 16];
+  __shared__ T red[32 * 16];
   const int a = blockIdx.x, chi = blockIdx.y, nv = ag.nv;
   const int l = threadIdx.x;
   const bool act = l < ag.asites;
@@ -53,49 +53,51 @@ __global__ void k_orthonormalise(T* P, AggGeom ag, int* err) {
   const long V = ag.g.V;
   const long fstride = (long)NR_SPINOR * V;
   const long choff = 12L * chi * V;  // chunk offset of this chirality's 6 complex numbers
+  // squared-norm ratio below which a column counts as linearly dependent
+  const T rank_tol = sizeof(T) == 8 ? T(1e-24) : T(1e-10);
   for (int j = 0; j < nv; ++j) {
     cx<T> v[6];
     if (act) ld_cx<T, 6>(P + j * fstride + choff, V, s, v);
     else
       for (int k = 0; k < 6; ++k) v[k] = cx<T>{0, 0};
-    double t0[1] = {0};
-    for (int k = 0; k < 6; ++k) t0[0] += (double)norm2(v[k]);
-    block_allreduce<double, 1>(t0, red);
-    const double n0 = t0[0];
+    T t0[1] = {0};
+    for (int k = 0; k < 6; ++k) t0[0] += norm2(v[k]);
+    block_allreduce<T, 1>(t0, red);
+    const T n0 = t0[0];
     for (int pass = 0; pass < 2; ++pass) {
       for (int i0 = 0; i0 < j; i0 += 8) {
-        double d[16];
+        T d[16];
         for (int m = 0; m < 16; ++m) d[m] = 0;
         if (act) {
           for (int ii = 0; ii < 8 && i0 + ii < j; ++ii) {
             cx<T> q[6];
             ld_cx<T, 6>(P + (i0 + ii) * fstride + choff, V, s, q);
-            for (int k = 0; k < 6; ++k) {
-              d[2 * ii] += (double)q[k].r * v[k].r + (double)q[k].i * v[k].i;
-              d[2 * ii + 1] += (double)q[k].r * v[k].i - (double)q[k].i * v[k].r;
-            }
+            cx<T> acc{0, 0};
+            for (int k = 0; k < 6; ++k) cfmac(acc, q[k], v[k]);
+            d[2 * ii] = acc.r;
+            d[2 * ii + 1] = acc.i;
           }
         }
-        block_allreduce<double, 16>(d, red);
+        block_allreduce<T, 16>(d, red);
         if (act) {
           for (int ii = 0; ii < 8 && i0 + ii < j; ++ii) {
             cx<T> q[6];
             ld_cx<T, 6>(P + (i0 + ii) * fstride + choff, V, s, q);
-            const cx<T> cc{(T)d[2 * ii], (T)d[2 * ii + 1]};
+            const cx<T> cc{d[2 * ii], d[2 * ii + 1]};
             for (int k = 0; k < 6; ++k) v[k] = v[k] - cc * q[k];
           }
         }
       }
     }
-    double t1[1] = {0};
-    for (int k = 0; k < 6; ++k) t1[0] += (double)norm2(v[k]);
-    block_allreduce<double, 1>(t1, red);
-    double nn = t1[0];
-    if (!(nn > 1e-24 * n0) || !(nn > 0)) {
+    T t1[1] = {0};
+    for (int k = 0; k < 6; ++k) t1[0] += norm2(v[k]);
+    block_allreduce<T, 1>(t1, red);
+    T nn = t1[0];
+    if (!(nn > rank_tol * n0) || !(nn > T(0))) {
       if (l == 0) atomicOr(err, ERRF_RANK);
-      nn = 1;
+      nn = T(1);
     }
-    const T inv = (T)(1.0 / sqrt(nn));
+    const T inv = T(1) / sqrt(nn);
     if (act) {
       for (int k = 0; k < 6; ++k) v[k] = inv * v[k];
       st_cx<T, 6>(P + j * fstride + choff, V, s, v);
@@ -245,69 +247,125 @@ __device__ __forceinline__ void build_hops(const T* __restrict__ P, const T* __r
   }
 }
 
+// operator column k = chi * Nv + j of block t applied at fine site s of
+// aggregate a: u = [D restricted to block t] (P_j masked to chirality chi)
 template <typename T>
-__global__ void k_coarse_build(const T* __restrict__ gauge, const T* __restrict__ clover, const T* __restrict__ P,
-                               T* __restrict__ Dc, AggGeom ag, T bc) {
-  __shared__ T red[32 * 16];
-  const int nv = ag.nv, n = 2 * nv;
-  const int kk = blockIdx.x, t = blockIdx.y, a = blockIdx.z;
-  const int chi = kk / nv, j = kk % nv;
-  const int l = threadIdx.x;
-  const bool act = l < ag.asites;
-  int lc[4], c[4];
-  const int s = act ? agg_site(ag, a, l, lc, c) : 0;
-  const long V = ag.g.V;
-  cx<T> u[12];
+__device__ __forceinline__ void column_op(const T* __restrict__ gauge, const T* __restrict__ clover,
+                                          const T* __restrict__ P, const AggGeom& ag, int s, const int c[4],
+                                          const int lc[4], int j, int chi, int t, T bc, cx<T> (&u)[12]) {
+  cx<T> acc[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) u[k] = cx<T>{0, 0};
+  for (int q = 0; q < 12; ++q) acc[q] = cx<T>{0, 0};
   bool on = false;
-  if (act) {
-    cx<T> acc[12];
+  build_hops<T, 0>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
+  build_hops<T, 1>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
+  build_hops<T, 2>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
+  build_hops<T, 3>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
+  if (t == 0) {
+    cx<T> p[12];
+    src_column<T>(P, ag.g.V, s, j, chi, p);
+    site_diag<T>(clover, ag.g.V, s, T(0), p, u);
+  } else {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = cx<T>{0, 0};
-    build_hops<T, 0>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
-    build_hops<T, 1>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
-    build_hops<T, 2>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
-    build_hops<T, 3>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
-    if (t == 0) {
-      cx<T> p[12];
-      src_column<T>(P, V, s, j, chi, p);
-      site_diag<T>(clover, (int)V, s, T(0), p, u);
-      on = true;
-    }
-#pragma unroll
-    for (int k = 0; k < 12; ++k) u[k] = u[k] - T(0.5) * acc[k];
+    for (int q = 0; q < 12; ++q) u[q] = cx<T>{0, 0};
   }
-  T* out = Dc + (((long)a * 9 + t) * n + kk) * n * 2;  // column kk of block t, [row] complex
-  for (int i0 = 0; i0 < nv; i0 += 4) {
-    T d[16];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) d[m] = 0;
-    if (act && on) {
+  for (int q = 0; q < 12; ++q) u[q] = u[q] - T(0.5) * acc[q];
+}
+
+// local site index within the aggregate of the f-th site that block t visits
+// (all sites for t = 0, the sites of the crossed face otherwise)
+__device__ __forceinline__ int block_site(const AggGeom& ag, int t, int f) {
+  if (t == 0) return f;
+  const int mu = (t - 1) >> 1;
+  const int fixed = ((t - 1) & 1) ? 0 : ag.agg[mu] - 1;
+  int lc[4], q = f;
 #pragma unroll
-      for (int ii = 0; ii < 4; ++ii) {
-        if (i0 + ii < nv) {
-          cx<T> p[12];
-          ld_cx<T, 12>(P + (long)(i0 + ii) * NR_SPINOR * V, V, s, p);
+  for (int d = 3; d >= 0; --d) {
+    if (d == mu) {
+      lc[d] = fixed;
+    } else {
+      lc[d] = q % ag.agg[d];
+      q /= ag.agg[d];
+    }
+  }
+  return ((lc[0] * ag.agg[1] + lc[1]) * ag.agg[2] + lc[2]) * ag.agg[3] + lc[3];
+}
+
+constexpr int kBuildThreads = 256;
+constexpr int kBuildOut = 13;  // outputs per thread: (2 Nv)^2 <= 13 * 256 for Nv <= 28
+
+// D_c(a, t) = P_a^dagger U_t, U_t = the 2 Nv operator columns of block t.
+// One CTA per (t, a); the visited sites are processed in tiles of TS sites
+// whose P values and U columns are staged in shared memory as
+//   Ps[(l * 12 + comp) * Nv + i],  Us[(l * 12 + comp) * 2Nv + k],
+// then every thread accumulates its fixed outputs (row, col) in registers.
+template <typename T>
+__global__ void __launch_bounds__(kBuildThreads) k_coarse_build(const T* __restrict__ gauge,
+                                                                const T* __restrict__ clover,
+                                                                const T* __restrict__ P, T* __restrict__ Dc,
+                                                                AggGeom ag, T bc, int TS) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nv = ag.nv, n = 2 * nv;
+  cx<T>* Ps = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* Us = Ps + (size_t)TS * 12 * nv;
+  const int t = blockIdx.x, a = blockIdx.y;
+  const int nsites = t == 0 ? ag.asites : ag.asites / ag.agg[(t - 1) >> 1];
+  const long V = ag.g.V;
+  cx<T> acc[kBuildOut];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            cx<T> acc{0, 0};
+  for (int m = 0; m < kBuildOut; ++m) acc[m] = cx<T>{0, 0};
+
+  for (int f0 = 0; f0 < nsites; f0 += TS) {
+    const int ts = min(TS, nsites - f0);
+    // stage P_i at the tile's sites
+    for (int e = threadIdx.x; e < ts * nv; e += blockDim.x) {
+      const int l = e / nv, i = e % nv;
+      int lc[4], c[4];
+      const int s = agg_site(ag, a, block_site(ag, t, f0 + l), lc, c);
+      cx<T> p[12];
+      ld_cx<T, 12>(P + (long)i * NR_SPINOR * V, V, s, p);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) cfmac(acc, p[6 * h + k], u[6 * h + k]);
-            d[4 * ii + 2 * h] = acc.r;
-            d[4 * ii + 2 * h + 1] = acc.i;
+      for (int q = 0; q < 12; ++q) Ps[((size_t)l * 12 + q) * nv + i] = p[q];
+    }
+    // operator columns at the tile's sites
+    for (int e = threadIdx.x; e < ts * n; e += blockDim.x) {
+      const int l = e / n, k = e % n;
+      int lc[4], c[4];
+      const int s = agg_site(ag, a, block_site(ag, t, f0 + l), lc, c);
+      cx<T> u[12];
+      column_op<T>(gauge, clover, P, ag, s, c, lc, k % nv, k / nv, t, bc, u);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) Us[((size_t)l * 12 + q) * n + k] = u[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < kBuildOut; ++m) {
+      const int o = threadIdx.x + m * kBuildThreads;
+      if (o < n * n) {
+        const int row = o / n, k = o % n;
+        const int chi = row / nv, i = row % nv;
+        cx<T> sum = acc[m];
+        for (int l = 0; l < ts; ++l) {
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            const size_t b = (size_t)l * 12 + 6 * chi + q;
+            cfmac(sum, Ps[b * nv + i], Us[b * n + k]);
           }
         }
+        acc[m] = sum;
       }
     }
-    block_allreduce<T, 16>(d, red);
-    if (l < 8) {
-      const int ii = l >> 1, h = l & 1;
-      if (i0 + ii < nv) {
-        const int row = h * nv + i0 + ii;
-        out[2 * row] = d[4 * ii + 2 * h];
-        out[2 * row + 1] = d[4 * ii + 2 * h + 1];
-      }
+    __syncthreads();
+  }
+  T* out = Dc + ((long)a * 9 + t) * n * n * 2;
+#pragma unroll
+  for (int m = 0; m < kBuildOut; ++m) {
+    const int o = threadIdx.x + m * kBuildThreads;
+    if (o < n * n) {
+      const int row = o / n, k = o % n;
+      out[2 * ((long)k * n + row)] = acc[m].r;
+      out[2 * ((long)k * n + row) + 1] = acc[m].i;
     }
   }
 }
@@ -315,9 +373,19 @@ __global__ void k_coarse_build(const T* __restrict__ gauge, const T* __restrict_
 template <typename T>
 void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, const AggGeom& ag, double bc_t,
                          cudaStream_t st) {
-  const int threads = (ag.asites + 31) / 32 * 32;
-  dim3 grid(2 * ag.nv, 9, ag.gc.V);
-  k_coarse_build<T><<<grid, threads, 0, st>>>(gauge, clover, P, Dc, ag, (T)bc_t);
+  const int nv = ag.nv;
+  const size_t per_site = (size_t)12 * 3 * nv * sizeof(cx<T>);  // Ps + Us per site
+  const size_t budget = 200 * 1024;
+  int TS = (int)(budget / per_site);
+  if (TS > 32) TS = 32;
+  if (TS < 1) TS = 1;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_coarse_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  dim3 grid(9, ag.gc.V);
+  k_coarse_build<T><<<grid, kBuildThreads, TS * per_site, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
 }
 
 // ===========================================================================
@@ -479,6 +547,10 @@ struct OEArgs {
   int odd;        // target parity
   int post;       // multiply by Dinv (odd targets only)
   int full_out;   // write into a full coarse vector at the site
+  // batch over right-hand sides (blockIdx.y): per-rhs strides in reals and an
+  // optional mask of active right-hand sides
+  long s_str, p_str, o_str;
+  const int* active;
 };
 
 template <typename T>
@@ -487,7 +559,11 @@ __global__ void k_oe_stencil(OEArgs<T> a) {
   const int nv = a.oe.nv, n = 2 * nv;
   cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);  // [9][n]
   cx<T>* accs = part + 9 * n;                          // [n]
-  const int k = blockIdx.x;
+  const int k = blockIdx.x, rb = blockIdx.y;
+  if (a.active && !a.active[rb]) return;  // uniform over the CTA
+  a.src += rb * a.s_str;
+  a.pre += rb * a.p_str;
+  a.out += rb * a.o_str;
   const int site = a.odd ? a.oe.odd_site[k] : a.oe.even_site[k];
   const int row = threadIdx.x % n, t = threadIdx.x / n;
   const cx<T>* B = reinterpret_cast<const cx<T>*>(a.Dc) + (long)site * 9 * n * n;
@@ -537,26 +613,27 @@ __global__ void k_oe_stencil(OEArgs<T> a) {
 }
 
 template <typename T>
-static void launch_oe_stencil(const OEArgs<T>& a, cudaStream_t st) {
+static void launch_oe_stencil(const OEArgs<T>& a, cudaStream_t st, int nrhs = 1) {
   const int n = 2 * a.oe.nv;
   const int threads = (9 * n + 31) / 32 * 32;
-  k_oe_stencil<T><<<a.oe.nhalf, threads, 10 * n * sizeof(cx<T>), st>>>(a);
+  dim3 grid(a.oe.nhalf, nrhs);
+  k_oe_stencil<T><<<grid, threads, 10 * n * sizeof(cx<T>), st>>>(a);
 }
 
 template <typename T>
 void launch_oe_hop_inv(const T* Dc, const T* Dinv, const T* ve, T* uo, const OEGeom& oe, cudaStream_t st) {
-  OEArgs<T> a{Dc, Dinv, ve, nullptr, uo, oe, T(0), T(1), 0, 1, 1, 0};
+  OEArgs<T> a{Dc, Dinv, ve, nullptr, uo, oe, T(0), T(1), 0, 1, 1, 0, 0, 0, 0, nullptr};
   launch_oe_stencil(a, st);
 }
 template <typename T>
 void launch_oe_even(const T* Dc, const T* ve, const T* uo, T* ye, const OEGeom& oe, double mu_c, int diag,
                     cudaStream_t st) {
-  OEArgs<T> a{Dc, nullptr, uo, ve, ye, oe, (T)mu_c, T(-1), diag ? 1 : 0, 0, 0, 0};
+  OEArgs<T> a{Dc, nullptr, uo, ve, ye, oe, (T)mu_c, T(-1), diag ? 1 : 0, 0, 0, 0, 0, 0, 0, nullptr};
   launch_oe_stencil(a, st);
 }
 template <typename T>
 void launch_oe_rhs(const T* Dc, const T* b, const T* to, T* bh, const OEGeom& oe, cudaStream_t st) {
-  OEArgs<T> a{Dc, nullptr, to, b, bh, oe, T(0), T(-1), 2, 0, 0, 0};
+  OEArgs<T> a{Dc, nullptr, to, b, bh, oe, T(0), T(-1), 2, 0, 0, 0, 0, 0, 0, nullptr};
   launch_oe_stencil(a, st);
 }
 
@@ -596,9 +673,76 @@ void launch_oe_reconstruct(const T* Dc, const T* Dinv, const T* b, const T* xe, 
   const int n = 2 * oe.nv;
   const long tot = (long)oe.nhalf * n;
   k_oe_scatter_even<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(xe, x, oe);
-  OEArgs<T> a{Dc, Dinv, xe, b, x, oe, T(0), T(-1), 2, 1, 1, 1};
+  OEArgs<T> a{Dc, Dinv, xe, b, x, oe, T(0), T(-1), 2, 1, 1, 1, 0, 0, 0, nullptr};
   launch_oe_stencil(a, st);
 }
+
+// ---- batched odd-even pieces (one launch for nrhs right-hand sides) -------
+template <typename T>
+__global__ void k_oe_inv_odd_b(const T* __restrict__ Dinv, const T* __restrict__ b, T* __restrict__ to, OEGeom oe,
+                               long bstr, long tstr, const int* __restrict__ active) {
+  const int n = 2 * oe.nv;
+  const int k = blockIdx.x, row = threadIdx.x, r = blockIdx.y;
+  if (row >= n || (active && !active[r])) return;
+  const int site = oe.odd_site[k];
+  const cx<T>* bb = reinterpret_cast<const cx<T>*>(b + r * bstr) + (long)site * n;
+  const cx<T>* Di = reinterpret_cast<const cx<T>*>(Dinv) + (long)k * n * n;
+  cx<T> acc{0, 0};
+  for (int col = 0; col < n; ++col) cfma(acc, Di[(long)col * n + row], bb[col]);
+  reinterpret_cast<cx<T>*>(to + r * tstr)[(long)k * n + row] = acc;
+}
+
+template <typename T>
+__global__ void k_oe_scatter_even_b(const T* __restrict__ xe, T* __restrict__ x, OEGeom oe, long estr, long xstr,
+                                    const int* __restrict__ active) {
+  const int n = 2 * oe.nv, r = blockIdx.y;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)oe.nhalf * n || (active && !active[r])) return;
+  const int k = (int)(e / n), row = (int)(e % n);
+  reinterpret_cast<cx<T>*>(x + r * xstr)[(long)oe.even_site[k] * n + row] =
+      reinterpret_cast<const cx<T>*>(xe + r * estr)[e];
+}
+
+template <typename T>
+void launch_oe_schur_b(const T* Dc, const T* Dinv, const T* ve, T* uo, T* ye, const OEGeom& oe, double mu_c,
+                       int nrhs, long vstr, long ustr, long ystr, const int* active, cudaStream_t st) {
+  OEArgs<T> h1{Dc, Dinv, ve, nullptr, uo, oe, T(0), T(1), 0, 1, 1, 0, vstr, 0, ustr, active};
+  launch_oe_stencil(h1, st, nrhs);
+  OEArgs<T> h2{Dc, nullptr, uo, ve, ye, oe, (T)mu_c, T(-1), 1, 0, 0, 0, ustr, vstr, ystr, active};
+  launch_oe_stencil(h2, st, nrhs);
+}
+
+template <typename T>
+void launch_oe_prepare_b(const T* Dc, const T* Dinv, const T* b, T* to, T* bh, const OEGeom& oe, int nrhs,
+                         long bstr, long cstr, cudaStream_t st) {
+  const int n = 2 * oe.nv;
+  dim3 g1(oe.nhalf, nrhs);
+  k_oe_inv_odd_b<T><<<g1, (n + 31) / 32 * 32, 0, st>>>(Dinv, b, to, oe, bstr, cstr, nullptr);
+  OEArgs<T> a{Dc, nullptr, to, b, bh, oe, T(0), T(-1), 2, 0, 0, 0, cstr, bstr, cstr, nullptr};
+  launch_oe_stencil(a, st, nrhs);
+}
+
+template <typename T>
+void launch_oe_reconstruct_b(const T* Dc, const T* Dinv, const T* b, const T* xe, T* x, const OEGeom& oe, int nrhs,
+                             long bstr, long estr, cudaStream_t st) {
+  const int n = 2 * oe.nv;
+  const long tot = (long)oe.nhalf * n;
+  dim3 g1((int)((tot + 255) / 256), nrhs);
+  k_oe_scatter_even_b<T><<<g1, 256, 0, st>>>(xe, x, oe, estr, bstr, nullptr);
+  OEArgs<T> a{Dc, Dinv, xe, b, x, oe, T(0), T(-1), 2, 1, 1, 1, estr, bstr, bstr, nullptr};
+  launch_oe_stencil(a, st, nrhs);
+}
+
+#define TM_INST_B(T)                                                                                              \
+  template void launch_oe_schur_b<T>(const T*, const T*, const T*, T*, T*, const OEGeom&, double, int, long, long, \
+                                     long, const int*, cudaStream_t);                                             \
+  template void launch_oe_prepare_b<T>(const T*, const T*, const T*, T*, T*, const OEGeom&, int, long, long,      \
+                                       cudaStream_t);                                                             \
+  template void launch_oe_reconstruct_b<T>(const T*, const T*, const T*, const T*, T*, const OEGeom&, int, long,  \
+                                           long, cudaStream_t);
+TM_INST_B(double)
+TM_INST_B(float)
+#undef TM_INST_B
 
 #define TM_INST(T)                                                                                               \
   template void launch_orthonormalise<T>(T*, const AggGeom&, int*, cudaStream_t);                              \

@@ -78,6 +78,8 @@ struct tm_handle {
   double* scratch = nullptr;  // reduction partials
   double* dsmall = nullptr;   // small device results
   double* hsmall = nullptr;   // pinned host mirror
+  double* hbig = nullptr;     // pinned host scratch for batched solves
+  size_t hbig_n = 0;
   std::map<std::string, Buf> work;
   bool gauge_ok = false, setup_ok = false;
   std::string err;
@@ -85,6 +87,7 @@ struct tm_handle {
   int kcycles = 0;
   // opt-in per-kernel timing (tm_profile)
   bool prof = false;
+  unsigned prof_mask = 0;  // classes timed with events (all classes are counted)
   struct Rec {
     int kind, units, nk;
     cudaEvent_t a, b;
@@ -163,8 +166,6 @@ void harvest(tm_handle* h, bool wait) {
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, r.a, r.b));
     h->prof_ms[r.kind] += ms;
-    h->prof_launch[r.kind] += r.nk;
-    h->prof_units[r.kind] += r.units;
     h->evpool.push_back(r.a);
     h->evpool.push_back(r.b);
   }
@@ -178,6 +179,9 @@ struct Prof {
   cudaEvent_t a = nullptr;
   Prof(tm_handle* hh, int k, int u = 1, int n = 1) : h(hh), kind(k), units(u), nk(n) {
     if (!h->prof) return;
+    h->prof_launch[kind] += nk;
+    h->prof_units[kind] += units;
+    if (!((h->prof_mask >> kind) & 1u)) return;
     if (h->recs.size() > 4096) harvest(h, false);
     a = take_event(h);
     CK(cudaEventRecord(a, h->st));
@@ -453,40 +457,235 @@ void build_coarse(tm_handle* h) {
   CKL();
 }
 
-// odd-even GMRES on D_c(delta mu) x = b (full coarse vectors, one rhs)
+// pinned host scratch of at least n doubles (grown on demand)
+double* host_scratch(tm_handle* h, size_t n) {
+  if (h->hbig_n < n) {
+    if (h->hbig) CK(cudaFreeHost(h->hbig));
+    h->hbig = nullptr;
+    h->hbig_n = 0;
+    CK(cudaMallocHost(&h->hbig, n * sizeof(double)));
+    h->hbig_n = n;
+  }
+  return h->hbig;
+}
+
+// Odd-even GMRES(coarse_restart) on D_c(delta mu) x_r = b_r for nrhs full
+// coarse vectors at once.  Every right-hand side runs its own GMRES (own
+// Hessenberg matrix, own restarts and stopping); the batch only shares
+// launches and one host synchronisation per Arnoldi step.  Finished right-hand
+// sides are masked out, so each one sees exactly the single-rhs arithmetic.
 template <typename T>
-KrylovOut coarse_solve(tm_handle* h, const T* b, T* x, double tol, int maxit) {
+std::vector<int> coarse_solve(tm_handle* h, const T* b, T* x, int nrhs, double tol, int maxit) {
+  using cd = std::complex<double>;
+  const int m = h->p.coarse_restart;
+  const long nc = (long)h->nhalf * h->n;        // complex numbers per compact vector
+  const long cv = 2 * nc;                        // reals per compact vector
+  const long cf = 2 * (long)h->gc.V * h->n;      // reals per full coarse vector
+  const long vstr = (long)(m + 1) * cv;          // per-rhs Krylov basis stride
+  const long ds = 4 * kMaxDots + 2;              // per-rhs small-result stride (doubles)
   const T* Dc = static_cast<const T*>(h->Dc);
   const T* Di = static_cast<const T*>(h->Dinv);
-  const long nc = (long)h->nhalf * h->n;  // complex per parity
-  T* to = W<T>(h, "c_to", 2 * nc);
-  T* bh = W<T>(h, "c_bh", 2 * nc);
-  T* xe = W<T>(h, "c_xe", 2 * nc);
-  T* uo = W<T>(h, "c_uo", 2 * nc);
-  {
-    Prof pf(h, PK_COARSE_OE, 1, 2);
-    launch_oe_inv_odd<T>(Di, b, to, h->oe, h->st);
-    CKL();
-    launch_oe_rhs<T>(Dc, b, to, bh, h->oe, h->st);
-    CKL();
-  }
+  T* to = W<T>(h, "cb_to", cv * nrhs);
+  T* bh = W<T>(h, "cb_bh", cv * nrhs);
+  T* xe = W<T>(h, "cb_xe", cv * nrhs);
+  T* uo = W<T>(h, "cb_uo", cv * nrhs);
+  T* w = W<T>(h, "cb_w", cv * nrhs);
+  T* Vb = W<T>(h, "cb_V", vstr * nrhs);
+  double* part = W<double>(h, "cb_part", std::max(multidot_scratch_doubles(nc, m + 1, nrhs), 2L * 304 * nrhs));
+  double* dd = W<double>(h, "cb_dots", ds * nrhs);
+  double* nrm = W<double>(h, "cb_nrm", nrhs);
+  int* act = W<int>(h, "cb_act", nrhs);
+  constexpr int kSlots = 8;  // mask uploads between two stream synchronisations
+  double* hb = host_scratch(h, (size_t)(ds + 1) * nrhs + (size_t)kSlots * nrhs);
+  double* hn_h = hb + (size_t)ds * nrhs;                     // [nrhs] norms
+  int* hact0 = reinterpret_cast<int*>(hn_h + nrhs);          // [kSlots][nrhs] masks
+  int slot = 0;  // an async upload reads its slot later: reuse slots only after a sync
   const double mc = mu_c(h);
-  auto S = [&](const T* ve, T* ye) {
-    Prof pf(h, PK_COARSE_OE, 1, 2);
-    launch_oe_hop_inv<T>(Dc, Di, ve, uo, h->oe, h->st);
-    CKL();
-    launch_oe_even<T>(Dc, ve, uo, ye, h->oe, mc, 1, h->st);
+
+  std::vector<double> bnorm(nrhs), beta(nrhs);
+  std::vector<int> iters(nrhs, 0), kk(nrhs, 0);
+  std::vector<char> active(nrhs), inner(nrhs);
+  std::vector<cd> H((size_t)nrhs * (m + 1) * m), g((size_t)nrhs * (m + 1)), sn((size_t)nrhs * m);
+  std::vector<double> cs((size_t)nrhs * m);
+
+  auto upload_mask = [&](const std::vector<char>& msk, const std::vector<int>* counts) {
+    if (slot >= kSlots) {
+      sync(h);
+      slot = 0;
+    }
+    int* hact = hact0 + (size_t)(slot++) * nrhs;
+    for (int r = 0; r < nrhs; ++r) hact[r] = msk[r] ? (counts ? (*counts)[r] : 1) : 0;
+    CK(cudaMemcpyAsync(act, hact, nrhs * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  };
+  auto count = [&](const std::vector<char>& msk) {
+    int c = 0;
+    for (char v : msk) c += v ? 1 : 0;
+    return c;
+  };
+  auto read_norms = [&]() {
+    CK(cudaMemcpyAsync(hn_h, nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    slot = 0;
+  };
+  auto schur = [&](const T* v, long vs, int units) {
+    Prof pf(h, PK_COARSE_OE, units, 2);
+    launch_oe_schur_b<T>(Dc, Di, v, uo, w, h->oe, mc, nrhs, vs, cv, cv, act, h->st);
     CKL();
   };
-  auto none = [](const T*, T*) {};
-  KrylovOut r = krylov<T, T>(h, "cg", S, S, none, false, bh, xe, false, nc, tol, h->p.coarse_restart, maxit);
+
   {
-    Prof pf(h, PK_COARSE_OE, 1, 2);
-    launch_oe_reconstruct<T>(Dc, Di, b, xe, x, h->oe, h->st);
+    Prof pf(h, PK_COARSE_OE, nrhs, 2);
+    launch_oe_prepare_b<T>(Dc, Di, b, to, bh, h->oe, nrhs, cf, cv, h->st);
     CKL();
   }
-  h->coarse_iters += r.iters;
-  return r;
+  {
+    Prof pf(h, PK_BLAS_COARSE, nrhs, 3);
+    launch_zero<T>(xe, cv * nrhs, h->st);
+    CKL();
+    launch_norm2_b<T>(bh, cv, nc, nrm, part, nrhs, nullptr, h->st);
+    CKL();
+  }
+  read_norms();
+  for (int r = 0; r < nrhs; ++r) {
+    bnorm[r] = std::sqrt(hn_h[r]);
+    if (!std::isfinite(bnorm[r])) raise(TM_ERR_NONFINITE, "non-finite coarse right-hand side");
+    beta[r] = bnorm[r];
+    active[r] = bnorm[r] > 0 && beta[r] > tol * bnorm[r] && iters[r] < maxit;
+  }
+  {
+    Prof pf(h, PK_BLAS_COARSE, nrhs);
+    launch_scale_copy_b<T>(bh, cv, Vb, vstr, nullptr, nc, nrhs, nullptr, h->st);
+    CKL();
+  }
+  while (count(active)) {
+    // v_0 = r / beta for the right-hand sides of this cycle
+    for (int r = 0; r < nrhs; ++r) hn_h[r] = beta[r] * beta[r];
+    CK(cudaMemcpyAsync(nrm, hn_h, nrhs * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    upload_mask(active, nullptr);
+    {
+      Prof pf(h, PK_BLAS_COARSE, count(active));
+      launch_scale_copy_b<T>(Vb, vstr, Vb, vstr, nrm, nc, nrhs, act, h->st);
+      CKL();
+    }
+    for (int r = 0; r < nrhs; ++r) {
+      inner[r] = active[r];
+      kk[r] = 0;
+      if (active[r]) {
+        std::fill(g.begin() + (size_t)r * (m + 1), g.begin() + (size_t)(r + 1) * (m + 1), cd(0));
+        g[(size_t)r * (m + 1)] = beta[r];
+      }
+    }
+    for (int k = 0; k < m && count(inner); ++k) {
+      const int na = count(inner);
+      upload_mask(inner, nullptr);
+      schur(Vb + (long)k * cv, vstr, na);
+      double* d1 = dd;
+      double* d2 = dd + 2 * (k + 1);
+      {
+        Prof pf(h, PK_BLAS_COARSE, na, 8);
+        launch_multidot_b<T>(Vb, vstr, cv, k + 1, w, cv, nc, d1, ds, part, nrhs, act, h->st);
+        CKL();
+        launch_multi_caxpy_b<T>(Vb, vstr, cv, k + 1, d1, ds, w, cv, nc, nrhs, act, h->st);
+        CKL();
+        launch_multidot_b<T>(Vb, vstr, cv, k + 1, w, cv, nc, d2, ds, part, nrhs, act, h->st);
+        CKL();
+        launch_multi_caxpy_b<T>(Vb, vstr, cv, k + 1, d2, ds, w, cv, nc, nrhs, act, h->st);
+        CKL();
+        launch_norm2_b<T>(w, cv, nc, nrm, part, nrhs, act, h->st);
+        CKL();
+        launch_scale_copy_b<T>(w, cv, Vb + (long)(k + 1) * cv, vstr, nrm, nc, nrhs, act, h->st);
+        CKL();
+      }
+      CK(cudaMemcpy2DAsync(hb, 4 * (k + 1) * sizeof(double), dd, ds * sizeof(double), 4 * (k + 1) * sizeof(double),
+                           nrhs, cudaMemcpyDeviceToHost, h->st));
+      read_norms();
+      for (int r = 0; r < nrhs; ++r) {
+        if (!inner[r]) continue;
+        const double hn = std::sqrt(hn_h[r]);
+        if (!std::isfinite(hn)) raise(TM_ERR_NONFINITE, "non-finite coarse Arnoldi vector");
+        const double* hr = hb + (size_t)r * 4 * (k + 1);
+        cd* Hr = H.data() + (size_t)r * (m + 1) * m;
+        cd* gr = g.data() + (size_t)r * (m + 1);
+        cd* snr = sn.data() + (size_t)r * m;
+        double* csr = cs.data() + (size_t)r * m;
+        std::vector<cd> col(m + 1, cd(0));
+        for (int j = 0; j <= k; ++j)
+          col[j] = cd(hr[2 * j] + hr[2 * (k + 1) + 2 * j], hr[2 * j + 1] + hr[2 * (k + 1) + 2 * j + 1]);
+        col[k + 1] = hn;
+        for (int j = 0; j < k; ++j) {
+          const cd t = csr[j] * col[j] + snr[j] * col[j + 1];
+          col[j + 1] = -std::conj(snr[j]) * col[j] + csr[j] * col[j + 1];
+          col[j] = t;
+        }
+        double c;
+        cd sg, rho;
+        givens(col[k], hn, c, sg, rho);
+        csr[k] = c;
+        snr[k] = sg;
+        col[k] = rho;
+        col[k + 1] = 0;
+        for (int j = 0; j <= m; ++j) Hr[(size_t)j * m + k] = col[j];
+        gr[k + 1] = -std::conj(sg) * gr[k];
+        gr[k] = c * gr[k];
+        ++iters[r];
+        kk[r] = k + 1;
+        if (hn == 0 || std::abs(gr[k + 1]) <= tol * bnorm[r] || iters[r] >= maxit) inner[r] = 0;
+      }
+    }
+    // x_r += V_r y_r with R y = g for this cycle's right-hand sides
+    int kmax = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!active[r]) continue;
+      const int k = kk[r];
+      kmax = std::max(kmax, k);
+      const cd* Hr = H.data() + (size_t)r * (m + 1) * m;
+      const cd* gr = g.data() + (size_t)r * (m + 1);
+      std::vector<cd> y(k);
+      for (int i = k - 1; i >= 0; --i) {
+        cd acc = gr[i];
+        for (int j = i + 1; j < k; ++j) acc -= Hr[(size_t)i * m + j] * y[j];
+        y[i] = acc / Hr[(size_t)i * m + i];
+      }
+      double* yr = hb + (size_t)r * ds;
+      for (int i = 0; i < k; ++i) {
+        yr[2 * i] = y[i].real();
+        yr[2 * i + 1] = y[i].imag();
+      }
+    }
+    CK(cudaMemcpyAsync(dd, hb, ds * nrhs * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    upload_mask(active, &kk);
+    {
+      Prof pf(h, PK_BLAS_COARSE, count(active));
+      launch_lincomb_b<T>(Vb, vstr, cv, kmax, dd, ds, xe, cv, nc, nrhs, act, h->st);
+      CKL();
+    }
+    // true residual of the reduced systems
+    upload_mask(active, nullptr);
+    schur(xe, cv, count(active));
+    {
+      Prof pf(h, PK_BLAS_COARSE, count(active), 4);
+      launch_sub_b<T>(bh, cv, w, cv, nc, nrhs, act, h->st);
+      CKL();
+      launch_norm2_b<T>(w, cv, nc, nrm, part, nrhs, act, h->st);
+      CKL();
+      launch_scale_copy_b<T>(w, cv, Vb, vstr, nullptr, nc, nrhs, act, h->st);
+      CKL();
+    }
+    read_norms();
+    for (int r = 0; r < nrhs; ++r) {
+      if (!active[r]) continue;
+      beta[r] = std::sqrt(hn_h[r]);
+      if (!std::isfinite(beta[r])) raise(TM_ERR_NONFINITE, "non-finite coarse residual");
+      active[r] = beta[r] > tol * bnorm[r] && iters[r] < maxit;
+    }
+  }
+  {
+    Prof pf(h, PK_COARSE_OE, nrhs, 2);
+    launch_oe_reconstruct_b<T>(Dc, Di, b, xe, x, h->oe, nrhs, cf, cv, h->st);
+    CKL();
+  }
+  for (int r = 0; r < nrhs; ++r) h->coarse_iters += iters[r];
+  return iters;
 }
 
 // z = B(v), eq. (1), nrhs fine fields in T
@@ -513,8 +712,7 @@ void kcycle(tm_handle* h, const T* v, T* z, int nrhs) {
     launch_restrict<T>(static_cast<const T*>(h->P), r, rc, h->ag, nrhs, h->st);
     CKL();
   }
-  for (int i = 0; i < nrhs; ++i)
-    coarse_solve<T>(h, rc + 2 * cc * i, ec + 2 * cc * i, h->p.coarse_tol, h->p.coarse_maxit);
+  coarse_solve<T>(h, rc, ec, nrhs, h->p.coarse_tol, h->p.coarse_maxit);
   {
     Prof pf(h, PK_PROLONG, nrhs);
     launch_prolong<T>(static_cast<const T*>(h->P), ec, z, h->ag, nrhs, true, h->st);
@@ -708,6 +906,7 @@ void tm_destroy(tm_handle* h) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (h->hsmall) cudaFreeHost(h->hsmall);
+  if (h->hbig) cudaFreeHost(h->hbig);
   for (auto& r : h->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -1058,13 +1257,13 @@ tm_status tm_coarse_solve(tm_handle* h, int prec, const void* b, void* x, double
   if (!h || !b || !x || maxit < 1 || tol < 0) return TM_ERR_ARG;
   API_BEGIN
   need_cycle_prec(h, prec);
-  KrylovOut r;
+  std::vector<int> r;
   if (prec == TM_F64)
-    r = coarse_solve<double>(h, static_cast<const double*>(b), static_cast<double*>(x), tol, maxit);
+    r = coarse_solve<double>(h, static_cast<const double*>(b), static_cast<double*>(x), 1, tol, maxit);
   else
-    r = coarse_solve<float>(h, static_cast<const float*>(b), static_cast<float*>(x), tol, maxit);
+    r = coarse_solve<float>(h, static_cast<const float*>(b), static_cast<float*>(x), 1, tol, maxit);
   sync(h);
-  if (iters) *iters = r.iters;
+  if (iters) *iters = r[0];
   API_END
 }
 
@@ -1192,6 +1391,7 @@ tm_status tm_profile(tm_handle* h, int enable) {
     h->prof_ms[k] = 0;
   }
   h->prof = enable != 0;
+  h->prof_mask = static_cast<unsigned>(enable);
   API_END
 }
 

@@ -93,6 +93,21 @@ template <typename T>
 void launch_oe_reconstruct(const T* Dc, const T* Dinv, const T* b, const T* xe, T* x, const OEGeom& oe,
                            cudaStream_t st);
 
+// batched odd-even pieces: nrhs right-hand sides at per-rhs strides (reals);
+// `active` (device, may be null) masks right-hand sides that are finished
+// ye = S ve with S = D_ee - D_eo D_oo^-1 D_oe (uo: odd-site work vectors)
+template <typename T>
+void launch_oe_schur_b(const T* Dc, const T* Dinv, const T* ve, T* uo, T* ye, const OEGeom& oe, double mu_c,
+                       int nrhs, long vstr, long ustr, long ystr, const int* active, cudaStream_t st);
+// to = Dinv b_o, bh = b_e - D_eo to  (b full vectors at stride bstr; to, bh compact at cstr)
+template <typename T>
+void launch_oe_prepare_b(const T* Dc, const T* Dinv, const T* b, T* to, T* bh, const OEGeom& oe, int nrhs,
+                         long bstr, long cstr, cudaStream_t st);
+// x = [xe ; Dinv (b_o - D_oe xe)]  (b, x full at bstr; xe compact at estr)
+template <typename T>
+void launch_oe_reconstruct_b(const T* Dc, const T* Dinv, const T* b, const T* xe, T* x, const OEGeom& oe, int nrhs,
+                             long bstr, long estr, cudaStream_t st);
+
 // ---- level-1 vectors (blas.cu) ----------------------------------------------
 // all BLAS works on flat arrays of n complex numbers stored as (re, im) pairs
 template <typename Ti, typename To>
@@ -120,6 +135,34 @@ void launch_norm2(const T* x, long ncx, int nrhs, double* dev_out, double* scrat
 // x_r *= s_r (s on device, double[nrhs], scale = 1 / sqrt(s_r) if inv_sqrt)
 template <typename T>
 void launch_scale(T* x, long ncx, int nrhs, const double* s, bool inv_sqrt, cudaStream_t st);
+
+// batched variants: right-hand side r uses X + r * xstr, y + r * ystr, ...;
+// inactive right-hand sides (active[r] == 0, active may be null) are skipped.
+// out[r * ostr + 2 j] (re, im) = sum conj(X_rj) y_r, j < k
+template <typename T>
+void launch_multidot_b(const T* X, long xstr, long ldx, int k, const T* y, long ystr, long ncx, double* out,
+                       long ostr, double* scratch, int nrhs, const int* active, cudaStream_t st);
+// y_r -= sum_j c[r * cstr + 2 j] X_rj
+template <typename T>
+void launch_multi_caxpy_b(const T* X, long xstr, long ldx, int k, const double* c, long cstr, T* y, long ystr,
+                          long ncx, int nrhs, const int* active, cudaStream_t st);
+// y_r += sum_{j < min(k, active[r])} c[r * cstr + 2 j] X_rj  (active[r]: term count, 0 = skip)
+template <typename T>
+void launch_lincomb_b(const T* X, long xstr, long ldx, int k, const double* c, long cstr, T* y, long ystr, long ncx,
+                      int nrhs, const int* active, cudaStream_t st);
+// out[r] = ||y_r||^2
+template <typename T>
+void launch_norm2_b(const T* y, long ystr, long ncx, double* out, double* scratch, int nrhs, const int* active,
+                    cudaStream_t st);
+// dst_r = src_r / sqrt(s[r]) (0 if s[r] <= 0), or dst_r = src_r when s is null
+template <typename T>
+void launch_scale_copy_b(const T* src, long sstr, T* dst, long dstr, const double* s, long ncx, int nrhs,
+                         const int* active, cudaStream_t st);
+// y_r = x_r - y_r
+template <typename T>
+void launch_sub_b(const T* x, long xstr, T* y, long ystr, long ncx, int nrhs, const int* active, cudaStream_t st);
+// scratch doubles that launch_multidot_b / launch_norm2_b need
+long multidot_scratch_doubles(long ncx, int k, int nrhs);
 
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs
 
