@@ -375,9 +375,9 @@ void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, con
                          cudaStream_t st) {
   const int nv = ag.nv;
   const size_t per_site = (size_t)12 * 3 * nv * sizeof(cx<T>);  // Ps + Us per site
-  const size_t budget = 200 * 1024;
+  const size_t budget = 100 * 1024;  // two CTAs per SM
   int TS = (int)(budget / per_site);
-  if (TS > 32) TS = 32;
+  if (TS > 16) TS = 16;
   if (TS < 1) TS = 1;
   static bool attr = false;
   if (!attr) {
@@ -612,12 +612,118 @@ __global__ void k_oe_stencil(OEArgs<T> a) {
   }
 }
 
+// Several right-hand sides per CTA: every D_c (and D_oo^-1) entry a thread
+// loads is applied to up to RB right-hand sides held in registers.  Each CTA
+// lists the active right-hand sides and takes group blockIdx.y of RB of them.
+template <typename T, int RB>
+__global__ void k_oe_stencil_mr(OEArgs<T> a, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nv = a.oe.nv, n = 2 * nv;
+  cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);  // [RB][9][n]
+  cx<T>* accs = part + (size_t)RB * 9 * n;            // [RB][n]
+  int* lst = reinterpret_cast<int*>(accs + (size_t)RB * n);  // [nrhs]
+  __shared__ int nact;
+  const int k = blockIdx.x;
+  const int site = a.odd ? a.oe.odd_site[k] : a.oe.even_site[k];
+  const int row = threadIdx.x % n, t = threadIdx.x / n;
+  const cx<T>* B = reinterpret_cast<const cx<T>*>(a.Dc) + (long)site * 9 * n * n;
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int r = 0; r < nrhs; ++r)
+      if (!a.active || a.active[r]) lst[c++] = r;
+    nact = c;
+  }
+  __syncthreads();
+  const int na = nact;
+  for (int g0 = blockIdx.y * RB; g0 < na && g0 < (int)(blockIdx.y + 1) * RB; g0 += RB) {
+    const int gn = min(RB, na - g0);
+    if (t < 9) {
+      cx<T> acc[RB];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) acc[q] = cx<T>{0, 0};
+      if (t == 0) {
+        if (a.mode == 1) {
+          for (int col = 0; col < n; ++col) {
+            const cx<T> bv = B[(long)col * n + row];
+#pragma unroll
+            for (int q = 0; q < RB; ++q)
+              if (q < gn) cfma(acc[q], bv, reinterpret_cast<const cx<T>*>(a.pre + lst[g0 + q] * a.p_str)[(long)k * n + col]);
+          }
+          const T sg = row < nv ? -a.mu_c : a.mu_c;
+#pragma unroll
+          for (int q = 0; q < RB; ++q)
+            if (q < gn) {
+              const cx<T> x = reinterpret_cast<const cx<T>*>(a.pre + lst[g0 + q] * a.p_str)[(long)k * n + row];
+              acc[q].r -= sg * x.i;
+              acc[q].i += sg * x.r;
+            }
+        } else if (a.mode == 2) {
+#pragma unroll
+          for (int q = 0; q < RB; ++q)
+            if (q < gn) acc[q] = reinterpret_cast<const cx<T>*>(a.pre + lst[g0 + q] * a.p_str)[(long)site * n + row];
+        }
+      } else {
+        const int nb = coarse_nb(a.oe.gc, site, t);
+        const long soff = (long)a.oe.cidx[nb] * n;
+        const cx<T>* Bt = B + (long)t * n * n;
+        for (int col = 0; col < n; ++col) {
+          const cx<T> bv = Bt[(long)col * n + row];
+#pragma unroll
+          for (int q = 0; q < RB; ++q)
+            if (q < gn) cfma(acc[q], bv, reinterpret_cast<const cx<T>*>(a.src + lst[g0 + q] * a.s_str)[soff + col]);
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) acc[q] = a.sgn * acc[q];
+      }
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+        if (q < gn) part[((size_t)q * 9 + t) * n + row] = acc[q];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < gn * n; e += blockDim.x) {
+      const int q = e / n, rr = e % n;
+      cx<T> s = part[((size_t)q * 9) * n + rr];
+      for (int tt = 1; tt < 9; ++tt) s = s + part[((size_t)q * 9 + tt) * n + rr];
+      accs[(size_t)q * n + rr] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < gn * n; e += blockDim.x) {
+      const int q = e / n, rr = e % n;
+      cx<T> res = accs[(size_t)q * n + rr];
+      if (a.post) {
+        const cx<T>* Di = reinterpret_cast<const cx<T>*>(a.Dinv) + (long)k * n * n;
+        res = cx<T>{0, 0};
+        for (int col = 0; col < n; ++col) cfma(res, Di[(long)col * n + rr], accs[(size_t)q * n + col]);
+      }
+      cx<T>* out = reinterpret_cast<cx<T>*>(a.out + lst[g0 + q] * a.o_str);
+      if (a.full_out)
+        out[(long)site * n + rr] = res;
+      else
+        out[(long)k * n + rr] = res;
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int kOeRB = 8;
+
 template <typename T>
 static void launch_oe_stencil(const OEArgs<T>& a, cudaStream_t st, int nrhs = 1) {
   const int n = 2 * a.oe.nv;
   const int threads = (9 * n + 31) / 32 * 32;
-  dim3 grid(a.oe.nhalf, nrhs);
-  k_oe_stencil<T><<<grid, threads, 10 * n * sizeof(cx<T>), st>>>(a);
+  if (nrhs <= 2) {
+    dim3 grid(a.oe.nhalf, nrhs);
+    k_oe_stencil<T><<<grid, threads, 10 * n * sizeof(cx<T>), st>>>(a);
+    return;
+  }
+  const size_t smem = (size_t)kOeRB * 10 * n * sizeof(cx<T>) + (size_t)nrhs * sizeof(int);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_oe_stencil_mr<T, kOeRB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    attr = true;
+  }
+  dim3 grid(a.oe.nhalf, (nrhs + kOeRB - 1) / kOeRB);
+  k_oe_stencil_mr<T, kOeRB><<<grid, threads, smem, st>>>(a, nrhs);
 }
 
 template <typename T>

@@ -53,8 +53,9 @@ __device__ __forceinline__ void block_hops(const cx<T>* __restrict__ rs, int BS,
   }
 }
 
+// FP32: two CTAs per SM (128 registers); FP64 would spill heavily at that bound
 template <typename T>
-__global__ void k_sap(SapArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sap(SapArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SapGeom& sg = a.sg;
   const Lat& g = sg.g;
