@@ -44,6 +44,10 @@ WORKLOADS = {
         L=(32, 16, 16, 16), eps=0.5, seed=1, c_sw=1.5, mu=0.003, delta=5.0, nv=20,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10,
         m0_key="16x16x16x32_eps0.5_seed1"),
+    "24x24x24x48_2lvl_nv24_12pt": dict(
+        L=(48, 24, 24, 24), eps=0.5, seed=1, c_sw=1.5, mu=0.002, delta=5.0, nv=24,
+        agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=5, tol=1e-10, nrhs=12, point=True,
+        m0_key="24x24x24x48_eps0.5_seed1"),
     "8x8x8x8_2lvl_nv8": dict(
         L=(8, 8, 8, 8), eps=0.5, seed=5, c_sw=1.5, mu=0.005, delta=5.0, nv=8,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, m0=-0.4),
@@ -84,19 +88,22 @@ def workload_m0(wl: dict) -> tuple[float, str]:
 # ---------------------------------------------------------------------------
 # algorithmic bytes per unit (one right-hand side) of each kernel class
 # ---------------------------------------------------------------------------
-def algorithmic_bytes(kind: str, wl: dict) -> float | None:
-    """Bytes per rhs unit that the kernel class must move at minimum.
+def algorithmic_bytes(kind: str, wl: dict) -> tuple[float, float] | None:
+    """(operator bytes per launch, vector bytes per rhs unit) a kernel class
+    must move at minimum; a launch over u right-hand sides moves op + u * vec.
 
-    dslash:   in spinor 24 + out 24 + 4 links x 12 + clover 72 = 168 reals/site
-    sap:      one colour launch: x everywhere (24 V) + b, links, clover, x-write
-              on the colour's half (24 + 48 + 72 + 24 = 168 reals x V/2)
-    restrict: fine spinor 24 + P (24 N_v) reals/site
-    prolong:  P (24 N_v) + fine in/out (48) reals/site
-    coarse_oe (one Schur application S = D_ee - D_eo D_oo^-1 D_oe per rhs):
-              the 9 D_c blocks of every coarse site and the odd-site inverses,
-              (9 + 1/2) (2 N_v)^2 complex per coarse site (vectors are small)
-    coarse_build (one build of D_c): P, links and clover read once
-              (24 N_v + 48 + 72 reals/site) and D_c written (9 (2 N_v)^2 complex/coarse site)
+    dslash:   op = 4 links x 12 + clover 72 = 120 reals/site;
+              vec = in + out spinor 48 reals/site
+    sap:      one colour: op = links + clover on the colour's half (120 V/2);
+              vec = x everywhere (24 V) + b and x-write on the half (48 V/2)
+    restrict: op = P (24 N_v reals/site); vec = fine spinor 24 reals/site
+    prolong:  op = P; vec = fine in/out 48 reals/site
+    coarse_oe (one Schur application S = D_ee - D_eo D_oo^-1 D_oe, two
+              launches): op = the 9 D_c blocks of every coarse site with the
+              odd-site inverses in place of the odd self blocks, 9 (2N_v)^2
+              complex per coarse site; vec = 2 coarse vectors
+    coarse_build (one build of D_c): op = P, links and clover read once and
+              D_c written; vec = 0
     """
     V = 1
     for n in wl["L"]:
@@ -106,20 +113,21 @@ def algorithmic_bytes(kind: str, wl: dict) -> float | None:
     for a in wl["agg"]:
         Vc //= a
     n = 2 * nv
+    f = 4  # FP32 cycle
     if kind == "dslash_f64":
-        return 168 * 8 * V
+        return 120 * 8 * V, 48 * 8 * V
     if kind == "dslash_f32":
-        return 168 * 4 * V
+        return 120 * f * V, 48 * f * V
     if kind == "sap":
-        return (24 * V + 168 * V / 2) * 4
+        return 120 * f * V / 2, (24 * V + 48 * V / 2) * f
     if kind == "restrict":
-        return (24 + 24 * nv) * 4 * V
+        return 24 * nv * f * V, 24 * f * V
     if kind == "prolong":
-        return (24 * nv + 48) * 4 * V
+        return 24 * nv * f * V, 48 * f * V
     if kind == "coarse_oe":
-        return 9.5 * n * n * 8 * Vc
+        return 9 * n * n * 2 * f * Vc, 2 * n * 2 * f * Vc
     if kind == "coarse_build":
-        return (24 * nv + 120) * 4 * V + 9 * n * n * 8 * Vc
+        return (24 * nv + 120) * f * V + 9 * n * n * 2 * f * Vc, 0.0
     return None
 
 
@@ -301,7 +309,11 @@ def main_native(args):
     L, nv, seed = wl["L"], wl["nv"], wl["seed"] + rank  # one independent replica per rank
     U = inputs.gauge_field(L, wl["eps"], seed)
     tv = inputs.random_test_vectors(L, nv, seed + inputs.TV_SEED_OFFSET)
-    b = inputs.gaussian_spinor(L, seed + inputs.RHS_SEED_OFFSET)
+    nrhs = wl.get("nrhs", 1)
+    if wl.get("point"):
+        b, _ = inputs.point_sources(L, seed + inputs.RHS_SEED_OFFSET)
+    else:
+        b = inputs.gaussian_spinor(L, seed + inputs.RHS_SEED_OFFSET)
     Ud, tvd, bd = (torch.from_numpy(a).cuda() for a in (U, tv, b))
     xd = torch.zeros_like(bd)
     Uh, tvh, bh = (torch.from_numpy(a).pin_memory() for a in (U, tv, b))
@@ -309,7 +321,7 @@ def main_native(args):
     stream = torch.cuda.current_stream()
     p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv,
                   agg=wl["agg"], sap_block=wl["sap_block"], setup_iters=wl["setup_iters"],
-                  cycle_prec=tm.TM_F32)
+                  cycle_prec=tm.TM_F32, max_rhs=nrhs)
     h = tm.tm_create(p, stream)
     infos = []
 
@@ -317,7 +329,7 @@ def main_native(args):
         tm.tm_load_gauge(h, Ug)
         tm.tm_setup(h, tvg)
         xg.zero_()
-        st, info = tm.tm_solve(h, bg, xg, 1, wl["tol"])
+        st, info = tm.tm_solve(h, bg, xg, nrhs, wl["tol"])
         if st != tm.TM_OK:
             raise RuntimeError(f"solve failed: {tm.tm_status_string(st)}")
         infos.append(info.as_dict())
@@ -384,17 +396,21 @@ def main_native(args):
     # per-step unit counts (per rhs unit) from the profile
     per_step = {k: v["units"] / K for k, v in prof.items()}
     launches = sum(v["launches"] for v in prof.values())
+    # kernel launches per profiled scope of a class (a Schur half is one
+    # launch; a build scope is orthonormalisation + build + odd-site inverses)
+    kernels_per_scope = {"coarse_build": 3, "coarse_oe": 2}
     roof = None
-    bytes_unit = algorithmic_bytes(dom, wl)
+    model = algorithmic_bytes(dom, wl)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    if bytes_unit is not None and prof[dom]["launches"]:
-        per_launch_bytes = bytes_unit * prof[dom]["units"] / prof[dom]["launches"]
-        avg_s = prof[dom]["ms"] / prof[dom]["launches"] / 1000.0
+    if model is not None and prof[dom]["launches"]:
+        scopes = prof[dom]["launches"] / kernels_per_scope.get(dom, 1)
+        per_launch_bytes = model[0] + model[1] * prof[dom]["units"] / scopes
+        avg_s = prof[dom]["ms"] / scopes / 1000.0
         achieved = per_launch_bytes / avg_s / 1e9
         tr = ncu_traffic(args.workload, dom)
-        traffic = tr * prof[dom]["units"] / prof[dom]["launches"] if tr else None
+        traffic = tr * prof[dom]["units"] / scopes if tr else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                 "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
                 "bytes_per_launch": per_launch_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
@@ -455,10 +471,11 @@ def main_native(args):
             "workload": args.workload, "lattice_TZYX": list(L), "sites": V, "levels": 2,
             "nv": nv, "aggregate": list(wl["agg"]), "sap_block": list(wl["sap_block"]),
             "m0": m0, "m0_source": m0_src, "c_sw": wl["c_sw"], "mu": wl["mu"],
-            "delta": wl["delta"], "setup_iters": wl["setup_iters"], "tol": wl["tol"], "nrhs": 1,
-            "step": "load gauge + clover, adaptive setup, FGMRES solve (one rhs)",
+            "delta": wl["delta"], "setup_iters": wl["setup_iters"], "tol": wl["tol"], "nrhs": nrhs,
+            "rhs": "12 spin-colour point sources" if wl.get("point") else "Gaussian",
+            "step": f"load gauge + clover, adaptive setup, FGMRES solve ({nrhs} rhs)",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": "inputs per step 603 MB > 129 MB L2 (no extra flush)",
+            "l2": "inputs per step > 129 MB L2 (no extra flush)",
         },
         "solve": {
             "outer_iters": [i["iters"] for i in step_infos],

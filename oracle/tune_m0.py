@@ -103,6 +103,7 @@ def tune_m0(U: np.ndarray, c_sw: float, target: float = 1e-3, bc_t: float = -1.0
 WORKLOADS = {
     # name: (L = T,Z,Y,X, eps, seed, c_sw)
     "16x16x16x32_eps0.5_seed1": ((32, 16, 16, 16), 0.5, 1, 1.5),
+    "24x24x24x48_eps0.5_seed1": ((48, 24, 24, 24), 0.5, 1, 1.5),
 }
 
 

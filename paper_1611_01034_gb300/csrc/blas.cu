@@ -328,29 +328,30 @@ void launch_multi_caxpy_b(const T* X, long xstr, long ldx, int k, const double* 
   k_multi_caxpy_b<T><<<grid, 256, 0, st>>>(X, xstr, ldx, k, c, cstr, y, ystr, ncx, active);
 }
 
-template <typename T>
-__global__ void k_lincomb_b(const T* __restrict__ X, long xstr, long ldx, int k, const double* __restrict__ c,
-                            long cstr, T* __restrict__ y, long ystr, long ncx, const int* __restrict__ active) {
+template <typename Tx, typename Ty>
+__global__ void k_lincomb_b(const Tx* __restrict__ X, long xstr, long ldx, int k, const double* __restrict__ c,
+                            long cstr, Ty* __restrict__ y, long ystr, long ncx, const int* __restrict__ active) {
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   if (active) k = min(k, active[r]);  // active[r] = number of terms for rhs r
-  cx<T>* yy = reinterpret_cast<cx<T>*>(y + r * ystr);
-  const T* Xr = X + r * xstr;
+  cx<Ty>* yy = reinterpret_cast<cx<Ty>*>(y + r * ystr);
+  const Tx* Xr = X + r * xstr;
   const double* cr = c + r * cstr;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
-    cx<T> acc = yy[i];
+    cx<Ty> acc = yy[i];
     for (int j = 0; j < k; ++j) {
-      const cx<T> cj{(T)cr[2 * j], (T)cr[2 * j + 1]};
-      cfma(acc, cj, reinterpret_cast<const cx<T>*>(Xr + (long)j * ldx)[i]);
+      const cx<Ty> cj{(Ty)cr[2 * j], (Ty)cr[2 * j + 1]};
+      const cx<Tx> xv = reinterpret_cast<const cx<Tx>*>(Xr + (long)j * ldx)[i];
+      cfma(acc, cj, cx<Ty>{(Ty)xv.r, (Ty)xv.i});
     }
     yy[i] = acc;
   }
 }
-template <typename T>
-void launch_lincomb_b(const T* X, long xstr, long ldx, int k, const double* c, long cstr, T* y, long ystr, long ncx,
-                      int nrhs, const int* active, cudaStream_t st) {
+template <typename Tx, typename Ty>
+void launch_lincomb_b(const Tx* X, long xstr, long ldx, int k, const double* c, long cstr, Ty* y, long ystr,
+                      long ncx, int nrhs, const int* active, cudaStream_t st) {
   dim3 grid(grid_for(ncx), nrhs);
-  k_lincomb_b<T><<<grid, 256, 0, st>>>(X, xstr, ldx, k, c, cstr, y, ystr, ncx, active);
+  k_lincomb_b<Tx, Ty><<<grid, 256, 0, st>>>(X, xstr, ldx, k, c, cstr, y, ystr, ncx, active);
 }
 
 template <typename T>
@@ -396,8 +397,6 @@ void launch_sub_b(const T* x, long xstr, T* y, long ystr, long ncx, int nrhs, co
                                      const int*, cudaStream_t);                                                   \
   template void launch_multi_caxpy_b<T>(const T*, long, long, int, const double*, long, T*, long, long, int,      \
                                         const int*, cudaStream_t);                                                \
-  template void launch_lincomb_b<T>(const T*, long, long, int, const double*, long, T*, long, long, int,          \
-                                    const int*, cudaStream_t);                                                    \
   template void launch_norm2_b<T>(const T*, long, long, double*, double*, int, const int*, cudaStream_t);         \
   template void launch_scale_copy_b<T>(const T*, long, T*, long, const double*, long, int, const int*,            \
                                        cudaStream_t);                                                             \
@@ -405,6 +404,12 @@ void launch_sub_b(const T* x, long xstr, T* y, long ystr, long ncx, int nrhs, co
 TM_INST_B(double)
 TM_INST_B(float)
 #undef TM_INST_B
+template void launch_lincomb_b<double, double>(const double*, long, long, int, const double*, long, double*, long,
+                                               long, int, const int*, cudaStream_t);
+template void launch_lincomb_b<float, float>(const float*, long, long, int, const double*, long, float*, long, long,
+                                             int, const int*, cudaStream_t);
+template void launch_lincomb_b<float, double>(const float*, long, long, int, const double*, long, double*, long,
+                                              long, int, const int*, cudaStream_t);
 
 #define TM_INST(T)                                                                                    \
   template void launch_zero<T>(T*, long, cudaStream_t);                                               \

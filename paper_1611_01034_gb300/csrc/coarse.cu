@@ -553,74 +553,19 @@ struct OEArgs {
   const int* active;
 };
 
-template <typename T>
-__global__ void k_oe_stencil(OEArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nv = a.oe.nv, n = 2 * nv;
-  cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);  // [9][n]
-  cx<T>* accs = part + 9 * n;                          // [n]
-  const int k = blockIdx.x, rb = blockIdx.y;
-  if (a.active && !a.active[rb]) return;  // uniform over the CTA
-  a.src += rb * a.s_str;
-  a.pre += rb * a.p_str;
-  a.out += rb * a.o_str;
-  const int site = a.odd ? a.oe.odd_site[k] : a.oe.even_site[k];
-  const int row = threadIdx.x % n, t = threadIdx.x / n;
-  const cx<T>* B = reinterpret_cast<const cx<T>*>(a.Dc) + (long)site * 9 * n * n;
-  if (t < 9) {
-    cx<T> acc{0, 0};
-    if (t == 0) {
-      if (a.mode == 1) {
-        const cx<T>* v = reinterpret_cast<const cx<T>*>(a.pre) + (long)k * n;
-        for (int col = 0; col < n; ++col) cfma(acc, B[(long)col * n + row], v[col]);
-        const cx<T> x = v[row];
-        const T sg = row < nv ? -a.mu_c : a.mu_c;
-        acc.r -= sg * x.i;
-        acc.i += sg * x.r;
-      } else if (a.mode == 2) {
-        acc = reinterpret_cast<const cx<T>*>(a.pre)[(long)site * n + row];
-      }
-    } else {
-      const int nb = coarse_nb(a.oe.gc, site, t);
-      const cx<T>* src = reinterpret_cast<const cx<T>*>(a.src) + (long)a.oe.cidx[nb] * n;
-      cx<T> h{0, 0};
-      const cx<T>* Bt = B + (long)t * n * n;
-      for (int col = 0; col < n; ++col) cfma(h, Bt[(long)col * n + row], src[col]);
-      acc = a.sgn * h;
-    }
-    part[t * n + row] = acc;
-  }
-  __syncthreads();
-  if (threadIdx.x < n) {
-    cx<T> acc = part[row];
-    for (int q = 1; q < 9; ++q) acc = acc + part[q * n + row];
-    accs[row] = acc;
-  }
-  __syncthreads();
-  if (threadIdx.x < n) {
-    cx<T> res = accs[row];
-    if (a.post) {
-      const cx<T>* Di = reinterpret_cast<const cx<T>*>(a.Dinv) + (long)k * n * n;
-      res = cx<T>{0, 0};
-      for (int col = 0; col < n; ++col) cfma(res, Di[(long)col * n + row], accs[col]);
-    }
-    cx<T>* out = reinterpret_cast<cx<T>*>(a.out);
-    if (a.full_out)
-      out[(long)site * n + row] = res;
-    else
-      out[(long)k * n + row] = res;
-  }
-}
-
-// Several right-hand sides per CTA: every D_c (and D_oo^-1) entry a thread
-// loads is applied to up to RB right-hand sides held in registers.  Each CTA
-// lists the active right-hand sides and takes group blockIdx.y of RB of them.
+// Several right-hand sides per CTA: the CTA lists the active right-hand
+// sides and takes group blockIdx.y of RB of them; it stages the group's
+// source vectors at the site's 8 neighbours (and its own, mode 1) in shared
+// memory, then thread (t, row) applies row `row` of block t to all RB of them,
+// so every D_c entry it loads is used RB times and the vector reads are
+// shared-memory broadcasts.
 template <typename T, int RB>
 __global__ void k_oe_stencil_mr(OEArgs<T> a, int nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nv = a.oe.nv, n = 2 * nv;
-  cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);  // [RB][9][n]
-  cx<T>* accs = part + (size_t)RB * 9 * n;            // [RB][n]
+  cx<T>* xs = reinterpret_cast<cx<T>*>(smem_raw);      // [9][RB][n] sources
+  cx<T>* part = xs + (size_t)9 * RB * n;                // [RB][9][n]
+  cx<T>* accs = part + (size_t)RB * 9 * n;              // [RB][n]
   int* lst = reinterpret_cast<int*>(accs + (size_t)RB * n);  // [nrhs]
   __shared__ int nact;
   const int k = blockIdx.x;
@@ -634,96 +579,109 @@ __global__ void k_oe_stencil_mr(OEArgs<T> a, int nrhs) {
     nact = c;
   }
   __syncthreads();
-  const int na = nact;
-  for (int g0 = blockIdx.y * RB; g0 < na && g0 < (int)(blockIdx.y + 1) * RB; g0 += RB) {
-    const int gn = min(RB, na - g0);
-    if (t < 9) {
-      cx<T> acc[RB];
+  const int g0 = blockIdx.y * RB;
+  if (g0 >= nact) return;  // uniform over the CTA
+  const int gn = min(RB, nact - g0);
+  // stage the sources
+  for (int e = threadIdx.x; e < 9 * gn * n; e += blockDim.x) {
+    const int tt = e / (gn * n), q = (e / n) % gn, col = e % n;
+    const int r = lst[g0 + q];
+    cx<T> v{0, 0};
+    if (tt == 0) {
+      if (a.mode == 1) v = reinterpret_cast<const cx<T>*>(a.pre + r * a.p_str)[(long)k * n + col];
+    } else {
+      const int nb = coarse_nb(a.oe.gc, site, tt);
+      v = reinterpret_cast<const cx<T>*>(a.src + r * a.s_str)[(long)a.oe.cidx[nb] * n + col];
+    }
+    xs[((size_t)tt * RB + q) * n + col] = v;
+  }
+  __syncthreads();
+  if (t < 9) {
+    cx<T> acc[RB];
 #pragma unroll
-      for (int q = 0; q < RB; ++q) acc[q] = cx<T>{0, 0};
-      if (t == 0) {
-        if (a.mode == 1) {
-          for (int col = 0; col < n; ++col) {
-            const cx<T> bv = B[(long)col * n + row];
+    for (int q = 0; q < RB; ++q) acc[q] = cx<T>{0, 0};
+    const bool apply = t > 0 || a.mode == 1;
+    if (apply) {
+      const cx<T>* Bt = B + (long)t * n * n;
+      const cx<T>* xt = xs + (size_t)t * RB * n;
+      for (int col = 0; col < n; ++col) {
+        const cx<T> bv = Bt[(long)col * n + row];
 #pragma unroll
-            for (int q = 0; q < RB; ++q)
-              if (q < gn) cfma(acc[q], bv, reinterpret_cast<const cx<T>*>(a.pre + lst[g0 + q] * a.p_str)[(long)k * n + col]);
+        for (int q = 0; q < RB; ++q)
+          if (q < gn) cfma(acc[q], bv, xt[(size_t)q * n + col]);
+      }
+    }
+    if (t == 0) {
+      if (a.mode == 1) {
+        const T sg = row < nv ? -a.mu_c : a.mu_c;  // i mu_c Gamma5_c
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+          if (q < gn) {
+            const cx<T> x = xs[(size_t)q * n + row];
+            acc[q].r -= sg * x.i;
+            acc[q].i += sg * x.r;
           }
-          const T sg = row < nv ? -a.mu_c : a.mu_c;
+      } else if (a.mode == 2) {
 #pragma unroll
-          for (int q = 0; q < RB; ++q)
-            if (q < gn) {
-              const cx<T> x = reinterpret_cast<const cx<T>*>(a.pre + lst[g0 + q] * a.p_str)[(long)k * n + row];
-              acc[q].r -= sg * x.i;
-              acc[q].i += sg * x.r;
-            }
-        } else if (a.mode == 2) {
-#pragma unroll
-          for (int q = 0; q < RB; ++q)
-            if (q < gn) acc[q] = reinterpret_cast<const cx<T>*>(a.pre + lst[g0 + q] * a.p_str)[(long)site * n + row];
-        }
-      } else {
-        const int nb = coarse_nb(a.oe.gc, site, t);
-        const long soff = (long)a.oe.cidx[nb] * n;
-        const cx<T>* Bt = B + (long)t * n * n;
-        for (int col = 0; col < n; ++col) {
-          const cx<T> bv = Bt[(long)col * n + row];
-#pragma unroll
-          for (int q = 0; q < RB; ++q)
-            if (q < gn) cfma(acc[q], bv, reinterpret_cast<const cx<T>*>(a.src + lst[g0 + q] * a.s_str)[soff + col]);
-        }
-#pragma unroll
-        for (int q = 0; q < RB; ++q) acc[q] = a.sgn * acc[q];
+        for (int q = 0; q < RB; ++q)
+          if (q < gn) acc[q] = reinterpret_cast<const cx<T>*>(a.pre + lst[g0 + q] * a.p_str)[(long)site * n + row];
       }
+    } else {
 #pragma unroll
-      for (int q = 0; q < RB; ++q)
-        if (q < gn) part[((size_t)q * 9 + t) * n + row] = acc[q];
+      for (int q = 0; q < RB; ++q) acc[q] = a.sgn * acc[q];
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < gn * n; e += blockDim.x) {
-      const int q = e / n, rr = e % n;
-      cx<T> s = part[((size_t)q * 9) * n + rr];
-      for (int tt = 1; tt < 9; ++tt) s = s + part[((size_t)q * 9 + tt) * n + rr];
-      accs[(size_t)q * n + rr] = s;
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+      if (q < gn) part[((size_t)q * 9 + t) * n + row] = acc[q];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < gn * n; e += blockDim.x) {
+    const int q = e / n, rr = e % n;
+    cx<T> sum = part[((size_t)q * 9) * n + rr];
+    for (int tt = 1; tt < 9; ++tt) sum = sum + part[((size_t)q * 9 + tt) * n + rr];
+    accs[(size_t)q * n + rr] = sum;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < gn * n; e += blockDim.x) {
+    const int q = e / n, rr = e % n;
+    cx<T> res = accs[(size_t)q * n + rr];
+    if (a.post) {
+      const cx<T>* Di = reinterpret_cast<const cx<T>*>(a.Dinv) + (long)k * n * n;
+      res = cx<T>{0, 0};
+      for (int col = 0; col < n; ++col) cfma(res, Di[(long)col * n + rr], accs[(size_t)q * n + col]);
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < gn * n; e += blockDim.x) {
-      const int q = e / n, rr = e % n;
-      cx<T> res = accs[(size_t)q * n + rr];
-      if (a.post) {
-        const cx<T>* Di = reinterpret_cast<const cx<T>*>(a.Dinv) + (long)k * n * n;
-        res = cx<T>{0, 0};
-        for (int col = 0; col < n; ++col) cfma(res, Di[(long)col * n + rr], accs[(size_t)q * n + col]);
-      }
-      cx<T>* out = reinterpret_cast<cx<T>*>(a.out + lst[g0 + q] * a.o_str);
-      if (a.full_out)
-        out[(long)site * n + rr] = res;
-      else
-        out[(long)k * n + rr] = res;
-    }
-    __syncthreads();
+    cx<T>* out = reinterpret_cast<cx<T>*>(a.out + lst[g0 + q] * a.o_str);
+    if (a.full_out)
+      out[(long)site * n + rr] = res;
+    else
+      out[(long)k * n + rr] = res;
   }
 }
 
-constexpr int kOeRB = 8;
+template <typename T, int RB>
+static void launch_oe_mr(const OEArgs<T>& a, cudaStream_t st, int nrhs) {
+  const int n = 2 * a.oe.nv;
+  const int threads = (9 * n + 31) / 32 * 32;
+  const size_t smem = (size_t)RB * 19 * n * sizeof(cx<T>) + (size_t)nrhs * sizeof(int);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_oe_stencil_mr<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  dim3 grid(a.oe.nhalf, (nrhs + RB - 1) / RB);
+  k_oe_stencil_mr<T, RB><<<grid, threads, smem, st>>>(a, nrhs);
+}
+
+// right-hand sides per CTA for batched launches (FP32 covers 12 point sources)
+template <typename T>
+constexpr int oe_batch_rb() { return sizeof(T) == 4 ? 12 : 4; }
 
 template <typename T>
 static void launch_oe_stencil(const OEArgs<T>& a, cudaStream_t st, int nrhs = 1) {
-  const int n = 2 * a.oe.nv;
-  const int threads = (9 * n + 31) / 32 * 32;
-  if (nrhs <= 2) {
-    dim3 grid(a.oe.nhalf, nrhs);
-    k_oe_stencil<T><<<grid, threads, 10 * n * sizeof(cx<T>), st>>>(a);
-    return;
-  }
-  const size_t smem = (size_t)kOeRB * 10 * n * sizeof(cx<T>) + (size_t)nrhs * sizeof(int);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_oe_stencil_mr<T, kOeRB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    attr = true;
-  }
-  dim3 grid(a.oe.nhalf, (nrhs + kOeRB - 1) / kOeRB);
-  k_oe_stencil_mr<T, kOeRB><<<grid, threads, smem, st>>>(a, nrhs);
+  if (nrhs == 1)
+    launch_oe_mr<T, 1>(a, st, 1);
+  else
+    launch_oe_mr<T, oe_batch_rb<T>()>(a, st, nrhs);
 }
 
 template <typename T>

@@ -131,6 +131,17 @@ T* W(tm_handle* h, const std::string& name, size_t count) {
 
 void sync(tm_handle* h) { CK(cudaStreamSynchronize(h->st)); }
 
+// like W, but zero-filled when (re)allocated: batched solvers run finished
+// right-hand sides through shared launches, so their slots must hold finite data
+template <typename T>
+T* Wz(tm_handle* h, const std::string& name, size_t count) {
+  Buf& b = h->work[name];
+  const bool fresh = b.n < count * sizeof(T);
+  T* p = W<T>(h, name, count);
+  if (fresh) CK(cudaMemsetAsync(p, 0, count * sizeof(T), h->st));
+  return p;
+}
+
 // ---------------------------------------------------------------------------
 // opt-in profiler: CUDA events around each launch on the handle's stream
 // ---------------------------------------------------------------------------
@@ -490,7 +501,7 @@ std::vector<int> coarse_solve(tm_handle* h, const T* b, T* x, int nrhs, double t
   T* xe = W<T>(h, "cb_xe", cv * nrhs);
   T* uo = W<T>(h, "cb_uo", cv * nrhs);
   T* w = W<T>(h, "cb_w", cv * nrhs);
-  T* Vb = W<T>(h, "cb_V", vstr * nrhs);
+  T* Vb = Wz<T>(h, "cb_V", vstr * nrhs);
   double* part = W<double>(h, "cb_part", std::max(multidot_scratch_doubles(nc, m + 1, nrhs), 2L * 304 * nrhs));
   double* dd = W<double>(h, "cb_dots", ds * nrhs);
   double* nrm = W<double>(h, "cb_nrm", nrhs);
@@ -656,7 +667,7 @@ std::vector<int> coarse_solve(tm_handle* h, const T* b, T* x, int nrhs, double t
     upload_mask(active, &kk);
     {
       Prof pf(h, PK_BLAS_COARSE, count(active));
-      launch_lincomb_b<T>(Vb, vstr, cv, kmax, dd, ds, xe, cv, nc, nrhs, act, h->st);
+      launch_lincomb_b<T, T>(Vb, vstr, cv, kmax, dd, ds, xe, cv, nc, nrhs, act, h->st);
       CKL();
     }
     // true residual of the reduced systems
@@ -796,6 +807,225 @@ KrylovOut solve_one(tm_handle* h, const double* b, double* x, double tol) {
     }
   };
   return krylov<double, T>(h, "fg", A, AZ, M, true, b, x, true, fr / 2, tol, h->p.restart, h->p.maxit);
+}
+
+// nb right-hand sides at once: nb independent FP64 FGMRES(restart) solves run
+// in lock-step (own Hessenberg matrix, restarts and stopping each), sharing
+// every launch: one multi-rhs D(mu) apply, one batched K-cycle (SAP,
+// restriction, batched coarse GMRES, prolongation) and batched CGS2 per step.
+// Finished right-hand sides are masked in the vector updates.  Layout: the
+// Krylov vectors of step j for all right-hand sides are one contiguous block
+// [nb][fine reals], so the multi-rhs operators apply to them directly.
+template <typename T>
+std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int nb, double tol) {
+  using cd = std::complex<double>;
+  const int m = h->p.restart, maxit = h->p.maxit;
+  const long fr = fine_reals(h), nc = fr / 2;
+  const long blk = fr * nb;               // one Krylov step for all right-hand sides
+  const long ds = 4 * kMaxDots + 2;
+  double* Vb = Wz<double>(h, "sb_V", (size_t)(m + 1) * blk);
+  T* Z = Wz<T>(h, "sb_Z", (size_t)m * blk);
+  double* w = W<double>(h, "sb_w", blk);
+  double* zt = std::is_same<T, double>::value ? nullptr : W<double>(h, "sb_z64", blk);
+  T* vt = std::is_same<T, double>::value ? nullptr : W<T>(h, "sb_vT", blk);
+  double* part = W<double>(h, "sb_part", std::max(multidot_scratch_doubles(nc, m + 1, nb), 2L * 304 * nb));
+  double* dd = W<double>(h, "sb_dots", ds * nb);
+  double* nrm = W<double>(h, "sb_nrm", nb);
+  int* act = W<int>(h, "sb_act", nb);
+  constexpr int kSlots = 8;
+  double* hb = host_scratch(h, (size_t)(ds + 1) * nb + (size_t)kSlots * nb);
+  double* hn_h = hb + (size_t)ds * nb;
+  int* hact0 = reinterpret_cast<int*>(hn_h + nb);
+  int slot = 0;
+  std::vector<KrylovOut> out(nb);
+  std::vector<double> bnorm(nb), beta(nb);
+  std::vector<int> kk(nb, 0);
+  std::vector<char> active(nb), inner(nb);
+  std::vector<cd> H((size_t)nb * (m + 1) * m), g((size_t)nb * (m + 1)), sn((size_t)nb * m);
+  std::vector<double> cs((size_t)nb * m);
+  auto count = [&](const std::vector<char>& msk) {
+    int c = 0;
+    for (char v : msk) c += v ? 1 : 0;
+    return c;
+  };
+  auto upload_mask = [&](const std::vector<char>& msk, const std::vector<int>* counts) {
+    if (slot >= kSlots) {
+      sync(h);
+      slot = 0;
+    }
+    int* ha = hact0 + (size_t)(slot++) * nb;
+    for (int r = 0; r < nb; ++r) ha[r] = msk[r] ? (counts ? (*counts)[r] : 1) : 0;
+    CK(cudaMemcpyAsync(act, ha, nb * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  };
+  auto read_norms = [&]() {
+    CK(cudaMemcpyAsync(hn_h, nrm, nb * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    slot = 0;
+  };
+  auto norms = [&](const double* v, const int* msk) {
+    Prof pf(h, PK_BLAS_FINE, nb, 2);
+    launch_norm2_b<double>(v, fr, nc, nrm, part, nb, msk, h->st);
+    CKL();
+  };
+  // preconditioner on the Krylov block v (all right-hand sides) into z
+  auto precondition = [&](const double* v, T* z) {
+    if constexpr (std::is_same<T, double>::value) {
+      kcycle<double>(h, v, z, nb);
+    } else {
+      {
+        Prof pf(h, PK_OTHER, nb);
+        launch_convert<double, T>(v, vt, blk, h->st);
+        CKL();
+      }
+      kcycle<T>(h, vt, z, nb);
+    }
+  };
+  auto apply_z = [&](const T* z, double* o) {
+    if constexpr (std::is_same<T, double>::value) {
+      dslash<double>(h, z, o, nullptr, nb);
+    } else {
+      {
+        Prof pf(h, PK_OTHER, nb);
+        launch_convert<T, double>(z, zt, blk, h->st);
+        CKL();
+      }
+      dslash<double>(h, zt, o, nullptr, nb);
+    }
+  };
+  norms(b, nullptr);
+  read_norms();
+  for (int r = 0; r < nb; ++r) {
+    bnorm[r] = std::sqrt(hn_h[r]);
+    if (!std::isfinite(bnorm[r])) raise(TM_ERR_NONFINITE, "non-finite right-hand side");
+  }
+  dslash<double>(h, x, Vb, b, nb);  // r = b - D x
+  norms(Vb, nullptr);
+  read_norms();
+  for (int r = 0; r < nb; ++r) {
+    beta[r] = std::sqrt(hn_h[r]);
+    active[r] = bnorm[r] > 0 && beta[r] > tol * bnorm[r] && out[r].iters < maxit;
+    if (bnorm[r] == 0) out[r].converged = true;
+  }
+  while (count(active)) {
+    for (int r = 0; r < nb; ++r) hn_h[r] = beta[r] * beta[r];
+    CK(cudaMemcpyAsync(nrm, hn_h, nb * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    upload_mask(active, nullptr);
+    {
+      Prof pf(h, PK_BLAS_FINE, count(active));
+      launch_scale_copy_b<double>(Vb, fr, Vb, fr, nrm, nc, nb, act, h->st);
+      CKL();
+    }
+    for (int r = 0; r < nb; ++r) {
+      inner[r] = active[r];
+      kk[r] = 0;
+      if (active[r]) {
+        std::fill(g.begin() + (size_t)r * (m + 1), g.begin() + (size_t)(r + 1) * (m + 1), cd(0));
+        g[(size_t)r * (m + 1)] = beta[r];
+      }
+    }
+    for (int k = 0; k < m && count(inner); ++k) {
+      const int na = count(inner);
+      double* vk = Vb + (long)k * blk;
+      T* zk = Z + (long)k * blk;
+      precondition(vk, zk);
+      apply_z(zk, w);
+      upload_mask(inner, nullptr);
+      double* d1 = dd;
+      double* d2 = dd + 2 * (k + 1);
+      {
+        Prof pf(h, PK_BLAS_FINE, na, 8);
+        launch_multidot_b<double>(Vb, fr, blk, k + 1, w, fr, nc, d1, ds, part, nb, act, h->st);
+        CKL();
+        launch_multi_caxpy_b<double>(Vb, fr, blk, k + 1, d1, ds, w, fr, nc, nb, act, h->st);
+        CKL();
+        launch_multidot_b<double>(Vb, fr, blk, k + 1, w, fr, nc, d2, ds, part, nb, act, h->st);
+        CKL();
+        launch_multi_caxpy_b<double>(Vb, fr, blk, k + 1, d2, ds, w, fr, nc, nb, act, h->st);
+        CKL();
+        launch_norm2_b<double>(w, fr, nc, nrm, part, nb, act, h->st);
+        CKL();
+        launch_scale_copy_b<double>(w, fr, Vb + (long)(k + 1) * blk, fr, nrm, nc, nb, act, h->st);
+        CKL();
+      }
+      CK(cudaMemcpy2DAsync(hb, 4 * (k + 1) * sizeof(double), dd, ds * sizeof(double), 4 * (k + 1) * sizeof(double), nb,
+                           cudaMemcpyDeviceToHost, h->st));
+      read_norms();
+      for (int r = 0; r < nb; ++r) {
+        if (!inner[r]) continue;
+        const double hn = std::sqrt(hn_h[r]);
+        if (!std::isfinite(hn)) raise(TM_ERR_NONFINITE, "non-finite Arnoldi vector");
+        const double* hr = hb + (size_t)r * 4 * (k + 1);
+        cd* Hr = H.data() + (size_t)r * (m + 1) * m;
+        cd* gr = g.data() + (size_t)r * (m + 1);
+        cd* snr = sn.data() + (size_t)r * m;
+        double* csr = cs.data() + (size_t)r * m;
+        std::vector<cd> col(m + 1, cd(0));
+        for (int j = 0; j <= k; ++j)
+          col[j] = cd(hr[2 * j] + hr[2 * (k + 1) + 2 * j], hr[2 * j + 1] + hr[2 * (k + 1) + 2 * j + 1]);
+        col[k + 1] = hn;
+        for (int j = 0; j < k; ++j) {
+          const cd t = csr[j] * col[j] + snr[j] * col[j + 1];
+          col[j + 1] = -std::conj(snr[j]) * col[j] + csr[j] * col[j + 1];
+          col[j] = t;
+        }
+        double c;
+        cd sg, rho;
+        givens(col[k], hn, c, sg, rho);
+        csr[k] = c;
+        snr[k] = sg;
+        col[k] = rho;
+        col[k + 1] = 0;
+        for (int j = 0; j <= m; ++j) Hr[(size_t)j * m + k] = col[j];
+        gr[k + 1] = -std::conj(sg) * gr[k];
+        gr[k] = c * gr[k];
+        ++out[r].iters;
+        kk[r] = k + 1;
+        if (hn == 0 || std::abs(gr[k + 1]) <= tol * bnorm[r] || out[r].iters >= maxit) inner[r] = 0;
+      }
+    }
+    int kmax = 0;
+    for (int r = 0; r < nb; ++r) {
+      if (!active[r]) continue;
+      const int k = kk[r];
+      kmax = std::max(kmax, k);
+      const cd* Hr = H.data() + (size_t)r * (m + 1) * m;
+      const cd* gr = g.data() + (size_t)r * (m + 1);
+      std::vector<cd> y(k);
+      for (int i = k - 1; i >= 0; --i) {
+        cd acc = gr[i];
+        for (int j = i + 1; j < k; ++j) acc -= Hr[(size_t)i * m + j] * y[j];
+        y[i] = acc / Hr[(size_t)i * m + i];
+      }
+      double* yr = hb + (size_t)r * ds;
+      for (int i = 0; i < k; ++i) {
+        yr[2 * i] = y[i].real();
+        yr[2 * i + 1] = y[i].imag();
+      }
+      ++out[r].restarts;
+    }
+    CK(cudaMemcpyAsync(dd, hb, ds * nb * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    upload_mask(active, &kk);
+    {
+      Prof pf(h, PK_BLAS_FINE, count(active));
+      launch_lincomb_b<T, double>(Z, fr, blk, kmax, dd, ds, x, fr, nc, nb, act, h->st);
+      CKL();
+    }
+    dslash<double>(h, x, Vb, b, nb);  // true residuals
+    upload_mask(active, nullptr);
+    norms(Vb, act);
+    read_norms();
+    for (int r = 0; r < nb; ++r) {
+      if (!active[r]) continue;
+      beta[r] = std::sqrt(hn_h[r]);
+      if (!std::isfinite(beta[r])) raise(TM_ERR_NONFINITE, "non-finite residual");
+      active[r] = beta[r] > tol * bnorm[r] && out[r].iters < maxit;
+    }
+  }
+  for (int r = 0; r < nb; ++r) {
+    out[r].relres = bnorm[r] > 0 ? beta[r] / bnorm[r] : 0.0;
+    out[r].converged = out[r].converged || beta[r] <= tol * bnorm[r];
+  }
+  return out;
 }
 
 // stage a natural (host or device) array of `bytes` on the device
@@ -1071,11 +1301,39 @@ tm_status tm_solve(tm_handle* h, const double* b, double* x, int nrhs, double to
     double* xd = xdev ? x : W<double>(h, "stage_x", one * nrhs / sizeof(double));
     if (!xdev) CK(cudaMemcpyAsync(xd, x, one * nrhs, cudaMemcpyHostToDevice, h->st));
     const long fr = fine_reals(h);
-    double* bf = W<double>(h, "s_b", fr);
-    double* xf = W<double>(h, "s_x", fr);
     h->coarse_iters = 0;
     h->kcycles = 0;
-    for (int r = 0; r < nrhs; ++r) {
+    const int batch = std::min(nrhs, h->p.max_rhs);
+    if (batch > 1) {
+      double* bf = W<double>(h, "sbatch_b", fr * batch);
+      double* xf = W<double>(h, "sbatch_x", fr * batch);
+      for (int r0 = 0; r0 < nrhs; r0 += batch) {
+        const int nb = std::min(batch, nrhs - r0);
+        {
+          Prof pf(h, PK_OTHER, nb, 2);
+          launch_pack_spinor<double>(bd + (size_t)r0 * V * 24, bf, h->g, nb, h->st);
+          CKL();
+          launch_pack_spinor<double>(xd + (size_t)r0 * V * 24, xf, h->g, nb, h->st);
+          CKL();
+        }
+        std::vector<KrylovOut> ks = h->p.cycle_prec == TM_F64 ? solve_batch<double>(h, bf, xf, nb, tol)
+                                                             : solve_batch<float>(h, bf, xf, nb, tol);
+        {
+          Prof pf(h, PK_OTHER, nb);
+          launch_unpack_spinor<double>(xf, xd + (size_t)r0 * V * 24, h->g, nb, h->st);
+          CKL();
+        }
+        for (const KrylovOut& k : ks) {
+          loc.iters += k.iters;
+          loc.restarts += k.restarts;
+          loc.true_relres = std::max(loc.true_relres, k.relres);
+          if (!k.converged) loc.converged = 0;
+        }
+      }
+    }
+    double* bf = W<double>(h, "s_b", fr);
+    double* xf = W<double>(h, "s_x", fr);
+    for (int r = (batch > 1 ? nrhs : 0); r < nrhs; ++r) {
       {
         Prof pf(h, PK_OTHER, 1, 2);
         launch_pack_spinor<double>(bd + (size_t)r * V * 24, bf, h->g, 1, h->st);

@@ -147,9 +147,9 @@ template <typename T>
 void launch_multi_caxpy_b(const T* X, long xstr, long ldx, int k, const double* c, long cstr, T* y, long ystr,
                           long ncx, int nrhs, const int* active, cudaStream_t st);
 // y_r += sum_{j < min(k, active[r])} c[r * cstr + 2 j] X_rj  (active[r]: term count, 0 = skip)
-template <typename T>
-void launch_lincomb_b(const T* X, long xstr, long ldx, int k, const double* c, long cstr, T* y, long ystr, long ncx,
-                      int nrhs, const int* active, cudaStream_t st);
+template <typename Tx, typename Ty>
+void launch_lincomb_b(const Tx* X, long xstr, long ldx, int k, const double* c, long cstr, Ty* y, long ystr,
+                      long ncx, int nrhs, const int* active, cudaStream_t st);
 // out[r] = ||y_r||^2
 template <typename T>
 void launch_norm2_b(const T* y, long ystr, long ncx, double* out, double* scratch, int nrhs, const int* active,
