@@ -164,6 +164,15 @@ tm_status tm_set_mu(tm_handle* h, double mu, double delta);
  * info filled), TM_ERR_NONFINITE. */
 tm_status tm_solve(tm_handle* h, const double* b, double* x, int nrhs, double tol, tm_solve_info* info);
 
+/* Squared-operator solve with one setup (Sec. 1: the same setup serves
+ * D(+mu) and D(-mu); Sec. 3: the squared operator is inverted by two solves
+ * of the non-squared operator): x = (D(mu)^dagger D(mu))^-1 b computed as
+ * D(mu)^-1 Gamma5 D(-mu)^-1 Gamma5 b, using D(mu)^dagger = Gamma5 D(-mu) Gamma5.
+ * The D(-mu) solve starts from zero, the D(mu) solve from x; both run to tol.
+ * Arguments, layouts and errors as tm_solve; info sums both solves.  The
+ * handle is left at +mu. */
+tm_status tm_solve_squared(tm_handle* h, const double* b, double* x, int nrhs, double tol, tm_solve_info* info);
+
 /* Bytes of one field of nrhs vectors: level 0 = fine spinors, level 1 =
  * coarse vectors; prec TM_F64 or TM_F32.  0 for invalid arguments. */
 size_t tm_field_bytes(const tm_handle* h, int level, int prec, int nrhs);

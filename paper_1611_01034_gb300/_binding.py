@@ -55,6 +55,7 @@ _SIGS = {
     "tm_setup_from_vectors": (c_int, [c_void_p, c_void_p]),
     "tm_set_mu": (c_int, [c_void_p, c_double, c_double]),
     "tm_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
+    "tm_solve_squared": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
     "tm_field_bytes": (c_size_t, [c_void_p, c_int, c_int, c_int]),
     "tm_pack": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
     "tm_unpack": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
@@ -179,6 +180,14 @@ def tm_set_mu(h, mu: float, delta: float) -> None:
 def tm_solve(h, b, x, nrhs: int, tol: float):
     info = tm_solve_info()
     st = lib().tm_solve(h, _ptr(b), _ptr(x), nrhs, tol, ctypes.byref(info))
+    if st not in (TM_OK, TM_ERR_NOT_CONVERGED):
+        _check(st, h)
+    return st, info
+
+
+def tm_solve_squared(h, b, x, nrhs: int, tol: float):
+    info = tm_solve_info()
+    st = lib().tm_solve_squared(h, _ptr(b), _ptr(x), nrhs, tol, ctypes.byref(info))
     if st not in (TM_OK, TM_ERR_NOT_CONVERGED):
         _check(st, h)
     return st, info

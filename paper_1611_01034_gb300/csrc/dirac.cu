@@ -61,6 +61,19 @@ template void launch_pack_spinor<float>(const double*, float*, const Lat&, int, 
 template void launch_unpack_spinor<double>(const double*, double*, const Lat&, int, cudaStream_t);
 template void launch_unpack_spinor<float>(const float*, double*, const Lat&, int, cudaStream_t);
 
+// out = Gamma5 in on natural spinors: gamma5 = diag(-1,-1,+1,+1) negates the
+// first six complex components (spins 0, 1) of every site
+__global__ void k_gamma5_nat(const double* __restrict__ in, double* __restrict__ out, long nsites) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nsites * 24; i += (long)gridDim.x * blockDim.x)
+    out[i] = (i % 24) < 12 ? -in[i] : in[i];
+}
+
+void launch_gamma5_nat(const double* in, double* out, long nsites, cudaStream_t st) {
+  long blocks = (nsites * 24 + 255) / 256;
+  if (blocks > 152L * 16) blocks = 152L * 16;
+  k_gamma5_nat<<<(int)blocks, 256, 0, st>>>(in, out, nsites);
+}
+
 // ===========================================================================
 // 3x3 matrices for the gauge-field kernels (FP64, setup only)
 // ===========================================================================

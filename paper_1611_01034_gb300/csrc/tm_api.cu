@@ -1071,6 +1071,79 @@ void unpack_fine(tm_handle* h, const void* f, double* nat, int nrhs) {
   CKL();
 }
 
+// Solve D(mu) x_r = b_r for natural device arrays (x holds the start vectors);
+// accumulates statistics into loc.
+void solve_core(tm_handle* h, const double* bd, double* xd, int nrhs, double tol, tm_solve_info& loc) {
+  const long V = h->g.V;
+  const long fr = fine_reals(h);
+  const int batch = std::min(nrhs, h->p.max_rhs);
+  if (batch > 1) {
+    double* bf = W<double>(h, "sbatch_b", fr * batch);
+    double* xf = W<double>(h, "sbatch_x", fr * batch);
+    for (int r0 = 0; r0 < nrhs; r0 += batch) {
+      const int nb = std::min(batch, nrhs - r0);
+      {
+        Prof pf(h, PK_OTHER, nb, 2);
+        launch_pack_spinor<double>(bd + (size_t)r0 * V * 24, bf, h->g, nb, h->st);
+        CKL();
+        launch_pack_spinor<double>(xd + (size_t)r0 * V * 24, xf, h->g, nb, h->st);
+        CKL();
+      }
+      std::vector<KrylovOut> ks = h->p.cycle_prec == TM_F64 ? solve_batch<double>(h, bf, xf, nb, tol)
+                                                           : solve_batch<float>(h, bf, xf, nb, tol);
+      {
+        Prof pf(h, PK_OTHER, nb);
+        launch_unpack_spinor<double>(xf, xd + (size_t)r0 * V * 24, h->g, nb, h->st);
+        CKL();
+      }
+      for (const KrylovOut& k : ks) {
+        loc.iters += k.iters;
+        loc.restarts += k.restarts;
+        loc.true_relres = std::max(loc.true_relres, k.relres);
+        if (!k.converged) loc.converged = 0;
+      }
+    }
+  }
+  double* bf = W<double>(h, "s_b", fr);
+  double* xf = W<double>(h, "s_x", fr);
+  for (int r = (batch > 1 ? nrhs : 0); r < nrhs; ++r) {
+    {
+      Prof pf(h, PK_OTHER, 1, 2);
+      launch_pack_spinor<double>(bd + (size_t)r * V * 24, bf, h->g, 1, h->st);
+      CKL();
+      launch_pack_spinor<double>(xd + (size_t)r * V * 24, xf, h->g, 1, h->st);
+      CKL();
+    }
+    KrylovOut k = h->p.cycle_prec == TM_F64 ? solve_one<double>(h, bf, xf, tol) : solve_one<float>(h, bf, xf, tol);
+    {
+      Prof pf(h, PK_OTHER);
+      launch_unpack_spinor<double>(xf, xd + (size_t)r * V * 24, h->g, 1, h->st);
+      CKL();
+    }
+    loc.iters += k.iters;
+    loc.restarts += k.restarts;
+    loc.true_relres = std::max(loc.true_relres, k.relres);
+    if (!k.converged) loc.converged = 0;
+  }
+}
+
+// mu and delta of the handle; the odd-site inverses of the coarse Schur
+// complement depend on mu_c = delta mu and are recomputed
+void apply_mu(tm_handle* h, double mu, double delta) {
+  h->p.mu = mu;
+  h->p.delta = delta;
+  if (h->setup_ok) {
+    if (h->p.cycle_prec == TM_F64)
+      launch_oe_invert<double>(static_cast<double*>(h->Dc), static_cast<double*>(h->Dinv), h->oe, mu_c(h), h->d_err,
+                               h->st);
+    else
+      launch_oe_invert<float>(static_cast<float*>(h->Dc), static_cast<float*>(h->Dinv), h->oe, mu_c(h), h->d_err,
+                              h->st);
+    CKL();
+    check_flags(h);
+  }
+}
+
 }  // namespace
 
 #define API_BEGIN try {
@@ -1272,18 +1345,7 @@ tm_status tm_set_mu(tm_handle* h, double mu, double delta) {
   if (!h) return TM_ERR_ARG;
   API_BEGIN
   if (!(delta >= 1.0) || !std::isfinite(mu)) raise(TM_ERR_ARG, "need finite mu and delta >= 1");
-  h->p.mu = mu;
-  h->p.delta = delta;
-  if (h->setup_ok) {
-    if (h->p.cycle_prec == TM_F64)
-      launch_oe_invert<double>(static_cast<double*>(h->Dc), static_cast<double*>(h->Dinv), h->oe, mu_c(h), h->d_err,
-                               h->st);
-    else
-      launch_oe_invert<float>(static_cast<float*>(h->Dc), static_cast<float*>(h->Dinv), h->oe, mu_c(h), h->d_err,
-                              h->st);
-    CKL();
-    check_flags(h);
-  }
+  apply_mu(h, mu, delta);
   API_END
 }
 
@@ -1300,58 +1362,9 @@ tm_status tm_solve(tm_handle* h, const double* b, double* x, int nrhs, double to
     const double* bd = stage_in(h, b, one * nrhs, "stage_b");
     double* xd = xdev ? x : W<double>(h, "stage_x", one * nrhs / sizeof(double));
     if (!xdev) CK(cudaMemcpyAsync(xd, x, one * nrhs, cudaMemcpyHostToDevice, h->st));
-    const long fr = fine_reals(h);
     h->coarse_iters = 0;
     h->kcycles = 0;
-    const int batch = std::min(nrhs, h->p.max_rhs);
-    if (batch > 1) {
-      double* bf = W<double>(h, "sbatch_b", fr * batch);
-      double* xf = W<double>(h, "sbatch_x", fr * batch);
-      for (int r0 = 0; r0 < nrhs; r0 += batch) {
-        const int nb = std::min(batch, nrhs - r0);
-        {
-          Prof pf(h, PK_OTHER, nb, 2);
-          launch_pack_spinor<double>(bd + (size_t)r0 * V * 24, bf, h->g, nb, h->st);
-          CKL();
-          launch_pack_spinor<double>(xd + (size_t)r0 * V * 24, xf, h->g, nb, h->st);
-          CKL();
-        }
-        std::vector<KrylovOut> ks = h->p.cycle_prec == TM_F64 ? solve_batch<double>(h, bf, xf, nb, tol)
-                                                             : solve_batch<float>(h, bf, xf, nb, tol);
-        {
-          Prof pf(h, PK_OTHER, nb);
-          launch_unpack_spinor<double>(xf, xd + (size_t)r0 * V * 24, h->g, nb, h->st);
-          CKL();
-        }
-        for (const KrylovOut& k : ks) {
-          loc.iters += k.iters;
-          loc.restarts += k.restarts;
-          loc.true_relres = std::max(loc.true_relres, k.relres);
-          if (!k.converged) loc.converged = 0;
-        }
-      }
-    }
-    double* bf = W<double>(h, "s_b", fr);
-    double* xf = W<double>(h, "s_x", fr);
-    for (int r = (batch > 1 ? nrhs : 0); r < nrhs; ++r) {
-      {
-        Prof pf(h, PK_OTHER, 1, 2);
-        launch_pack_spinor<double>(bd + (size_t)r * V * 24, bf, h->g, 1, h->st);
-        CKL();
-        launch_pack_spinor<double>(xd + (size_t)r * V * 24, xf, h->g, 1, h->st);
-        CKL();
-      }
-      KrylovOut k = h->p.cycle_prec == TM_F64 ? solve_one<double>(h, bf, xf, tol) : solve_one<float>(h, bf, xf, tol);
-      {
-        Prof pf(h, PK_OTHER);
-        launch_unpack_spinor<double>(xf, xd + (size_t)r * V * 24, h->g, 1, h->st);
-        CKL();
-      }
-      loc.iters += k.iters;
-      loc.restarts += k.restarts;
-      loc.true_relres = std::max(loc.true_relres, k.relres);
-      if (!k.converged) loc.converged = 0;
-    }
+    solve_core(h, bd, xd, nrhs, tol, loc);
     if (!xdev) CK(cudaMemcpyAsync(x, xd, one * nrhs, cudaMemcpyDeviceToHost, h->st));
     sync(h);
     loc.coarse_iters = h->coarse_iters;
@@ -1368,6 +1381,60 @@ tm_status tm_solve(tm_handle* h, const double* b, double* x, int nrhs, double to
   } catch (const std::exception& e) {
     h->err = e.what();
     st = TM_ERR_CUDA;
+  }
+  if (info) *info = loc;
+  return st;
+}
+
+tm_status tm_solve_squared(tm_handle* h, const double* b, double* x, int nrhs, double tol, tm_solve_info* info) {
+  if (!h || !b || !x || nrhs < 1 || !(tol > 0)) return TM_ERR_ARG;
+  tm_solve_info loc{};
+  loc.converged = 1;
+  tm_status st = TM_OK;
+  const double mu = h->p.mu;
+  try {
+    if (!h->setup_ok) raise(TM_ERR_STATE, "tm_setup must come first");
+    const long V = h->g.V;
+    const size_t one = (size_t)V * 12 * 2 * sizeof(double);
+    const bool xdev = is_device_ptr(x);
+    const double* bd = stage_in(h, b, one * nrhs, "stage_b");
+    double* xd = xdev ? x : W<double>(h, "stage_x", one * nrhs / sizeof(double));
+    if (!xdev) CK(cudaMemcpyAsync(xd, x, one * nrhs, cudaMemcpyHostToDevice, h->st));
+    double* y = W<double>(h, "sq_y", one * nrhs / sizeof(double));
+    double* z = W<double>(h, "sq_z", one * nrhs / sizeof(double));
+    h->coarse_iters = 0;
+    h->kcycles = 0;
+    launch_gamma5_nat(bd, y, (long)V * nrhs, h->st);  // y = Gamma5 b
+    CKL();
+    CK(cudaMemsetAsync(z, 0, one * nrhs, h->st));
+    apply_mu(h, -mu, h->p.delta);  // D(-mu) z = Gamma5 b, same setup
+    solve_core(h, y, z, nrhs, tol, loc);
+    launch_gamma5_nat(z, y, (long)V * nrhs, h->st);  // y = Gamma5 z
+    CKL();
+    apply_mu(h, mu, h->p.delta);  // D(mu) x = Gamma5 z
+    solve_core(h, y, xd, nrhs, tol, loc);
+    if (!xdev) CK(cudaMemcpyAsync(x, xd, one * nrhs, cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    loc.coarse_iters = h->coarse_iters;
+    loc.kcycles = h->kcycles;
+    if (!loc.converged) {
+      h->err = "solver reached maxit";
+      st = TM_ERR_NOT_CONVERGED;
+    } else {
+      h->err.clear();
+    }
+  } catch (const TmError& e) {
+    h->err = e.m;
+    st = e.s;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    st = TM_ERR_CUDA;
+  }
+  if (h->p.mu != mu) {  // leave the handle at +mu even after an error
+    try {
+      apply_mu(h, mu, h->p.delta);
+    } catch (...) {
+    }
   }
   if (info) *info = loc;
   return st;

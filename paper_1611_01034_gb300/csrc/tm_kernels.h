@@ -19,6 +19,8 @@ void launch_pack_gauge(const double* nat, double* g64, float* g32, const Lat& g,
 // clover blocks (m0 + 4 included, mu-free) from the natural gauge field
 void launch_clover(const double* nat, double* c64, float* c32, const Lat& g, double m0, double c_sw,
                    cudaStream_t st);
+// out = Gamma5 in on natural spinor arrays of nsites sites (in may equal out)
+void launch_gamma5_nat(const double* in, double* out, long nsites, cudaStream_t st);
 // out = D(mu) in (res == nullptr) or out = b - D(mu) in
 template <typename T>
 void launch_dslash(const T* gauge, const T* clover, const T* in, T* out, const T* b, const Lat& g,

@@ -127,3 +127,25 @@ def test_two_level_solve_matches_dense_lu():
     # the preconditioner is doing its job: far fewer steps than unpreconditioned GMRES
     plain = gmres(tl.op.apply, b, tol=1e-10, restart=25, maxit=res.iters * 3)
     assert not plain.converged
+
+
+def test_squared_operator_solve_with_one_setup():
+    """Sec. 1 and 3: one setup serves D(+mu) and D(-mu); (D^dagger D)^-1 b
+    from two non-squared solves satisfies D(mu)^dagger D(mu) x = b, with
+    D(mu)^dagger applied as Gamma5 D(-mu) Gamma5 and checked densely."""
+    from oracle.dirac import gamma5_field
+    L = (4, 4, 4, 4)
+    prm = AMGParams(m0=1 / (2 * 0.13) - 4, c_sw=1.0, mu=0.01, delta=2.0, nv=8,
+                    agg=(2, 2, 2, 2), sap_block=(2, 2, 2, 2), setup_iters=1)
+    tl = TwoLevel(inputs.gauge_field(L, 0.3, 1), prm)
+    tl.setup(inputs.random_test_vectors(L, prm.nv, 2001))
+    b = inputs.gaussian_spinor(L, 1001)
+    x, (r1, r2) = tl.solve_squared(b, tol=1e-11)
+    assert r1.converged and r2.converged and tl.prm.mu == 0.01
+    D = dense_matrix(tl.op.apply, L)
+    ddx = D.conj().T @ (D @ x.ravel())
+    assert np.linalg.norm(ddx - b.ravel()) / np.linalg.norm(b) < 1e-8
+    # D(mu)^dagger = Gamma5 D(-mu) Gamma5 on a vector
+    Dm = tl.op.with_mu(-tl.op.mu)
+    y = inputs.gaussian_spinor(L, 5)
+    assert np.allclose(gamma5_field(Dm.apply(gamma5_field(y))).ravel(), D.conj().T @ y.ravel(), atol=1e-12)
