@@ -72,7 +72,12 @@ enum {
   TM_EXPORT_DC = 1,      /* D_c blocks, [Tc][Zc][Yc][Xc][9][2Nv row][2Nv col], mu-free;
                             block 0 self, 1 + 2 mu forward (to x+mu), 2 + 2 mu backward */
   TM_EXPORT_CLOVER = 2,  /* A(x) chiral blocks incl. (m0+4), [T][Z][Y][X][2][6][6] */
-  TM_EXPORT_TV = 3       /* current test vectors, natural [Nv][T][Z][Y][X][4][3] */
+  TM_EXPORT_TV = 3,      /* current test vectors, natural [Nv][T][Z][Y][X][4][3] */
+  /* three-level handles only (levels = 3), after a setup; level-1 vectors
+     are natural [Tc][Zc][Yc][Xc][2Nv] complex128 */
+  TM_EXPORT_P2 = 4,      /* P2 columns as level-1 vectors, [2Nv2][level-1 vector] */
+  TM_EXPORT_DC2 = 5,     /* D_c2 blocks, [T2][Z2][Y2][X2][9][2Nv2 row][2Nv2 col], mu-free */
+  TM_EXPORT_TV1 = 6      /* level-1 test vectors, [Nv2][level-1 vector] */
 };
 
 typedef struct {
@@ -97,6 +102,19 @@ typedef struct {
   int maxit;            /* outer FGMRES iteration cap */
   int cycle_prec;       /* TM_F64 or TM_F32: precision of smoother, P, D_c, coarse solve */
   int max_rhs;          /* largest nrhs passed to field-level calls */
+  /* Third level (Sec. 2: DD-alphaAMG recurses; the paper runs three levels
+     on its large lattices).  levels = 2 ignores everything below. */
+  int levels;           /* 2 or 3 */
+  int nv2;              /* level-1 test vectors (1..28) */
+  int agg2[4];          /* level-2 aggregate dims in coarse sites; level-2 extents even */
+  int sap_block1[4];    /* level-1 SAP block dims; block counts per dimension even */
+  int mr_iters1;        /* MR steps per level-1 block solve */
+  int pre_smooth1;      /* level-1 j of eq. (1) */
+  int post_smooth1;     /* level-1 k of eq. (1) */
+  int init_sweeps1;     /* level-1 SAP sweeps on D_c1 w = 0 applied to the random w */
+  int coarse_setup_iters; /* level-1 adaptive passes inside each fine setup iteration */
+  double coarsest_tol;  /* level-2 GMRES tolerance */
+  int coarsest_maxit;   /* level-2 GMRES iteration cap */
 } tm_params;
 
 typedef struct {
@@ -111,7 +129,10 @@ typedef struct {
 /* Fill p with the defaults: bc_t = -1, delta = 1, nv = 20, agg = sap_block
  * = 4^4, mr_iters = 4, pre = 0, post = 4, init_sweeps = 3, setup_iters = 3,
  * coarse_tol = 5e-2, coarse_restart = 30, coarse_maxit = 200, restart = 25,
- * maxit = 1000, cycle_prec = TM_F32, max_rhs = 1.  L, m0, c_sw, mu are 0. */
+ * maxit = 1000, cycle_prec = TM_F32, max_rhs = 1, levels = 2, nv2 = 28,
+ * agg2 = sap_block1 = 2^4, mr_iters1 = 4, pre_smooth1 = 0, post_smooth1 = 2,
+ * init_sweeps1 = 3, coarse_setup_iters = 3, coarsest_tol = 5e-2,
+ * coarsest_maxit = 200.  L, m0, c_sw, mu are 0. */
 void tm_params_default(tm_params* p);
 
 /* Validate p and allocate a handle bound to a CUDA stream (cudaStream_t,
@@ -142,12 +163,20 @@ tm_status tm_load_gauge(tm_handle* h, const double* gauge);
  * (per aggregate and chirality thin QR, Gamma5 P = P Gamma5_c) and
  * D_c(delta mu) are built; then setup_iters times every v_i <- B(v_i) with
  * the current K-cycle B, normalised, and P, D_c rebuilt.
+ * Three levels (levels = 3): test_vectors continues with nv2 level-1 random
+ * vectors (natural [nv2][Tc][Zc][Yc][Xc][2Nv]); after P, D_c1 they get
+ * init_sweeps1 level-1 SAP sweeps on D_c1(mu) w = 0, are normalised and give
+ * P2, D_c2; each fine iteration then also rebuilds P2, D_c2 from the current
+ * w_j, and finally coarse_setup_iters times every w_j <- B1(w_j) with the
+ * level-1 K-cycle, normalised, P2 and D_c2 rebuilt (Sec. 3: the fine and the
+ * coarse setup iteration counts).
  * Errors: TM_ERR_STATE (no gauge), TM_ERR_ARG (rank-deficient aggregate),
  * TM_ERR_NONFINITE. */
 tm_status tm_setup(tm_handle* h, const double* test_vectors);
 
 /* Build P and D_c directly from the given vectors (no smoothing, no
- * iterations): the interpolation of Sec. 1 for a fixed set of v_i. */
+ * iterations): the interpolation of Sec. 1 for a fixed set of v_i (with three
+ * levels also P2, D_c2 from the appended level-1 vectors, as in tm_setup). */
 tm_status tm_setup_from_vectors(tm_handle* h, const double* test_vectors);
 
 /* Change mu and delta without a new setup (Sec. 1: D_c(mu) = D_c +
@@ -225,6 +254,21 @@ tm_status tm_coarse_solve(tm_handle* h, int prec, const void* b, void* x, double
  *     threads, other streams) race on the array: serialise them. */
 tm_status tm_coarse_solve_noalloc(tm_handle* h, int prec, const void* b, void* x, double tol, int maxit,
                                   int* iters);
+
+/* Three-level handles: the level-1 pieces of the recursive cycle (Sec. 2),
+ * all on level-1 fields in cycle_prec after a setup; TM_ERR_ARG on a
+ * two-level handle.  With three levels, level 1 of tm_apply applies
+ * D_c1(mu) (the first coarse level keeps the fine twisted mass) and level 2
+ * applies D_c2(delta mu); tm_coarse_solve solves on level 2.
+ *   tm_sap1:      sweeps red/black SAP sweeps on D_c1(mu) x = b (b may be NULL)
+ *                 with mr_iters1 MR steps per block, x updated in place.
+ *   tm_restrict1: c2 = P2^dagger c1.   tm_prolong1: c1 (+)= P2 c2.
+ *   tm_kcycle1:   z = B1(v): eq. (1) on level 1 with pre_smooth1 / post_smooth1
+ *                 sweeps and a level-2 GMRES to coarsest_tol. */
+tm_status tm_sap1(tm_handle* h, int prec, const void* b, void* x, int sweeps, int nrhs);
+tm_status tm_restrict1(tm_handle* h, int prec, const void* c1, void* c2, int nrhs);
+tm_status tm_prolong1(tm_handle* h, int prec, const void* c2, void* c1, int nrhs, int accumulate);
+tm_status tm_kcycle1(tm_handle* h, int prec, const void* v, void* z, int nrhs);
 
 /* A7 preconditioner: z = B(v), one application of eq. (1) from a zero start
  * (pre SAP sweeps, coarse correction, post SAP sweeps).  Fine fields in

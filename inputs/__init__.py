@@ -121,6 +121,15 @@ def random_test_vectors(L, nv: int, seed: int) -> np.ndarray:
     return gaussian_spinor(L, seed, nrhs=nv)
 
 
+def random_coarse_vectors(Lc, n: int, count: int, seed: int) -> np.ndarray:
+    """Random vectors on a coarse lattice with n complex components per site
+    (the level-1 starting vectors w_j of a three-level setup, or coarse
+    right-hand sides).  Shape [count, Tc,Zc,Yc,Xc, n]; re, im ~ N(0, 1) i.i.d."""
+    rng = np.random.default_rng(seed)
+    shape = (count,) + tuple(int(x) for x in Lc) + (n,)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
 def random_gauge_transform(L, seed: int, eps: float = 1.0) -> np.ndarray:
     """A random SU(3) matrix g(x) per site, shape [T,Z,Y,X,3,3]."""
     T, Z, Y, X = (int(v) for v in L)

@@ -13,6 +13,7 @@ TM_ERR_NOT_CONVERGED, TM_ERR_TIMEOUT, TM_ERR_NOT_SU3 = -4, -5, -6
 TM_ERR_NONFINITE, TM_ERR_STATE = -7, -8
 TM_F64, TM_F32 = 0, 1
 TM_EXPORT_P, TM_EXPORT_DC, TM_EXPORT_CLOVER, TM_EXPORT_TV = 0, 1, 2, 3
+TM_EXPORT_P2, TM_EXPORT_DC2, TM_EXPORT_TV1 = 4, 5, 6
 
 
 class tm_params(ctypes.Structure):
@@ -23,6 +24,9 @@ class tm_params(ctypes.Structure):
         ("post_smooth", c_int), ("init_sweeps", c_int), ("setup_iters", c_int),
         ("coarse_tol", c_double), ("coarse_restart", c_int), ("coarse_maxit", c_int),
         ("restart", c_int), ("maxit", c_int), ("cycle_prec", c_int), ("max_rhs", c_int),
+        ("levels", c_int), ("nv2", c_int), ("agg2", c_int * 4), ("sap_block1", c_int * 4),
+        ("mr_iters1", c_int), ("pre_smooth1", c_int), ("post_smooth1", c_int), ("init_sweeps1", c_int),
+        ("coarse_setup_iters", c_int), ("coarsest_tol", c_double), ("coarsest_maxit", c_int),
     ]
 
 
@@ -66,6 +70,10 @@ _SIGS = {
     "tm_coarse_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, POINTER(c_int)]),
     "tm_coarse_solve_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, POINTER(c_int)]),
     "tm_kcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
+    "tm_sap1": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
+    "tm_restrict1": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
+    "tm_prolong1": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
+    "tm_kcycle1": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "tm_export": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
     "tm_synchronize": (c_int, [c_void_p]),
     "tm_profile": (c_int, [c_void_p, c_int]),
@@ -237,6 +245,22 @@ def tm_coarse_solve_noalloc(h, prec, b, x, tol, maxit) -> int:
 
 def tm_kcycle(h, prec, v, z, nrhs) -> None:
     _check(lib().tm_kcycle(h, prec, _ptr(v), _ptr(z), nrhs), h)
+
+
+def tm_sap1(h, prec, b, x, sweeps, nrhs) -> None:
+    _check(lib().tm_sap1(h, prec, _ptr(b), _ptr(x), sweeps, nrhs), h)
+
+
+def tm_restrict1(h, prec, c1, c2, nrhs) -> None:
+    _check(lib().tm_restrict1(h, prec, _ptr(c1), _ptr(c2), nrhs), h)
+
+
+def tm_prolong1(h, prec, c2, c1, nrhs, accumulate) -> None:
+    _check(lib().tm_prolong1(h, prec, _ptr(c2), _ptr(c1), nrhs, int(accumulate)), h)
+
+
+def tm_kcycle1(h, prec, v, z, nrhs) -> None:
+    _check(lib().tm_kcycle1(h, prec, _ptr(v), _ptr(z), nrhs), h)
 
 
 def tm_export(h, what, out, nbytes) -> None:

@@ -78,8 +78,21 @@ struct tm_handle {
   double* scratch = nullptr;  // reduction partials
   double* dsmall = nullptr;   // small device results
   double* hsmall = nullptr;   // pinned host mirror
-  double* hbig = nullptr;     // pinned host scratch for batched solves
-  size_t hbig_n = 0;
+  std::map<std::string, std::pair<double*, size_t>> hbufs;  // pinned host scratch per solver
+  // three levels: level-1 aggregation P2 and the coarsest operator D_c2
+  bool three = false;
+  Lat gc2{};
+  int n2 = 0, nhalf2 = 0;
+  CSapGeom csg{};
+  CAggGeom cag{};
+  OEGeom oe2{};
+  void* tv1 = nullptr;   // level-1 test vectors (Nv2 level-1 fields)
+  void* P2 = nullptr;
+  void* Dc2 = nullptr;
+  void* Dinv2 = nullptr;
+  int* d_even2 = nullptr;
+  int* d_odd2 = nullptr;
+  int* d_cidx2 = nullptr;
   std::map<std::string, Buf> work;
   bool gauge_ok = false, setup_ok = false;
   std::string err;
@@ -147,10 +160,11 @@ T* Wz(tm_handle* h, const std::string& name, size_t count) {
 // ---------------------------------------------------------------------------
 enum ProfKind {
   PK_DSLASH64 = 0, PK_DSLASH32, PK_SAP, PK_RESTRICT, PK_PROLONG, PK_COARSE_OE, PK_BLAS_FINE, PK_BLAS_COARSE,
-  PK_BUILD, PK_OTHER, PK_N
+  PK_BUILD, PK_OTHER, PK_CSAP, PK_LEVEL1, PK_N
 };
-const char* const kProfNames[PK_N] = {"dslash_f64", "dslash_f32",  "sap",         "restrict",     "prolong",
-                                      "coarse_oe",  "blas_fine",   "blas_coarse", "coarse_build", "other"};
+const char* const kProfNames[PK_N] = {"dslash_f64", "dslash_f32",   "sap",          "restrict",
+                                      "prolong",    "coarse_oe",    "blas_fine",    "blas_coarse",
+                                      "coarse_build", "other",      "coarse_sap",   "level1"};
 
 cudaEvent_t take_event(tm_handle* h) {
   if (!h->evpool.empty()) {
@@ -464,20 +478,39 @@ void build_coarse(tm_handle* h) {
   CKL();
   launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, static_cast<T*>(h->Dc), h->ag, h->p.bc_t, h->st);
   CKL();
-  launch_oe_invert<T>(static_cast<T*>(h->Dc), static_cast<T*>(h->Dinv), h->oe, mu_c(h), h->d_err, h->st);
-  CKL();
+  if (!h->three) {  // with three levels the odd-even solve runs on level 2
+    launch_oe_invert<T>(static_cast<T*>(h->Dc), static_cast<T*>(h->Dinv), h->oe, mu_c(h), h->d_err, h->st);
+    CKL();
+  }
 }
 
 // pinned host scratch of at least n doubles (grown on demand)
-double* host_scratch(tm_handle* h, size_t n) {
-  if (h->hbig_n < n) {
-    if (h->hbig) CK(cudaFreeHost(h->hbig));
-    h->hbig = nullptr;
-    h->hbig_n = 0;
-    CK(cudaMallocHost(&h->hbig, n * sizeof(double)));
-    h->hbig_n = n;
+// (solvers nest: the fine FGMRES calls the K-cycle, whose level-1 FGMRES calls
+// the coarsest GMRES, so each solver keeps its own buffer)
+double* host_scratch(tm_handle* h, const char* key, size_t n) {
+  auto& b = h->hbufs[key];
+  if (b.second < n) {
+    if (b.first) CK(cudaFreeHost(b.first));
+    b.first = nullptr;
+    b.second = 0;
+    CK(cudaMallocHost(&b.first, n * sizeof(double)));
+    b.second = n;
   }
-  return h->hbig;
+  return b.first;
+}
+
+// the level an odd-even GMRES runs on
+struct OELevel {
+  const void* Dc;
+  const void* Dinv;
+  OEGeom oe;
+  int n, nhalf, Vc;
+  double mu_c;
+};
+
+OELevel coarsest_level(tm_handle* h) {
+  if (h->three) return OELevel{h->Dc2, h->Dinv2, h->oe2, h->n2, h->nhalf2, h->gc2.V, mu_c(h)};
+  return OELevel{h->Dc, h->Dinv, h->oe, h->n, h->nhalf, h->gc.V, mu_c(h)};
 }
 
 // Odd-even GMRES(coarse_restart) on D_c(delta mu) x_r = b_r for nrhs full
@@ -486,16 +519,16 @@ double* host_scratch(tm_handle* h, size_t n) {
 // launches and one host synchronisation per Arnoldi step.  Finished right-hand
 // sides are masked out, so each one sees exactly the single-rhs arithmetic.
 template <typename T>
-std::vector<int> coarse_solve(tm_handle* h, const T* b, T* x, int nrhs, double tol, int maxit) {
+std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x, int nrhs, double tol, int maxit) {
   using cd = std::complex<double>;
   const int m = h->p.coarse_restart;
-  const long nc = (long)h->nhalf * h->n;        // complex numbers per compact vector
+  const long nc = (long)lv.nhalf * lv.n;         // complex numbers per compact vector
   const long cv = 2 * nc;                        // reals per compact vector
-  const long cf = 2 * (long)h->gc.V * h->n;      // reals per full coarse vector
+  const long cf = 2 * (long)lv.Vc * lv.n;        // reals per full coarse vector
   const long vstr = (long)(m + 1) * cv;          // per-rhs Krylov basis stride
   const long ds = 4 * kMaxDots + 2;              // per-rhs small-result stride (doubles)
-  const T* Dc = static_cast<const T*>(h->Dc);
-  const T* Di = static_cast<const T*>(h->Dinv);
+  const T* Dc = static_cast<const T*>(lv.Dc);
+  const T* Di = static_cast<const T*>(lv.Dinv);
   T* to = W<T>(h, "cb_to", cv * nrhs);
   T* bh = W<T>(h, "cb_bh", cv * nrhs);
   T* xe = W<T>(h, "cb_xe", cv * nrhs);
@@ -507,11 +540,11 @@ std::vector<int> coarse_solve(tm_handle* h, const T* b, T* x, int nrhs, double t
   double* nrm = W<double>(h, "cb_nrm", nrhs);
   int* act = W<int>(h, "cb_act", nrhs);
   constexpr int kSlots = 8;  // mask uploads between two stream synchronisations
-  double* hb = host_scratch(h, (size_t)(ds + 1) * nrhs + (size_t)kSlots * nrhs);
+  double* hb = host_scratch(h, "cb", (size_t)(ds + 1) * nrhs + (size_t)kSlots * nrhs);
   double* hn_h = hb + (size_t)ds * nrhs;                     // [nrhs] norms
   int* hact0 = reinterpret_cast<int*>(hn_h + nrhs);          // [kSlots][nrhs] masks
   int slot = 0;  // an async upload reads its slot later: reuse slots only after a sync
-  const double mc = mu_c(h);
+  const double mc = lv.mu_c;
 
   std::vector<double> bnorm(nrhs), beta(nrhs);
   std::vector<int> iters(nrhs, 0), kk(nrhs, 0);
@@ -540,13 +573,13 @@ std::vector<int> coarse_solve(tm_handle* h, const T* b, T* x, int nrhs, double t
   };
   auto schur = [&](const T* v, long vs, int units) {
     Prof pf(h, PK_COARSE_OE, units, 2);
-    launch_oe_schur_b<T>(Dc, Di, v, uo, w, h->oe, mc, nrhs, vs, cv, cv, act, h->st);
+    launch_oe_schur_b<T>(Dc, Di, v, uo, w, lv.oe, mc, nrhs, vs, cv, cv, act, h->st);
     CKL();
   };
 
   {
     Prof pf(h, PK_COARSE_OE, nrhs, 2);
-    launch_oe_prepare_b<T>(Dc, Di, b, to, bh, h->oe, nrhs, cf, cv, h->st);
+    launch_oe_prepare_b<T>(Dc, Di, b, to, bh, lv.oe, nrhs, cf, cv, h->st);
     CKL();
   }
   {
@@ -692,12 +725,18 @@ std::vector<int> coarse_solve(tm_handle* h, const T* b, T* x, int nrhs, double t
   }
   {
     Prof pf(h, PK_COARSE_OE, nrhs, 2);
-    launch_oe_reconstruct_b<T>(Dc, Di, b, xe, x, h->oe, nrhs, cf, cv, h->st);
+    launch_oe_reconstruct_b<T>(Dc, Di, b, xe, x, lv.oe, nrhs, cf, cv, h->st);
     CKL();
   }
   for (int r = 0; r < nrhs; ++r) h->coarse_iters += iters[r];
   return iters;
 }
+
+template <typename T>
+void level1_solve(tm_handle* h, const T* b1, T* x1, int nrhs, double tol, int maxit);
+template <typename Tv, typename Tz, typename FR, typename FAZ, typename FM>
+std::vector<KrylovOut> fgmres_b(tm_handle* h, const std::string& tag, int pk, FR resid, FAZ AZ, FM M, const Tv* b,
+                                Tv* x, int nb, long ncx, double tol, int m, int maxit);
 
 // z = B(v), eq. (1), nrhs fine fields in T
 template <typename T>
@@ -723,7 +762,10 @@ void kcycle(tm_handle* h, const T* v, T* z, int nrhs) {
     launch_restrict<T>(static_cast<const T*>(h->P), r, rc, h->ag, nrhs, h->st);
     CKL();
   }
-  coarse_solve<T>(h, rc, ec, nrhs, h->p.coarse_tol, h->p.coarse_maxit);
+  if (h->three)
+    level1_solve<T>(h, rc, ec, nrhs, h->p.coarse_tol, h->p.coarse_maxit);
+  else
+    coarse_solve<T>(h, coarsest_level(h), rc, ec, nrhs, h->p.coarse_tol, h->p.coarse_maxit);
   {
     Prof pf(h, PK_PROLONG, nrhs);
     launch_prolong<T>(static_cast<const T*>(h->P), ec, z, h->ag, nrhs, true, h->st);
@@ -731,6 +773,111 @@ void kcycle(tm_handle* h, const T* v, T* z, int nrhs) {
   }
   sap_sweeps<T>(h, v, z, h->p.post_smooth, nrhs);
   h->kcycles += nrhs;
+}
+
+// ---------------------------------------------------------------------------
+// first coarse level of three (Sec. 2: the standard hierarchy has three levels)
+// ---------------------------------------------------------------------------
+long level1_cx(tm_handle* h) { return (long)h->gc.V * h->n; }
+long level2_cx(tm_handle* h) { return (long)h->gc2.V * h->n2; }
+// twisted mass of level 1: mu itself with three levels, delta mu when it is the coarsest
+double mu_level1(tm_handle* h) { return h->three ? h->p.mu : mu_c(h); }
+
+template <typename T>
+void coarse_apply1(tm_handle* h, const T* in, T* out, int nrhs) {
+  Prof pf(h, PK_LEVEL1, nrhs);
+  launch_coarse_apply<T>(static_cast<const T*>(h->Dc), in, out, h->gc, h->p.nv, mu_level1(h), nrhs, h->st);
+  CKL();
+}
+
+template <typename T>
+void csap_sweeps(tm_handle* h, const T* b, T* x, int sweeps, int nrhs) {
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (int colour = 0; colour < 2; ++colour) {
+      Prof pf(h, PK_CSAP, nrhs);
+      launch_csap_colour<T>(static_cast<const T*>(h->Dc), b, x, h->csg, h->p.mu, h->p.mr_iters1, colour, nrhs,
+                            h->st);
+      CKL();
+    }
+}
+
+// z1 = B1(v1): the level-1 K-cycle (coarse SAP, P2^dagger, coarsest odd-even
+// GMRES on D_c2(delta mu), P2, coarse SAP)
+template <typename T>
+void kcycle1(tm_handle* h, const T* v, T* z, int nrhs) {
+  const long c1 = 2 * level1_cx(h), c2 = 2 * level2_cx(h);
+  {
+    Prof pf(h, PK_OTHER, nrhs);
+    launch_zero<T>(z, c1 * nrhs, h->st);
+    CKL();
+  }
+  csap_sweeps<T>(h, v, z, h->p.pre_smooth1, nrhs);
+  const T* r = v;
+  if (h->p.pre_smooth1 > 0) {
+    T* rr = W<T>(h, "k1_r", c1 * nrhs);
+    coarse_apply1<T>(h, z, rr, nrhs);
+    launch_sub_b<T>(v, c1, rr, c1, c1 / 2, nrhs, nullptr, h->st);
+    CKL();
+    r = rr;
+  }
+  T* r2 = W<T>(h, "k1_r2", c2 * nrhs);
+  T* e2 = W<T>(h, "k1_e2", c2 * nrhs);
+  {
+    Prof pf(h, PK_LEVEL1, nrhs);
+    launch_crestrict<T>(static_cast<const T*>(h->P2), r, r2, h->cag, nrhs, h->st);
+    CKL();
+  }
+  coarse_solve<T>(h, coarsest_level(h), r2, e2, nrhs, h->p.coarsest_tol, h->p.coarsest_maxit);
+  {
+    Prof pf(h, PK_LEVEL1, nrhs);
+    launch_cprolong<T>(static_cast<const T*>(h->P2), e2, z, h->cag, nrhs, true, h->st);
+    CKL();
+  }
+  csap_sweeps<T>(h, v, z, h->p.post_smooth1, nrhs);
+}
+
+// the coarse solve of the fine K-cycle with three levels: FGMRES(coarse_restart)
+// on D_c1(mu) from zero, preconditioned by the level-1 K-cycle
+template <typename T>
+void level1_solve(tm_handle* h, const T* b1, T* x1, int nrhs, double tol, int maxit) {
+  const long ncx = level1_cx(h);
+  {
+    Prof pf(h, PK_OTHER, nrhs);
+    launch_zero<T>(x1, 2 * ncx * nrhs, h->st);
+    CKL();
+  }
+  auto resid = [&](const T* xx, T* r) {
+    coarse_apply1<T>(h, xx, r, nrhs);
+    launch_sub_b<T>(b1, 2 * ncx, r, 2 * ncx, ncx, nrhs, nullptr, h->st);
+    CKL();
+  };
+  auto AZ = [&](const T* z, T* o) { coarse_apply1<T>(h, z, o, nrhs); };
+  auto M = [&](const T* v, T* z) { kcycle1<T>(h, v, z, nrhs); };
+  std::vector<KrylovOut> ks =
+      fgmres_b<T, T>(h, "l1", PK_BLAS_COARSE, resid, AZ, M, b1, x1, nrhs, ncx, tol, h->p.coarse_restart, maxit);
+  for (const KrylovOut& k : ks) h->coarse_iters += k.iters;
+}
+
+// P2 (holding the level-1 test vectors) -> orthonormal P2, D_c2, odd-site inverses
+template <typename T>
+void build_level2(tm_handle* h) {
+  Prof pf(h, PK_BUILD, 1, 3);
+  launch_corth<T>(static_cast<T*>(h->P2), h->cag, h->d_err, h->st);
+  CKL();
+  launch_cbuild<T>(static_cast<const T*>(h->Dc), static_cast<const T*>(h->P2), static_cast<T*>(h->Dc2), h->cag,
+                   h->st);
+  CKL();
+  launch_oe_invert<T>(static_cast<T*>(h->Dc2), static_cast<T*>(h->Dinv2), h->oe2, mu_c(h), h->d_err, h->st);
+  CKL();
+}
+
+template <typename T>
+void normalise_vecs(tm_handle* h, T* f, long ncx, int nrhs) {
+  Prof pf(h, PK_OTHER, nrhs, 3);
+  launch_norm2<T>(f, ncx, nrhs, h->dsmall, h->scratch, kScratchBlocks, h->st);
+  CKL();
+  launch_scale<T>(f, ncx, nrhs, h->dsmall, true, h->st);
+  CKL();
 }
 
 template <typename T>
@@ -745,7 +892,7 @@ void normalise_fields(tm_handle* h, T* f, int nrhs) {
 
 template <typename T>
 void setup_impl(tm_handle* h, const double* tv_dev, bool adaptive) {
-  const int nv = h->p.nv;
+  const int nv = h->p.nv, nv2 = h->p.nv2;
   const long fr = fine_reals(h);
   T* tv = static_cast<T*>(h->tv);
   T* P = static_cast<T*>(h->P);
@@ -760,6 +907,22 @@ void setup_impl(tm_handle* h, const double* tv_dev, bool adaptive) {
   }
   CK(cudaMemcpyAsync(P, tv, fr * nv * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
   build_coarse<T>(h);
+  const long c1 = 2 * level1_cx(h);
+  T* tv1 = static_cast<T*>(h->tv1);
+  T* P2 = static_cast<T*>(h->P2);
+  if (h->three) {  // level-1 initial phase from the level-1 random vectors
+    {
+      Prof pf(h, PK_OTHER, nv2);
+      launch_convert<double, T>(tv_dev + (size_t)nv * fr, tv1, c1 * nv2, h->st);
+      CKL();
+    }
+    if (adaptive) {
+      csap_sweeps<T>(h, nullptr, tv1, h->p.init_sweeps1, nv2);
+      normalise_vecs<T>(h, tv1, c1 / 2, nv2);
+    }
+    CK(cudaMemcpyAsync(P2, tv1, c1 * nv2 * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+    build_level2<T>(h);
+  }
   check_flags(h);
   if (adaptive) {
     T* z = W<T>(h, "setup_z", fr * nv);
@@ -769,7 +932,22 @@ void setup_impl(tm_handle* h, const double* tv_dev, bool adaptive) {
       normalise_fields<T>(h, tv, nv);
       CK(cudaMemcpyAsync(P, tv, fr * nv * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
       build_coarse<T>(h);
+      if (h->three) {
+        CK(cudaMemcpyAsync(P2, tv1, c1 * nv2 * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+        build_level2<T>(h);
+      }
       check_flags(h);
+    }
+    if (h->three) {
+      T* z1 = W<T>(h, "setup_z1", c1 * nv2);
+      for (int it = 0; it < h->p.coarse_setup_iters; ++it) {
+        kcycle1<T>(h, tv1, z1, nv2);
+        CK(cudaMemcpyAsync(tv1, z1, c1 * nv2 * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+        normalise_vecs<T>(h, tv1, c1 / 2, nv2);
+        CK(cudaMemcpyAsync(P2, tv1, c1 * nv2 * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+        build_level2<T>(h);
+        check_flags(h);
+      }
     }
   }
   sync(h);
@@ -816,24 +994,27 @@ KrylovOut solve_one(tm_handle* h, const double* b, double* x, double tol) {
 // Finished right-hand sides are masked in the vector updates.  Layout: the
 // Krylov vectors of step j for all right-hand sides are one contiguous block
 // [nb][fine reals], so the multi-rhs operators apply to them directly.
-template <typename T>
-std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int nb, double tol) {
+// Generic batched flexible GMRES(m): basis vectors in Tv, preconditioned
+// vectors in Tz, vectors of ncx complex numbers (fr = 2 ncx reals).
+//   resid(x, r): r = b - A x for all nb right-hand sides (contiguous blocks)
+//   AZ(z, w):    w = A z
+//   M(v, z):     z = preconditioner(v)
+template <typename Tv, typename Tz, typename FR, typename FAZ, typename FM>
+std::vector<KrylovOut> fgmres_b(tm_handle* h, const std::string& tag, int pk, FR resid, FAZ AZ, FM M, const Tv* b,
+                                Tv* x, int nb, long ncx, double tol, int m, int maxit) {
   using cd = std::complex<double>;
-  const int m = h->p.restart, maxit = h->p.maxit;
-  const long fr = fine_reals(h), nc = fr / 2;
+  const long fr = 2 * ncx, nc = ncx;
   const long blk = fr * nb;               // one Krylov step for all right-hand sides
   const long ds = 4 * kMaxDots + 2;
-  double* Vb = Wz<double>(h, "sb_V", (size_t)(m + 1) * blk);
-  T* Z = Wz<T>(h, "sb_Z", (size_t)m * blk);
-  double* w = W<double>(h, "sb_w", blk);
-  double* zt = std::is_same<T, double>::value ? nullptr : W<double>(h, "sb_z64", blk);
-  T* vt = std::is_same<T, double>::value ? nullptr : W<T>(h, "sb_vT", blk);
-  double* part = W<double>(h, "sb_part", std::max(multidot_scratch_doubles(nc, m + 1, nb), 2L * 304 * nb));
-  double* dd = W<double>(h, "sb_dots", ds * nb);
-  double* nrm = W<double>(h, "sb_nrm", nb);
-  int* act = W<int>(h, "sb_act", nb);
+  Tv* Vb = Wz<Tv>(h, tag + "_V", (size_t)(m + 1) * blk);
+  Tz* Z = Wz<Tz>(h, tag + "_Z", (size_t)m * blk);
+  Tv* w = W<Tv>(h, tag + "_w", blk);
+  double* part = W<double>(h, tag + "_part", std::max(multidot_scratch_doubles(nc, m + 1, nb), 2L * 304 * nb));
+  double* dd = W<double>(h, tag + "_dots", ds * nb);
+  double* nrm = W<double>(h, tag + "_nrm", nb);
+  int* act = W<int>(h, tag + "_act", nb);
   constexpr int kSlots = 8;
-  double* hb = host_scratch(h, (size_t)(ds + 1) * nb + (size_t)kSlots * nb);
+  double* hb = host_scratch(h, tag.c_str(), (size_t)(ds + 1) * nb + (size_t)kSlots * nb);
   double* hn_h = hb + (size_t)ds * nb;
   int* hact0 = reinterpret_cast<int*>(hn_h + nb);
   int slot = 0;
@@ -862,35 +1043,10 @@ std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int
     sync(h);
     slot = 0;
   };
-  auto norms = [&](const double* v, const int* msk) {
-    Prof pf(h, PK_BLAS_FINE, nb, 2);
-    launch_norm2_b<double>(v, fr, nc, nrm, part, nb, msk, h->st);
+  auto norms = [&](const Tv* v, const int* msk) {
+    Prof pf(h, pk, nb, 2);
+    launch_norm2_b<Tv>(v, fr, nc, nrm, part, nb, msk, h->st);
     CKL();
-  };
-  // preconditioner on the Krylov block v (all right-hand sides) into z
-  auto precondition = [&](const double* v, T* z) {
-    if constexpr (std::is_same<T, double>::value) {
-      kcycle<double>(h, v, z, nb);
-    } else {
-      {
-        Prof pf(h, PK_OTHER, nb);
-        launch_convert<double, T>(v, vt, blk, h->st);
-        CKL();
-      }
-      kcycle<T>(h, vt, z, nb);
-    }
-  };
-  auto apply_z = [&](const T* z, double* o) {
-    if constexpr (std::is_same<T, double>::value) {
-      dslash<double>(h, z, o, nullptr, nb);
-    } else {
-      {
-        Prof pf(h, PK_OTHER, nb);
-        launch_convert<T, double>(z, zt, blk, h->st);
-        CKL();
-      }
-      dslash<double>(h, zt, o, nullptr, nb);
-    }
   };
   norms(b, nullptr);
   read_norms();
@@ -898,7 +1054,7 @@ std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int
     bnorm[r] = std::sqrt(hn_h[r]);
     if (!std::isfinite(bnorm[r])) raise(TM_ERR_NONFINITE, "non-finite right-hand side");
   }
-  dslash<double>(h, x, Vb, b, nb);  // r = b - D x
+  resid(x, Vb);  // r = b - A x
   norms(Vb, nullptr);
   read_norms();
   for (int r = 0; r < nb; ++r) {
@@ -911,8 +1067,8 @@ std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int
     CK(cudaMemcpyAsync(nrm, hn_h, nb * sizeof(double), cudaMemcpyHostToDevice, h->st));
     upload_mask(active, nullptr);
     {
-      Prof pf(h, PK_BLAS_FINE, count(active));
-      launch_scale_copy_b<double>(Vb, fr, Vb, fr, nrm, nc, nb, act, h->st);
+      Prof pf(h, pk, count(active));
+      launch_scale_copy_b<Tv>(Vb, fr, Vb, fr, nrm, nc, nb, act, h->st);
       CKL();
     }
     for (int r = 0; r < nb; ++r) {
@@ -925,26 +1081,26 @@ std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int
     }
     for (int k = 0; k < m && count(inner); ++k) {
       const int na = count(inner);
-      double* vk = Vb + (long)k * blk;
-      T* zk = Z + (long)k * blk;
-      precondition(vk, zk);
-      apply_z(zk, w);
+      Tv* vk = Vb + (long)k * blk;
+      Tz* zk = Z + (long)k * blk;
+      M(vk, zk);
+      AZ(zk, w);
       upload_mask(inner, nullptr);
       double* d1 = dd;
       double* d2 = dd + 2 * (k + 1);
       {
-        Prof pf(h, PK_BLAS_FINE, na, 8);
-        launch_multidot_b<double>(Vb, fr, blk, k + 1, w, fr, nc, d1, ds, part, nb, act, h->st);
+        Prof pf(h, pk, na, 8);
+        launch_multidot_b<Tv>(Vb, fr, blk, k + 1, w, fr, nc, d1, ds, part, nb, act, h->st);
         CKL();
-        launch_multi_caxpy_b<double>(Vb, fr, blk, k + 1, d1, ds, w, fr, nc, nb, act, h->st);
+        launch_multi_caxpy_b<Tv>(Vb, fr, blk, k + 1, d1, ds, w, fr, nc, nb, act, h->st);
         CKL();
-        launch_multidot_b<double>(Vb, fr, blk, k + 1, w, fr, nc, d2, ds, part, nb, act, h->st);
+        launch_multidot_b<Tv>(Vb, fr, blk, k + 1, w, fr, nc, d2, ds, part, nb, act, h->st);
         CKL();
-        launch_multi_caxpy_b<double>(Vb, fr, blk, k + 1, d2, ds, w, fr, nc, nb, act, h->st);
+        launch_multi_caxpy_b<Tv>(Vb, fr, blk, k + 1, d2, ds, w, fr, nc, nb, act, h->st);
         CKL();
-        launch_norm2_b<double>(w, fr, nc, nrm, part, nb, act, h->st);
+        launch_norm2_b<Tv>(w, fr, nc, nrm, part, nb, act, h->st);
         CKL();
-        launch_scale_copy_b<double>(w, fr, Vb + (long)(k + 1) * blk, fr, nrm, nc, nb, act, h->st);
+        launch_scale_copy_b<Tv>(w, fr, Vb + (long)(k + 1) * blk, fr, nrm, nc, nb, act, h->st);
         CKL();
       }
       CK(cudaMemcpy2DAsync(hb, 4 * (k + 1) * sizeof(double), dd, ds * sizeof(double), 4 * (k + 1) * sizeof(double), nb,
@@ -1006,11 +1162,11 @@ std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int
     CK(cudaMemcpyAsync(dd, hb, ds * nb * sizeof(double), cudaMemcpyHostToDevice, h->st));
     upload_mask(active, &kk);
     {
-      Prof pf(h, PK_BLAS_FINE, count(active));
-      launch_lincomb_b<T, double>(Z, fr, blk, kmax, dd, ds, x, fr, nc, nb, act, h->st);
+      Prof pf(h, pk, count(active));
+      launch_lincomb_b<Tz, Tv>(Z, fr, blk, kmax, dd, ds, x, fr, nc, nb, act, h->st);
       CKL();
     }
-    dslash<double>(h, x, Vb, b, nb);  // true residuals
+    resid(x, Vb);  // true residuals
     upload_mask(active, nullptr);
     norms(Vb, act);
     read_norms();
@@ -1026,6 +1182,42 @@ std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int
     out[r].converged = out[r].converged || beta[r] <= tol * bnorm[r];
   }
   return out;
+}
+
+// the fine level: FP64 FGMRES, K-cycle in T
+template <typename T>
+std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int nb, double tol) {
+  const long fr = fine_reals(h);
+  const long blk = fr * nb;
+  double* zt = std::is_same<T, double>::value ? nullptr : W<double>(h, "sb_z64", blk);
+  T* vt = std::is_same<T, double>::value ? nullptr : W<T>(h, "sb_vT", blk);
+  auto resid = [&](const double* xx, double* r) { dslash<double>(h, xx, r, b, nb); };
+  auto M = [&](const double* v, T* z) {
+    if constexpr (std::is_same<T, double>::value) {
+      kcycle<double>(h, v, z, nb);
+    } else {
+      {
+        Prof pf(h, PK_OTHER, nb);
+        launch_convert<double, T>(v, vt, blk, h->st);
+        CKL();
+      }
+      kcycle<T>(h, vt, z, nb);
+    }
+  };
+  auto AZ = [&](const T* z, double* o) {
+    if constexpr (std::is_same<T, double>::value) {
+      dslash<double>(h, z, o, nullptr, nb);
+    } else {
+      {
+        Prof pf(h, PK_OTHER, nb);
+        launch_convert<T, double>(z, zt, blk, h->st);
+        CKL();
+      }
+      dslash<double>(h, zt, o, nullptr, nb);
+    }
+  };
+  return fgmres_b<double, T>(h, "sb", PK_BLAS_FINE, resid, AZ, M, b, x, nb, fr / 2, tol, h->p.restart,
+                             h->p.maxit);
 }
 
 // stage a natural (host or device) array of `bytes` on the device
@@ -1061,6 +1253,27 @@ void validate(const tm_params* p) {
   if (p->bc_t != 1.0 && p->bc_t != -1.0) bad("bc_t must be +1 or -1");
   if (!(p->delta >= 1.0)) bad("delta must be >= 1");
   if (p->max_rhs < 1) bad("max_rhs must be >= 1");
+  if (p->levels != 2 && p->levels != 3) bad("levels must be 2 or 3");
+  if (p->levels == 3) {
+    long a2 = 1, b1 = 1;
+    for (int d = 0; d < 4; ++d) {
+      const int l1 = p->L[d] / p->agg[d];
+      if (p->agg2[d] < 1 || l1 % p->agg2[d]) bad("level-1 lattice not divisible by agg2");
+      const int l2 = l1 / p->agg2[d];
+      if (l2 < 2 || l2 % 2) bad("level-2 extents must be even and >= 2 (odd-even coarsest solve)");
+      if (p->sap_block1[d] < 1 || l1 % p->sap_block1[d]) bad("level-1 lattice not divisible by sap_block1");
+      const int nb = l1 / p->sap_block1[d];
+      if (nb < 2 || nb % 2) bad("level-1 SAP block count per dimension must be even and >= 2");
+      a2 *= p->agg2[d];
+      b1 *= p->sap_block1[d];
+    }
+    if (p->nv2 < 1 || p->nv2 > 28) bad("nv2 must be in 1..28");
+    if (a2 * 2 * p->nv > 1024) bad("agg2 volume x 2 nv must be <= 1024");
+    if (b1 * 2 * p->nv > 1024) bad("sap_block1 volume x 2 nv must be <= 1024");
+    if (p->mr_iters1 < 0 || p->pre_smooth1 < 0 || p->post_smooth1 < 0 || p->init_sweeps1 < 0 ||
+        p->coarse_setup_iters < 0 || p->coarsest_maxit < 1)
+      bad("negative level-1 iteration count");
+  }
   const double lv = (double)p->L[0] * p->L[1] * p->L[2] * p->L[3];
   if (lv * 24.0 * p->max_rhs > 4.0e9 || lv * 24.0 * p->nv > 4.0e9) bad("lattice too large for 32-bit site indexing");
 }
@@ -1133,12 +1346,13 @@ void apply_mu(tm_handle* h, double mu, double delta) {
   h->p.mu = mu;
   h->p.delta = delta;
   if (h->setup_ok) {
+    void* Dc = h->three ? h->Dc2 : h->Dc;
+    void* Di = h->three ? h->Dinv2 : h->Dinv;
+    const OEGeom& oe = h->three ? h->oe2 : h->oe;
     if (h->p.cycle_prec == TM_F64)
-      launch_oe_invert<double>(static_cast<double*>(h->Dc), static_cast<double*>(h->Dinv), h->oe, mu_c(h), h->d_err,
-                               h->st);
+      launch_oe_invert<double>(static_cast<double*>(Dc), static_cast<double*>(Di), oe, mu_c(h), h->d_err, h->st);
     else
-      launch_oe_invert<float>(static_cast<float*>(h->Dc), static_cast<float*>(h->Dinv), h->oe, mu_c(h), h->d_err,
-                              h->st);
+      launch_oe_invert<float>(static_cast<float*>(Dc), static_cast<float*>(Di), oe, mu_c(h), h->d_err, h->st);
     CKL();
     check_flags(h);
   }
@@ -1181,6 +1395,16 @@ void tm_params_default(tm_params* p) {
   p->maxit = 1000;
   p->cycle_prec = TM_F32;
   p->max_rhs = 1;
+  p->levels = 2;
+  p->nv2 = 28;
+  for (int d = 0; d < 4; ++d) p->agg2[d] = p->sap_block1[d] = 2;
+  p->mr_iters1 = 4;
+  p->pre_smooth1 = 0;
+  p->post_smooth1 = 2;
+  p->init_sweeps1 = 3;
+  p->coarse_setup_iters = 3;
+  p->coarsest_tol = 5e-2;
+  p->coarsest_maxit = 200;
 }
 
 const char* tm_status_string(int s) {
@@ -1209,7 +1433,11 @@ void tm_destroy(tm_handle* h) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (h->hsmall) cudaFreeHost(h->hsmall);
-  if (h->hbig) cudaFreeHost(h->hbig);
+  for (auto& kv : h->hbufs)
+    if (kv.second.first) cudaFreeHost(kv.second.first);
+  void* p3[] = {h->tv1, h->P2, h->Dc2, h->Dinv2, h->d_even2, h->d_odd2, h->d_cidx2};
+  for (void* q : p3)
+    if (q) cudaFree(q);
   for (auto& r : h->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -1286,6 +1514,57 @@ tm_status tm_create(tm_handle** out, const tm_params* p, void* stream) {
     h->P = dalloc((size_t)p->nv * NR_SPINOR * V * cs);
     h->Dc = dalloc((size_t)h->gc.V * 9 * h->n * h->n * 2 * cs);
     h->Dinv = dalloc((size_t)h->nhalf * h->n * h->n * 2 * cs);
+    if (p->levels == 3) {
+      h->three = true;
+      int L2[4];
+      for (int d = 0; d < 4; ++d) L2[d] = Lc[d] / p->agg2[d];
+      h->gc2 = make_lat(L2);
+      h->n2 = 2 * p->nv2;
+      h->nhalf2 = h->gc2.V / 2;
+      h->csg.g = h->gc;
+      h->csg.n = h->n;
+      h->csg.bsites = 1;
+      h->cag.g1 = h->gc;
+      h->cag.g2 = h->gc2;
+      h->cag.asites = 1;
+      h->cag.nv1 = p->nv;
+      h->cag.nv2 = p->nv2;
+      for (int d = 0; d < 4; ++d) {
+        h->csg.blk[d] = p->sap_block1[d];
+        h->csg.nb[d] = Lc[d] / p->sap_block1[d];
+        h->csg.bsites *= p->sap_block1[d];
+        h->cag.agg[d] = p->agg2[d];
+        h->cag.asites *= p->agg2[d];
+      }
+      std::vector<int> ev2, od2, cidx2(h->gc2.V);
+      for (int a = 0; a < h->gc2.V; ++a) {
+        int c[4];
+        site_coords(h->gc2, a, c);
+        if ((c[0] + c[1] + c[2] + c[3]) % 2 == 0) {
+          cidx2[a] = (int)ev2.size();
+          ev2.push_back(a);
+        } else {
+          cidx2[a] = (int)od2.size();
+          od2.push_back(a);
+        }
+      }
+      h->d_even2 = static_cast<int*>(dalloc(ev2.size() * sizeof(int)));
+      h->d_odd2 = static_cast<int*>(dalloc(od2.size() * sizeof(int)));
+      h->d_cidx2 = static_cast<int*>(dalloc(cidx2.size() * sizeof(int)));
+      CK(cudaMemcpy(h->d_even2, ev2.data(), ev2.size() * sizeof(int), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_odd2, od2.data(), od2.size() * sizeof(int), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_cidx2, cidx2.data(), cidx2.size() * sizeof(int), cudaMemcpyHostToDevice));
+      h->oe2.gc = h->gc2;
+      h->oe2.nv = p->nv2;
+      h->oe2.nhalf = h->nhalf2;
+      h->oe2.even_site = h->d_even2;
+      h->oe2.odd_site = h->d_odd2;
+      h->oe2.cidx = h->d_cidx2;
+      h->tv1 = dalloc((size_t)p->nv2 * h->gc.V * h->n * 2 * cs);
+      h->P2 = dalloc((size_t)p->nv2 * h->gc.V * h->n * 2 * cs);
+      h->Dc2 = dalloc((size_t)h->gc2.V * 9 * h->n2 * h->n2 * 2 * cs);
+      h->Dinv2 = dalloc((size_t)h->nhalf2 * h->n2 * h->n2 * 2 * cs);
+    }
     h->scratch = static_cast<double*>(dalloc((size_t)kScratchBlocks * kMaxDots * 2 * sizeof(double)));
     h->dsmall = static_cast<double*>(dalloc(kSmall * sizeof(double)));
     CK(cudaMallocHost(&h->hsmall, kSmall * sizeof(double)));
@@ -1324,7 +1603,8 @@ static tm_status setup_common(tm_handle* h, const double* tv, bool adaptive) {
   API_BEGIN
   if (!h->gauge_ok) raise(TM_ERR_STATE, "tm_load_gauge must come first");
   h->setup_ok = false;
-  const size_t bytes = (size_t)h->p.nv * h->g.V * 12 * 2 * sizeof(double);
+  size_t bytes = (size_t)h->p.nv * h->g.V * 12 * 2 * sizeof(double);
+  if (h->three) bytes += (size_t)h->p.nv2 * h->gc.V * h->n * 2 * sizeof(double);  // level-1 random vectors
   const double* d = stage_in(h, tv, bytes, "stage_tv");
   h->coarse_iters = 0;
   h->kcycles = 0;
@@ -1444,6 +1724,7 @@ size_t tm_field_bytes(const tm_handle* h, int level, int prec, int nrhs) {
   if (!h || nrhs < 1 || (prec != TM_F64 && prec != TM_F32)) return 0;
   if (level == 0) return (size_t)nrhs * NR_SPINOR * h->g.V * csize(prec);
   if (level == 1) return (size_t)nrhs * h->gc.V * h->n * 2 * csize(prec);
+  if (level == 2 && h->three) return (size_t)nrhs * h->gc2.V * h->n2 * 2 * csize(prec);
   return 0;
 }
 
@@ -1463,8 +1744,8 @@ tm_status tm_pack(tm_handle* h, int level, int prec, const double* natural, void
       launch_pack_spinor<float>(natural, static_cast<float*>(field), h->g, nrhs, h->st);
     else
       raise(TM_ERR_ARG, "bad precision");
-  } else if (level == 1) {
-    const long nre = (long)nrhs * h->gc.V * h->n * 2;
+  } else if (level == 1 || (level == 2 && h->three)) {
+    const long nre = (long)nrhs * 2 * (level == 1 ? level1_cx(h) : level2_cx(h));
     if (prec == TM_F64)
       launch_convert<double, double>(natural, static_cast<double*>(field), nre, h->st);
     else if (prec == TM_F32)
@@ -1490,8 +1771,8 @@ tm_status tm_unpack(tm_handle* h, int level, int prec, const void* field, double
       unpack_fine<float>(h, field, natural, nrhs);
     else
       raise(TM_ERR_ARG, "bad precision");
-  } else if (level == 1) {
-    const long nre = (long)nrhs * h->gc.V * h->n * 2;
+  } else if (level == 1 || (level == 2 && h->three)) {
+    const long nre = (long)nrhs * 2 * (level == 1 ? level1_cx(h) : level2_cx(h));
     if (prec == TM_F64)
       launch_convert<double, double>(static_cast<const double*>(field), natural, nre, h->st);
     else if (prec == TM_F32)
@@ -1526,10 +1807,19 @@ tm_status tm_apply(tm_handle* h, int level, int prec, const void* in, void* out,
     need_cycle_prec(h, prec);
     if (prec == TM_F64)
       launch_coarse_apply<double>(static_cast<const double*>(h->Dc), static_cast<const double*>(in),
-                                  static_cast<double*>(out), h->gc, h->p.nv, mu_c(h), nrhs, h->st);
+                                  static_cast<double*>(out), h->gc, h->p.nv, mu_level1(h), nrhs, h->st);
     else
       launch_coarse_apply<float>(static_cast<const float*>(h->Dc), static_cast<const float*>(in),
-                                 static_cast<float*>(out), h->gc, h->p.nv, mu_c(h), nrhs, h->st);
+                                 static_cast<float*>(out), h->gc, h->p.nv, mu_level1(h), nrhs, h->st);
+    CKL();
+  } else if (level == 2 && h->three) {
+    need_cycle_prec(h, prec);
+    if (prec == TM_F64)
+      launch_coarse_apply<double>(static_cast<const double*>(h->Dc2), static_cast<const double*>(in),
+                                  static_cast<double*>(out), h->gc2, h->p.nv2, mu_c(h), nrhs, h->st);
+    else
+      launch_coarse_apply<float>(static_cast<const float*>(h->Dc2), static_cast<const float*>(in),
+                                 static_cast<float*>(out), h->gc2, h->p.nv2, mu_c(h), nrhs, h->st);
     CKL();
   } else {
     raise(TM_ERR_ARG, "level must be 0 or 1");
@@ -1584,9 +1874,11 @@ tm_status tm_coarse_solve(tm_handle* h, int prec, const void* b, void* x, double
   need_cycle_prec(h, prec);
   std::vector<int> r;
   if (prec == TM_F64)
-    r = coarse_solve<double>(h, static_cast<const double*>(b), static_cast<double*>(x), 1, tol, maxit);
+    r = coarse_solve<double>(h, coarsest_level(h), static_cast<const double*>(b), static_cast<double*>(x), 1, tol,
+                             maxit);
   else
-    r = coarse_solve<float>(h, static_cast<const float*>(b), static_cast<float*>(x), 1, tol, maxit);
+    r = coarse_solve<float>(h, coarsest_level(h), static_cast<const float*>(b), static_cast<float*>(x), 1, tol,
+                            maxit);
   sync(h);
   if (iters) *iters = r[0];
   API_END
@@ -1694,6 +1986,49 @@ tm_status tm_export(tm_handle* h, int what, double* out, size_t bytes) {
             k += 2;
           }
       }
+  } else if ((what == TM_EXPORT_P2 || what == TM_EXPORT_TV1 || what == TM_EXPORT_DC2) && h->three) {
+    if (!h->setup_ok) raise(TM_ERR_STATE, "needs a setup");
+    const int nv1 = h->p.nv, n1 = h->n, nv2 = h->p.nv2, n2 = h->n2;
+    const long V1 = h->gc.V;
+    auto fetch = [&](const void* src, size_t cnt) {
+      std::vector<double> raw(cnt);
+      if (h->p.cycle_prec == TM_F64) {
+        CK(cudaMemcpyAsync(raw.data(), src, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        sync(h);
+      } else {
+        std::vector<float> rf(cnt);
+        CK(cudaMemcpyAsync(rf.data(), src, cnt * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+        sync(h);
+        for (size_t i = 0; i < cnt; ++i) raw[i] = rf[i];
+      }
+      return raw;
+    };
+    if (what == TM_EXPORT_TV1) {
+      host = fetch(h->tv1, (size_t)nv2 * V1 * n1 * 2);
+    } else if (what == TM_EXPORT_P2) {
+      std::vector<double> raw = fetch(h->P2, (size_t)nv2 * V1 * n1 * 2);
+      host.assign((size_t)2 * nv2 * V1 * n1 * 2, 0.0);
+      for (int chi = 0; chi < 2; ++chi)
+        for (int j = 0; j < nv2; ++j)
+          for (long x = 0; x < V1; ++x)
+            for (int i = 0; i < nv1; ++i) {
+              const size_t src = (((size_t)j * V1 + x) * n1 + chi * nv1 + i) * 2;
+              const size_t dst = ((((size_t)chi * nv2 + j) * V1 + x) * n1 + chi * nv1 + i) * 2;
+              host[dst] = raw[src];
+              host[dst + 1] = raw[src + 1];
+            }
+    } else {
+      const size_t cnt = (size_t)h->gc2.V * 9 * n2 * n2;
+      std::vector<double> raw = fetch(h->Dc2, cnt * 2);
+      host.assign(cnt * 2, 0.0);
+      for (size_t blk = 0; blk < (size_t)h->gc2.V * 9; ++blk)
+        for (int col = 0; col < n2; ++col)
+          for (int row = 0; row < n2; ++row) {
+            const size_t src = (blk * n2 + col) * n2 + row, dst = (blk * n2 + row) * n2 + col;
+            host[2 * dst] = raw[2 * src];
+            host[2 * dst + 1] = raw[2 * src + 1];
+          }
+    }
   } else {
     raise(TM_ERR_ARG, "unknown export");
   }
@@ -1704,6 +2039,61 @@ tm_status tm_export(tm_handle* h, int what, double* out, size_t bytes) {
   } else {
     std::memcpy(out, host.data(), host.size() * sizeof(double));
   }
+  API_END
+}
+
+static void need_three(tm_handle* h, int prec) {
+  if (!h->three) raise(TM_ERR_ARG, "needs a three-level handle");
+  need_cycle_prec(h, prec);
+}
+
+tm_status tm_sap1(tm_handle* h, int prec, const void* b, void* x, int sweeps, int nrhs) {
+  if (!h || !x || sweeps < 0 || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  need_three(h, prec);
+  if (prec == TM_F64)
+    csap_sweeps<double>(h, static_cast<const double*>(b), static_cast<double*>(x), sweeps, nrhs);
+  else
+    csap_sweeps<float>(h, static_cast<const float*>(b), static_cast<float*>(x), sweeps, nrhs);
+  API_END
+}
+
+tm_status tm_restrict1(tm_handle* h, int prec, const void* c1, void* c2, int nrhs) {
+  if (!h || !c1 || !c2 || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  need_three(h, prec);
+  if (prec == TM_F64)
+    launch_crestrict<double>(static_cast<const double*>(h->P2), static_cast<const double*>(c1),
+                             static_cast<double*>(c2), h->cag, nrhs, h->st);
+  else
+    launch_crestrict<float>(static_cast<const float*>(h->P2), static_cast<const float*>(c1), static_cast<float*>(c2),
+                            h->cag, nrhs, h->st);
+  CKL();
+  API_END
+}
+
+tm_status tm_prolong1(tm_handle* h, int prec, const void* c2, void* c1, int nrhs, int accumulate) {
+  if (!h || !c1 || !c2 || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  need_three(h, prec);
+  if (prec == TM_F64)
+    launch_cprolong<double>(static_cast<const double*>(h->P2), static_cast<const double*>(c2),
+                            static_cast<double*>(c1), h->cag, nrhs, accumulate != 0, h->st);
+  else
+    launch_cprolong<float>(static_cast<const float*>(h->P2), static_cast<const float*>(c2), static_cast<float*>(c1),
+                           h->cag, nrhs, accumulate != 0, h->st);
+  CKL();
+  API_END
+}
+
+tm_status tm_kcycle1(tm_handle* h, int prec, const void* v, void* z, int nrhs) {
+  if (!h || !v || !z || v == z || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  need_three(h, prec);
+  if (prec == TM_F64)
+    kcycle1<double>(h, static_cast<const double*>(v), static_cast<double*>(z), nrhs);
+  else
+    kcycle1<float>(h, static_cast<const float*>(v), static_cast<float*>(z), nrhs);
   API_END
 }
 
@@ -1926,6 +2316,7 @@ extern "C" tm_status tm_coarse_solve_noalloc(tm_handle* h, int prec, const void*
   if (!h || !b || !x || maxit < 1 || tol < 0) return TM_ERR_ARG;
   API_BEGIN
   if (prec != TM_F64 && prec != TM_F32) raise(TM_ERR_ARG, "bad precision");
+  if (h->three) raise(TM_ERR_ARG, "tm_coarse_solve_noalloc serves two-level handles");
   const size_t need = noalloc_bytes(h, prec, h->p.coarse_restart);
   if (need > kNoAllocBytes)
     raise(TM_ERR_ARG, "tm_coarse_solve_noalloc: this coarse system needs " + std::to_string(need) +

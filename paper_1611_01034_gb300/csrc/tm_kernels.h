@@ -95,6 +95,36 @@ template <typename T>
 void launch_oe_reconstruct(const T* Dc, const T* Dinv, const T* b, const T* xe, T* x, const OEGeom& oe,
                            cudaStream_t st);
 
+// ---- first coarse level of a three-level hierarchy (coarse2.cu) -------------
+struct CSapGeom {
+  Lat g;       // level-1 lattice
+  int blk[4];  // SAP block dims (coarse sites); block counts per dimension even
+  int nb[4];
+  int bsites;
+  int n;       // components per level-1 site (2 Nv1)
+};
+struct CAggGeom {
+  Lat g1, g2;  // level-1 and level-2 lattices
+  int agg[4];
+  int asites;
+  int nv1, nv2;
+};
+// one colour of SAP on D_c1(mu) x = b (b may be null), nrhs level-1 vectors
+template <typename T>
+void launch_csap_colour(const T* Dc, const T* b, T* x, const CSapGeom& sg, double mu, int n_mr, int colour,
+                        int nrhs, cudaStream_t st);
+// P2 <- per (aggregate, chirality) CGS2 of the Nv2 level-1 fields in P2
+template <typename T>
+void launch_corth(T* P2, const CAggGeom& ag, int* err, cudaStream_t st);
+template <typename T>
+void launch_crestrict(const T* P2, const T* r1, T* r2, const CAggGeom& ag, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_cprolong(const T* P2, const T* e2, T* x1, const CAggGeom& ag, int nrhs, bool accumulate,
+                     cudaStream_t st);
+// D_c2 blocks (mu-free) = P2^dagger D_c1(0) P2
+template <typename T>
+void launch_cbuild(const T* Dc1, const T* P2, T* Dc2, const CAggGeom& ag, cudaStream_t st);
+
 // batched odd-even pieces: nrhs right-hand sides at per-rhs strides (reals);
 // `active` (device, may be null) masks right-hand sides that are finished
 // ye = S ve with S = D_ee - D_eo D_oo^-1 D_oe (uo: odd-site work vectors)

@@ -43,6 +43,8 @@ def test_defaults_and_status_strings(lib):
     p = tm.tm_params_default()
     assert p.nv == 20 and list(p.agg) == [4, 4, 4, 4] and p.bc_t == -1.0
     assert p.cycle_prec == tm.TM_F32 and p.delta == 1.0
+    assert p.levels == 2 and p.nv2 == 28 and list(p.agg2) == [2, 2, 2, 2] and list(p.sap_block1) == [2, 2, 2, 2]
+    assert (p.pre_smooth1, p.post_smooth1, p.coarse_setup_iters, p.coarsest_maxit) == (0, 2, 3, 200)
     assert tm.tm_status_string(tm.TM_ERR_NOT_CONVERGED) == "not converged"
     assert tm.tm_status_string(12345) == "unknown status"
 
@@ -56,6 +58,11 @@ def test_defaults_and_status_strings(lib):
     dict(L=(8, 8, 8, 8), cycle_prec=7),
     dict(L=(8, 8, 8, 8), bc_t=0.3),
     dict(L=(32, 32, 32, 32), agg=(8, 8, 8, 4)),          # aggregate volume > 1024
+    dict(L=(8, 8, 8, 8), levels=4),
+    dict(L=(8, 8, 8, 8), levels=3),                       # level-2 extents 1
+    dict(L=(16, 16, 16, 16), levels=3, nv2=29),
+    dict(L=(16, 16, 16, 16), levels=3, sap_block1=(4, 2, 2, 2)),  # one level-1 SAP block in T
+    dict(L=(16, 16, 16, 16), levels=3, nv=20, agg2=(4, 2, 2, 2), sap_block1=(2, 2, 2, 2)),  # not divisible
 ])
 def test_invalid_parameters_rejected_before_any_device_call(lib, bad):
     import paper_1611_01034_gb300 as tm
