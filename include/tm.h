@@ -57,7 +57,7 @@ typedef enum {
   TM_ERR_CUDA = -2,          /* a CUDA runtime call or kernel launch failed */
   TM_ERR_OOM = -3,           /* device allocation failed */
   TM_ERR_NOT_CONVERGED = -4, /* solve hit maxit; x holds the best iterate */
-  TM_ERR_TIMEOUT = -5,       /* reserved for bounded device-side waits */
+  TM_ERR_TIMEOUT = -5,       /* a bounded device-side wait ran out (tensor-core kernels) */
   TM_ERR_NOT_SU3 = -6,       /* a link is not unitary with det 1 (tolerance 1e-10) */
   TM_ERR_NONFINITE = -7,     /* NaN or Inf in an input or a reduction */
   TM_ERR_STATE = -8          /* call out of order (e.g. solve before setup) */
@@ -115,6 +115,11 @@ typedef struct {
   int coarse_setup_iters; /* level-1 adaptive passes inside each fine setup iteration */
   double coarsest_tol;  /* level-2 GMRES tolerance */
   int coarsest_maxit;   /* level-2 GMRES iteration cap */
+  /* Odd-even Schur complement of the coarsest level (Sec. 3) on the tensor
+     cores: 0 = CUDA cores (FP32/FP64), 1 = TF32 products, 2 = TF32 with the
+     vectors split in two TF32 parts, 3 = 3xTF32 (operator split as well, about
+     FP32 accuracy).  1..3 need cycle_prec = TM_F32; FP32 accumulation. */
+  int coarse_mma;
 } tm_params;
 
 typedef struct {
@@ -132,7 +137,7 @@ typedef struct {
  * maxit = 1000, cycle_prec = TM_F32, max_rhs = 1, levels = 2, nv2 = 28,
  * agg2 = sap_block1 = 2^4, mr_iters1 = 4, pre_smooth1 = 0, post_smooth1 = 2,
  * init_sweeps1 = 3, coarse_setup_iters = 3, coarsest_tol = 5e-2,
- * coarsest_maxit = 200.  L, m0, c_sw, mu are 0. */
+ * coarsest_maxit = 200, coarse_mma = 0.  L, m0, c_sw, mu are 0. */
 void tm_params_default(tm_params* p);
 
 /* Validate p and allocate a handle bound to a CUDA stream (cudaStream_t,
@@ -231,6 +236,14 @@ tm_status tm_prolong(tm_handle* h, int prec, const void* coarse, void* fine, int
  * the reduced right-hand side or maxit steps.  One coarse field each (device,
  * cycle_prec).  *iters (may be NULL) receives the step count. */
 tm_status tm_coarse_solve(tm_handle* h, int prec, const void* b, void* x, double tol, int maxit, int* iters);
+
+/* y_e = S v_e with S = D_ee - D_eo D_oo^-1 D_oe the odd-even Schur
+ * complement of the coarsest operator D_c(delta mu) (Sec. 3: the coarsest
+ * level is solved on S by GMRES).  v_e, y_e: distinct device arrays of nrhs
+ * compact even vectors [nrhs][Vc/2][2N_v] complex (even sites in lexicographic
+ * order), prec = cycle_prec, after a setup.  With coarse_mma > 0 and nrhs <=
+ * 32 this runs on the tensor cores; TM_ERR_TIMEOUT if a device wait ran out. */
+tm_status tm_schur(tm_handle* h, int prec, const void* ve, void* ye, int nrhs);
 
 /* Allocation-free variant of tm_coarse_solve (the paper has no counterpart;
  * this is a library convenience).  Some callers cannot call cudaMalloc when

@@ -104,6 +104,8 @@ WORKLOADS = {
     # name: (L = T,Z,Y,X, eps, seed, c_sw)
     "16x16x16x32_eps0.5_seed1": ((32, 16, 16, 16), 0.5, 1, 1.5),
     "24x24x24x48_eps0.5_seed1": ((48, 24, 24, 24), 0.5, 1, 1.5),
+    # the 48^3x96 field strength and clover coefficient, tuned on a 16^3x32 volume
+    "16x16x16x32_eps0.6_seed1_csw1.57551": ((32, 16, 16, 16), 0.6, 1, 1.57551),
 }
 
 

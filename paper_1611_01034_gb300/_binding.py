@@ -27,6 +27,7 @@ class tm_params(ctypes.Structure):
         ("levels", c_int), ("nv2", c_int), ("agg2", c_int * 4), ("sap_block1", c_int * 4),
         ("mr_iters1", c_int), ("pre_smooth1", c_int), ("post_smooth1", c_int), ("init_sweeps1", c_int),
         ("coarse_setup_iters", c_int), ("coarsest_tol", c_double), ("coarsest_maxit", c_int),
+        ("coarse_mma", c_int),
     ]
 
 
@@ -70,6 +71,7 @@ _SIGS = {
     "tm_coarse_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, POINTER(c_int)]),
     "tm_coarse_solve_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, POINTER(c_int)]),
     "tm_kcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
+    "tm_schur": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "tm_sap1": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
     "tm_restrict1": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "tm_prolong1": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
@@ -245,6 +247,10 @@ def tm_coarse_solve_noalloc(h, prec, b, x, tol, maxit) -> int:
 
 def tm_kcycle(h, prec, v, z, nrhs) -> None:
     _check(lib().tm_kcycle(h, prec, _ptr(v), _ptr(z), nrhs), h)
+
+
+def tm_schur(h, prec, ve, ye, nrhs) -> None:
+    _check(lib().tm_schur(h, prec, _ptr(ve), _ptr(ye), nrhs), h)
 
 
 def tm_sap1(h, prec, b, x, sweeps, nrhs) -> None:

@@ -93,6 +93,9 @@ struct tm_handle {
   int* d_even2 = nullptr;
   int* d_odd2 = nullptr;
   int* d_cidx2 = nullptr;
+  // odd-even Schur complement of the coarsest level on the tensor cores
+  bool tc_on = false;
+  TcGeom tc{};
   std::map<std::string, Buf> work;
   bool gauge_ok = false, setup_ok = false;
   std::string err;
@@ -228,6 +231,7 @@ void check_flags(tm_handle* h) {
     if (f & ERRF_NOT_SU3) raise(TM_ERR_NOT_SU3, "gauge link not in SU(3) within 1e-10");
     if (f & ERRF_RANK) raise(TM_ERR_ARG, "test vectors are rank deficient on an aggregate");
     if (f & ERRF_SINGULAR) raise(TM_ERR_ARG, "singular coarse self block");
+    if (f & ERRF_TIMEOUT) raise(TM_ERR_TIMEOUT, "a bounded device-side wait ran out");
     raise(TM_ERR_NONFINITE, "non-finite value");
   }
 }
@@ -481,6 +485,12 @@ void build_coarse(tm_handle* h) {
   if (!h->three) {  // with three levels the odd-even solve runs on level 2
     launch_oe_invert<T>(static_cast<T*>(h->Dc), static_cast<T*>(h->Dinv), h->oe, mu_c(h), h->d_err, h->st);
     CKL();
+    if constexpr (std::is_same<T, float>::value) {
+      if (h->tc_on) {
+        tc_build(static_cast<const float*>(h->Dc), static_cast<const float*>(h->Dinv), h->oe, h->tc, h->st);
+        CKL();
+      }
+    }
   }
 }
 
@@ -506,11 +516,13 @@ struct OELevel {
   OEGeom oe;
   int n, nhalf, Vc;
   double mu_c;
+  const TcGeom* tc;  // tensor-core tiles of this level (or null)
 };
 
 OELevel coarsest_level(tm_handle* h) {
-  if (h->three) return OELevel{h->Dc2, h->Dinv2, h->oe2, h->n2, h->nhalf2, h->gc2.V, mu_c(h)};
-  return OELevel{h->Dc, h->Dinv, h->oe, h->n, h->nhalf, h->gc.V, mu_c(h)};
+  const TcGeom* tc = h->tc_on ? &h->tc : nullptr;
+  if (h->three) return OELevel{h->Dc2, h->Dinv2, h->oe2, h->n2, h->nhalf2, h->gc2.V, mu_c(h), tc};
+  return OELevel{h->Dc, h->Dinv, h->oe, h->n, h->nhalf, h->gc.V, mu_c(h), tc};
 }
 
 // Odd-even GMRES(coarse_restart) on D_c(delta mu) x_r = b_r for nrhs full
@@ -571,8 +583,18 @@ std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x,
     sync(h);
     slot = 0;
   };
+  bool use_tc = false;
+  if constexpr (std::is_same<T, float>::value)
+    use_tc = lv.tc && tc_supported(lv.oe.nv, nrhs, h->p.coarse_mma);
   auto schur = [&](const T* v, long vs, int units) {
     Prof pf(h, PK_COARSE_OE, units, 2);
+    if constexpr (std::is_same<T, float>::value) {
+      if (use_tc) {
+        launch_tc_schur(*lv.tc, lv.oe, v, uo, w, mc, nrhs, vs, cv, cv, act, h->p.coarse_mma, h->d_err, h->st);
+        CKL();
+        return;
+      }
+    }
     launch_oe_schur_b<T>(Dc, Di, v, uo, w, lv.oe, mc, nrhs, vs, cv, cv, act, h->st);
     CKL();
   };
@@ -729,6 +751,7 @@ std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x,
     CKL();
   }
   for (int r = 0; r < nrhs; ++r) h->coarse_iters += iters[r];
+  if (use_tc) check_flags(h);  // bounded waits inside the tensor-core kernel
   return iters;
 }
 
@@ -869,6 +892,12 @@ void build_level2(tm_handle* h) {
   CKL();
   launch_oe_invert<T>(static_cast<T*>(h->Dc2), static_cast<T*>(h->Dinv2), h->oe2, mu_c(h), h->d_err, h->st);
   CKL();
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->tc_on) {
+      tc_build(static_cast<const float*>(h->Dc2), static_cast<const float*>(h->Dinv2), h->oe2, h->tc, h->st);
+      CKL();
+    }
+  }
 }
 
 template <typename T>
@@ -1250,6 +1279,8 @@ void validate(const tm_params* p) {
   if (p->coarse_restart < 1 || p->coarse_restart > kMaxDots - 2) bad("coarse_restart must be in 1..126");
   if (p->maxit < 1 || p->coarse_maxit < 1) bad("maxit must be >= 1");
   if (p->cycle_prec != TM_F64 && p->cycle_prec != TM_F32) bad("cycle_prec must be TM_F64 or TM_F32");
+  if (p->coarse_mma < 0 || p->coarse_mma > 3) bad("coarse_mma must be 0..3");
+  if (p->coarse_mma > 0 && p->cycle_prec != TM_F32) bad("coarse_mma needs cycle_prec = TM_F32");
   if (p->bc_t != 1.0 && p->bc_t != -1.0) bad("bc_t must be +1 or -1");
   if (!(p->delta >= 1.0)) bad("delta must be >= 1");
   if (p->max_rhs < 1) bad("max_rhs must be >= 1");
@@ -1354,6 +1385,10 @@ void apply_mu(tm_handle* h, double mu, double delta) {
     else
       launch_oe_invert<float>(static_cast<float*>(Dc), static_cast<float*>(Di), oe, mu_c(h), h->d_err, h->st);
     CKL();
+    if (h->tc_on) {  // the odd tiles carry D_oo^-1(mu)
+      tc_build_odd(static_cast<const float*>(Dc), static_cast<const float*>(Di), oe, h->tc, h->st);
+      CKL();
+    }
     check_flags(h);
   }
 }
@@ -1405,6 +1440,7 @@ void tm_params_default(tm_params* p) {
   p->coarse_setup_iters = 3;
   p->coarsest_tol = 5e-2;
   p->coarsest_maxit = 200;
+  p->coarse_mma = 0;
 }
 
 const char* tm_status_string(int s) {
@@ -1435,7 +1471,8 @@ void tm_destroy(tm_handle* h) {
   if (h->hsmall) cudaFreeHost(h->hsmall);
   for (auto& kv : h->hbufs)
     if (kv.second.first) cudaFreeHost(kv.second.first);
-  void* p3[] = {h->tv1, h->P2, h->Dc2, h->Dinv2, h->d_even2, h->d_odd2, h->d_cidx2};
+  void* p3[] = {h->tv1, h->P2, h->Dc2, h->Dinv2, h->d_even2, h->d_odd2, h->d_cidx2,
+                h->tc.even, h->tc.even_lo, h->tc.odd, h->tc.odd_lo, h->tc.nbr_e, h->tc.nbr_o};
   for (void* q : p3)
     if (q) cudaFree(q);
   for (auto& r : h->recs) {
@@ -1564,6 +1601,21 @@ tm_status tm_create(tm_handle** out, const tm_params* p, void* stream) {
       h->P2 = dalloc((size_t)p->nv2 * h->gc.V * h->n * 2 * cs);
       h->Dc2 = dalloc((size_t)h->gc2.V * 9 * h->n2 * h->n2 * 2 * cs);
       h->Dinv2 = dalloc((size_t)h->nhalf2 * h->n2 * h->n2 * 2 * cs);
+    }
+    if (p->coarse_mma > 0) {  // tensor-core tiles of the coarsest odd-even level
+      const int nvc = h->three ? p->nv2 : p->nv, nh = h->three ? h->nhalf2 : h->nhalf;
+      h->tc_on = true;
+      h->tc.kp = (2 * nvc + 7) / 8 * 8;
+      h->tc.mp = (4 * nvc + 7) / 8 * 8;
+      const size_t tile = (size_t)h->tc.kp * h->tc.mp * sizeof(float);
+      h->tc.even = static_cast<float*>(dalloc((size_t)nh * 9 * tile));
+      h->tc.odd = static_cast<float*>(dalloc((size_t)nh * 8 * tile));
+      if (p->coarse_mma == 3) {
+        h->tc.even_lo = static_cast<float*>(dalloc((size_t)nh * 9 * tile));
+        h->tc.odd_lo = static_cast<float*>(dalloc((size_t)nh * 8 * tile));
+      }
+      h->tc.nbr_e = static_cast<int*>(dalloc((size_t)nh * 9 * sizeof(int)));
+      h->tc.nbr_o = static_cast<int*>(dalloc((size_t)nh * 8 * sizeof(int)));
     }
     h->scratch = static_cast<double*>(dalloc((size_t)kScratchBlocks * kMaxDots * 2 * sizeof(double)));
     h->dsmall = static_cast<double*>(dalloc(kSmall * sizeof(double)));
@@ -2039,6 +2091,33 @@ tm_status tm_export(tm_handle* h, int what, double* out, size_t bytes) {
   } else {
     std::memcpy(out, host.data(), host.size() * sizeof(double));
   }
+  API_END
+}
+
+tm_status tm_schur(tm_handle* h, int prec, const void* ve, void* ye, int nrhs) {
+  if (!h || !ve || !ye || ve == ye || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  need_cycle_prec(h, prec);
+  const OELevel lv = coarsest_level(h);
+  const long cv = 2L * lv.nhalf * lv.n;
+  Prof pf(h, PK_COARSE_OE, nrhs, 2);
+  if (prec == TM_F32) {
+    float* uo = W<float>(h, "sch_uo", cv * nrhs);
+    if (lv.tc && tc_supported(lv.oe.nv, nrhs, h->p.coarse_mma))
+      launch_tc_schur(*lv.tc, lv.oe, static_cast<const float*>(ve), uo, static_cast<float*>(ye), lv.mu_c, nrhs, cv, cv,
+                      cv, nullptr, h->p.coarse_mma, h->d_err, h->st);
+    else
+      launch_oe_schur_b<float>(static_cast<const float*>(lv.Dc), static_cast<const float*>(lv.Dinv),
+                               static_cast<const float*>(ve), uo, static_cast<float*>(ye), lv.oe, lv.mu_c, nrhs, cv,
+                               cv, cv, nullptr, h->st);
+  } else {
+    double* uo = W<double>(h, "sch_uo64", cv * nrhs);
+    launch_oe_schur_b<double>(static_cast<const double*>(lv.Dc), static_cast<const double*>(lv.Dinv),
+                              static_cast<const double*>(ve), uo, static_cast<double*>(ye), lv.oe, lv.mu_c, nrhs, cv,
+                              cv, cv, nullptr, h->st);
+  }
+  CKL();
+  check_flags(h);
   API_END
 }
 

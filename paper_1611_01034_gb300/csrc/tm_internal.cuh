@@ -299,6 +299,7 @@ enum : int {
   ERRF_RANK = 2,
   ERRF_SINGULAR = 4,
   ERRF_NONFINITE = 8,
+  ERRF_TIMEOUT = 16,  // a bounded device-side wait ran out
 };
 
 // ---------------------------------------------------------------------------

@@ -140,6 +140,30 @@ template <typename T>
 void launch_oe_reconstruct_b(const T* Dc, const T* Dinv, const T* b, const T* xe, T* x, const OEGeom& oe, int nrhs,
                              long bstr, long estr, cudaStream_t st);
 
+// ---- odd-even Schur complement on the tensor cores (coarse_tc.cu) ------------
+// Pre-tiled FP32 operator blocks (TF32-rounded, K-major UMMA layout: kp = n
+// padded to 8 columns, mp = 2n padded to 8 rows) for the odd-even coarse solve.
+struct TcGeom {
+  int kp = 0, mp = 0;
+  float* even = nullptr;     // [nhalf][9] self block and hops of even sites
+  float* even_lo = nullptr;  // residual parts for 3xTF32 (or null)
+  float* odd = nullptr;      // [nhalf][8] D_oo^-1 B_t of odd sites
+  float* odd_lo = nullptr;
+  int* nbr_e = nullptr;      // [nhalf][9]
+  int* nbr_o = nullptr;      // [nhalf][8]
+};
+constexpr int kTcSmemBytes = 200 * 1024;
+// can the tensor-core path take nrhs right-hand sides with split products (1..3)?
+bool tc_supported(int nv, int nrhs, int split);
+// neighbour tables, even tiles and odd tiles (after D_c and D_oo^-1 exist)
+void tc_build(const float* Dc, const float* Dinv, const OEGeom& oe, const TcGeom& tg, cudaStream_t st);
+// odd tiles only (they carry D_oo^-1, so they follow mu)
+void tc_build_odd(const float* Dc, const float* Dinv, const OEGeom& oe, const TcGeom& tg, cudaStream_t st);
+// ye = S ve for nrhs compact even vectors (uo: odd work vectors); `split` TF32 products
+void launch_tc_schur(const TcGeom& tg, const OEGeom& oe, const float* ve, float* uo, float* ye, double mu_c,
+                     int nrhs, long vstr, long ustr, long ystr, const int* active, int split, int* err,
+                     cudaStream_t st);
+
 // ---- level-1 vectors (blas.cu) ----------------------------------------------
 // all BLAS works on flat arrays of n complex numbers stored as (re, im) pairs
 template <typename Ti, typename To>
