@@ -331,6 +331,7 @@ def main_native(args):
     xh = torch.zeros(bh.shape, dtype=bh.dtype).pin_memory()
     stream = torch.cuda.current_stream()
     extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart") if k in wl}
+    extra["coarse_mma"] = args.coarse_mma if args.coarse_mma is not None else wl.get("coarse_mma", 0)
     p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv,
                   agg=wl["agg"], sap_block=wl["sap_block"], setup_iters=wl["setup_iters"],
                   cycle_prec=tm.TM_F32, max_rhs=rb, levels=levels, **extra)
@@ -490,7 +491,7 @@ def main_native(args):
             "workload": args.workload, "lattice_TZYX": list(L), "sites": V, "levels": levels,
             **({"nv2": wl["nv2"], "aggregate2": list(wl["agg2"]), "sap_block1": list(wl["sap_block1"]),
                 "coarse_setup_iters": wl["coarse_setup_iters"]} if levels == 3 else {}),
-            "restart": p.restart, "rhs_per_solve_call": rb,
+            "restart": p.restart, "rhs_per_solve_call": rb, "coarse_mma": p.coarse_mma,
             "nv": nv, "aggregate": list(wl["agg"]), "sap_block": list(wl["sap_block"]),
             "m0": m0, "m0_source": m0_src, "c_sw": wl["c_sw"], "mu": wl["mu"],
             "delta": wl["delta"], "setup_iters": wl["setup_iters"], "tol": wl["tol"], "nrhs": nrhs,
@@ -562,6 +563,8 @@ def main():
     ap.add_argument("--write-counts", action="store_true")
     ap.add_argument("--oracle-worker", default=None)
     ap.add_argument("--m0", type=float, default=None, help="override the workload's tuned m0")
+    ap.add_argument("--coarse-mma", type=int, default=None,
+                    help="override the workload's coarse_mma (0 CUDA cores, 1..3 TF32 tensor-core products)")
     args = ap.parse_args()
     if args.oracle_worker:
         print(json.dumps(oracle_unit_costs(args.oracle_worker)))

@@ -18,9 +18,10 @@
 // Im y = D[2i][R_pad+q] + D[2i+1][q] combine two neighbouring TMEM lanes of
 // the same warp (one shuffle).
 //
-// Operator blocks are kept pre-tiled in HBM in the canonical K-major,
-// no-swizzle UMMA layout (8-row x 16-byte core matrices), so one bulk TMA copy
-// (cp.async.bulk) moves a whole block into shared memory.  Targets:
+// Operator blocks are kept pre-tiled in HBM in the K-major UMMA layout with
+// 64-byte swizzle (the layout the tensor core reads without shared-memory bank
+// conflicts), so one bulk TMA copy (cp.async.bulk) moves a whole block into
+// shared memory.  Targets:
 //   odd  sites: u_o = sum_{t=1..8} [D_oo^-1 B_t] v_e(nb_t)   (blocks premultiplied)
 //   even sites: y_e = A_self v_e - sum_{t=1..8} B_t u_o(nb_t) + i mu_c Gamma5_c v_e
 // TF32 keeps 10 explicit mantissa bits; `split` adds the residual parts
@@ -41,8 +42,13 @@ namespace tmamg {
 
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kGatherWarps = 8;                            // warps 2 .. 9
+constexpr int kIssuers = 2;                                // MMA issuing warps 1 and 14
+constexpr int kTcThreads = (2 + kGatherWarps + 4 + 1) * 32;  // + epilogue warps 10 .. 13, issuer 14
 constexpr uint32_t kSpinLimit = 1u << 22;
+// independent accumulators per target: consecutive MMAs rotate over them so the
+// tensor pipe never waits for the previous product into the same TMEM columns
+constexpr int kAcc = 4;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -84,10 +90,11 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// shared-memory matrix descriptor: K-major, no swizzle
-__device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((su32(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// shared-memory matrix descriptor: K-major, 64-byte swizzle (8-row atoms of
+// 64-byte rows, 512 bytes apart), start address advanced within an atom row
+__device__ __forceinline__ uint64_t sdesc(const void* p) {
+  return (uint64_t)((su32(p) >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(512u >> 4) << 32) | (1ull << 46) |
+         (4ull << 61);
 }
 
 // instruction descriptor: kind::tf32, D F32, A/B TF32, both K-major, M = 128
@@ -131,9 +138,14 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// byte offset of element (row, k) in a K-major no-swizzle tile whose K extent is kp
-__host__ __device__ __forceinline__ uint32_t tile_off(int row, int k, int kp) {
-  return (uint32_t)(((row >> 3) * (kp >> 2) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+// Byte offset of FP32 element (row, k) in a K-major tile with 64-byte swizzle:
+// K is cut into chunks of 16 elements (64 bytes), each chunk holds all `rows`
+// rows at 64 bytes apiece, and inside every 512-byte block the 16-byte unit
+// index is XORed with (row / 2) mod 4.  Chunks are 512-byte aligned when rows
+// is a multiple of 8.
+__host__ __device__ __forceinline__ uint32_t tile_off(int row, int k, int rows) {
+  const uint32_t o = (uint32_t)row * 64u + (uint32_t)(k & 15) * 4u;
+  return (uint32_t)(k >> 4) * (uint32_t)rows * 64u + (o ^ (((o >> 7) & 3u) << 4));
 }
 
 struct TcArgs {
@@ -161,18 +173,21 @@ struct TcShared {
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
   __shared__ TcShared sh;
+  // swizzle atoms need 512-byte alignment of every tile: align the base explicitly
+  unsigned char* smem = smem_dyn + ((1024u - (su32(smem_dyn) & 1023u)) & 1023u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = a.stages, N = 2 * a.rp;
   const uint32_t TB = (uint32_t)a.mp * a.kp * 4;  // operator tile bytes
   const uint32_t BB = (uint32_t)N * a.kp * 4;     // B operand bytes
-  const uint32_t guard = 512u * a.kp > TB ? 512u * a.kp - TB : 0u;
+  const uint32_t guard = (uint32_t)(128 - a.mp) * 64u;  // rows mp..127 of the last chunk
   unsigned char* A = smem;
   unsigned char* Alo = A + (size_t)S * TB;
   unsigned char* Bh = Alo + (a.split == 3 ? (size_t)S * TB : 0) + guard;
   unsigned char* Bl = Bh + (size_t)S * BB;
-  const uint32_t ncols = N * 2 <= 32 ? 32 : (N * 2 <= 64 ? 64 : (N * 2 <= 128 ? 128 : 256));
+  const int ncol_need = 2 * kAcc * N;  // two target slots of kAcc accumulators
+  const uint32_t ncols = ncol_need <= 32 ? 32 : (ncol_need <= 64 ? 64 : (ncol_need <= 128 ? 128 : (ncol_need <= 256 ? 256 : 512)));
   volatile int* abort = &sh.abort;
 
   // zero the B operands once: padded rows (rhs >= R) and columns (k >= n) stay zero
@@ -184,14 +199,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&sh.full_a[s], 1);
-      mbar_init(&sh.full_b[s], 2);
-      mbar_init(&sh.empty[s], 1);
+      mbar_init(&sh.full_b[s], 1);
+      mbar_init(&sh.empty[s], kIssuers);
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&sh.tfull[i], 1);
+      mbar_init(&sh.tfull[i], kIssuers);
       mbar_init(&sh.tempty[i], 4);
     }
-    mbar_init(&sh.drain, 1);
+    mbar_init(&sh.drain, kIssuers);
     sh.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -238,11 +253,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
         }
       }
     }
-  } else if (warp == 1) {
-    // ---- MMA issue -----------------------------------------------------------------
+  } else if (warp == 1 || warp == 2 + kGatherWarps + 4) {
+    // ---- MMA issue: two issuing threads, MMA ci of a target goes to issuer ci % 2 and
+    // accumulator ci % kAcc (a single issuing thread cannot keep the tensor pipe busy
+    // with these small products) -------------------------------------------------------------
+    const int iss = warp == 1 ? 0 : 1;
     if (lane == 0) {
       const uint32_t idesc = idesc_tf32(N);
-      const uint32_t sbo = (uint32_t)(a.kp >> 2) * 128u;
       long g = 0;
       int j = 0;
       bool ok = true;
@@ -253,11 +270,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
           break;
         }
         tc_after();
-        const uint32_t d = tmem + (uint32_t)(slot * N);
+        const uint32_t d0 = tmem + (uint32_t)(slot * kAcc * N);
+        int ci = 0;  // MMA counter within the target: accumulator ci % kAcc, overwrite on first use
         for (int t = 0; t < a.nt; ++t, ++g) {
           const int s = (int)(g % S);
           const uint32_t par = (uint32_t)((g / S) & 1);
-          if (!mbar_wait(&sh.full_a[s], par, abort) || !mbar_wait(&sh.full_b[s], par, abort)) {
+          if (!mbar_wait(&sh.full_b[s], par, abort)) {  // the gather warp saw the tile land
             ok = false;
             break;
           }
@@ -267,11 +285,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
           const unsigned char* Bs = Bh + (size_t)s * BB;
           const unsigned char* Bls = Bl + (size_t)s * BB;
           for (int ks = 0; ks < a.kp / 8; ++ks) {
-            const uint64_t ad = sdesc(As + ks * 256, 128u, sbo);
-            const uint64_t bd = sdesc(Bs + ks * 256, 128u, sbo);
-            mma_tf32(d, ad, bd, idesc, (t > 0 || ks > 0) ? 1u : 0u);
-            if (a.split >= 2) mma_tf32(d, ad, sdesc(Bls + ks * 256, 128u, sbo), idesc, 1u);
-            if (a.split == 3) mma_tf32(d, sdesc(Als + ks * 256, 128u, sbo), bd, idesc, 1u);
+            const uint32_t ao = (uint32_t)(ks >> 1) * (uint32_t)a.mp * 64u + (uint32_t)(ks & 1) * 32u;
+            const uint32_t bo = (uint32_t)(ks >> 1) * (uint32_t)N * 64u + (uint32_t)(ks & 1) * 32u;
+            const uint64_t ad = sdesc(As + ao);
+            const uint64_t bd = sdesc(Bs + bo);
+            if (ci % kIssuers == iss) mma_tf32(d0 + (uint32_t)((ci % kAcc) * N), ad, bd, idesc, ci >= kAcc ? 1u : 0u);
+            ++ci;
+            if (a.split >= 2) {
+              if (ci % kIssuers == iss)
+                mma_tf32(d0 + (uint32_t)((ci % kAcc) * N), ad, sdesc(Bls + bo), idesc, ci >= kAcc ? 1u : 0u);
+              ++ci;
+            }
+            if (a.split == 3) {
+              if (ci % kIssuers == iss)
+                mma_tf32(d0 + (uint32_t)((ci % kAcc) * N), sdesc(Als + ao), bd, idesc, ci >= kAcc ? 1u : 0u);
+              ++ci;
+            }
           }
           mma_commit(&sh.empty[s]);
         }
@@ -284,42 +313,70 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
       volatile int never = 0;
       if (!mbar_wait(&sh.drain, 0u, &never)) atomicOr(a.err, ERRF_TIMEOUT);
     }
-  } else if (warp == 2 || warp == 3) {
+  } else if (warp < 2 + kGatherWarps) {
     // ---- B operand: gather, sign, split, store ------------------------------------------
-    const int tid = threadIdx.x - 64;
-    long g = 0;
+    // gather warp w fills stages w, w + G, ...; lane = (rhs q mod 8) * 4 + (k mod 4), so a
+    // warp's stores cover one 128-byte row group of a core-matrix column (no bank conflicts).
+    // G <= S keeps every waiter within one phase of its stage's empty barrier (the parity
+    // test cannot tell phases two apart).
+    const int w = warp - 2;
+    const int G = kGatherWarps < S ? kGatherWarps : S;
+    const int qq = lane >> 2, cc = lane & 3;
+    const int nq = a.rp >> 3, nc4 = (a.n + 3) >> 2;
+    int ntl = 0;
+    for (int k = blockIdx.x; k < a.ntgt; k += gridDim.x) ++ntl;
+    const long total = (long)ntl * a.nt;
     bool ok = true;
-    for (int k = blockIdx.x; k < a.ntgt && ok; k += gridDim.x)
-      for (int t = 0; t < a.nt; ++t, ++g) {
-        const int s = (int)(g % S);
-        if (!mbar_wait(&sh.empty[s], (uint32_t)((g / S) & 1) ^ 1u, abort)) {
-          ok = false;
-          break;
+    for (long g = w; w < G && g < total; g += G) {
+      const int jl = (int)(g / a.nt), t = (int)(g % a.nt);
+      const int k = blockIdx.x + jl * gridDim.x;
+      const int j = a.nbr[(long)k * a.nt + t];
+      const int s = (int)(g % S);
+      if (!mbar_wait(&sh.empty[s], (uint32_t)((g / S) & 1) ^ 1u, abort)) {
+        ok = false;
+        break;
+      }
+      const bool self = t == 0 && a.src0;
+      const float* src = self ? a.src0 : a.src1;
+      const long str = self ? a.s0_str : a.s1_str;
+      const float sg = self ? 1.f : a.sign1;
+      unsigned char* Bs = Bh + (size_t)s * BB;
+      unsigned char* Bls = Bl + (size_t)s * BB;
+      constexpr int U = 4;
+      for (int p0 = 0; p0 < nq * nc4; p0 += U) {
+        float2 v[U];
+        int qv[U], cv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int pr = p0 + u;
+          qv[u] = (pr / nc4) * 8 + qq;
+          cv[u] = (pr % nc4) * 4 + cc;
+          v[u] = make_float2(0.f, 0.f);
+          if (pr < nq * nc4 && qv[u] < a.R && cv[u] < a.n && (!a.active || a.active[qv[u]]))
+            v[u] = reinterpret_cast<const float2*>(src + qv[u] * str)[(long)j * a.n + cv[u]];
         }
-        const int j = a.nbr[(long)k * a.nt + t];
-        const bool self = t == 0 && a.src0;
-        const float* src = self ? a.src0 : a.src1;
-        const long str = self ? a.s0_str : a.s1_str;
-        const float sg = self ? 1.f : a.sign1;
-        unsigned char* Bs = Bh + (size_t)s * BB;
-        unsigned char* Bls = Bl + (size_t)s * BB;
-        for (int e = tid; e < a.R * a.n; e += 64) {
-          const int q = e / a.n, c = e - q * a.n;
-          float2 v = make_float2(0.f, 0.f);
-          if (!a.active || a.active[q]) v = reinterpret_cast<const float2*>(src + q * str)[(long)j * a.n + c];
-          const float re = sg * v.x, im = sg * v.y;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (p0 + u >= nq * nc4 || qv[u] >= a.R || cv[u] >= a.n) continue;
+          const float re = sg * v[u].x, im = sg * v[u].y;
           const float rh = tf32_round(re), ih = tf32_round(im);
-          *reinterpret_cast<float*>(Bs + tile_off(q, c, a.kp)) = rh;
-          *reinterpret_cast<float*>(Bs + tile_off(a.rp + q, c, a.kp)) = ih;
+          *reinterpret_cast<float*>(Bs + tile_off(qv[u], cv[u], N)) = rh;
+          *reinterpret_cast<float*>(Bs + tile_off(a.rp + qv[u], cv[u], N)) = ih;
           if (a.split >= 2) {
-            *reinterpret_cast<float*>(Bls + tile_off(q, c, a.kp)) = re - rh;
-            *reinterpret_cast<float*>(Bls + tile_off(a.rp + q, c, a.kp)) = im - ih;
+            *reinterpret_cast<float*>(Bls + tile_off(qv[u], cv[u], N)) = re - rh;
+            *reinterpret_cast<float*>(Bls + tile_off(a.rp + qv[u], cv[u], N)) = im - ih;
           }
         }
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.full_b[s]);
       }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        // the stage is ready once its operator tile has landed as well
+        if (!mbar_wait(&sh.full_a[s], (uint32_t)((g / S) & 1), abort)) ok = false;
+        else mbar_arrive(&sh.full_b[s]);
+      }
+      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+    }
     if (!ok && lane == 0) fail();
   } else {
     // ---- epilogue: TMEM -> registers -> y ---------------------------------------------------
@@ -337,8 +394,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
         break;
       }
       tc_after();
-      const uint32_t base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(slot * N);
+      const uint32_t base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(slot * kAcc * N);
       for (int c0 = 0; c0 < N; c0 += 16) tmem_ld16(base + (uint32_t)c0, acc + c0);
+      for (int ai = 1; ai < kAcc; ++ai)
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float part[16];
+          tmem_ld16(base + (uint32_t)(ai * N + c0), part);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[c0 + i] += part[i];
+        }
       tc_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.tempty[slot]);
@@ -383,8 +447,8 @@ __global__ void k_tc_tiles_even(const float* __restrict__ Dc, float* __restrict_
       v = (mm & 1) ? b.i : b.r;
     }
     const float h = tf32_round(v);
-    out[tile_off(mm, c, kp) / 4] = h;
-    if (outl) outl[tile_off(mm, c, kp) / 4] = v - h;
+    out[tile_off(mm, c, mp) / 4] = h;
+    if (outl) outl[tile_off(mm, c, mp) / 4] = v - h;
   }
 }
 
@@ -415,8 +479,8 @@ __global__ void k_tc_tiles_odd(const float* __restrict__ Dc, const float* __rest
       v = (mm & 1) ? acc.i : acc.r;
     }
     const float h = tf32_round(v);
-    out[tile_off(mm, c, kp) / 4] = h;
-    if (outl) outl[tile_off(mm, c, kp) / 4] = v - h;
+    out[tile_off(mm, c, mp) / 4] = h;
+    if (outl) outl[tile_off(mm, c, mp) / 4] = v - h;
   }
 }
 
@@ -447,9 +511,9 @@ int g_sms = 0;
 int tc_stages(const TcGeom& tg, int R, int split) {
   const int rp = (R + 7) / 8 * 8, N = 2 * rp;
   const long TB = (long)tg.mp * tg.kp * 4, BB = (long)N * tg.kp * 4;
-  const long guard = 512L * tg.kp > TB ? 512L * tg.kp - TB : 0;
+  const long guard = (128L - tg.mp) * 64;
   const long per = TB * (split == 3 ? 2 : 1) + BB * (split >= 2 ? 2 : 1);
-  long s = (kTcSmemBytes - guard) / per;
+  long s = (kTcSmemBytes - 1024 - guard) / per;
   return (int)(s > 16 ? 16 : s);
 }
 
@@ -469,7 +533,7 @@ void launch_tc(const TcArgs& a, cudaStream_t st) {
 bool tc_supported(int nv, int nrhs, int split) {
   if (2 * nv > 64 || nrhs < 1 || nrhs > 32 || split < 1 || split > 3) return false;
   TcGeom tg{};
-  tg.kp = (2 * nv + 7) / 8 * 8;
+  tg.kp = (2 * nv + 15) / 16 * 16;
   tg.mp = (4 * nv + 7) / 8 * 8;
   return tc_stages(tg, nrhs, split) >= 2;
 }

@@ -1605,7 +1605,7 @@ tm_status tm_create(tm_handle** out, const tm_params* p, void* stream) {
     if (p->coarse_mma > 0) {  // tensor-core tiles of the coarsest odd-even level
       const int nvc = h->three ? p->nv2 : p->nv, nh = h->three ? h->nhalf2 : h->nhalf;
       h->tc_on = true;
-      h->tc.kp = (2 * nvc + 7) / 8 * 8;
+      h->tc.kp = (2 * nvc + 15) / 16 * 16;
       h->tc.mp = (4 * nvc + 7) / 8 * 8;
       const size_t tile = (size_t)h->tc.kp * h->tc.mp * sizeof(float);
       h->tc.even = static_cast<float*>(dalloc((size_t)nh * 9 * tile));

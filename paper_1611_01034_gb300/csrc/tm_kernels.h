@@ -141,8 +141,9 @@ void launch_oe_reconstruct_b(const T* Dc, const T* Dinv, const T* b, const T* xe
                              long bstr, long estr, cudaStream_t st);
 
 // ---- odd-even Schur complement on the tensor cores (coarse_tc.cu) ------------
-// Pre-tiled FP32 operator blocks (TF32-rounded, K-major UMMA layout: kp = n
-// padded to 8 columns, mp = 2n padded to 8 rows) for the odd-even coarse solve.
+// Pre-tiled FP32 operator blocks (TF32-rounded, K-major UMMA layout with 64-byte
+// swizzle: kp = n padded to 16 columns, mp = 2n padded to 8 rows) for the
+// odd-even coarse solve.
 struct TcGeom {
   int kp = 0, mp = 0;
   float* even = nullptr;     // [nhalf][9] self block and hops of even sites
