@@ -46,13 +46,13 @@ WORKLOADS = {
         m0_key="16x16x16x32_eps0.5_seed1"),
     "24x24x24x48_2lvl_nv24_12pt": dict(
         L=(48, 24, 24, 24), eps=0.5, seed=1, c_sw=1.5, mu=0.002, delta=5.0, nv=24,
-        agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=5, tol=1e-10, nrhs=12, point=True,
+        agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=5, tol=1e-10, nrhs=12, point=True, coarse_mma=1,
         m0_key="16x16x16x32_eps0.5_seed1"),  # same field strength; the critical mass is a bulk quantity
     "48x48x48x96_3lvl_nv24_28_12pt": dict(
         L=(96, 48, 48, 48), eps=0.6, seed=1, c_sw=1.57551, mu=0.0009, delta=5.0, nv=24,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, nrhs=12, point=True,
         levels=3, nv2=28, agg2=(2, 2, 2, 2), sap_block1=(2, 2, 2, 2), coarse_setup_iters=3,
-        restart=16, rhs_batch=1, m0_key="16x16x16x32_eps0.6_seed1_csw1.57551"),
+        restart=16, rhs_batch=1, coarse_mma=1, m0_key="16x16x16x32_eps0.6_seed1_csw1.57551"),
     "8x8x8x8_2lvl_nv8": dict(
         L=(8, 8, 8, 8), eps=0.5, seed=5, c_sw=1.5, mu=0.005, delta=5.0, nv=8,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, m0=-0.4),

@@ -585,7 +585,7 @@ std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x,
   };
   bool use_tc = false;
   if constexpr (std::is_same<T, float>::value)
-    use_tc = lv.tc && tc_supported(lv.oe.nv, nrhs, h->p.coarse_mma);
+    use_tc = lv.tc && nrhs >= 2 && tc_supported(lv.oe.nv, nrhs, h->p.coarse_mma);  // one rhs: CUDA cores
   auto schur = [&](const T* v, long vs, int units) {
     Prof pf(h, PK_COARSE_OE, units, 2);
     if constexpr (std::is_same<T, float>::value) {
