@@ -63,8 +63,8 @@ typedef enum {
   TM_ERR_STATE = -8          /* call out of order (e.g. solve before setup) */
 } tm_status;
 
-/* storage/arithmetic precision of a field */
-enum { TM_F64 = 0, TM_F32 = 1 };
+/* storage/arithmetic precision of a field (TM_F16: learned-layer inference only) */
+enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2 };
 
 /* what tm_export copies out */
 enum {
@@ -120,6 +120,12 @@ typedef struct {
      vectors split in two TF32 parts, 3 = 3xTF32 (operator split as well, about
      FP32 accuracy).  1..3 need cycle_prec = TM_F32; FP32 accumulation. */
   int coarse_mma;
+  /* Stage after the K-cycle in the solve's preconditioner (not in the paper):
+     0 = none, 1 = learned layer z = B(v) + N(v - D B(v)) (tm_nn_*), 2 = one SAP
+     sweep in place of N (the stand-in the learned layer is judged against).
+     nn_prec: TM_F32, or TM_F16 for FP16 hidden channels and weights. */
+  int nn_mode;
+  int nn_prec;
 } tm_params;
 
 typedef struct {
@@ -137,7 +143,8 @@ typedef struct {
  * maxit = 1000, cycle_prec = TM_F32, max_rhs = 1, levels = 2, nv2 = 28,
  * agg2 = sap_block1 = 2^4, mr_iters1 = 4, pre_smooth1 = 0, post_smooth1 = 2,
  * init_sweeps1 = 3, coarse_setup_iters = 3, coarsest_tol = 5e-2,
- * coarsest_maxit = 200, coarse_mma = 0.  L, m0, c_sw, mu are 0. */
+ * coarsest_maxit = 200, coarse_mma = 0, nn_mode = 0, nn_prec = TM_F32.
+ * L, m0, c_sw, mu are 0. */
 void tm_params_default(tm_params* p);
 
 /* Validate p and allocate a handle bound to a CUDA stream (cudaStream_t,
@@ -282,6 +289,37 @@ tm_status tm_sap1(tm_handle* h, int prec, const void* b, void* x, int sweeps, in
 tm_status tm_restrict1(tm_handle* h, int prec, const void* c1, void* c2, int nrhs);
 tm_status tm_prolong1(tm_handle* h, int prec, const void* c2, void* c1, int nrhs, int accumulate);
 tm_status tm_kcycle1(tm_handle* h, int prec, const void* v, void* z, int nrhs);
+
+/* Learned gauge-covariant layer (an addition; the paper has no learned parts).
+ * N = L2 o L1, L1: 1 -> 8 and L2: 8 -> 1 spinor channels, no nonlinearity:
+ *   y_o(x) = sum_i sum_d W[o][i][d] (T_d psi_i)(x), d = self, then +T, -T, +Z,
+ *   -Z, +Y, -Y, +X, -X; (T_{+mu} psi)(x) = U_mu(x) psi(x + mu), (T_{-mu} psi)(x) =
+ *   U_mu(x - mu)^dagger psi(x - mu) (boundary factor bc_t across T); W[o][i][d]
+ *   a complex 4 x 4 spin matrix acting trivially on colour.
+ * Weights: 2304 complex numbers as interleaved doubles (host memory), W1
+ * [8][1][9][4][4] then W2 [1][8][9][4][4] (row index first).  Default: zero.
+ *   tm_nn_set_weights / tm_nn_get_weights copy them in or out (set resets the
+ *     optimiser state).
+ *   tm_nn_apply: out = N(in) (accumulate = 0) or out += N(in); in, out
+ *     distinct device arrays of nrhs FP32 fine fields (tm_field_bytes(h, 0,
+ *     TM_F32, nrhs)); prec TM_F32 or TM_F16.  Needs a gauge field.
+ *   tm_nn_pairs: training pairs from random errors e0 (natural spinors, host
+ *     or device, npairs of them): e = (1 - B D) e0 with the current K-cycle B
+ *     and r = D e, written as FP32 fine fields.  Needs a setup with cycle_prec
+ *     = TM_F32.
+ *   tm_nn_grad: loss L = sum_p ||N(r_p) - e_p||^2 / sum_p ||e_p||^2 and its
+ *     Wirtinger gradient dL/d conj(W) (2304 complex, interleaved; either
+ *     output may be NULL).
+ *   tm_nn_train: `epochs` passes of Adam (beta 0.9, 0.999, eps 1e-8, step lr)
+ *     over minibatches of `batch` pairs in order, FP32 forward and backward on
+ *     the GPU; losses (may be NULL) receives the mean loss of each epoch. */
+tm_status tm_nn_set_weights(tm_handle* h, const double* w);
+tm_status tm_nn_get_weights(tm_handle* h, double* w);
+tm_status tm_nn_apply(tm_handle* h, int prec, const void* in, void* out, int nrhs, int accumulate);
+tm_status tm_nn_pairs(tm_handle* h, const double* e0, void* r, void* e, int npairs);
+tm_status tm_nn_grad(tm_handle* h, const void* r, const void* e, int npairs, double* grad, double* loss);
+tm_status tm_nn_train(tm_handle* h, const void* r, const void* e, int npairs, int epochs, int batch, double lr,
+                      double* losses);
 
 /* A7 preconditioner: z = B(v), one application of eq. (1) from a zero start
  * (pre SAP sweeps, coarse correction, post SAP sweeps).  Fine fields in

@@ -11,7 +11,7 @@ library_path = os.path.join(_HERE, "libtmamg.so")
 TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_OOM = 0, -1, -2, -3
 TM_ERR_NOT_CONVERGED, TM_ERR_TIMEOUT, TM_ERR_NOT_SU3 = -4, -5, -6
 TM_ERR_NONFINITE, TM_ERR_STATE = -7, -8
-TM_F64, TM_F32 = 0, 1
+TM_F64, TM_F32, TM_F16 = 0, 1, 2
 TM_EXPORT_P, TM_EXPORT_DC, TM_EXPORT_CLOVER, TM_EXPORT_TV = 0, 1, 2, 3
 TM_EXPORT_P2, TM_EXPORT_DC2, TM_EXPORT_TV1 = 4, 5, 6
 
@@ -27,7 +27,7 @@ class tm_params(ctypes.Structure):
         ("levels", c_int), ("nv2", c_int), ("agg2", c_int * 4), ("sap_block1", c_int * 4),
         ("mr_iters1", c_int), ("pre_smooth1", c_int), ("post_smooth1", c_int), ("init_sweeps1", c_int),
         ("coarse_setup_iters", c_int), ("coarsest_tol", c_double), ("coarsest_maxit", c_int),
-        ("coarse_mma", c_int),
+        ("coarse_mma", c_int), ("nn_mode", c_int), ("nn_prec", c_int),
     ]
 
 
@@ -72,6 +72,12 @@ _SIGS = {
     "tm_coarse_solve_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, POINTER(c_int)]),
     "tm_kcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "tm_schur": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
+    "tm_nn_set_weights": (c_int, [c_void_p, c_void_p]),
+    "tm_nn_get_weights": (c_int, [c_void_p, c_void_p]),
+    "tm_nn_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
+    "tm_nn_pairs": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
+    "tm_nn_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, POINTER(c_double)]),
+    "tm_nn_train": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_double, c_void_p]),
     "tm_sap1": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
     "tm_restrict1": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "tm_prolong1": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
@@ -251,6 +257,47 @@ def tm_kcycle(h, prec, v, z, nrhs) -> None:
 
 def tm_schur(h, prec, ve, ye, nrhs) -> None:
     _check(lib().tm_schur(h, prec, _ptr(ve), _ptr(ye), nrhs), h)
+
+
+def tm_nn_set_weights(h, w) -> None:
+    """w: 2304 complex weights (W1 [8,1,9,4,4] then W2 [1,8,9,4,4])."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(w, dtype=np.complex128).ravel())
+    if a.size != 2304:
+        raise ValueError("expected 2304 complex weights")
+    _check(lib().tm_nn_set_weights(h, _ptr(a)), h)
+
+
+def tm_nn_get_weights(h):
+    import numpy as np
+    a = np.zeros(2304, dtype=np.complex128)
+    _check(lib().tm_nn_get_weights(h, _ptr(a)), h)
+    return a
+
+
+def tm_nn_apply(h, prec, inp, out, nrhs, accumulate=False) -> None:
+    _check(lib().tm_nn_apply(h, prec, _ptr(inp), _ptr(out), nrhs, int(accumulate)), h)
+
+
+def tm_nn_pairs(h, e0, r, e, npairs) -> None:
+    _check(lib().tm_nn_pairs(h, _ptr(e0), _ptr(r), _ptr(e), npairs), h)
+
+
+def tm_nn_grad(h, r, e, npairs):
+    """(loss, gradient dL/d conj(W) as 2304 complex)."""
+    import numpy as np
+    g = np.zeros(2304, dtype=np.complex128)
+    loss = c_double(0)
+    _check(lib().tm_nn_grad(h, _ptr(r), _ptr(e), npairs, _ptr(g), ctypes.byref(loss)), h)
+    return loss.value, g
+
+
+def tm_nn_train(h, r, e, npairs, epochs, batch, lr):
+    """Adam training; returns the mean loss of every epoch."""
+    import numpy as np
+    losses = np.zeros(epochs, dtype=np.float64)
+    _check(lib().tm_nn_train(h, _ptr(r), _ptr(e), npairs, epochs, batch, lr, _ptr(losses)), h)
+    return losses
 
 
 def tm_sap1(h, prec, b, x, sweeps, nrhs) -> None:

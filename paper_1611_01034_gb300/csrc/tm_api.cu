@@ -12,6 +12,8 @@
 #include <complex>
 #include <cstring>
 #include <type_traits>
+
+#include <cuda_fp16.h>
 #include <map>
 #include <mutex>
 #include <string>
@@ -96,6 +98,12 @@ struct tm_handle {
   // odd-even Schur complement of the coarsest level on the tensor cores
   bool tc_on = false;
   TcGeom tc{};
+  // learned gauge-covariant layer: weights (W1 then W2), device copies, Adam state
+  std::vector<std::complex<double>> nn_w;
+  float2* d_nnw = nullptr;    // [5][1152]: W1, W2, W1 and W2 rounded to FP16, W2 adjoint
+  double2* d_nngrad = nullptr;  // [2][1152]
+  std::vector<double> adam_m, adam_v;
+  long adam_t = 0;
   std::map<std::string, Buf> work;
   bool gauge_ok = false, setup_ok = false;
   std::string err;
@@ -163,11 +171,12 @@ T* Wz(tm_handle* h, const std::string& name, size_t count) {
 // ---------------------------------------------------------------------------
 enum ProfKind {
   PK_DSLASH64 = 0, PK_DSLASH32, PK_SAP, PK_RESTRICT, PK_PROLONG, PK_COARSE_OE, PK_BLAS_FINE, PK_BLAS_COARSE,
-  PK_BUILD, PK_OTHER, PK_CSAP, PK_LEVEL1, PK_N
+  PK_BUILD, PK_OTHER, PK_CSAP, PK_LEVEL1, PK_NN, PK_N
 };
 const char* const kProfNames[PK_N] = {"dslash_f64", "dslash_f32",   "sap",          "restrict",
                                       "prolong",    "coarse_oe",    "blas_fine",    "blas_coarse",
-                                      "coarse_build", "other",      "coarse_sap",   "level1"};
+                                      "coarse_build", "other",      "coarse_sap",   "level1",
+                                      "nn"};
 
 cudaEvent_t take_event(tm_handle* h) {
   if (!h->evpool.empty()) {
@@ -982,6 +991,138 @@ void setup_impl(tm_handle* h, const double* tv_dev, bool adaptive) {
   sync(h);
 }
 
+// ---------------------------------------------------------------------------
+// learned gauge-covariant layer (not part of the paper's method)
+// ---------------------------------------------------------------------------
+constexpr int kNnLayer = kNnWeights / 2;  // complex weights per layer
+
+void nn_upload(tm_handle* h) {
+  if (!h->d_nnw) {
+    h->d_nnw = static_cast<float2*>(dalloc((size_t)5 * kNnLayer * sizeof(float2)));
+    h->d_nngrad = static_cast<double2*>(dalloc((size_t)2 * kNnLayer * sizeof(double2)));
+  }
+  std::vector<float2> buf((size_t)5 * kNnLayer);
+  for (int k = 0; k < kNnWeights; ++k) {
+    const float re = (float)h->nn_w[k].real(), im = (float)h->nn_w[k].imag();
+    buf[k] = make_float2(re, im);
+    buf[kNnWeights + k] = make_float2(__half2float(__float2half(re)), __half2float(__float2half(im)));
+  }
+  // adjoint of layer 2: W2adj[i][0][opp(d)][s][t] = conj(W2[0][i][d][t][s])
+  for (int i = 0; i < kNnHidden; ++i)
+    for (int d = 0; d < 9; ++d) {
+      const int od = d == 0 ? 0 : (((d - 1) & 1) ? d - 1 : d + 1);
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          const std::complex<double> w = h->nn_w[kNnLayer + (i * 9 + d) * 16 + b * 4 + a];
+          buf[(size_t)4 * kNnLayer + (i * 9 + od) * 16 + a * 4 + b] = make_float2((float)w.real(), (float)-w.imag());
+        }
+    }
+  CK(cudaMemcpyAsync(h->d_nnw, buf.data(), buf.size() * sizeof(float2), cudaMemcpyHostToDevice, h->st));
+  sync(h);
+}
+
+void need_nn(tm_handle* h) {
+  if (!h->gauge_ok) raise(TM_ERR_STATE, "needs a gauge field");
+  if (h->nn_w.empty()) {
+    h->nn_w.assign(kNnWeights, std::complex<double>(0, 0));
+    nn_upload(h);
+  }
+}
+
+// out (+)= N(in) for nrhs FP32 fine fields; FP16 hidden channels and weights when half
+void nn_forward(tm_handle* h, const float* in, float* out, int nrhs, bool accumulate, bool half) {
+  need_nn(h);
+  Prof pf(h, PK_NN, nrhs, 2);
+  const size_t hid = (size_t)kNnHidden * 24 * h->g.V * nrhs;
+  void* hb = half ? static_cast<void*>(W<__half>(h, "nn_hid16", hid)) : static_cast<void*>(W<float>(h, "nn_hid", hid));
+  const float2* w1 = h->d_nnw + (half ? kNnWeights : 0);
+  const float2* w2 = w1 + kNnLayer;
+  nn_layer1(in, hb, half, h->g32, w1, h->g, h->p.bc_t, nrhs, h->st);
+  CKL();
+  nn_layer2(hb, half, out, accumulate, h->g32, w2, h->g, h->p.bc_t, nrhs, h->st);
+  CKL();
+}
+
+// loss sum_p ||N(r_p) - e_p||^2 and Wirtinger gradients (not yet divided by sum_p ||e_p||^2)
+double nn_grad_sum(tm_handle* h, const float* r, const float* e, int npairs, std::vector<std::complex<double>>& G,
+                   double& esum) {
+  need_nn(h);
+  const long fr = fine_reals(h);
+  const int chunk = 16;
+  const size_t hid = (size_t)kNnHidden * 24 * h->g.V * chunk;
+  float* hb = W<float>(h, "nn_hid", hid);
+  float* gh = W<float>(h, "nn_gh", hid);
+  float* y = W<float>(h, "nn_y", (size_t)fr * chunk);
+  float2* part = W<float2>(h, "nn_part", (size_t)nn_wgrad_partial_floats2(h->g, chunk));
+  G.assign(kNnWeights, std::complex<double>(0, 0));
+  double loss = 0;
+  esum = 0;
+  std::vector<double2> hg((size_t)kNnWeights);
+  for (int p0 = 0; p0 < npairs; p0 += chunk) {
+    const int nr = std::min(chunk, npairs - p0);
+    const float* rp = r + (size_t)p0 * fr;
+    const float* ep = e + (size_t)p0 * fr;
+    {
+      Prof pf(h, PK_NN, nr, 10);
+      nn_layer1(rp, hb, false, h->g32, h->d_nnw, h->g, h->p.bc_t, nr, h->st);
+      CKL();
+      nn_layer2(hb, false, y, false, h->g32, h->d_nnw + kNnLayer, h->g, h->p.bc_t, nr, h->st);
+      CKL();
+      launch_caxpby<float>(-1, 0, ep, 1, 0, y, (fr / 2) * nr, h->st);  // y = N(r) - e
+      CKL();
+      launch_norm2<float>(y, fr / 2, nr, h->dsmall, h->scratch, kScratchBlocks, h->st);
+      CKL();
+      launch_norm2<float>(ep, fr / 2, nr, h->dsmall + kMaxDots, h->scratch, kScratchBlocks, h->st);
+      CKL();
+      nn_grad_w2(hb, y, h->g32, h->g, h->p.bc_t, nr, part, h->d_nngrad + kNnLayer, h->st);
+      CKL();
+      nn_layer2_adjoint(y, gh, h->g32, h->d_nnw + 4 * kNnLayer, h->g, h->p.bc_t, nr, h->st);
+      CKL();
+      nn_grad_w1(rp, gh, h->g32, h->g, h->p.bc_t, nr, part, h->d_nngrad, h->st);
+      CKL();
+    }
+    CK(cudaMemcpyAsync(h->hsmall, h->dsmall, (kMaxDots + nr) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(hg.data(), h->d_nngrad, hg.size() * sizeof(double2), cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    for (int q = 0; q < nr; ++q) {
+      loss += h->hsmall[q];
+      esum += h->hsmall[kMaxDots + q];
+    }
+    for (int k = 0; k < kNnWeights; ++k) G[k] += std::complex<double>(hg[k].x, hg[k].y);
+  }
+  if (!std::isfinite(loss)) raise(TM_ERR_NONFINITE, "non-finite loss");
+  return loss;
+}
+
+// z = B(v), then the optional stage after the K-cycle: z += N(v - D z) (learned
+// layer) or z += one SAP sweep on D e = v - D z from zero (its stand-in)
+template <typename T>
+void precond(tm_handle* h, const T* v, T* z, int nrhs) {
+  kcycle<T>(h, v, z, nrhs);
+  if (h->p.nn_mode == 0) return;
+  const long fr = fine_reals(h);
+  T* rr = W<T>(h, "nn_rr", fr * nrhs);
+  dslash<T>(h, z, rr, v, nrhs);  // rr = v - D z
+  if (h->p.nn_mode == 1) {
+    if constexpr (std::is_same<T, float>::value) {
+      nn_forward(h, rr, z, nrhs, true, h->p.nn_prec == TM_F16);
+    } else {
+      raise(TM_ERR_ARG, "the learned layer runs in FP32 or FP16 (cycle_prec = TM_F32)");
+    }
+  } else {
+    T* ee = W<T>(h, "nn_ee", fr * nrhs);
+    {
+      Prof pf(h, PK_OTHER, nrhs);
+      launch_zero<T>(ee, fr * nrhs, h->st);
+      CKL();
+    }
+    sap_sweeps<T>(h, rr, ee, 1, nrhs);
+    Prof pf(h, PK_OTHER, nrhs);
+    launch_caxpby<T>(1, 0, ee, 1, 0, z, (fr / 2) * nrhs, h->st);
+    CKL();
+  }
+}
+
 // FGMRES in FP64 preconditioned by the K-cycle in T; b, x packed FP64 fields
 template <typename T>
 KrylovOut solve_one(tm_handle* h, const double* b, double* x, double tol) {
@@ -1003,14 +1144,14 @@ KrylovOut solve_one(tm_handle* h, const double* b, double* x, double tol) {
   };
   auto M = [&](const double* v, T* z) {
     if constexpr (std::is_same<T, double>::value) {
-      kcycle<double>(h, v, z, 1);
+      precond<double>(h, v, z, 1);
     } else {
       {
         Prof pf(h, PK_OTHER);
         launch_convert<double, T>(v, vt, fr, h->st);
         CKL();
       }
-      kcycle<T>(h, vt, z, 1);
+      precond<T>(h, vt, z, 1);
     }
   };
   return krylov<double, T>(h, "fg", A, AZ, M, true, b, x, true, fr / 2, tol, h->p.restart, h->p.maxit);
@@ -1223,14 +1364,14 @@ std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int
   auto resid = [&](const double* xx, double* r) { dslash<double>(h, xx, r, b, nb); };
   auto M = [&](const double* v, T* z) {
     if constexpr (std::is_same<T, double>::value) {
-      kcycle<double>(h, v, z, nb);
+      precond<double>(h, v, z, nb);
     } else {
       {
         Prof pf(h, PK_OTHER, nb);
         launch_convert<double, T>(v, vt, blk, h->st);
         CKL();
       }
-      kcycle<T>(h, vt, z, nb);
+      precond<T>(h, vt, z, nb);
     }
   };
   auto AZ = [&](const T* z, double* o) {
@@ -1281,6 +1422,9 @@ void validate(const tm_params* p) {
   if (p->cycle_prec != TM_F64 && p->cycle_prec != TM_F32) bad("cycle_prec must be TM_F64 or TM_F32");
   if (p->coarse_mma < 0 || p->coarse_mma > 3) bad("coarse_mma must be 0..3");
   if (p->coarse_mma > 0 && p->cycle_prec != TM_F32) bad("coarse_mma needs cycle_prec = TM_F32");
+  if (p->nn_mode < 0 || p->nn_mode > 2) bad("nn_mode must be 0, 1 or 2");
+  if (p->nn_mode == 1 && p->cycle_prec != TM_F32) bad("the learned layer needs cycle_prec = TM_F32");
+  if (p->nn_prec != TM_F32 && p->nn_prec != TM_F16) bad("nn_prec must be TM_F32 or TM_F16");
   if (p->bc_t != 1.0 && p->bc_t != -1.0) bad("bc_t must be +1 or -1");
   if (!(p->delta >= 1.0)) bad("delta must be >= 1");
   if (p->max_rhs < 1) bad("max_rhs must be >= 1");
@@ -1441,6 +1585,8 @@ void tm_params_default(tm_params* p) {
   p->coarsest_tol = 5e-2;
   p->coarsest_maxit = 200;
   p->coarse_mma = 0;
+  p->nn_mode = 0;
+  p->nn_prec = TM_F32;
 }
 
 const char* tm_status_string(int s) {
@@ -1472,7 +1618,8 @@ void tm_destroy(tm_handle* h) {
   for (auto& kv : h->hbufs)
     if (kv.second.first) cudaFreeHost(kv.second.first);
   void* p3[] = {h->tv1, h->P2, h->Dc2, h->Dinv2, h->d_even2, h->d_odd2, h->d_cidx2,
-                h->tc.even, h->tc.even_lo, h->tc.odd, h->tc.odd_lo, h->tc.nbr_e, h->tc.nbr_o};
+                h->tc.even, h->tc.even_lo, h->tc.odd, h->tc.odd_lo, h->tc.nbr_e, h->tc.nbr_o,
+                h->d_nnw, h->d_nngrad};
   for (void* q : p3)
     if (q) cudaFree(q);
   for (auto& r : h->recs) {
@@ -2118,6 +2265,134 @@ tm_status tm_schur(tm_handle* h, int prec, const void* ve, void* ye, int nrhs) {
   }
   CKL();
   check_flags(h);
+  API_END
+}
+
+tm_status tm_nn_set_weights(tm_handle* h, const double* w) {
+  if (!h || !w) return TM_ERR_ARG;
+  API_BEGIN
+  h->nn_w.resize(kNnWeights);
+  for (int k = 0; k < kNnWeights; ++k) {
+    h->nn_w[k] = std::complex<double>(w[2 * k], w[2 * k + 1]);
+    if (!std::isfinite(w[2 * k]) || !std::isfinite(w[2 * k + 1])) raise(TM_ERR_NONFINITE, "non-finite weight");
+  }
+  h->adam_m.assign(2 * kNnWeights, 0.0);
+  h->adam_v.assign(2 * kNnWeights, 0.0);
+  h->adam_t = 0;
+  nn_upload(h);
+  API_END
+}
+
+tm_status tm_nn_get_weights(tm_handle* h, double* w) {
+  if (!h || !w) return TM_ERR_ARG;
+  API_BEGIN
+  for (int k = 0; k < kNnWeights; ++k) {
+    const std::complex<double> v = k < (int)h->nn_w.size() ? h->nn_w[k] : std::complex<double>(0, 0);
+    w[2 * k] = v.real();
+    w[2 * k + 1] = v.imag();
+  }
+  API_END
+}
+
+tm_status tm_nn_apply(tm_handle* h, int prec, const void* in, void* out, int nrhs, int accumulate) {
+  if (!h || !in || !out || in == out || nrhs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  if (prec != TM_F32 && prec != TM_F16) raise(TM_ERR_ARG, "prec must be TM_F32 or TM_F16");
+  nn_forward(h, static_cast<const float*>(in), static_cast<float*>(out), nrhs, accumulate != 0, prec == TM_F16);
+  API_END
+}
+
+tm_status tm_nn_pairs(tm_handle* h, const double* e0, void* r, void* e, int npairs) {
+  if (!h || !e0 || !r || !e || npairs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  if (!h->setup_ok) raise(TM_ERR_STATE, "needs a setup");
+  need_cycle_prec(h, TM_F32);
+  const long fr = fine_reals(h);
+  const double* src = stage_in(h, e0, (size_t)npairs * fr * sizeof(double), "stage_nn");
+  float* ef = static_cast<float*>(e);
+  float* rf = static_cast<float*>(r);
+  const int chunk = std::max(1, std::min(npairs, h->p.max_rhs));
+  float* r0 = W<float>(h, "nn_r0", (size_t)fr * chunk);
+  float* z = W<float>(h, "nn_z", (size_t)fr * chunk);
+  for (int p0 = 0; p0 < npairs; p0 += chunk) {
+    const int nr = std::min(chunk, npairs - p0);
+    float* ep = ef + (size_t)p0 * fr;
+    {
+      Prof pf(h, PK_OTHER, nr);
+      launch_pack_spinor<float>(src + (size_t)p0 * fr, ep, h->g, nr, h->st);
+      CKL();
+    }
+    dslash<float>(h, ep, r0, nullptr, nr);  // r0 = D e0
+    kcycle<float>(h, r0, z, nr);             // z = B D e0
+    {
+      Prof pf(h, PK_OTHER, nr);
+      launch_caxpby<float>(-1, 0, z, 1, 0, ep, (fr / 2) * nr, h->st);  // e = (1 - B D) e0
+      CKL();
+    }
+    dslash<float>(h, ep, rf + (size_t)p0 * fr, nullptr, nr);  // r = D e
+  }
+  sync(h);
+  API_END
+}
+
+tm_status tm_nn_grad(tm_handle* h, const void* r, const void* e, int npairs, double* grad, double* loss) {
+  if (!h || !r || !e || npairs < 1) return TM_ERR_ARG;
+  API_BEGIN
+  std::vector<std::complex<double>> G;
+  double esum = 0;
+  const double l = nn_grad_sum(h, static_cast<const float*>(r), static_cast<const float*>(e), npairs, G, esum);
+  if (!(esum > 0)) raise(TM_ERR_ARG, "all errors are zero");
+  if (loss) *loss = l / esum;
+  if (grad)
+    for (int k = 0; k < kNnWeights; ++k) {
+      grad[2 * k] = G[k].real() / esum;
+      grad[2 * k + 1] = G[k].imag() / esum;
+    }
+  API_END
+}
+
+tm_status tm_nn_train(tm_handle* h, const void* r, const void* e, int npairs, int epochs, int batch, double lr,
+                      double* losses) {
+  if (!h || !r || !e || npairs < 1 || epochs < 1 || batch < 1 || !(lr > 0)) return TM_ERR_ARG;
+  API_BEGIN
+  need_nn(h);
+  if (h->adam_m.size() != (size_t)2 * kNnWeights) {
+    h->adam_m.assign(2 * kNnWeights, 0.0);
+    h->adam_v.assign(2 * kNnWeights, 0.0);
+    h->adam_t = 0;
+  }
+  const long fr = fine_reals(h);
+  const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+  for (int ep = 0; ep < epochs; ++ep) {
+    double lsum = 0, esum_all = 0;
+    for (int p0 = 0; p0 < npairs; p0 += batch) {
+      const int nb = std::min(batch, npairs - p0);
+      std::vector<std::complex<double>> G;
+      double esum = 0;
+      const double l = nn_grad_sum(h, static_cast<const float*>(r) + (size_t)p0 * fr,
+                                   static_cast<const float*>(e) + (size_t)p0 * fr, nb, G, esum);
+      lsum += l;
+      esum_all += esum;
+      if (!(esum > 0)) continue;
+      ++h->adam_t;
+      const double c1 = 1 - std::pow(b1, (double)h->adam_t), c2 = 1 - std::pow(b2, (double)h->adam_t);
+      for (int k = 0; k < kNnWeights; ++k) {
+        // steepest descent of the real loss in (Re W, Im W): 2 dL/d conj(W)
+        const double gr[2] = {2 * G[k].real() / esum, 2 * G[k].imag() / esum};
+        double upd[2];
+        for (int c = 0; c < 2; ++c) {
+          double& m = h->adam_m[2 * k + c];
+          double& v = h->adam_v[2 * k + c];
+          m = b1 * m + (1 - b1) * gr[c];
+          v = b2 * v + (1 - b2) * gr[c] * gr[c];
+          upd[c] = lr * (m / c1) / (std::sqrt(v / c2) + eps);
+        }
+        h->nn_w[k] -= std::complex<double>(upd[0], upd[1]);
+      }
+      nn_upload(h);
+    }
+    if (losses) losses[ep] = esum_all > 0 ? lsum / esum_all : 0.0;
+  }
   API_END
 }
 

@@ -165,6 +165,25 @@ void launch_tc_schur(const TcGeom& tg, const OEGeom& oe, const float* ve, float*
                      int nrhs, long vstr, long ustr, long ystr, const int* active, int split, int* err,
                      cudaStream_t st);
 
+// ---- learned gauge-covariant layer (nn.cu) ------------------------------------
+// weights: complex float2 [Cout][Cin][9 directions][4][4]; hidden fields
+// [rhs][8][V][12 complex] in FP32 or FP16; fine fields in the chunked layout
+constexpr int kNnHidden = 8;
+constexpr int kNnWeights = 2 * kNnHidden * 9 * 16;  // complex weights of both layers
+long nn_wgrad_partial_floats2(const Lat& g, int nrhs);
+void nn_layer1(const float* r, void* hid, bool half, const float* gauge, const float2* W1, const Lat& g, double bc,
+               int nrhs, cudaStream_t st);
+void nn_layer2(const void* hid, bool half, float* y, bool accumulate, const float* gauge, const float2* W2,
+               const Lat& g, double bc, int nrhs, cudaStream_t st);
+// gh = L2^dagger gy (W2adj: conjugate-transposed weights with reversed directions)
+void nn_layer2_adjoint(const float* gy, float* gh, const float* gauge, const float2* W2adj, const Lat& g, double bc,
+                       int nrhs, cudaStream_t st);
+// summed over the nrhs samples: out[o][i][d][s][t] = sum_x g_o(x)[s] conj(T_d psi_i(x)[t]) (FP64)
+void nn_grad_w2(const float* hid, const float* gy, const float* gauge, const Lat& g, double bc, int nrhs,
+                float2* partial, double2* out, cudaStream_t st);
+void nn_grad_w1(const float* r, const float* gh, const float* gauge, const Lat& g, double bc, int nrhs,
+                float2* partial, double2* out, cudaStream_t st);
+
 // ---- level-1 vectors (blas.cu) ----------------------------------------------
 // all BLAS works on flat arrays of n complex numbers stored as (re, im) pairs
 template <typename Ti, typename To>
