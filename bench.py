@@ -52,11 +52,18 @@ WORKLOADS = {
         L=(96, 48, 48, 48), eps=0.6, seed=1, c_sw=1.57551, mu=0.0009, delta=5.0, nv=24,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, nrhs=12, point=True,
         levels=3, nv2=28, agg2=(2, 2, 2, 2), sap_block1=(2, 2, 2, 2), coarse_setup_iters=3,
-        restart=16, rhs_batch=1, coarse_mma=1, m0_key="16x16x16x32_eps0.6_seed1_csw1.57551"),
+        restart=16, rhs_batch=1, coarse_mma=1, m0_key="16x16x16x32_eps0.6_seed1_csw1.57551",
+        device_inputs=True),
     "8x8x8x8_2lvl_nv8": dict(
         L=(8, 8, 8, 8), eps=0.5, seed=5, c_sw=1.5, mu=0.005, delta=5.0, nv=8,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, m0=-0.4),
 }
+# learned preconditioner stage, trained on 8 seeded fields and tested on 4 held-out ones
+LEARNED = dict(L=(16, 16, 16, 16), eps=0.5, c_sw=1.5, mu=0.003, delta=5.0, nv=20, agg=(4, 4, 4, 4),
+               sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, m0_key="16x16x16x32_eps0.5_seed1",
+               train_seeds=tuple(range(101, 109)), test_seeds=tuple(range(201, 205)), pairs_per_field=256,
+               epochs=8, batch=32, lr=2e-3)
+WORKLOADS["16x16x16x16_learned"] = dict(LEARNED)
 DEFAULT_WORKLOAD = "16x16x16x32_2lvl_nv20"
 COUNTS_FILE = os.path.join(ROOT, "profiles", "bench_unit_counts.json")
 
@@ -313,22 +320,41 @@ def main_native(args):
     m0, m0_src = (args.m0, "command line") if args.m0 is not None else workload_m0(wl)
     L, nv, seed = wl["L"], wl["nv"], wl["seed"] + rank  # one independent replica per rank
     U = inputs.gauge_field(L, wl["eps"], seed)
-    tv = inputs.random_test_vectors(L, nv, seed + inputs.TV_SEED_OFFSET)
     levels = wl.get("levels", 2)
-    if levels == 3:  # level-1 random vectors follow the fine ones
-        Lc1 = tuple(L[d] // wl["agg"][d] for d in range(4))
-        w0 = inputs.random_coarse_vectors(Lc1, 2 * nv, wl["nv2"], seed + inputs.TV_SEED_OFFSET + 1)
-        tv = np.concatenate([tv.ravel(), w0.ravel()])
     nrhs = wl.get("nrhs", 1)
     rb = wl.get("rhs_batch", nrhs)  # right-hand sides per tm_solve call
-    if wl.get("point"):
-        b, _ = inputs.point_sources(L, seed + inputs.RHS_SEED_OFFSET)
+    V = 1
+    for n in L:
+        V *= n
+    Lc1 = tuple(L[d] // wl["agg"][d] for d in range(4))
+    n_w = wl["nv2"] * (V // (wl["agg"][0] * wl["agg"][1] * wl["agg"][2] * wl["agg"][3])) * 2 * nv \
+        if levels == 3 else 0
+    if wl.get("device_inputs"):
+        # the FP64 test vectors (tens of GB) are drawn on the device with a seeded
+        # generator; the point sources are built there too; no host copies
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(seed + inputs.TV_SEED_OFFSET)
+        tvd = torch.randn((nv * V * 12 + n_w,), dtype=torch.complex128, device="cuda", generator=gen)
+        x0 = inputs.point_source_site(L, seed + inputs.RHS_SEED_OFFSET)
+        site = ((x0[0] * L[1] + x0[1]) * L[2] + x0[2]) * L[3] + x0[3]
+        bd = torch.zeros((12, V, 4, 3), dtype=torch.complex128, device="cuda")
+        for k in range(12):
+            bd[k, site, k // 3, k % 3] = 1.0
+        Ud = torch.from_numpy(U).cuda()
+        Uh = tvh = bh = xh = None
     else:
-        b = inputs.gaussian_spinor(L, seed + inputs.RHS_SEED_OFFSET)
-    Ud, tvd, bd = (torch.from_numpy(a).cuda() for a in (U, tv, b))
+        tv = inputs.random_test_vectors(L, nv, seed + inputs.TV_SEED_OFFSET)
+        if levels == 3:  # level-1 random vectors follow the fine ones
+            w0 = inputs.random_coarse_vectors(Lc1, 2 * nv, wl["nv2"], seed + inputs.TV_SEED_OFFSET + 1)
+            tv = np.concatenate([tv.ravel(), w0.ravel()])
+        if wl.get("point"):
+            b, _ = inputs.point_sources(L, seed + inputs.RHS_SEED_OFFSET)
+        else:
+            b = inputs.gaussian_spinor(L, seed + inputs.RHS_SEED_OFFSET)
+        Ud, tvd, bd = (torch.from_numpy(a).cuda() for a in (U, tv, b))
+        Uh, tvh, bh = (torch.from_numpy(a).pin_memory() for a in (U, tv, b))
+        xh = torch.zeros(bh.shape, dtype=bh.dtype).pin_memory()
     xd = torch.zeros_like(bd)
-    Uh, tvh, bh = (torch.from_numpy(a).pin_memory() for a in (U, tv, b))
-    xh = torch.zeros(bh.shape, dtype=bh.dtype).pin_memory()
     stream = torch.cuda.current_stream()
     extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart") if k in wl}
     extra["coarse_mma"] = args.coarse_mma if args.coarse_mma is not None else wl.get("coarse_mma", 0)
@@ -393,13 +419,14 @@ def main_native(args):
     step_infos = list(infos)
     del Ud, tvd, bd, xd  # the host-buffer run stages its own copies
     torch.cuda.empty_cache()
-    # end-to-end through the C ABI with pinned host buffers
-    step(Uh, tvh, bh, xh)
-    sec_e2e = timed(Uh, tvh, bh, xh, args.steps, profile=False)
-    # correctness of the last solution: true residual by the GPU is in info; spot-check
-    x_last = xh.numpy()
-    h2d = (Uh.numel() + tvh.numel() + bh.numel() + xh.numel()) * 16
-    d2h = xh.numel() * 16
+    sec_e2e = None
+    h2d = d2h = 0
+    if Uh is not None:
+        # end-to-end through the C ABI with pinned host buffers
+        step(Uh, tvh, bh, xh)
+        sec_e2e = timed(Uh, tvh, bh, xh, args.steps, profile=False)
+        h2d = (Uh.numel() + tvh.numel() + bh.numel() + xh.numel()) * 16
+        d2h = xh.numel() * 16
     tm.tm_destroy(h)
 
     if rank != 0:
@@ -470,9 +497,6 @@ def main_native(args):
                    "note": "unit counts per step of the hot path (algorithmic counts of this "
                            "method on this workload), used to scale the oracle's per-unit costs"},
                   open(COUNTS_FILE, "w"), indent=1)
-    V = 1
-    for n in L:
-        V *= n
     line = {
         "metric": "solve seconds to 1e-10 rel. residual; D(mu) HBM GB/s and D_c TFLOP/s vs peak",
         "value": round(value, 5),
@@ -505,8 +529,10 @@ def main_native(args):
             "coarse_iters": [i["coarse_iters"] for i in step_infos],
             "true_relres": max(i["true_relres"] for i in step_infos),
         },
-        "e2e": {"value": round(sec_e2e / units_total, 5), "unit": "s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": ({"value": round(sec_e2e / units_total, 5), "unit": "s",
+                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h} if sec_e2e is not None else
+                {"value": None, "reason": "inputs generated on the device: pinned host copies of the FP64 "
+                                          "test vectors would not fit the host memory twice"}),
         "gpu_launches": int(launches),
         "roofline": roof,
         "kernels_one_step": kernels,
@@ -521,6 +547,108 @@ def main_native(args):
 # ---------------------------------------------------------------------------
 # reference arm: the oracle alone
 # ---------------------------------------------------------------------------
+def main_learned(args):
+    """Train the learned layer on 8 fields, then solve on 4 held-out fields with
+    no stage after the K-cycle, the learned layer (FP16 inference) and one SAP
+    sweep in its place; report solve times (setup excluded) and iterations."""
+    import numpy as np
+    import torch
+    import inputs
+    import paper_1611_01034_gb300 as tm
+
+    wl = WORKLOADS[args.workload]
+    m0, m0_src = workload_m0(wl)
+    L, nv = wl["L"], wl["nv"]
+    stream = torch.cuda.current_stream()
+
+    def handle(mode):
+        p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv, agg=wl["agg"],
+                      sap_block=wl["sap_block"], setup_iters=wl["setup_iters"], cycle_prec=tm.TM_F32,
+                      max_rhs=16, nn_mode=mode, nn_prec=tm.TM_F16)
+        return tm.tm_create(p, stream)
+
+    fr_bytes = None
+    h = handle(0)
+    rng = np.random.default_rng(7)
+    w0 = 0.02 * (rng.standard_normal(2304) + 1j * rng.standard_normal(2304))
+    tm.tm_nn_set_weights(h, w0)
+    pairs = []
+    t0 = time.time()
+    npp = wl["pairs_per_field"]
+    for seed in wl["train_seeds"]:
+        U = torch.from_numpy(inputs.gauge_field(L, wl["eps"], seed)).cuda()
+        tv = torch.from_numpy(inputs.random_test_vectors(L, nv, seed + inputs.TV_SEED_OFFSET)).cuda()
+        tm.tm_load_gauge(h, U)
+        tm.tm_setup(h, tv)
+        fr_bytes = tm.tm_field_bytes(h, 0, tm.TM_F32, npp)
+        r = torch.zeros(fr_bytes, dtype=torch.uint8, device="cuda")
+        e = torch.zeros_like(r)
+        e0 = torch.from_numpy(inputs.gaussian_spinor(L, seed + 3000, nrhs=npp)).cuda()
+        tm.tm_nn_pairs(h, e0, r, e, npp)
+        pairs.append((U, r, e))
+        del tv, e0
+    torch.cuda.synchronize()
+    t_pairs = time.time() - t0
+    t0 = time.time()
+    losses = []
+    for ep in range(wl["epochs"]):
+        lsum = 0.0
+        for U, r, e in pairs:
+            tm.tm_load_gauge(h, U)
+            lsum += float(tm.tm_nn_train(h, r, e, npp, 1, wl["batch"], wl["lr"])[0])
+        losses.append(lsum / len(pairs))
+    t_train = time.time() - t0
+    w = tm.tm_nn_get_weights(h)
+    tm.tm_destroy(h)
+    del pairs
+    torch.cuda.empty_cache()
+
+    modes = {"plain": 0, "learned_fp16": 1, "sap_standin": 2}
+    res = {k: {"solve_s": [], "iters": [], "true_relres": []} for k in modes}
+    for seed in wl["test_seeds"]:
+        U = torch.from_numpy(inputs.gauge_field(L, wl["eps"], seed)).cuda()
+        tv = torch.from_numpy(inputs.random_test_vectors(L, nv, seed + inputs.TV_SEED_OFFSET)).cuda()
+        b = torch.from_numpy(inputs.gaussian_spinor(L, seed + inputs.RHS_SEED_OFFSET)).cuda()
+        for name, mode in modes.items():
+            hh = handle(mode)
+            tm.tm_load_gauge(hh, U)
+            tm.tm_setup(hh, tv)
+            tm.tm_nn_set_weights(hh, w)
+            times = []
+            for rep_ in range(1 + max(1, args.steps)):
+                x = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st, info = tm.tm_solve(hh, b, x, 1, wl["tol"])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if st != tm.TM_OK:
+                    raise RuntimeError(f"solve failed ({name}): {tm.tm_status_string(st)}")
+                if rep_ > 0:
+                    times.append(e0.elapsed_time(e1) / 1000.0)
+            res[name]["solve_s"].append(statistics.median(times))
+            res[name]["iters"].append(info.iters)
+            res[name]["true_relres"].append(info.true_relres)
+            tm.tm_destroy(hh)
+    summary = {k: {"solve_s_mean": round(statistics.mean(v["solve_s"]), 5),
+                   "iters": v["iters"], "max_true_relres": max(v["true_relres"])} for k, v in res.items()}
+    print(json.dumps({
+        "metric": "solve seconds to 1e-10 rel. residual (held-out fields, setup excluded)",
+        "value": summary["learned_fp16"]["solve_s_mean"], "unit": "s", "n_gpus": 1,
+        "higher_is_better": False, "dtype": "f64 outer / f32 cycle / f16 learned layer",
+        "data": "synthetic (seeded random SU(3) fields U = exp(0.5 i H); Gaussian rhs)",
+        "config": {"workload": args.workload, "lattice_TZYX": list(L), "m0": m0, "m0_source": m0_src,
+                   "mu": wl["mu"], "delta": wl["delta"], "nv": nv, "train_fields": list(wl["train_seeds"]),
+                   "test_fields": list(wl["test_seeds"]), "pairs": npp * len(wl["train_seeds"]),
+                   "epochs": wl["epochs"], "batch": wl["batch"], "lr": wl["lr"]},
+        "training": {"pairs_s": round(t_pairs, 2), "train_s": round(t_train, 2),
+                     "loss_per_epoch": [round(l, 5) for l in losses]},
+        "comparison": summary,
+    }), flush=True)
+
+
 def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -571,6 +699,8 @@ def main():
         return
     if args.impl == "reference":
         main_reference(args)
+    elif args.workload == "16x16x16x16_learned":
+        main_learned(args)
     else:
         main_native(args)
 

@@ -97,6 +97,12 @@ def gaussian_spinor(L, seed: int, nrhs: int | None = None) -> np.ndarray:
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
 
 
+def point_source_site(L, seed: int) -> tuple:
+    """The site x0 of the twelve point sources (drawn uniformly, seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return tuple(int(rng.integers(0, int(n))) for n in L)
+
+
 def point_sources(L, seed: int) -> tuple[np.ndarray, tuple]:
     """Twelve spin-colour point sources at one random site x0.
 
@@ -104,8 +110,7 @@ def point_sources(L, seed: int) -> tuple[np.ndarray, tuple]:
     to delta_{x,x0} delta_{s,s0} delta_{c,c0}.
     """
     T, Z, Y, X = (int(v) for v in L)
-    rng = np.random.Generator(np.random.PCG64(seed))
-    x0 = tuple(int(rng.integers(0, n)) for n in (T, Z, Y, X))
+    x0 = point_source_site(L, seed)
     b = np.zeros((12, T, Z, Y, X, 4, 3), dtype=np.complex128)
     for s in range(4):
         for c in range(3):

@@ -1450,7 +1450,8 @@ void validate(const tm_params* p) {
       bad("negative level-1 iteration count");
   }
   const double lv = (double)p->L[0] * p->L[1] * p->L[2] * p->L[3];
-  if (lv * 24.0 * p->max_rhs > 4.0e9 || lv * 24.0 * p->nv > 4.0e9) bad("lattice too large for 32-bit site indexing");
+  // sites and the reals of one field are indexed in 32 bits; offsets between fields in 64 bits
+  if (lv * 24.0 >= 2147483647.0) bad("lattice too large for 32-bit site indexing");
 }
 
 template <typename T>
