@@ -81,6 +81,14 @@ def gauge_field(L, eps: float, seed: int) -> np.ndarray:
     return _expi_hermitian(H, eps)
 
 
+def evolve_gauge(U: np.ndarray, eta: float, seed: int) -> np.ndarray:
+    """A nearby gauge field exp(i*eta*H'(x)) U_mu(x) with a fresh random H'
+    (a stand-in for one molecular-dynamics step of an HMC trajectory)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    R = _expi_hermitian(random_hermitian_traceless(rng, U.shape[:-2]), eta)
+    return np.einsum("...ij,...jk->...ik", R, U)
+
+
 def unit_gauge(L) -> np.ndarray:
     """The free field U_mu(x) = 1."""
     T, Z, Y, X = (int(v) for v in L)

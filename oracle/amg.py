@@ -131,6 +131,19 @@ class TwoLevel:
         self.test_vectors = v
         return v
 
+    def update(self, iters: int, v: np.ndarray | None = None) -> np.ndarray:
+        """Setup update (Sec. 3: after the gauge field changes the setup is updated
+        by a few iterations instead of rebuilt): P and D_c from the current test
+        vectors on this operator, then `iters` iterations v_i <- B(v_i) as in setup."""
+        v = (self.test_vectors if v is None else v).copy()
+        self.build_coarse(v)
+        for _ in range(iters):
+            v = np.stack([self.kcycle(v[i]) for i in range(v.shape[0])])
+            v = normalise(v)
+            self.build_coarse(v)
+        self.test_vectors = v
+        return v
+
     # -- solve -----------------------------------------------------------------------
     def solve(self, b: np.ndarray, tol: float = 1e-10, x0=None):
         prm = self.prm

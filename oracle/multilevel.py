@@ -319,6 +319,24 @@ class ThreeLevel:
         self.test_vectors, self.test_vectors1 = v, w
         return v, w
 
+    def update(self, fine_iters: int, coarse_iters: int, v=None, w=None):
+        """Setup update (Sec. 3: one fine and three first-coarse-grid iterations
+        after the gauge field changes): P1, D_c1 and P2, D_c2 from the current
+        test vectors, then the fine and the level-1 iterations of setup."""
+        v = (self.test_vectors if v is None else v).copy()
+        w = (self.test_vectors1 if w is None else w).copy()
+        self.build_level1(v)
+        self.build_level2(w)
+        for _ in range(fine_iters):
+            v = normalise(np.stack([self.kcycle(v[i]) for i in range(v.shape[0])]))
+            self.build_level1(v)
+            self.build_level2(w)
+        for _ in range(coarse_iters):
+            w = normalise(np.stack([self.kcycle1(w[j]) for j in range(w.shape[0])]))
+            self.build_level2(w)
+        self.test_vectors, self.test_vectors1 = v, w
+        return v, w
+
     def solve(self, b: np.ndarray, tol: float = 1e-10, x0=None):
         prm = self.prm
         return gmres(self.op.apply, b, x0=x0, tol=tol, restart=prm.restart, maxit=prm.maxit, M=self.kcycle)
