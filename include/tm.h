@@ -191,6 +191,15 @@ tm_status tm_setup(tm_handle* h, const double* test_vectors);
  * levels also P2, D_c2 from the appended level-1 vectors, as in tm_setup). */
 tm_status tm_setup_from_vectors(tm_handle* h, const double* test_vectors);
 
+/* Setup update after the gauge field changed (Sec. 3: during an HMC
+ * trajectory the setup is updated by one fine and three first-coarse-grid
+ * iterations instead of rebuilt).  Call after tm_load_gauge with the new
+ * field: P and D_c (and P2, D_c2) are rebuilt from the test vectors of the
+ * last setup, then fine_iters times v_i <- B(v_i) and, with three levels,
+ * coarse_iters times w_j <- B1(w_j), as in tm_setup.  Errors: TM_ERR_STATE
+ * (no gauge field, or no earlier setup on this handle). */
+tm_status tm_setup_update(tm_handle* h, int fine_iters, int coarse_iters);
+
 /* Change mu and delta without a new setup (Sec. 1: D_c(mu) = D_c +
  * i mu Gamma5_c, so only the diagonal shift and the odd-site inverses of the
  * coarse Schur complement change; one setup serves D(+mu) and D(-mu)). */

@@ -24,7 +24,7 @@ from ._binding import (  # noqa: F401
     tm_params_default, tm_create, tm_destroy, tm_status_string, tm_last_error,
     tm_load_gauge, tm_setup, tm_setup_from_vectors, tm_set_mu, tm_solve, tm_solve_squared,
     tm_field_bytes, tm_pack, tm_unpack, tm_apply, tm_sap, tm_restrict, tm_prolong,
-    tm_coarse_solve, tm_coarse_solve_noalloc, tm_kcycle, tm_schur, tm_nn_set_weights, tm_nn_get_weights, tm_nn_apply, tm_nn_pairs,
+    tm_coarse_solve, tm_coarse_solve_noalloc, tm_kcycle, tm_setup_update, tm_schur, tm_nn_set_weights, tm_nn_get_weights, tm_nn_apply, tm_nn_pairs,
     tm_nn_grad, tm_nn_train, tm_sap1, tm_restrict1, tm_prolong1, tm_kcycle1,
     tm_export, tm_synchronize,
     tm_profile, tm_profile_kinds, tm_profile_name, tm_profile_read,

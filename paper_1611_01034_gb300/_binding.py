@@ -72,6 +72,7 @@ _SIGS = {
     "tm_coarse_solve_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, POINTER(c_int)]),
     "tm_kcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "tm_schur": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
+    "tm_setup_update": (c_int, [c_void_p, c_int, c_int]),
     "tm_nn_set_weights": (c_int, [c_void_p, c_void_p]),
     "tm_nn_get_weights": (c_int, [c_void_p, c_void_p]),
     "tm_nn_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
@@ -253,6 +254,10 @@ def tm_coarse_solve_noalloc(h, prec, b, x, tol, maxit) -> int:
 
 def tm_kcycle(h, prec, v, z, nrhs) -> None:
     _check(lib().tm_kcycle(h, prec, _ptr(v), _ptr(z), nrhs), h)
+
+
+def tm_setup_update(h, fine_iters, coarse_iters=0) -> None:
+    _check(lib().tm_setup_update(h, fine_iters, coarse_iters), h)
 
 
 def tm_schur(h, prec, ve, ye, nrhs) -> None:

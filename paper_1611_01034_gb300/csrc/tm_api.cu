@@ -106,6 +106,7 @@ struct tm_handle {
   long adam_t = 0;
   std::map<std::string, Buf> work;
   bool gauge_ok = false, setup_ok = false;
+  bool tv_ok = false;  // test vectors of an earlier setup are present (they survive a new gauge field)
   std::string err;
   long long coarse_iters = 0;
   int kcycles = 0;
@@ -929,6 +930,22 @@ void normalise_fields(tm_handle* h, T* f, int nrhs) {
 }
 
 template <typename T>
+void setup_iterate(tm_handle* h, int fine, int coarse);
+
+// P, D_c (and P2, D_c2) rebuilt from the current test vectors, e.g. on a new gauge field
+template <typename T>
+void setup_rebuild(tm_handle* h) {
+  const long fr = fine_reals(h);
+  CK(cudaMemcpyAsync(h->P, h->tv, fr * h->p.nv * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+  build_coarse<T>(h);
+  if (h->three) {
+    CK(cudaMemcpyAsync(h->P2, h->tv1, 2 * level1_cx(h) * h->p.nv2 * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+    build_level2<T>(h);
+  }
+  check_flags(h);
+}
+
+template <typename T>
 void setup_impl(tm_handle* h, const double* tv_dev, bool adaptive) {
   const int nv = h->p.nv, nv2 = h->p.nv2;
   const long fr = fine_reals(h);
@@ -962,9 +979,25 @@ void setup_impl(tm_handle* h, const double* tv_dev, bool adaptive) {
     build_level2<T>(h);
   }
   check_flags(h);
-  if (adaptive) {
+  if (adaptive) setup_iterate<T>(h, h->p.setup_iters, h->p.coarse_setup_iters);
+  sync(h);
+}
+
+// setup iterations from the current test vectors: `fine` times v_i <- B(v_i),
+// normalised, P, D_c (and P2, D_c2 from the current level-1 vectors) rebuilt;
+// then with three levels `coarse` times w_j <- B1(w_j), normalised, P2, D_c2 rebuilt
+template <typename T>
+void setup_iterate(tm_handle* h, int fine, int coarse) {
+  const int nv = h->p.nv, nv2 = h->p.nv2;
+  const long fr = fine_reals(h);
+  T* tv = static_cast<T*>(h->tv);
+  T* P = static_cast<T*>(h->P);
+  const long c1 = 2 * level1_cx(h);
+  T* tv1 = static_cast<T*>(h->tv1);
+  T* P2 = static_cast<T*>(h->P2);
+  {
     T* z = W<T>(h, "setup_z", fr * nv);
-    for (int it = 0; it < h->p.setup_iters; ++it) {
+    for (int it = 0; it < fine; ++it) {
       kcycle<T>(h, tv, z, nv);
       CK(cudaMemcpyAsync(tv, z, fr * nv * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
       normalise_fields<T>(h, tv, nv);
@@ -978,7 +1011,7 @@ void setup_impl(tm_handle* h, const double* tv_dev, bool adaptive) {
     }
     if (h->three) {
       T* z1 = W<T>(h, "setup_z1", c1 * nv2);
-      for (int it = 0; it < h->p.coarse_setup_iters; ++it) {
+      for (int it = 0; it < coarse; ++it) {
         kcycle1<T>(h, tv1, z1, nv2);
         CK(cudaMemcpyAsync(tv1, z1, c1 * nv2 * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
         normalise_vecs<T>(h, tv1, c1 / 2, nv2);
@@ -1812,6 +1845,25 @@ static tm_status setup_common(tm_handle* h, const double* tv, bool adaptive) {
     setup_impl<double>(h, d, adaptive);
   else
     setup_impl<float>(h, d, adaptive);
+  h->setup_ok = true;
+  h->tv_ok = true;
+  API_END
+}
+
+tm_status tm_setup_update(tm_handle* h, int fine_iters, int coarse_iters) {
+  if (!h || fine_iters < 0 || coarse_iters < 0) return TM_ERR_ARG;
+  API_BEGIN
+  if (!h->gauge_ok) raise(TM_ERR_STATE, "tm_load_gauge must come first");
+  if (!h->tv_ok) raise(TM_ERR_STATE, "needs the test vectors of an earlier setup");
+  h->setup_ok = false;
+  if (h->p.cycle_prec == TM_F64) {
+    setup_rebuild<double>(h);
+    setup_iterate<double>(h, fine_iters, coarse_iters);
+  } else {
+    setup_rebuild<float>(h);
+    setup_iterate<float>(h, fine_iters, coarse_iters);
+  }
+  sync(h);
   h->setup_ok = true;
   API_END
 }
