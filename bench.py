@@ -52,7 +52,7 @@ WORKLOADS = {
         L=(96, 48, 48, 48), eps=0.6, seed=1, c_sw=1.57551, mu=0.0009, delta=5.0, nv=24,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, nrhs=12, point=True,
         levels=3, nv2=28, agg2=(2, 2, 2, 2), sap_block1=(2, 2, 2, 2), coarse_setup_iters=3,
-        restart=16, rhs_batch=1, coarse_mma=1, m0_key="16x16x16x32_eps0.6_seed1_csw1.57551",
+        restart=16, rhs_batch=1, coarse_mma=1, sap1_prec=2, m0_key="16x16x16x32_eps0.6_seed1_csw1.57551",
         device_inputs=True),
     "8x8x8x8_2lvl_nv8": dict(
         L=(8, 8, 8, 8), eps=0.5, seed=5, c_sw=1.5, mu=0.005, delta=5.0, nv=8,
@@ -356,7 +356,8 @@ def main_native(args):
         xh = torch.zeros(bh.shape, dtype=bh.dtype).pin_memory()
     xd = torch.zeros_like(bd)
     stream = torch.cuda.current_stream()
-    extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart") if k in wl}
+    extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec")
+             if k in wl}
     extra["coarse_mma"] = args.coarse_mma if args.coarse_mma is not None else wl.get("coarse_mma", 0)
     p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv,
                   agg=wl["agg"], sap_block=wl["sap_block"], setup_iters=wl["setup_iters"],
@@ -516,6 +517,7 @@ def main_native(args):
             **({"nv2": wl["nv2"], "aggregate2": list(wl["agg2"]), "sap_block1": list(wl["sap_block1"]),
                 "coarse_setup_iters": wl["coarse_setup_iters"]} if levels == 3 else {}),
             "restart": p.restart, "rhs_per_solve_call": rb, "coarse_mma": p.coarse_mma,
+            **({"sap1_prec": "f16" if p.sap1_prec == 2 else "f32"} if levels == 3 else {}),
             "nv": nv, "aggregate": list(wl["agg"]), "sap_block": list(wl["sap_block"]),
             "m0": m0, "m0_source": m0_src, "c_sw": wl["c_sw"], "mu": wl["mu"],
             "delta": wl["delta"], "setup_iters": wl["setup_iters"], "tol": wl["tol"], "nrhs": nrhs,

@@ -126,6 +126,10 @@ typedef struct {
      nn_prec: TM_F32, or TM_F16 for FP16 hidden channels and weights. */
   int nn_mode;
   int nn_prec;
+  /* Storage of the level-1 operator blocks read by the level-1 SAP smoother
+     (three levels, cycle_prec = TM_F32): TM_F32, or TM_F16 for an FP16 copy
+     (half the bytes; FP32 arithmetic).  The level-1 Krylov solve keeps FP32. */
+  int sap1_prec;
 } tm_params;
 
 typedef struct {
@@ -143,7 +147,8 @@ typedef struct {
  * maxit = 1000, cycle_prec = TM_F32, max_rhs = 1, levels = 2, nv2 = 28,
  * agg2 = sap_block1 = 2^4, mr_iters1 = 4, pre_smooth1 = 0, post_smooth1 = 2,
  * init_sweeps1 = 3, coarse_setup_iters = 3, coarsest_tol = 5e-2,
- * coarsest_maxit = 200, coarse_mma = 0, nn_mode = 0, nn_prec = TM_F32.
+ * coarsest_maxit = 200, coarse_mma = 0, nn_mode = 0, nn_prec = TM_F32,
+ * sap1_prec = TM_F32.
  * L, m0, c_sw, mu are 0. */
 void tm_params_default(tm_params* p);
 

@@ -8,9 +8,22 @@
 // is N_v2 such fields (field j holds column j of P2_{a,chi} in the chirality-chi
 // half of every site of aggregate a), D_c1 and D_c2 are stored like the first
 // coarse operator: [site][9 blocks][col][row].
+#include <cuda_fp16.h>
+
 #include "tm_kernels.h"
 
 namespace tmamg {
+
+// D_c1 block entry: stored in T, or as FP16 (re, im) pairs when H (arithmetic stays in T)
+template <typename T, bool H>
+__device__ __forceinline__ cx<T> ld_blk(const void* __restrict__ Dc, long idx) {
+  if constexpr (H) {
+    const float2 f = __half22float2(reinterpret_cast<const __half2*>(Dc)[idx]);
+    return cx<T>{(T)f.x, (T)f.y};
+  } else {
+    return reinterpret_cast<const cx<T>*>(Dc)[idx];
+  }
+}
 
 __device__ __forceinline__ int c_nb(const Lat& g, int s, int t) {
   if (t == 0) return s;
@@ -23,8 +36,8 @@ __device__ __forceinline__ int c_nb(const Lat& g, int s, int t) {
 // ===========================================================================
 // coarse SAP: one colour; CTA = one block of level-1 sites, thread = (site, row)
 // ===========================================================================
-template <typename T>
-__global__ void k_csap(const T* __restrict__ Dc, const T* __restrict__ b, T* __restrict__ x, CSapGeom sg, T mu,
+template <typename T, bool H>
+__global__ void k_csap(const void* __restrict__ Dc, const T* __restrict__ b, T* __restrict__ x, CSapGeom sg, T mu,
                        int n_mr, int colour) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = sg.n, BS = sg.bsites;
@@ -62,15 +75,15 @@ __global__ void k_csap(const T* __restrict__ Dc, const T* __restrict__ b, T* __r
   }
   for (int d = 0; d < 4; ++d) c[d] = bc4[d] * sg.blk[d] + lc[d];
   const int s = ((c[0] * g.L[1] + c[1]) * g.L[2] + c[2]) * g.L[3] + c[3];
-  const cx<T>* B = reinterpret_cast<const cx<T>*>(Dc) + (long)s * 9 * n * n;
+  const long B = (long)s * 9 * n * n;  // block entries of site s
   const T sg5 = row < n / 2 ? -mu : mu;  // i mu Gamma5_c
   cx<T> r{0, 0}, e{0, 0};
   if (act) {
     cx<T> acc{0, 0};
     for (int t = 0; t < 9; ++t) {
       const cx<T>* src = xx + (long)c_nb(g, s, t) * n;
-      const cx<T>* Bt = B + (long)t * n * n;
-      for (int col = 0; col < n; ++col) cfma(acc, Bt[(long)col * n + row], src[col]);
+      const long Bt = B + (long)t * n * n;
+      for (int col = 0; col < n; ++col) cfma(acc, ld_blk<T, H>(Dc, Bt + (long)col * n + row), src[col]);
     }
     const cx<T> xs = xx[(long)s * n + row];
     acc.r -= sg5 * xs.i;
@@ -91,9 +104,9 @@ __global__ void k_csap(const T* __restrict__ Dc, const T* __restrict__ b, T* __r
           if (bwd ? lc[mu_d] == 0 : lc[mu_d] == sg.blk[mu_d] - 1) continue;  // leaves the block
           ln = bwd ? l - lst[mu_d] : l + lst[mu_d];
         }
-        const cx<T>* Bt = B + (long)t * n * n;
+        const long Bt = B + (long)t * n * n;
         const cx<T>* src = rs + (size_t)ln * n;
-        for (int col = 0; col < n; ++col) cfma(q, Bt[(long)col * n + row], src[col]);
+        for (int col = 0; col < n; ++col) cfma(q, ld_blk<T, H>(Dc, Bt + (long)col * n + row), src[col]);
       }
       q.r -= sg5 * r.i;
       q.i += sg5 * r.r;
@@ -116,11 +129,26 @@ __global__ void k_csap(const T* __restrict__ Dc, const T* __restrict__ b, T* __r
 
 template <typename T>
 void launch_csap_colour(const T* Dc, const T* b, T* x, const CSapGeom& sg, double mu, int n_mr, int colour,
-                        int nrhs, cudaStream_t st) {
+                        int nrhs, cudaStream_t st, const void* Dc_half) {
   const int threads = (sg.bsites * sg.n + 31) / 32 * 32;
   const size_t smem = (size_t)sg.bsites * sg.n * sizeof(cx<T>) + 32 * 3 * sizeof(T);
   dim3 grid(sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2, nrhs);
-  k_csap<T><<<grid, threads, smem, st>>>(Dc, b, x, sg, (T)mu, n_mr, colour);
+  if (Dc_half)
+    k_csap<T, true><<<grid, threads, smem, st>>>(Dc_half, b, x, sg, (T)mu, n_mr, colour);
+  else
+    k_csap<T, false><<<grid, threads, smem, st>>>(Dc, b, x, sg, (T)mu, n_mr, colour);
+}
+
+// FP16 (re, im) copy of FP32 coarse blocks
+__global__ void k_to_half2(const float2* __restrict__ in, __half2* __restrict__ out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = __float22half2_rn(in[i]);
+}
+
+void launch_blocks_to_half(const float* Dc, void* out, long ncx, cudaStream_t st) {
+  long b = (ncx + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  k_to_half2<<<(int)b, 256, 0, st>>>(reinterpret_cast<const float2*>(Dc), static_cast<__half2*>(out), ncx);
 }
 
 // ===========================================================================
@@ -393,7 +421,7 @@ void launch_cbuild(const T* Dc1, const T* P2, T* Dc2, const CAggGeom& ag, cudaSt
 
 #define TM_INST(T)                                                                                           \
   template void launch_csap_colour<T>(const T*, const T*, T*, const CSapGeom&, double, int, int, int,       \
-                                      cudaStream_t);                                                         \
+                                      cudaStream_t, const void*);                                            \
   template void launch_corth<T>(T*, const CAggGeom&, int*, cudaStream_t);                                   \
   template void launch_crestrict<T>(const T*, const T*, T*, const CAggGeom&, int, cudaStream_t);            \
   template void launch_cprolong<T>(const T*, const T*, T*, const CAggGeom&, int, bool, cudaStream_t);       \

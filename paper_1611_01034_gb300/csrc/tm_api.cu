@@ -95,6 +95,7 @@ struct tm_handle {
   int* d_even2 = nullptr;
   int* d_odd2 = nullptr;
   int* d_cidx2 = nullptr;
+  void* Dc1h = nullptr;  // FP16 copy of D_c1 for the level-1 SAP (sap1_prec = TM_F16)
   // odd-even Schur complement of the coarsest level on the tensor cores
   bool tc_on = false;
   TcGeom tc{};
@@ -492,6 +493,12 @@ void build_coarse(tm_handle* h) {
   CKL();
   launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, static_cast<T*>(h->Dc), h->ag, h->p.bc_t, h->st);
   CKL();
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->Dc1h) {  // FP16 blocks for the level-1 SAP
+      launch_blocks_to_half(static_cast<const float*>(h->Dc), h->Dc1h, (long)h->gc.V * 9 * h->n * h->n, h->st);
+      CKL();
+    }
+  }
   if (!h->three) {  // with three levels the odd-even solve runs on level 2
     launch_oe_invert<T>(static_cast<T*>(h->Dc), static_cast<T*>(h->Dinv), h->oe, mu_c(h), h->d_err, h->st);
     CKL();
@@ -829,7 +836,7 @@ void csap_sweeps(tm_handle* h, const T* b, T* x, int sweeps, int nrhs) {
     for (int colour = 0; colour < 2; ++colour) {
       Prof pf(h, PK_CSAP, nrhs);
       launch_csap_colour<T>(static_cast<const T*>(h->Dc), b, x, h->csg, h->p.mu, h->p.mr_iters1, colour, nrhs,
-                            h->st);
+                            h->st, std::is_same<T, float>::value ? h->Dc1h : nullptr);
       CKL();
     }
 }
@@ -1458,6 +1465,9 @@ void validate(const tm_params* p) {
   if (p->nn_mode < 0 || p->nn_mode > 2) bad("nn_mode must be 0, 1 or 2");
   if (p->nn_mode == 1 && p->cycle_prec != TM_F32) bad("the learned layer needs cycle_prec = TM_F32");
   if (p->nn_prec != TM_F32 && p->nn_prec != TM_F16) bad("nn_prec must be TM_F32 or TM_F16");
+  if (p->sap1_prec != TM_F32 && p->sap1_prec != TM_F16) bad("sap1_prec must be TM_F32 or TM_F16");
+  if (p->sap1_prec == TM_F16 && (p->levels != 3 || p->cycle_prec != TM_F32))
+    bad("sap1_prec = TM_F16 needs levels = 3 and cycle_prec = TM_F32");
   if (p->bc_t != 1.0 && p->bc_t != -1.0) bad("bc_t must be +1 or -1");
   if (!(p->delta >= 1.0)) bad("delta must be >= 1");
   if (p->max_rhs < 1) bad("max_rhs must be >= 1");
@@ -1621,6 +1631,7 @@ void tm_params_default(tm_params* p) {
   p->coarse_mma = 0;
   p->nn_mode = 0;
   p->nn_prec = TM_F32;
+  p->sap1_prec = TM_F32;
 }
 
 const char* tm_status_string(int s) {
@@ -1653,7 +1664,7 @@ void tm_destroy(tm_handle* h) {
     if (kv.second.first) cudaFreeHost(kv.second.first);
   void* p3[] = {h->tv1, h->P2, h->Dc2, h->Dinv2, h->d_even2, h->d_odd2, h->d_cidx2,
                 h->tc.even, h->tc.even_lo, h->tc.odd, h->tc.odd_lo, h->tc.nbr_e, h->tc.nbr_o,
-                h->d_nnw, h->d_nngrad};
+                h->d_nnw, h->d_nngrad, h->Dc1h};
   for (void* q : p3)
     if (q) cudaFree(q);
   for (auto& r : h->recs) {
@@ -1782,6 +1793,7 @@ tm_status tm_create(tm_handle** out, const tm_params* p, void* stream) {
       h->P2 = dalloc((size_t)p->nv2 * h->gc.V * h->n * 2 * cs);
       h->Dc2 = dalloc((size_t)h->gc2.V * 9 * h->n2 * h->n2 * 2 * cs);
       h->Dinv2 = dalloc((size_t)h->nhalf2 * h->n2 * h->n2 * 2 * cs);
+      if (p->sap1_prec == TM_F16) h->Dc1h = dalloc((size_t)h->gc.V * 9 * h->n * h->n * 4);
     }
     if (p->coarse_mma > 0) {  // tensor-core tiles of the coarsest odd-even level
       const int nvc = h->three ? p->nv2 : p->nv, nh = h->three ? h->nhalf2 : h->nhalf;

@@ -109,10 +109,13 @@ struct CAggGeom {
   int asites;
   int nv1, nv2;
 };
-// one colour of SAP on D_c1(mu) x = b (b may be null), nrhs level-1 vectors
+// one colour of SAP on D_c1(mu) x = b (b may be null), nrhs level-1 vectors;
+// with Dc_half (FP16 copy of the FP32 blocks) the blocks are read from it
 template <typename T>
 void launch_csap_colour(const T* Dc, const T* b, T* x, const CSapGeom& sg, double mu, int n_mr, int colour,
-                        int nrhs, cudaStream_t st);
+                        int nrhs, cudaStream_t st, const void* Dc_half = nullptr);
+// FP16 (re, im) copy of ncx complex FP32 numbers
+void launch_blocks_to_half(const float* Dc, void* out, long ncx, cudaStream_t st);
 // P2 <- per (aggregate, chirality) CGS2 of the Nv2 level-1 fields in P2
 template <typename T>
 void launch_corth(T* P2, const CAggGeom& ag, int* err, cudaStream_t st);

@@ -123,6 +123,20 @@ def test_coarse_sap_sweeps(name, with_b):
 
 
 @pytest.mark.parametrize("name", list(CASES))
+def test_coarse_sap_fp16_blocks(name):
+    # FP16 copy of the level-1 blocks read by the smoother (11 significant bits; FP32 arithmetic)
+    t = Three(name, F32, sap1_prec=tm.TM_F16)
+    t.from_vectors()
+    g = t.g
+    b = t.rand1(1)
+    x0 = 0.3 * t.rand1(2)
+    sap = CoarseSAP(t.tl.Dc1, g.p.sap_block1, g.p.mr_iters1)
+    fx = g.pack(1, F32, x0)
+    tm.tm_sap1(g.h, F32, g.pack(1, F32, b), fx, 2, 1)
+    assert rel(g.unpack(1, F32, fx, x0.shape), sap.smooth(b, x0, 2)) <= 5e-3
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_level_transfers_and_applies(name):
     t = Three(name)
     t.from_vectors()
@@ -213,9 +227,9 @@ def test_three_level_adaptive_setup(name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("prec", [F64, F32])
-def test_three_level_solve_true_residual(name, prec):
-    t = Three(name, prec, setup_iters=2, coarse_setup_iters=2)
+@pytest.mark.parametrize("prec,sap1", [(F64, 1), (F32, 1), (F32, 2)])
+def test_three_level_solve_true_residual(name, prec, sap1):
+    t = Three(name, prec, setup_iters=2, coarse_setup_iters=2, sap1_prec=sap1)
     g = t.g
     tm.tm_setup(g.h, t.vectors())
     op = Operator(t.U, t.prm.m0, t.prm.c_sw, t.prm.mu)
