@@ -42,7 +42,7 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "16x16x16x32_2lvl_nv20": dict(
         L=(32, 16, 16, 16), eps=0.5, seed=1, c_sw=1.5, mu=0.003, delta=5.0, nv=20,
-        agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10,
+        agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, coarse_mma=1,
         m0_key="16x16x16x32_eps0.5_seed1"),
     "24x24x24x48_2lvl_nv24_12pt": dict(
         L=(48, 24, 24, 24), eps=0.5, seed=1, c_sw=1.5, mu=0.002, delta=5.0, nv=24,
