@@ -492,6 +492,12 @@ def main_native(args):
                    "unit_costs_s": {k: round(v, 4) for k, v in costs.items() if not k.startswith("_")}}
         except Exception as e:  # report, do not hide
             cpu = {"value": None, "error": str(e)[:300]}
+    scale = None
+    if rank == 0 and world == 1 and not args.no_scale_kernels and args.workload == DEFAULT_WORKLOAD:
+        try:
+            scale = kernels_at_scale(peaks)
+        except Exception as e:  # report, do not hide
+            scale = {"error": str(e)[:300]}
     if args.write_counts:
         os.makedirs(os.path.dirname(COUNTS_FILE), exist_ok=True)
         json.dump({"workload": args.workload, "counts_per_step": counts,
@@ -538,6 +544,7 @@ def main_native(args):
         "gpu_launches": int(launches),
         "roofline": roof,
         "kernels_one_step": kernels,
+        "kernels_at_scale": scale,
         "clocks": clk,
         "cpu_baseline": cpu,
     }
@@ -549,6 +556,79 @@ def main_native(args):
 # ---------------------------------------------------------------------------
 # reference arm: the oracle alone
 # ---------------------------------------------------------------------------
+def kernels_at_scale(peaks: dict) -> dict:
+    """D(mu) applies and the tensor-core coarse Schur complement on a 24^3x48
+    lattice (inputs larger than L2), timed with CUDA events on the library's
+    stream: the D(mu) HBM GB/s and D_c TFLOP/s of the benchmark's metric."""
+    import numpy as np
+    import torch
+    import inputs
+    import paper_1611_01034_gb300 as tm
+
+    L, nv = (48, 24, 24, 24), 24
+    V = 1
+    for n in L:
+        V *= n
+    stream = torch.cuda.current_stream()
+    U = torch.from_numpy(inputs.gauge_field(L, 0.5, 1)).cuda()
+    p = tm.params(L=L, m0=-0.41769, c_sw=1.5, mu=0.002, delta=5.0, nv=nv, agg=(4, 4, 4, 4),
+                  sap_block=(4, 4, 4, 4), cycle_prec=tm.TM_F32, coarse_mma=1, max_rhs=12)
+    h = tm.tm_create(p, stream)
+    tm.tm_load_gauge(h, U)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {"lattice_TZYX": list(L)}
+
+    def timed(fn, k=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k / 1e3
+
+    for prec, name, esz in ((tm.TM_F32, "dslash_f32", 4), (tm.TM_F64, "dslash_f64", 8)):
+        nb = tm.tm_field_bytes(h, 0, prec, 1)
+        a = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+        b = torch.zeros_like(a)
+        a.view(torch.float32 if esz == 4 else torch.float64).normal_()
+        t = timed(lambda: tm.tm_apply(h, 0, prec, a, b, 1))
+        byts = V * esz * (48 + 120)   # spinor in + out, 4 links x 12 reals, clover 72 reals per site
+        out[name] = {"us": round(t * 1e6, 1), "algorithmic_bytes": byts, "achieved_gbs": round(byts / t / 1e9, 1),
+                     "frac_of_measured_hbm": round(byts / t / 1e9 / hbm, 4),
+                     "tflops": round(V * 2232 / t / 1e12, 3)}
+        del a, b
+    # 12-rhs odd-even coarse Schur complement on the tensor cores (TF32) after a setup from random vectors
+    tv = torch.from_numpy(inputs.random_test_vectors(L, nv, 1 + inputs.TV_SEED_OFFSET)).cuda()
+    tm.tm_setup_from_vectors(h, tv)
+    del tv
+    nh = V // 256 // 2
+    n = 2 * nv
+    R = 12
+    v = torch.randn(R * nh * n * 2, device="cuda", dtype=torch.float32)
+    y = torch.zeros_like(v)
+    kinds = [tm.tm_profile_name(k) for k in range(tm.tm_profile_kinds())]
+    for _ in range(3):
+        tm.tm_schur(h, tm.TM_F32, v, y, R)
+    tm.tm_profile(h, 1 << kinds.index("coarse_oe"))
+    K = 20
+    for _ in range(K):
+        tm.tm_schur(h, tm.TM_F32, v, y, R)
+    t = tm.tm_profile_read(h)["coarse_oe"]["ms"] / K / 1e3
+    tm.tm_profile(h, False)
+    flops = nh * 17 * n * n * 8 * R           # complex multiply-adds of the 17 blocks per site pair
+    tiles = nh * 17 * (2 * n) * n * 4         # operator bytes read (FP32 tiles)
+    out["coarse_schur_tf32"] = {"coarse_sites_per_parity": nh, "nv": nv, "nrhs": R, "us": round(t * 1e6, 1),
+                                "tflops": round(flops / t / 1e12, 2), "operator_gbs": round(tiles / t / 1e9, 1),
+                                "frac_of_measured_bf16": round(flops / t / 1e12 / float(peaks.get("bf16_tflops", 1900.0)), 4)}
+    tm.tm_destroy(h)
+    return out
+
+
 def main_learned(args):
     """Train the learned layer on 8 fields, then solve on 4 held-out fields with
     no stage after the K-cycle, the learned layer (FP16 inference) and one SAP
@@ -691,6 +771,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--write-counts", action="store_true")
+    ap.add_argument("--no-scale-kernels", action="store_true",
+                    help="skip the D(mu) and coarse Schur measurements on the 24^3x48 lattice")
     ap.add_argument("--oracle-worker", default=None)
     ap.add_argument("--m0", type=float, default=None, help="override the workload's tuned m0")
     ap.add_argument("--coarse-mma", type=int, default=None,

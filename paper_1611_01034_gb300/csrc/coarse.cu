@@ -118,9 +118,10 @@ void launch_orthonormalise(T* P, const AggGeom& ag, int* err, cudaStream_t st) {
 // ===========================================================================
 template <typename T>
 __global__ void k_restrict(const T* __restrict__ P, const T* __restrict__ fine, T* __restrict__ coarse,
-                           AggGeom ag) {
+                           AggGeom ag, int nrhs) {
   __shared__ T red[32 * 16];
-  const int a = blockIdx.x, rhs = blockIdx.y, nv = ag.nv;
+  // right-hand sides fastest over the CTAs: an aggregate's P columns are reused from L2
+  const int a = blockIdx.x / nrhs, rhs = blockIdx.x % nrhs, nv = ag.nv;
   const int l = threadIdx.x;
   const bool act = l < ag.asites;
   int lc[4], c[4];
@@ -161,8 +162,8 @@ __global__ void k_restrict(const T* __restrict__ P, const T* __restrict__ fine, 
 template <typename T>
 void launch_restrict(const T* P, const T* fine, T* coarse, const AggGeom& ag, int nrhs, cudaStream_t st) {
   const int threads = (ag.asites + 31) / 32 * 32;
-  dim3 grid(ag.gc.V, nrhs);
-  k_restrict<T><<<grid, threads, 0, st>>>(P, fine, coarse, ag);
+  dim3 grid((unsigned)ag.gc.V * (unsigned)nrhs);
+  k_restrict<T><<<grid, threads, 0, st>>>(P, fine, coarse, ag, nrhs);
 }
 
 // ===========================================================================
@@ -170,9 +171,9 @@ void launch_restrict(const T* P, const T* fine, T* coarse, const AggGeom& ag, in
 // ===========================================================================
 template <typename T, bool ACC>
 __global__ void k_prolong(const T* __restrict__ P, const T* __restrict__ coarse, T* __restrict__ fine,
-                          AggGeom ag) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const int rhs = blockIdx.y, nv = ag.nv;
+                          AggGeom ag, int nrhs) {
+  const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;  // right-hand sides fastest (P reuse)
+  const int rhs = blockIdx.x % nrhs, nv = ag.nv;
   const long V = ag.g.V;
   if (s >= V) return;
   int c[4];
@@ -201,11 +202,11 @@ __global__ void k_prolong(const T* __restrict__ P, const T* __restrict__ coarse,
 template <typename T>
 void launch_prolong(const T* P, const T* coarse, T* fine, const AggGeom& ag, int nrhs, bool accumulate,
                     cudaStream_t st) {
-  dim3 grid((ag.g.V + 127) / 128, nrhs);
+  dim3 grid((unsigned)((ag.g.V + 127) / 128) * (unsigned)nrhs);
   if (accumulate)
-    k_prolong<T, true><<<grid, 128, 0, st>>>(P, coarse, fine, ag);
+    k_prolong<T, true><<<grid, 128, 0, st>>>(P, coarse, fine, ag, nrhs);
   else
-    k_prolong<T, false><<<grid, 128, 0, st>>>(P, coarse, fine, ag);
+    k_prolong<T, false><<<grid, 128, 0, st>>>(P, coarse, fine, ag, nrhs);
 }
 
 // ===========================================================================
@@ -404,11 +405,11 @@ __device__ __forceinline__ int coarse_nb(const Lat& gc, int a, int t) {
 // threads (t, row): partial sums over columns, reduced over t in shared memory
 template <typename T>
 __global__ void k_coarse_apply(const T* __restrict__ Dc, const T* __restrict__ v, T* __restrict__ y, Lat gc, int nv,
-                               T mu_c) {
+                               T mu_c, int nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);  // [9][n]
   const int n = 2 * nv;
-  const int a = blockIdx.x, rhs = blockIdx.y;
+  const int a = blockIdx.x / nrhs, rhs = blockIdx.x % nrhs;  // right-hand sides fastest (block reuse in L2)
   const int row = threadIdx.x % n, t = threadIdx.x / n;
   const cx<T>* vv = reinterpret_cast<const cx<T>*>(v) + (long)rhs * gc.V * n;
   if (t < 9) {
@@ -436,8 +437,8 @@ void launch_coarse_apply(const T* Dc, const T* v, T* y, const Lat& gc, int nv, d
                          cudaStream_t st) {
   const int n = 2 * nv;
   const int threads = (9 * n + 31) / 32 * 32;
-  dim3 grid(gc.V, nrhs);
-  k_coarse_apply<T><<<grid, threads, 9 * n * sizeof(cx<T>), st>>>(Dc, v, y, gc, nv, (T)mu_c);
+  dim3 grid((unsigned)gc.V * (unsigned)nrhs);
+  k_coarse_apply<T><<<grid, threads, 9 * n * sizeof(cx<T>), st>>>(Dc, v, y, gc, nv, (T)mu_c, nrhs);
 }
 
 // ===========================================================================

@@ -38,16 +38,16 @@ __device__ __forceinline__ int c_nb(const Lat& g, int s, int t) {
 // ===========================================================================
 template <typename T, bool H>
 __global__ void k_csap(const void* __restrict__ Dc, const T* __restrict__ b, T* __restrict__ x, CSapGeom sg, T mu,
-                       int n_mr, int colour) {
+                       int n_mr, int colour, int nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = sg.n, BS = sg.bsites;
   cx<T>* rs = reinterpret_cast<cx<T>*>(smem_raw);  // [BS][n]
   T* red = reinterpret_cast<T*>(rs + (size_t)BS * n);
   const Lat& g = sg.g;
-  const long off = (long)blockIdx.y * g.V * n;
+  const long off = (long)(blockIdx.x % nrhs) * g.V * n;  // right-hand sides fastest (block reuse in L2)
   const cx<T>* bb = b ? reinterpret_cast<const cx<T>*>(b) + off : nullptr;
   cx<T>* xx = reinterpret_cast<cx<T>*>(x) + off;
-  int k = blockIdx.x;
+  int k = blockIdx.x / nrhs;
   const int nbxh = sg.nb[3] / 2;
   int bc4[4];
   const int bxh = k % nbxh;
@@ -132,11 +132,11 @@ void launch_csap_colour(const T* Dc, const T* b, T* x, const CSapGeom& sg, doubl
                         int nrhs, cudaStream_t st, const void* Dc_half) {
   const int threads = (sg.bsites * sg.n + 31) / 32 * 32;
   const size_t smem = (size_t)sg.bsites * sg.n * sizeof(cx<T>) + 32 * 3 * sizeof(T);
-  dim3 grid(sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2, nrhs);
+  dim3 grid((unsigned)(sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2) * (unsigned)nrhs);
   if (Dc_half)
-    k_csap<T, true><<<grid, threads, smem, st>>>(Dc_half, b, x, sg, (T)mu, n_mr, colour);
+    k_csap<T, true><<<grid, threads, smem, st>>>(Dc_half, b, x, sg, (T)mu, n_mr, colour, nrhs);
   else
-    k_csap<T, false><<<grid, threads, smem, st>>>(Dc, b, x, sg, (T)mu, n_mr, colour);
+    k_csap<T, false><<<grid, threads, smem, st>>>(Dc, b, x, sg, (T)mu, n_mr, colour, nrhs);
 }
 
 // FP16 (re, im) copy of FP32 coarse blocks

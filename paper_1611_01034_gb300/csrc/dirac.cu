@@ -271,13 +271,17 @@ struct DslashArgs {
   Lat g;
   T mu;
   T bc;
+  int nrhs;
 };
 
+// right-hand sides vary fastest over the CTAs so the links and clover of a site
+// block are read from DRAM once and reused from L2 by the other right-hand sides
 template <typename T, bool RES>
 __global__ void __launch_bounds__(128) k_dslash(DslashArgs<T> a) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rhs = a.nrhs == 1 ? 0 : (int)(blockIdx.x % a.nrhs);
+  const int s = (a.nrhs == 1 ? blockIdx.x : blockIdx.x / a.nrhs) * blockDim.x + threadIdx.x;
   if (s >= a.g.V) return;
-  const long off = (long)blockIdx.y * NR_SPINOR * a.g.V;
+  const long off = (long)rhs * NR_SPINOR * a.g.V;
   const T* in = a.in + off;
   int c[4];
   site_coords(a.g, s, c);
@@ -301,8 +305,8 @@ __global__ void __launch_bounds__(128) k_dslash(DslashArgs<T> a) {
 template <typename T>
 void launch_dslash(const T* gauge, const T* clover, const T* in, T* out, const T* b, const Lat& g, double mu,
                    double bc_t, int nrhs, cudaStream_t st) {
-  DslashArgs<T> a{gauge, clover, in, out, b, g, (T)mu, (T)bc_t};
-  dim3 grid((g.V + 127) / 128, nrhs);
+  DslashArgs<T> a{gauge, clover, in, out, b, g, (T)mu, (T)bc_t, nrhs};
+  dim3 grid((unsigned)((g.V + 127) / 128) * (unsigned)nrhs);
   if (b)
     k_dslash<T, true><<<grid, 128, 0, st>>>(a);
   else

@@ -31,6 +31,7 @@ struct SapArgs {
   T bc;
   int n_mr;
   int colour;
+  int nrhs;
 };
 
 template <typename T, int MU>
@@ -62,11 +63,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sap(SapArgs<T> 
   const int BS = sg.bsites;
   cx<T>* rs = reinterpret_cast<cx<T>*>(smem_raw);  // [12][BS]
   T* red = reinterpret_cast<T*>(rs + 12 * BS);     // [32 * 3]
-  const long off = (long)blockIdx.y * NR_SPINOR * g.V;
+  // consecutive CTAs take the same block for consecutive right-hand sides, so
+  // the block's links and clover are read from DRAM once and then from L2
+  const int rhs = blockIdx.x % a.nrhs;
+  const long off = (long)rhs * NR_SPINOR * g.V;
   T* x = a.x + off;
 
-  // the blockIdx.x-th block of this colour
-  int k = blockIdx.x;
+  // the (blockIdx.x / nrhs)-th block of this colour
+  int k = blockIdx.x / a.nrhs;
   const int nbxh = sg.nb[3] / 2;
   int bc4[4];
   const int bxh = k % nbxh;
@@ -176,8 +180,8 @@ void launch_sap_colour(const T* gauge, const T* clover, const T* b, T* x, const 
     attr_set = true;
   }
   const int nblk_colour = sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2;
-  SapArgs<T> a{gauge, clover, b, x, sg, (T)mu, (T)bc_t, n_mr, colour};
-  dim3 grid(nblk_colour, nrhs);
+  SapArgs<T> a{gauge, clover, b, x, sg, (T)mu, (T)bc_t, n_mr, colour, nrhs};
+  dim3 grid(nblk_colour * nrhs);
   k_sap<T><<<grid, threads, smem, st>>>(a);
 }
 
