@@ -359,6 +359,9 @@ def main_native(args):
     extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec")
              if k in wl}
     extra["coarse_mma"] = args.coarse_mma if args.coarse_mma is not None else wl.get("coarse_mma", 0)
+    for kv in args.param or []:  # solver-parameter overrides, e.g. --param coarse_tol=0.02
+        k, v = kv.split("=", 1)
+        extra[k] = float(v) if "." in v or "e" in v else int(v)
     p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv,
                   agg=wl["agg"], sap_block=wl["sap_block"], setup_iters=wl["setup_iters"],
                   cycle_prec=tm.TM_F32, max_rhs=rb, levels=levels, **extra)
@@ -523,6 +526,7 @@ def main_native(args):
             **({"nv2": wl["nv2"], "aggregate2": list(wl["agg2"]), "sap_block1": list(wl["sap_block1"]),
                 "coarse_setup_iters": wl["coarse_setup_iters"]} if levels == 3 else {}),
             "restart": p.restart, "rhs_per_solve_call": rb, "coarse_mma": p.coarse_mma,
+            "coarse_tol": p.coarse_tol, "post_smooth": p.post_smooth, "mr_iters": p.mr_iters,
             **({"sap1_prec": "f16" if p.sap1_prec == 2 else "f32"} if levels == 3 else {}),
             "nv": nv, "aggregate": list(wl["agg"]), "sap_block": list(wl["sap_block"]),
             "m0": m0, "m0_source": m0_src, "c_sw": wl["c_sw"], "mu": wl["mu"],
@@ -771,6 +775,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--write-counts", action="store_true")
+    ap.add_argument("--param", action="append", help="override a tm_params field: name=value")
     ap.add_argument("--no-scale-kernels", action="store_true",
                     help="skip the D(mu) and coarse Schur measurements on the 24^3x48 lattice")
     ap.add_argument("--oracle-worker", default=None)
