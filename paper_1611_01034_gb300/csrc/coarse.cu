@@ -294,7 +294,11 @@ __device__ __forceinline__ int block_site(const AggGeom& ag, int t, int f) {
 }
 
 constexpr int kBuildThreads = 256;
-constexpr int kBuildOut = 13;  // outputs per thread: (2 Nv)^2 <= 13 * 256 for Nv <= 28
+// register tiles of the projection: a thread owns kTR rows (one chirality) x kTC
+// columns of a block, so every P value it loads from shared memory serves kTC
+// outputs and every operator value kTR outputs; kTiles tiles per thread cover
+// 2 ceil(Nv / kTR) ceil(2 Nv / kTC) <= 392 tiles for Nv <= 28
+constexpr int kTR = 4, kTC = 2, kTiles = 2;
 
 // D_c(a, t) = P_a^dagger U_t, U_t = the 2 Nv operator columns of block t.
 // One CTA per (t, a); the visited sites are processed in tiles of TS sites
@@ -302,7 +306,7 @@ constexpr int kBuildOut = 13;  // outputs per thread: (2 Nv)^2 <= 13 * 256 for N
 //   Ps[(l * 12 + comp) * Nv + i],  Us[(l * 12 + comp) * 2Nv + k],
 // then every thread accumulates its fixed outputs (row, col) in registers.
 template <typename T>
-__global__ void __launch_bounds__(kBuildThreads) k_coarse_build(const T* __restrict__ gauge,
+__global__ void __launch_bounds__(kBuildThreads, sizeof(T) == 4 ? 2 : 1) k_coarse_build(const T* __restrict__ gauge,
                                                                 const T* __restrict__ clover,
                                                                 const T* __restrict__ P, T* __restrict__ Dc,
                                                                 AggGeom ag, T bc, int TS) {
@@ -313,9 +317,15 @@ __global__ void __launch_bounds__(kBuildThreads) k_coarse_build(const T* __restr
   const int t = blockIdx.x, a = blockIdx.y;
   const int nsites = t == 0 ? ag.asites : ag.asites / ag.agg[(t - 1) >> 1];
   const long V = ag.g.V;
-  cx<T> acc[kBuildOut];
+  const int nib = (nv + kTR - 1) / kTR, nkb = (n + kTC - 1) / kTC;
+  const int ntiles = 2 * nib * nkb;
+  cx<T> acc[kTiles][kTR][kTC];
 #pragma unroll
-  for (int m = 0; m < kBuildOut; ++m) acc[m] = cx<T>{0, 0};
+  for (int m = 0; m < kTiles; ++m)
+#pragma unroll
+    for (int ri = 0; ri < kTR; ++ri)
+#pragma unroll
+      for (int kj = 0; kj < kTC; ++kj) acc[m][ri][kj] = cx<T>{0, 0};
 
   for (int f0 = 0; f0 < nsites; f0 += TS) {
     const int ts = min(TS, nsites - f0);
@@ -341,32 +351,47 @@ __global__ void __launch_bounds__(kBuildThreads) k_coarse_build(const T* __restr
     }
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < kBuildOut; ++m) {
-      const int o = threadIdx.x + m * kBuildThreads;
-      if (o < n * n) {
-        const int row = o / n, k = o % n;
-        const int chi = row / nv, i = row % nv;
-        cx<T> sum = acc[m];
+    for (int m = 0; m < kTiles; ++m) {
+      const int tile = threadIdx.x + m * kBuildThreads;
+      if (tile < ntiles) {
+        const int chi = tile / (nib * nkb), rem = tile % (nib * nkb);
+        const int i0 = (rem / nkb) * kTR, k0 = (rem % nkb) * kTC;
         for (int l = 0; l < ts; ++l) {
 #pragma unroll
           for (int q = 0; q < 6; ++q) {
             const size_t b = (size_t)l * 12 + 6 * chi + q;
-            cfmac(sum, Ps[b * nv + i], Us[b * n + k]);
+            cx<T> pv[kTR], uv[kTC];
+#pragma unroll
+            for (int ri = 0; ri < kTR; ++ri) pv[ri] = i0 + ri < nv ? Ps[b * nv + i0 + ri] : cx<T>{0, 0};
+#pragma unroll
+            for (int kj = 0; kj < kTC; ++kj) uv[kj] = k0 + kj < n ? Us[b * n + k0 + kj] : cx<T>{0, 0};
+#pragma unroll
+            for (int ri = 0; ri < kTR; ++ri)
+#pragma unroll
+              for (int kj = 0; kj < kTC; ++kj) cfmac(acc[m][ri][kj], pv[ri], uv[kj]);
           }
         }
-        acc[m] = sum;
       }
     }
     __syncthreads();
   }
   T* out = Dc + ((long)a * 9 + t) * n * n * 2;
 #pragma unroll
-  for (int m = 0; m < kBuildOut; ++m) {
-    const int o = threadIdx.x + m * kBuildThreads;
-    if (o < n * n) {
-      const int row = o / n, k = o % n;
-      out[2 * ((long)k * n + row)] = acc[m].r;
-      out[2 * ((long)k * n + row) + 1] = acc[m].i;
+  for (int m = 0; m < kTiles; ++m) {
+    const int tile = threadIdx.x + m * kBuildThreads;
+    if (tile < ntiles) {
+      const int chi = tile / (nib * nkb), rem = tile % (nib * nkb);
+      const int i0 = (rem / nkb) * kTR, k0 = (rem % nkb) * kTC;
+#pragma unroll
+      for (int ri = 0; ri < kTR; ++ri)
+#pragma unroll
+        for (int kj = 0; kj < kTC; ++kj) {
+          const int row = chi * nv + i0 + ri, k = k0 + kj;
+          if (i0 + ri < nv && k < n) {
+            out[2 * ((long)k * n + row)] = acc[m][ri][kj].r;
+            out[2 * ((long)k * n + row) + 1] = acc[m][ri][kj].i;
+          }
+        }
     }
   }
 }
