@@ -376,6 +376,104 @@ void launch_scale_copy_b(const T* src, long sstr, T* dst, long dstr, const doubl
   k_scale_copy_b<T><<<grid, 256, 0, st>>>(src, sstr, dst, dstr, s, ncx, active);
 }
 
+// --- the same steps taking the per-block partial sums of the preceding
+// reduction directly (one launch less each): every CTA sums the partials in
+// the same fixed order, CTA 0 also stores the result for the host.  Few
+// partial blocks (kFusedParts) and few consumer CTAs per rhs (kFusedCtas) keep
+// the redundant partial reads small. ---------------------------------------------
+constexpr int kFusedParts = 16, kFusedCtas = 64;
+static inline int fused_parts(long ncx) {
+  const int G = dot_grid(ncx);
+  return G < kFusedParts ? G : kFusedParts;
+}
+static inline int fused_ctas(long n) {
+  const int G = grid_for(n);
+  return G < kFusedCtas ? G : kFusedCtas;
+}
+
+template <typename T>
+void launch_multidot_b_partials(const T* X, long xstr, long ldx, int k, const T* y, long ystr, long ncx,
+                                double* scratch, int nrhs, const int* active, cudaStream_t st) {
+  dim3 grid(fused_parts(ncx), (k + 7) / 8, nrhs);
+  k_multidot_partial_b<T><<<grid, 256, 0, st>>>(X, xstr, ldx, k, y, ystr, ncx, scratch, active);
+}
+
+template <typename T>
+__global__ void k_multi_caxpy_bp(const T* __restrict__ X, long xstr, long ldx, int k, const double* __restrict__ part,
+                                 int G, double* __restrict__ cout_, long cstr, T* __restrict__ y, long ystr, long ncx,
+                                 const int* __restrict__ active) {
+  extern __shared__ double cs_[];  // [k][2]
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const double* p = part + ((long)r * k + j) * G * 2;
+    double a = 0, b = 0;
+    for (int q = 0; q < G; ++q) {
+      a += p[2 * q];
+      b += p[2 * q + 1];
+    }
+    cs_[2 * j] = a;
+    cs_[2 * j + 1] = b;
+    if (blockIdx.x == 0) {
+      cout_[r * cstr + 2 * j] = a;
+      cout_[r * cstr + 2 * j + 1] = b;
+    }
+  }
+  __syncthreads();
+  cx<T>* yy = reinterpret_cast<cx<T>*>(y + r * ystr);
+  const T* Xr = X + r * xstr;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
+    cx<T> acc = yy[i];
+    for (int j = 0; j < k; ++j) {
+      const cx<T> cj{(T)cs_[2 * j], (T)cs_[2 * j + 1]};
+      acc = acc - cj * reinterpret_cast<const cx<T>*>(Xr + (long)j * ldx)[i];
+    }
+    yy[i] = acc;
+  }
+}
+template <typename T>
+void launch_multi_caxpy_bp(const T* X, long xstr, long ldx, int k, const double* part, long ncx_dot, double* c,
+                           long cstr, T* y, long ystr, long ncx, int nrhs, const int* active, cudaStream_t st) {
+  dim3 grid(fused_ctas(ncx), nrhs);
+  k_multi_caxpy_bp<T><<<grid, 256, (size_t)2 * k * sizeof(double), st>>>(X, xstr, ldx, k, part, fused_parts(ncx_dot),
+                                                                        c, cstr, y, ystr, ncx, active);
+}
+
+template <typename T>
+void launch_norm2_b_partials(const T* y, long ystr, long ncx, double* scratch, int nrhs, const int* active,
+                             cudaStream_t st) {
+  dim3 grid(fused_parts(ncx), nrhs);
+  k_norm2_partial_b<T><<<grid, 256, 0, st>>>(y, ystr, ncx, scratch, active);
+}
+
+template <typename T>
+__global__ void k_scale_copy_bp(const T* __restrict__ src, long sstr, T* __restrict__ dst, long dstr,
+                                const double* __restrict__ part, int G, double* __restrict__ nrm, long ncx,
+                                const int* __restrict__ active) {
+  __shared__ double sc_;
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  if (threadIdx.x == 0) {
+    double a = 0;
+    for (int q = 0; q < G; ++q) a += part[((long)r * G + q) * 2];
+    sc_ = a;
+    if (blockIdx.x == 0) nrm[r] = a;
+  }
+  __syncthreads();
+  const double sc = sc_;
+  const T f = (T)(sc > 0 ? 1.0 / sqrt(sc) : 0.0);
+  const T* a = src + r * sstr;
+  T* b = dst + r * dstr;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * ncx; i += (long)gridDim.x * blockDim.x)
+    b[i] = a[i] * f;
+}
+template <typename T>
+void launch_scale_copy_bp(const T* src, long sstr, T* dst, long dstr, const double* part, double* nrm, long ncx,
+                          int nrhs, const int* active, cudaStream_t st) {
+  dim3 grid(fused_ctas(2 * ncx), nrhs);
+  k_scale_copy_bp<T><<<grid, 256, 0, st>>>(src, sstr, dst, dstr, part, fused_parts(ncx), nrm, ncx, active);
+}
+
 template <typename T>
 __global__ void k_sub_b(const T* __restrict__ x, long xstr, T* __restrict__ y, long ystr, long ncx,
                         const int* __restrict__ active) {
@@ -391,6 +489,18 @@ void launch_sub_b(const T* x, long xstr, T* y, long ystr, long ncx, int nrhs, co
   dim3 grid(grid_for(2 * ncx), nrhs);
   k_sub_b<T><<<grid, 256, 0, st>>>(x, xstr, y, ystr, ncx, active);
 }
+
+#define TM_INST_BP(T)                                                                                        \
+  template void launch_multidot_b_partials<T>(const T*, long, long, int, const T*, long, long, double*, int,    \
+                                              const int*, cudaStream_t);                                       \
+  template void launch_multi_caxpy_bp<T>(const T*, long, long, int, const double*, long, double*, long, T*,     \
+                                         long, long, int, const int*, cudaStream_t);                           \
+  template void launch_norm2_b_partials<T>(const T*, long, long, double*, int, const int*, cudaStream_t);       \
+  template void launch_scale_copy_bp<T>(const T*, long, T*, long, const double*, double*, long, int,            \
+                                        const int*, cudaStream_t);
+TM_INST_BP(double)
+TM_INST_BP(float)
+#undef TM_INST_BP
 
 #define TM_INST_B(T)                                                                                              \
   template void launch_multidot_b<T>(const T*, long, long, int, const T*, long, long, double*, long, double*, int, \

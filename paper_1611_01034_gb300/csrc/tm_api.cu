@@ -128,6 +128,7 @@ struct tm_handle {
 namespace {
 
 constexpr int kScratchBlocks = kReduceBlocks;
+constexpr long kFuseMaxCx = 1L << 18;  // batched Arnoldi vectors up to this many complex numbers use fused reductions
 constexpr int kMaxDots = 128;
 constexpr int kSmall = 4096;
 
@@ -665,18 +666,19 @@ std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x,
       double* d1 = dd;
       double* d2 = dd + 2 * (k + 1);
       {
-        Prof pf(h, PK_BLAS_COARSE, na, 8);
-        launch_multidot_b<T>(Vb, vstr, cv, k + 1, w, cv, nc, d1, ds, part, nrhs, act, h->st);
+        // CGS2 in six launches: each reduction's partial sums feed the next step directly
+        Prof pf(h, PK_BLAS_COARSE, na, 6);
+        launch_multidot_b_partials<T>(Vb, vstr, cv, k + 1, w, cv, nc, part, nrhs, act, h->st);
         CKL();
-        launch_multi_caxpy_b<T>(Vb, vstr, cv, k + 1, d1, ds, w, cv, nc, nrhs, act, h->st);
+        launch_multi_caxpy_bp<T>(Vb, vstr, cv, k + 1, part, nc, d1, ds, w, cv, nc, nrhs, act, h->st);
         CKL();
-        launch_multidot_b<T>(Vb, vstr, cv, k + 1, w, cv, nc, d2, ds, part, nrhs, act, h->st);
+        launch_multidot_b_partials<T>(Vb, vstr, cv, k + 1, w, cv, nc, part, nrhs, act, h->st);
         CKL();
-        launch_multi_caxpy_b<T>(Vb, vstr, cv, k + 1, d2, ds, w, cv, nc, nrhs, act, h->st);
+        launch_multi_caxpy_bp<T>(Vb, vstr, cv, k + 1, part, nc, d2, ds, w, cv, nc, nrhs, act, h->st);
         CKL();
-        launch_norm2_b<T>(w, cv, nc, nrm, part, nrhs, act, h->st);
+        launch_norm2_b_partials<T>(w, cv, nc, part, nrhs, act, h->st);
         CKL();
-        launch_scale_copy_b<T>(w, cv, Vb + (long)(k + 1) * cv, vstr, nrm, nc, nrhs, act, h->st);
+        launch_scale_copy_bp<T>(w, cv, Vb + (long)(k + 1) * cv, vstr, part, nrm, nc, nrhs, act, h->st);
         CKL();
       }
       CK(cudaMemcpy2DAsync(hb, 4 * (k + 1) * sizeof(double), dd, ds * sizeof(double), 4 * (k + 1) * sizeof(double),
@@ -1298,8 +1300,22 @@ std::vector<KrylovOut> fgmres_b(tm_handle* h, const std::string& tag, int pk, FR
       upload_mask(inner, nullptr);
       double* d1 = dd;
       double* d2 = dd + 2 * (k + 1);
-      {
-        Prof pf(h, pk, na, 8);
+      if (nc <= kFuseMaxCx) {  // short vectors: the launches dominate, fuse the reductions
+        Prof pf(h, pk, na, 6);
+        launch_multidot_b_partials<Tv>(Vb, fr, blk, k + 1, w, fr, nc, part, nb, act, h->st);
+        CKL();
+        launch_multi_caxpy_bp<Tv>(Vb, fr, blk, k + 1, part, nc, d1, ds, w, fr, nc, nb, act, h->st);
+        CKL();
+        launch_multidot_b_partials<Tv>(Vb, fr, blk, k + 1, w, fr, nc, part, nb, act, h->st);
+        CKL();
+        launch_multi_caxpy_bp<Tv>(Vb, fr, blk, k + 1, part, nc, d2, ds, w, fr, nc, nb, act, h->st);
+        CKL();
+        launch_norm2_b_partials<Tv>(w, fr, nc, part, nb, act, h->st);
+        CKL();
+        launch_scale_copy_bp<Tv>(w, fr, Vb + (long)(k + 1) * blk, fr, part, nrm, nc, nb, act, h->st);
+        CKL();
+      } else {
+        Prof pf(h, pk, na, 9);
         launch_multidot_b<Tv>(Vb, fr, blk, k + 1, w, fr, nc, d1, ds, part, nb, act, h->st);
         CKL();
         launch_multi_caxpy_b<Tv>(Vb, fr, blk, k + 1, d1, ds, w, fr, nc, nb, act, h->st);

@@ -242,6 +242,21 @@ template <typename T>
 void launch_sub_b(const T* x, long xstr, T* y, long ystr, long ncx, int nrhs, const int* active, cudaStream_t st);
 // scratch doubles that launch_multidot_b / launch_norm2_b need
 long multidot_scratch_doubles(long ncx, int k, int nrhs);
+// fused pairs: the partial sums of a multidot / norm go straight into the next
+// step, which reduces them itself (the final values are also written to c / nrm):
+//   multidot partials -> y_r -= sum_j c_rj X_rj;   norm partials -> dst_r = src_r / ||src_r||
+template <typename T>
+void launch_multidot_b_partials(const T* X, long xstr, long ldx, int k, const T* y, long ystr, long ncx,
+                                double* scratch, int nrhs, const int* active, cudaStream_t st);
+template <typename T>
+void launch_multi_caxpy_bp(const T* X, long xstr, long ldx, int k, const double* part, long ncx_dot, double* c,
+                           long cstr, T* y, long ystr, long ncx, int nrhs, const int* active, cudaStream_t st);
+template <typename T>
+void launch_norm2_b_partials(const T* y, long ystr, long ncx, double* scratch, int nrhs, const int* active,
+                             cudaStream_t st);
+template <typename T>
+void launch_scale_copy_bp(const T* src, long sstr, T* dst, long dstr, const double* part, double* nrm, long ncx,
+                          int nrhs, const int* active, cudaStream_t st);
 
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs
 
