@@ -122,7 +122,7 @@ typedef struct {
   int coarse_mma;
   /* Stage after the K-cycle in the solve's preconditioner (not in the paper):
      0 = none, 1 = learned layer z = B(v) + N(v - D B(v)) (tm_nn_*), 2 = one SAP
-     sweep in place of N (the stand-in the learned layer is judged against).
+     sweep in place of N (the stand-in the learned layer is compared with).
      nn_prec: TM_F32, or TM_F16 for FP16 hidden channels and weights. */
   int nn_mode;
   int nn_prec;

@@ -18,7 +18,7 @@ Paper passages followed
   (D(mu)^dagger D(mu))^-1 = D(mu)^-1 Gamma5 D(-mu)^-1 Gamma5, using
   D(mu)^dagger = Gamma5 D(-mu) Gamma5.
 
-Readings (listed in DESIGN.md)
+Readings (choices where the paper is silent)
 ------------------------------
 * B(v): x = 0; j sweeps of SAP on D x = v; r = v - D x; e_c = coarse solve of
   D_c(delta*mu) e_c = P^dagger r; x += P e_c; k sweeps of SAP on D x = v.

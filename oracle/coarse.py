@@ -14,7 +14,7 @@ Paper passages followed
   delta*mu with delta >= 1.
 * Sec. 3: odd-even preconditioning is used on the coarsest level.
 
-Readings (listed in DESIGN.md)
+Readings (choices where the paper is silent)
 ------------------------------
 * Aggregate = block of ``agg`` dims; each aggregate is split by chirality
   (spins {0,1} have gamma5 = -1, spins {2,3} have +1), giving 2 N_v coarse

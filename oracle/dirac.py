@@ -8,7 +8,7 @@ Paper passages followed
 * Sec. 2, eq. (2): gamma_5 = diag(-1, -1, +1, +1); the other gamma matrices
   may be chosen freely; lexicographic site order TZYX.
 
-Readings where the paper is silent (listed in the design doc as well)
+Readings where the paper is silent
 ----------------------------------------------------------------
 * Gamma matrices: chiral basis gamma_k = [[0, -i sigma_k], [i sigma_k, 0]]
   (k = 1, 2, 3), gamma_4 = [[0, -1], [-1, 0]]; lattice directions

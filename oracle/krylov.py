@@ -11,7 +11,7 @@ Paper passages followed
 * Sec. 3: the coarsest level is solved with odd-even preconditioning (here:
   GMRES on the Schur complement, :mod:`oracle.coarse`).
 
-Readings (listed in DESIGN.md)
+Readings (choices where the paper is silent)
 ------------------------------
 * Right preconditioning, x = x0 + Z y.  Arnoldi by classical Gram-Schmidt
   applied twice (CGS2).  The least-squares problem is reduced by complex

@@ -14,7 +14,7 @@ Paper passages followed
   MGCoarseSetupIter setup iterations on the first coarse grid.
 * Sec. 3: odd-even preconditioning on the coarsest level and in the smoother.
 
-Readings (listed in DESIGN.md)
+Readings (choices where the paper is silent)
 ------------------------------
 * Level 1 carries D_c1(mu) = P1^dagger D_W P1 + i mu Gamma5_c (mu itself);
   level 2 D_c2(delta mu) = P2^dagger D_c1(0) P2 + i delta mu Gamma5_c2.

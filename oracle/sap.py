@@ -9,7 +9,7 @@ Paper passages followed
 * Sec. 3: odd-even preconditioning is used in the smoother (and on the
   coarsest level) but not on the full fine operator.
 
-Readings where the paper is silent (listed in the design doc)
+Readings where the paper is silent
 --------------------------------------------------------
 * Domains are the blocks of ``block`` dims.  A block's colour is the parity
   of the sum of its block coordinates; colour 0 ("red") goes first.
