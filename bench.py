@@ -322,7 +322,7 @@ def main_native(args):
     U = inputs.gauge_field(L, wl["eps"], seed)
     levels = wl.get("levels", 2)
     nrhs = wl.get("nrhs", 1)
-    rb = wl.get("rhs_batch", nrhs)  # right-hand sides per tm_solve call
+    rb = args.rhs_batch or wl.get("rhs_batch", nrhs)  # right-hand sides per tm_solve call
     V = 1
     for n in L:
         V *= n
@@ -362,9 +362,10 @@ def main_native(args):
     for kv in args.param or []:  # solver-parameter overrides, e.g. --param coarse_tol=0.02
         k, v = kv.split("=", 1)
         extra[k] = float(v) if "." in v or "e" in v else int(v)
+    extra.setdefault("cycle_prec", tm.TM_F32)
     p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv,
                   agg=wl["agg"], sap_block=wl["sap_block"], setup_iters=wl["setup_iters"],
-                  cycle_prec=tm.TM_F32, max_rhs=rb, levels=levels, **extra)
+                  max_rhs=rb, levels=levels, **extra)
     h = tm.tm_create(p, stream)
     infos = []
 
@@ -518,7 +519,7 @@ def main_native(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 outer / f32 cycle",
+        "dtype": "f64 outer / f32 cycle" if p.cycle_prec == tm.TM_F32 else "f64",
         "data": f"synthetic (seeded random SU(3) field U = exp({wl['eps']} i H); "
                 + ("12 point sources)" if wl.get("point") else "Gaussian rhs)"),
         "config": {
@@ -776,6 +777,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--write-counts", action="store_true")
     ap.add_argument("--param", action="append", help="override a tm_params field: name=value")
+    ap.add_argument("--rhs-batch", type=int, default=None, help="right-hand sides per tm_solve call")
     ap.add_argument("--no-scale-kernels", action="store_true",
                     help="skip the D(mu) and coarse Schur measurements on the 24^3x48 lattice")
     ap.add_argument("--oracle-worker", default=None)
