@@ -66,8 +66,11 @@ __global__ void k_multidot_partial(const T* __restrict__ X, long ldx, int k, con
     for (int jj = 0; jj < 8; ++jj) {
       if (j0 + jj < k) {
         const cx<T> xv = reinterpret_cast<const cx<T>*>(X + (long)(j0 + jj) * ldx)[i];
-        d[2 * jj] += xv.r * yv.r + xv.i * yv.i;
-        d[2 * jj + 1] += xv.r * yv.i - xv.i * yv.r;
+        // conj(x) y as four fused multiply-adds (FP64 arithmetic is the limit on GB300)
+        d[2 * jj] = fma(xv.r, yv.r, d[2 * jj]);
+        d[2 * jj] = fma(xv.i, yv.i, d[2 * jj]);
+        d[2 * jj + 1] = fma(xv.r, yv.i, d[2 * jj + 1]);
+        d[2 * jj + 1] = fma(-xv.i, yv.r, d[2 * jj + 1]);
       }
     }
   }
@@ -113,7 +116,8 @@ __global__ void k_norm2_partial(const T* __restrict__ x, long ncx, double* __res
   T d[2] = {0, 0};
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
     const cx<T> v = xx[i];
-    d[0] += v.r * v.r + v.i * v.i;
+    d[0] = fma(v.r, v.r, d[0]);
+    d[0] = fma(v.i, v.i, d[0]);
   }
   block_allreduce<T, 2>(d, red);
   if (threadIdx.x < 2) part[((long)r * gridDim.x + blockIdx.x) * 2 + threadIdx.x] = (double)d[threadIdx.x];
@@ -143,13 +147,15 @@ void launch_norm2(const T* x, long ncx, int nrhs, double* dev_out, double* scrat
 template <typename T>
 __global__ void k_multi_caxpy(const T* __restrict__ X, long ldx, int k, const double* __restrict__ c, T sign,
                               T* __restrict__ y, long ncx) {
+  __shared__ cx<T> cs_[128];  // -sign c_j, formed once per CTA
+  for (int j = threadIdx.x; j < k; j += blockDim.x) cs_[j] = cx<T>{-sign * (T)c[2 * j], -sign * (T)c[2 * j + 1]};
+  __syncthreads();
   cx<T>* yy = reinterpret_cast<cx<T>*>(y);
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
     cx<T> acc = yy[i];
     for (int j = 0; j < k; ++j) {
-      const cx<T> cj{(T)(sign * (T)c[2 * j]), (T)(sign * (T)c[2 * j + 1])};
       const cx<T> xv = reinterpret_cast<const cx<T>*>(X + (long)j * ldx)[i];
-      acc = acc - cj * xv;
+      cfma(acc, cs_[j], xv);
     }
     yy[i] = acc;
   }
@@ -227,8 +233,11 @@ __global__ void k_multidot_partial_b(const T* __restrict__ X, long xstr, long ld
     for (int jj = 0; jj < 8; ++jj) {
       if (j0 + jj < k) {
         const cx<T> xv = reinterpret_cast<const cx<T>*>(Xr + (long)(j0 + jj) * ldx)[i];
-        d[2 * jj] += xv.r * yv.r + xv.i * yv.i;
-        d[2 * jj + 1] += xv.r * yv.i - xv.i * yv.r;
+        // conj(x) y as four fused multiply-adds (FP64 arithmetic is the limit on GB300)
+        d[2 * jj] = fma(xv.r, yv.r, d[2 * jj]);
+        d[2 * jj] = fma(xv.i, yv.i, d[2 * jj]);
+        d[2 * jj + 1] = fma(xv.r, yv.i, d[2 * jj + 1]);
+        d[2 * jj + 1] = fma(-xv.i, yv.r, d[2 * jj + 1]);
       }
     }
   }
@@ -278,7 +287,8 @@ __global__ void k_norm2_partial_b(const T* __restrict__ y, long ystr, long ncx, 
   T d[2] = {0, 0};
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
     const cx<T> v = yy[i];
-    d[0] += v.r * v.r + v.i * v.i;
+    d[0] = fma(v.r, v.r, d[0]);
+    d[0] = fma(v.i, v.i, d[0]);
   }
   block_allreduce<T, 2>(d, red);
   if (threadIdx.x < 2) part[((long)r * gridDim.x + blockIdx.x) * 2 + threadIdx.x] = (double)d[threadIdx.x];
@@ -307,17 +317,17 @@ void launch_norm2_b(const T* y, long ystr, long ncx, double* out, double* scratc
 template <typename T>
 __global__ void k_multi_caxpy_b(const T* __restrict__ X, long xstr, long ldx, int k, const double* __restrict__ c,
                                 long cstr, T* __restrict__ y, long ystr, long ncx, const int* __restrict__ active) {
+  __shared__ cx<T> cs_[128];  // -c_j, formed once per CTA
   const int r = blockIdx.y;
   if (active && !active[r]) return;
+  const double* cr = c + r * cstr;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) cs_[j] = cx<T>{-(T)cr[2 * j], -(T)cr[2 * j + 1]};
+  __syncthreads();
   cx<T>* yy = reinterpret_cast<cx<T>*>(y + r * ystr);
   const T* Xr = X + r * xstr;
-  const double* cr = c + r * cstr;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
     cx<T> acc = yy[i];
-    for (int j = 0; j < k; ++j) {
-      const cx<T> cj{(T)cr[2 * j], (T)cr[2 * j + 1]};
-      acc = acc - cj * reinterpret_cast<const cx<T>*>(Xr + (long)j * ldx)[i];
-    }
+    for (int j = 0; j < k; ++j) cfma(acc, cs_[j], reinterpret_cast<const cx<T>*>(Xr + (long)j * ldx)[i]);
     yy[i] = acc;
   }
 }
@@ -426,7 +436,7 @@ __global__ void k_multi_caxpy_bp(const T* __restrict__ X, long xstr, long ldx, i
     cx<T> acc = yy[i];
     for (int j = 0; j < k; ++j) {
       const cx<T> cj{(T)cs_[2 * j], (T)cs_[2 * j + 1]};
-      acc = acc - cj * reinterpret_cast<const cx<T>*>(Xr + (long)j * ldx)[i];
+      cfma(acc, -cj, reinterpret_cast<const cx<T>*>(Xr + (long)j * ldx)[i]);
     }
     yy[i] = acc;
   }
