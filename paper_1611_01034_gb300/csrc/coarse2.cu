@@ -118,7 +118,7 @@ __global__ void k_csap(const void* __restrict__ Dc, const T* __restrict__ b, T* 
     const cx<T> alpha = dots[2] > T(0) ? cx<T>{dots[0] / dots[2], dots[1] / dots[2]} : cx<T>{0, 0};
     if (act) {
       cfma(e, alpha, r);
-      r = r - alpha * q;
+      cfma(r, -alpha, q);
     }
     __syncthreads();
     if (act) rs[(size_t)l * n + row] = r;

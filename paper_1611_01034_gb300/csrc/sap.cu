@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sap(SapArgs<T> 
 #pragma unroll
       for (int i = 0; i < 12; ++i) {
         q[i] = q[i] - half * acc[i];
-        dots[0] += q[i].r * r[i].r + q[i].i * r[i].i;  // Re <q, r>
-        dots[1] += q[i].r * r[i].i - q[i].i * r[i].r;  // Im <q, r>
-        dots[2] += q[i].r * q[i].r + q[i].i * q[i].i;  // <q, q>
+        dots[0] = fma(q[i].r, r[i].r, fma(q[i].i, r[i].i, dots[0]));   // Re <q, r>
+        dots[1] = fma(q[i].r, r[i].i, fma(-q[i].i, r[i].r, dots[1]));  // Im <q, r>
+        dots[2] = fma(q[i].r, q[i].r, fma(q[i].i, q[i].i, dots[2]));   // <q, q>
       }
     }
     block_allreduce<T, 3>(dots, red);
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sap(SapArgs<T> 
 #pragma unroll
       for (int i = 0; i < 12; ++i) {
         cfma(e[i], alpha, r[i]);
-        r[i] = r[i] - alpha * q[i];
+        cfma(r[i], -alpha, q[i]);
       }
     }
     __syncthreads();
