@@ -446,14 +446,16 @@ def main_native(args):
     launches = sum(v["launches"] for v in prof.values())
     # kernel launches per profiled scope of a class (a Schur half is one
     # launch; a build scope is orthonormalisation + build + odd-site inverses)
-    kernels_per_scope = {"coarse_build": 3, "coarse_oe": 2}
+    kernels_per_scope = {"coarse_oe": 2}
     roof = None
     model = algorithmic_bytes(dom, wl)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     if model is not None and prof[dom]["launches"]:
-        scopes = prof[dom]["launches"] / kernels_per_scope.get(dom, 1)
+        # a build scope counts one unit (one D_c) whatever kernels it launches
+        scopes = prof[dom]["units"] if dom == "coarse_build" else \
+            prof[dom]["launches"] / kernels_per_scope.get(dom, 1)
         per_launch_bytes = model[0] + model[1] * prof[dom]["units"] / scopes
         avg_s = prof[dom]["ms"] / scopes / 1000.0
         achieved = per_launch_bytes / avg_s / 1e9
@@ -477,7 +479,7 @@ def main_native(args):
         "restrict": per_step["restrict"],
         "prolong": per_step["prolong"],
         "coarse_iter": per_step["coarse_oe"],
-        "coarse_build": prof["coarse_build"]["launches"] / K,
+        "coarse_build": prof["coarse_build"]["units"] / K,
     }
     cpu = None
     if levels == 3:

@@ -214,64 +214,132 @@ void launch_prolong(const T* P, const T* coarse, T* fine, const AggGeom& ag, int
 //   block 0:        P_a^dagger [A + hops inside a] P_a
 //   block 1 + 2 mu: P_a^dagger [hops from a's upper mu-face into a + mu] P_{a+mu}
 //   block 2 + 2 mu: P_a^dagger [hops from a's lower mu-face into a - mu] P_{a-mu}
-// One CTA per (column k, block t, aggregate a); thread = fine site of a.
+// One CTA per (block t, aggregate a); the operator columns of a tile of sites
+// are staged in shared memory, then projected onto P_a^dagger.
 // ===========================================================================
-template <typename T>
-__device__ __forceinline__ void src_column(const T* __restrict__ P, long V, int s, int j, int chi, cx<T> (&p)[12]) {
-  ld_cx<T, 12>(P + (long)j * NR_SPINOR * V, V, s, p);
+
+// The two chirality columns (chi = 0, 1) of test vector j share the loads of
+// P_j and of the link: with P_j masked to chirality 0 the projected half
+// spinor is h = p_up, with P_j masked to chirality 1 it is h = -A p_dn, and each
+// multiplies the link once.
+// acc0/acc1 += sign (1 - gamma_MU) U (P_j masked to chi), U = U_MU(x) at sl
+template <typename T, int MU>
+__device__ __forceinline__ void hop_fwd_pair(const cx<T> (&p)[12], const T* __restrict__ gauge, int V, int sl,
+                                             T sign, cx<T> (&acc0)[12], cx<T> (&acc1)[12]) {
+  Link<T> U;
+  ld_link(gauge, V, MU, sl, U);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) p[6 * (1 - chi) + k] = cx<T>{0, 0};
+  for (int r = 0; r < 2; ++r) {
+    const int lo = 3 * (2 + gperm(MU, r)), ph = conjph(gphase(MU, r));
+    cx<T> h[3], w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) h[k] = sign * p[3 * r + k];
+    su3_mul(U, h, w);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc0[3 * r + k] = acc0[3 * r + k] + w[k];
+      acc0[lo + k] = acc0[lo + k] - mulp(w[k], ph);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) h[k] = -sign * mulp(p[lo + k], gphase(MU, r));
+    su3_mul(U, h, w);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc1[3 * r + k] = acc1[3 * r + k] + w[k];
+      acc1[lo + k] = acc1[lo + k] - mulp(w[k], ph);
+    }
+  }
+}
+
+// acc0/acc1 += sign (1 + gamma_MU) U^dagger (P_j masked to chi), U = U_MU(x - MU) at sl
+template <typename T, int MU>
+__device__ __forceinline__ void hop_bwd_pair(const cx<T> (&p)[12], const T* __restrict__ gauge, int V, int sl,
+                                             T sign, cx<T> (&acc0)[12], cx<T> (&acc1)[12]) {
+  Link<T> U;
+  ld_link(gauge, V, MU, sl, U);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int lo = 3 * (2 + gperm(MU, r)), ph = conjph(gphase(MU, r));
+    cx<T> h[3], w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) h[k] = sign * p[3 * r + k];
+    su3_dag_mul(U, h, w);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc0[3 * r + k] = acc0[3 * r + k] + w[k];
+      acc0[lo + k] = acc0[lo + k] + mulp(w[k], ph);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) h[k] = sign * mulp(p[lo + k], gphase(MU, r));
+    su3_dag_mul(U, h, w);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc1[3 * r + k] = acc1[3 * r + k] + w[k];
+      acc1[lo + k] = acc1[lo + k] + mulp(w[k], ph);
+    }
+  }
 }
 
 template <typename T, int MU>
-__device__ __forceinline__ void build_hops(const T* __restrict__ P, const T* __restrict__ gauge, const AggGeom& ag,
-                                           int s, const int c[4], const int lc[4], int j, int chi, int t, T bc,
-                                           bool& on, cx<T> (&acc)[12]) {
+__device__ __forceinline__ void build_hops_pair(const T* __restrict__ P, const T* __restrict__ gauge,
+                                                const AggGeom& ag, int s, const int c[4], const int lc[4], int j,
+                                                int t, T bc, cx<T> (&acc0)[12], cx<T> (&acc1)[12]) {
   const Lat& g = ag.g;
+  const T* Pj = P + (long)j * NR_SPINOR * g.V;
   const bool up = lc[MU] == ag.agg[MU] - 1, lo = lc[MU] == 0;
   // forward hop: inside a for t == 0 unless on the upper face; block 1+2MU on it
   if ((t == 0 && !up) || (t == 1 + 2 * MU && up)) {
     const int sf = nb_fwd(g, s, c, MU);
     cx<T> p[12];
-    src_column<T>(P, g.V, sf, j, chi, p);
+    ld_cx<T, 12>(Pj, g.V, sf, p);
     const T sign = (MU == 0 && c[0] == g.L[0] - 1) ? bc : T(1);
-    hop_fwd_p<T, MU>(p, gauge, g.V, s, sign, acc);
-    on = true;
+    hop_fwd_pair<T, MU>(p, gauge, g.V, s, sign, acc0, acc1);
   }
   if ((t == 0 && !lo) || (t == 2 + 2 * MU && lo)) {
     const int sb = nb_bwd(g, s, c, MU);
     cx<T> p[12];
-    src_column<T>(P, g.V, sb, j, chi, p);
+    ld_cx<T, 12>(Pj, g.V, sb, p);
     const T sign = (MU == 0 && c[0] == 0) ? bc : T(1);
-    hop_bwd_p<T, MU>(p, gauge, g.V, sb, sign, acc);
-    on = true;
+    hop_bwd_pair<T, MU>(p, gauge, g.V, sb, sign, acc0, acc1);
   }
 }
 
-// operator column k = chi * Nv + j of block t applied at fine site s of
-// aggregate a: u = [D restricted to block t] (P_j masked to chirality chi)
+// operator columns k = j (chi = 0) and k = Nv + j (chi = 1) of block t at fine
+// site s of aggregate a: u_chi = [D restricted to block t] (P_j masked to chi)
 template <typename T>
-__device__ __forceinline__ void column_op(const T* __restrict__ gauge, const T* __restrict__ clover,
-                                          const T* __restrict__ P, const AggGeom& ag, int s, const int c[4],
-                                          const int lc[4], int j, int chi, int t, T bc, cx<T> (&u)[12]) {
-  cx<T> acc[12];
+__device__ __forceinline__ void column_op_pair(const T* __restrict__ gauge, const T* __restrict__ clover,
+                                               const T* __restrict__ P, const AggGeom& ag, int s, const int c[4],
+                                               const int lc[4], int j, int t, T bc, cx<T> (&u0)[12],
+                                               cx<T> (&u1)[12]) {
+  cx<T> acc0[12], acc1[12];
 #pragma unroll
-  for (int q = 0; q < 12; ++q) acc[q] = cx<T>{0, 0};
-  bool on = false;
-  build_hops<T, 0>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
-  build_hops<T, 1>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
-  build_hops<T, 2>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
-  build_hops<T, 3>(P, gauge, ag, s, c, lc, j, chi, t, bc, on, acc);
+  for (int q = 0; q < 12; ++q) acc0[q] = acc1[q] = cx<T>{0, 0};
+  build_hops_pair<T, 0>(P, gauge, ag, s, c, lc, j, t, bc, acc0, acc1);
+  build_hops_pair<T, 1>(P, gauge, ag, s, c, lc, j, t, bc, acc0, acc1);
+  build_hops_pair<T, 2>(P, gauge, ag, s, c, lc, j, t, bc, acc0, acc1);
+  build_hops_pair<T, 3>(P, gauge, ag, s, c, lc, j, t, bc, acc0, acc1);
   if (t == 0) {
-    cx<T> p[12];
-    src_column<T>(P, ag.g.V, s, j, chi, p);
-    site_diag<T>(clover, ag.g.V, s, T(0), p, u);
+    // the clover term is block diagonal in chirality: A P_j splits into the
+    // chirality-0 rows of column j and the chirality-1 rows of column Nv + j
+    cx<T> p[12], y[12];
+    ld_cx<T, 12>(P + (long)j * NR_SPINOR * ag.g.V, ag.g.V, s, p);
+    site_diag<T>(clover, ag.g.V, s, T(0), p, y);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      u0[q] = y[q];
+      u0[6 + q] = cx<T>{0, 0};
+      u1[q] = cx<T>{0, 0};
+      u1[6 + q] = y[6 + q];
+    }
   } else {
 #pragma unroll
-    for (int q = 0; q < 12; ++q) u[q] = cx<T>{0, 0};
+    for (int q = 0; q < 12; ++q) u0[q] = u1[q] = cx<T>{0, 0};
   }
 #pragma unroll
-  for (int q = 0; q < 12; ++q) u[q] = u[q] - T(0.5) * acc[q];
+  for (int q = 0; q < 12; ++q) {
+    u0[q] = u0[q] - T(0.5) * acc0[q];
+    u1[q] = u1[q] - T(0.5) * acc1[q];
+  }
 }
 
 // local site index within the aggregate of the f-th site that block t visits
@@ -294,105 +362,114 @@ __device__ __forceinline__ int block_site(const AggGeom& ag, int t, int f) {
 }
 
 constexpr int kBuildThreads = 256;
-// register tiles of the projection: a thread owns kTR rows (one chirality) x kTC
-// columns of a block, so every P value it loads from shared memory serves kTC
-// outputs and every operator value kTR outputs; kTiles tiles per thread cover
-// 2 ceil(Nv / kTR) ceil(2 Nv / kTC) <= 392 tiles for Nv <= 28
-constexpr int kTR = 4, kTC = 2, kTiles = 2;
+// register tiles of the projection: a thread owns kTR rows (one chirality) x KTC
+// columns of a block, so every P value it loads from shared memory serves KTC
+// outputs and every operator value kTR outputs; one tile per thread, KTC the
+// smallest of 2, 3, 4 with 2 ceil(Nv / kTR) ceil(2 Nv / KTC) <= 256 tiles
+// (KTC = 2 up to Nv = 21, 3 up to 27, 4 for 28)
+constexpr int kTR = 4;
+
+__host__ __device__ constexpr int build_tiles(int nv, int ktc) {
+  return 2 * ((nv + kTR - 1) / kTR) * ((2 * nv + ktc - 1) / ktc);
+}
+
+// row strides (in complex numbers) of the staged P values and operator columns:
+// each holds 12 * width entries of one site, padded to 1 mod 16 so that the
+// threads of a warp, which take consecutive sites, store to distinct banks
+__host__ __device__ __forceinline__ int build_row_stride(int width) {
+  return 12 * width + ((1 - 12 * width) % 16 + 16) % 16;
+}
 
 // D_c(a, t) = P_a^dagger U_t, U_t = the 2 Nv operator columns of block t.
 // One CTA per (t, a); the visited sites are processed in tiles of TS sites
 // whose P values and U columns are staged in shared memory as
-//   Ps[(l * 12 + comp) * Nv + i],  Us[(l * 12 + comp) * 2Nv + k],
-// then every thread accumulates its fixed outputs (row, col) in registers.
-template <typename T>
+//   Ps[l * LP + comp * Nv + i],  Us[l * LU + comp * 2Nv + k],
+// the staging threads taking consecutive sites so that neighbouring threads
+// read neighbouring fine sites; then every thread accumulates its fixed
+// outputs (row, col) in registers.
+template <typename T, int KTC>
 __global__ void __launch_bounds__(kBuildThreads, sizeof(T) == 4 ? 2 : 1) k_coarse_build(const T* __restrict__ gauge,
                                                                 const T* __restrict__ clover,
                                                                 const T* __restrict__ P, T* __restrict__ Dc,
                                                                 AggGeom ag, T bc, int TS) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nv = ag.nv, n = 2 * nv;
+  const int LP = build_row_stride(nv), LU = build_row_stride(n);
   cx<T>* Ps = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* Us = Ps + (size_t)TS * 12 * nv;
+  cx<T>* Us = Ps + (size_t)TS * LP;
   const int t = blockIdx.x, a = blockIdx.y;
   const int nsites = t == 0 ? ag.asites : ag.asites / ag.agg[(t - 1) >> 1];
   const long V = ag.g.V;
-  const int nib = (nv + kTR - 1) / kTR, nkb = (n + kTC - 1) / kTC;
-  const int ntiles = 2 * nib * nkb;
-  cx<T> acc[kTiles][kTR][kTC];
+  const int nib = (nv + kTR - 1) / kTR, nkb = (n + KTC - 1) / KTC;
+  const bool owner = threadIdx.x < 2 * nib * nkb;
+  cx<T> acc[kTR][KTC];
 #pragma unroll
-  for (int m = 0; m < kTiles; ++m)
+  for (int ri = 0; ri < kTR; ++ri)
 #pragma unroll
-    for (int ri = 0; ri < kTR; ++ri)
-#pragma unroll
-      for (int kj = 0; kj < kTC; ++kj) acc[m][ri][kj] = cx<T>{0, 0};
+    for (int kj = 0; kj < KTC; ++kj) acc[ri][kj] = cx<T>{0, 0};
 
   for (int f0 = 0; f0 < nsites; f0 += TS) {
     const int ts = min(TS, nsites - f0);
     // stage P_i at the tile's sites
     for (int e = threadIdx.x; e < ts * nv; e += blockDim.x) {
-      const int l = e / nv, i = e % nv;
+      const int l = e % ts, i = e / ts;
       int lc[4], c[4];
       const int s = agg_site(ag, a, block_site(ag, t, f0 + l), lc, c);
       cx<T> p[12];
       ld_cx<T, 12>(P + (long)i * NR_SPINOR * V, V, s, p);
 #pragma unroll
-      for (int q = 0; q < 12; ++q) Ps[((size_t)l * 12 + q) * nv + i] = p[q];
+      for (int q = 0; q < 12; ++q) Ps[(size_t)l * LP + q * nv + i] = p[q];
     }
-    // operator columns at the tile's sites
-    for (int e = threadIdx.x; e < ts * n; e += blockDim.x) {
-      const int l = e / n, k = e % n;
+    // operator columns at the tile's sites, both chiralities of one test vector per thread
+    for (int e = threadIdx.x; e < ts * nv; e += blockDim.x) {
+      const int l = e % ts, j = e / ts;
       int lc[4], c[4];
       const int s = agg_site(ag, a, block_site(ag, t, f0 + l), lc, c);
-      cx<T> u[12];
-      column_op<T>(gauge, clover, P, ag, s, c, lc, k % nv, k / nv, t, bc, u);
+      cx<T> u0[12], u1[12];
+      column_op_pair<T>(gauge, clover, P, ag, s, c, lc, j, t, bc, u0, u1);
 #pragma unroll
-      for (int q = 0; q < 12; ++q) Us[((size_t)l * 12 + q) * n + k] = u[q];
+      for (int q = 0; q < 12; ++q) {
+        Us[(size_t)l * LU + q * n + j] = u0[q];
+        Us[(size_t)l * LU + q * n + nv + j] = u1[q];
+      }
     }
     __syncthreads();
+    if (owner) {
+      const int chi = threadIdx.x / (nib * nkb), rem = threadIdx.x % (nib * nkb);
+      const int i0 = (rem / nkb) * kTR, k0 = (rem % nkb) * KTC;
+      for (int l = 0; l < ts; ++l) {
 #pragma unroll
-    for (int m = 0; m < kTiles; ++m) {
-      const int tile = threadIdx.x + m * kBuildThreads;
-      if (tile < ntiles) {
-        const int chi = tile / (nib * nkb), rem = tile % (nib * nkb);
-        const int i0 = (rem / nkb) * kTR, k0 = (rem % nkb) * kTC;
-        for (int l = 0; l < ts; ++l) {
+        for (int q = 0; q < 6; ++q) {
+          const cx<T>* pr = Ps + (size_t)l * LP + (6 * chi + q) * nv;
+          const cx<T>* ur = Us + (size_t)l * LU + (6 * chi + q) * n;
+          cx<T> pv[kTR], uv[KTC];
 #pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            const size_t b = (size_t)l * 12 + 6 * chi + q;
-            cx<T> pv[kTR], uv[kTC];
+          for (int ri = 0; ri < kTR; ++ri) pv[ri] = i0 + ri < nv ? pr[i0 + ri] : cx<T>{0, 0};
 #pragma unroll
-            for (int ri = 0; ri < kTR; ++ri) pv[ri] = i0 + ri < nv ? Ps[b * nv + i0 + ri] : cx<T>{0, 0};
+          for (int kj = 0; kj < KTC; ++kj) uv[kj] = k0 + kj < n ? ur[k0 + kj] : cx<T>{0, 0};
 #pragma unroll
-            for (int kj = 0; kj < kTC; ++kj) uv[kj] = k0 + kj < n ? Us[b * n + k0 + kj] : cx<T>{0, 0};
+          for (int ri = 0; ri < kTR; ++ri)
 #pragma unroll
-            for (int ri = 0; ri < kTR; ++ri)
-#pragma unroll
-              for (int kj = 0; kj < kTC; ++kj) cfmac(acc[m][ri][kj], pv[ri], uv[kj]);
-          }
+            for (int kj = 0; kj < KTC; ++kj) cfmac(acc[ri][kj], pv[ri], uv[kj]);
         }
       }
     }
     __syncthreads();
   }
-  T* out = Dc + ((long)a * 9 + t) * n * n * 2;
+  if (owner) {
+    const int chi = threadIdx.x / (nib * nkb), rem = threadIdx.x % (nib * nkb);
+    const int i0 = (rem / nkb) * kTR, k0 = (rem % nkb) * KTC;
+    T* out = Dc + ((long)a * 9 + t) * n * n * 2;
 #pragma unroll
-  for (int m = 0; m < kTiles; ++m) {
-    const int tile = threadIdx.x + m * kBuildThreads;
-    if (tile < ntiles) {
-      const int chi = tile / (nib * nkb), rem = tile % (nib * nkb);
-      const int i0 = (rem / nkb) * kTR, k0 = (rem % nkb) * kTC;
+    for (int ri = 0; ri < kTR; ++ri)
 #pragma unroll
-      for (int ri = 0; ri < kTR; ++ri)
-#pragma unroll
-        for (int kj = 0; kj < kTC; ++kj) {
-          const int row = chi * nv + i0 + ri, k = k0 + kj;
-          if (i0 + ri < nv && k < n) {
-            out[2 * ((long)k * n + row)] = acc[m][ri][kj].r;
-            out[2 * ((long)k * n + row) + 1] = acc[m][ri][kj].i;
-          }
+      for (int kj = 0; kj < KTC; ++kj) {
+        const int row = chi * nv + i0 + ri, k = k0 + kj;
+        if (i0 + ri < nv && k < n) {
+          out[2 * ((long)k * n + row)] = acc[ri][kj].r;
+          out[2 * ((long)k * n + row) + 1] = acc[ri][kj].i;
         }
-    }
+      }
   }
 }
 
@@ -400,19 +477,31 @@ template <typename T>
 void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, const AggGeom& ag, double bc_t,
                          cudaStream_t st) {
   const int nv = ag.nv;
-  const size_t per_site = (size_t)12 * 3 * nv * sizeof(cx<T>);  // Ps + Us per site
+  const size_t per_site = (size_t)(build_row_stride(nv) + build_row_stride(2 * nv)) * sizeof(cx<T>);  // Ps + Us
   const size_t budget = 100 * 1024;  // two CTAs per SM
   int TS = (int)(budget / per_site);
   if (TS > 16) TS = 16;
   if (TS < 1) TS = 1;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_coarse_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_coarse_build<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_coarse_build<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_coarse_build<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   dim3 grid(9, ag.gc.V);
-  k_coarse_build<T><<<grid, kBuildThreads, TS * per_site, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
+  const size_t smem = TS * per_site;
+  if (build_tiles(nv, 2) <= kBuildThreads)
+    k_coarse_build<T, 2><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
+  else if (build_tiles(nv, 3) <= kBuildThreads)
+    k_coarse_build<T, 3><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
+  else
+    k_coarse_build<T, 4><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
 }
+
+static_assert(build_tiles(21, 2) <= kBuildThreads && build_tiles(27, 3) <= kBuildThreads &&
+                  build_tiles(28, 4) <= kBuildThreads,
+              "one register tile per thread up to Nv = 28");
 
 // ===========================================================================
 // coarse stencil helpers
@@ -442,6 +531,7 @@ __global__ void k_coarse_apply(const T* __restrict__ Dc, const T* __restrict__ v
     const cx<T>* src = vv + (long)nb * n;
     const cx<T>* B = reinterpret_cast<const cx<T>*>(Dc) + ((long)a * 9 + t) * n * n;
     cx<T> acc{0, 0};
+#pragma unroll 8
     for (int col = 0; col < n; ++col) cfma(acc, B[(long)col * n + row], src[col]);
     part[t * n + row] = acc;
   }
@@ -630,6 +720,7 @@ __global__ void k_oe_stencil_mr(OEArgs<T> a, int nrhs) {
     if (apply) {
       const cx<T>* Bt = B + (long)t * n * n;
       const cx<T>* xt = xs + (size_t)t * RB * n;
+#pragma unroll 8
       for (int col = 0; col < n; ++col) {
         const cx<T> bv = Bt[(long)col * n + row];
 #pragma unroll
@@ -674,6 +765,7 @@ __global__ void k_oe_stencil_mr(OEArgs<T> a, int nrhs) {
     if (a.post) {
       const cx<T>* Di = reinterpret_cast<const cx<T>*>(a.Dinv) + (long)k * n * n;
       res = cx<T>{0, 0};
+#pragma unroll 8
       for (int col = 0; col < n; ++col) cfma(res, Di[(long)col * n + rr], accs[(size_t)q * n + col]);
     }
     cx<T>* out = reinterpret_cast<cx<T>*>(a.out + lst[g0 + q] * a.o_str);
@@ -737,6 +829,7 @@ __global__ void k_oe_inv_odd(const T* __restrict__ Dinv, const T* __restrict__ b
   const cx<T>* bb = reinterpret_cast<const cx<T>*>(b) + (long)site * n;
   const cx<T>* Di = reinterpret_cast<const cx<T>*>(Dinv) + (long)k * n * n;
   cx<T> acc{0, 0};
+#pragma unroll 8
   for (int col = 0; col < n; ++col) cfma(acc, Di[(long)col * n + row], bb[col]);
   reinterpret_cast<cx<T>*>(to)[(long)k * n + row] = acc;
 }
@@ -778,6 +871,7 @@ __global__ void k_oe_inv_odd_b(const T* __restrict__ Dinv, const T* __restrict__
   const cx<T>* bb = reinterpret_cast<const cx<T>*>(b + r * bstr) + (long)site * n;
   const cx<T>* Di = reinterpret_cast<const cx<T>*>(Dinv) + (long)k * n * n;
   cx<T> acc{0, 0};
+#pragma unroll 8
   for (int col = 0; col < n; ++col) cfma(acc, Di[(long)col * n + row], bb[col]);
   reinterpret_cast<cx<T>*>(to + r * tstr)[(long)k * n + row] = acc;
 }

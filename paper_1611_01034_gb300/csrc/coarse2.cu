@@ -83,6 +83,7 @@ __global__ void k_csap(const void* __restrict__ Dc, const T* __restrict__ b, T* 
     for (int t = 0; t < 9; ++t) {
       const cx<T>* src = xx + (long)c_nb(g, s, t) * n;
       const long Bt = B + (long)t * n * n;
+#pragma unroll 8
       for (int col = 0; col < n; ++col) cfma(acc, ld_blk<T, H>(Dc, Bt + (long)col * n + row), src[col]);
     }
     const cx<T> xs = xx[(long)s * n + row];
@@ -106,6 +107,7 @@ __global__ void k_csap(const void* __restrict__ Dc, const T* __restrict__ b, T* 
         }
         const long Bt = B + (long)t * n * n;
         const cx<T>* src = rs + (size_t)ln * n;
+#pragma unroll 8
         for (int col = 0; col < n; ++col) cfma(q, ld_blk<T, H>(Dc, Bt + (long)col * n + row), src[col]);
       }
       q.r -= sg5 * r.i;

@@ -489,7 +489,11 @@ KrylovOut krylov(tm_handle* h, const std::string& tag, FA A, FAZ AZ, FM M, bool 
 template <typename T>
 void build_coarse(tm_handle* h) {
   T* P = static_cast<T*>(h->P);
-  Prof pf(h, PK_BUILD, 1, 3);
+  constexpr bool f32 = std::is_same<T, float>::value;
+  // orthonormalisation + build, the FP16 copy, the odd-site inverses and the
+  // three tensor-core tile kernels
+  const int nk = 2 + (f32 && h->Dc1h ? 1 : 0) + (h->three ? 0 : 1) + (f32 && h->tc_on && !h->three ? 3 : 0);
+  Prof pf(h, PK_BUILD, 1, nk);
   launch_orthonormalise<T>(P, h->ag, h->d_err, h->st);
   CKL();
   launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, static_cast<T*>(h->Dc), h->ag, h->p.bc_t, h->st);
@@ -903,7 +907,7 @@ void level1_solve(tm_handle* h, const T* b1, T* x1, int nrhs, double tol, int ma
 // P2 (holding the level-1 test vectors) -> orthonormal P2, D_c2, odd-site inverses
 template <typename T>
 void build_level2(tm_handle* h) {
-  Prof pf(h, PK_BUILD, 1, 3);
+  Prof pf(h, PK_BUILD, 1, 3 + (std::is_same<T, float>::value && h->tc_on ? 3 : 0));
   launch_corth<T>(static_cast<T*>(h->P2), h->cag, h->d_err, h->st);
   CKL();
   launch_cbuild<T>(static_cast<const T*>(h->Dc), static_cast<const T*>(h->P2), static_cast<T*>(h->Dc2), h->cag,
@@ -1581,6 +1585,7 @@ void apply_mu(tm_handle* h, double mu, double delta) {
   h->p.mu = mu;
   h->p.delta = delta;
   if (h->setup_ok) {
+    Prof pf(h, PK_BUILD, 0, h->tc_on ? 2 : 1);  // no new D_c: zero build units
     void* Dc = h->three ? h->Dc2 : h->Dc;
     void* Di = h->three ? h->Dinv2 : h->Dinv;
     const OEGeom& oe = h->three ? h->oe2 : h->oe;
