@@ -120,6 +120,7 @@ struct tm_handle {
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> evpool;
+  cudaEvent_t pipe_ev[2] = {nullptr, nullptr};  // the coarse GMRES's double-buffered step results
   long long prof_launch[16] = {};
   long long prof_units[16] = {};
   double prof_ms[16] = {};
@@ -574,11 +575,14 @@ std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x,
   double* nrm = W<double>(h, "cb_nrm", nrhs);
   int* act = W<int>(h, "cb_act", nrhs);
   constexpr int kSlots = 8;  // mask uploads between two stream synchronisations
-  double* hb = host_scratch(h, "cb", (size_t)(ds + 1) * nrhs + (size_t)kSlots * nrhs);
+  double* hb = host_scratch(h, "cb", (size_t)3 * (ds + 1) * nrhs + (size_t)kSlots * nrhs);
   double* hn_h = hb + (size_t)ds * nrhs;                     // [nrhs] norms
   int* hact0 = reinterpret_cast<int*>(hn_h + nrhs);          // [kSlots][nrhs] masks
+  double* hpipe = hn_h + nrhs + (size_t)kSlots * nrhs;       // [2][ds + 1][nrhs] Arnoldi step results
   int slot = 0;  // an async upload reads its slot later: reuse slots only after a sync
   const double mc = lv.mu_c;
+  for (cudaEvent_t& e : h->pipe_ev)
+    if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
   std::vector<double> bnorm(nrhs), beta(nrhs);
   std::vector<int> iters(nrhs, 0), kk(nrhs, 0);
@@ -663,9 +667,20 @@ std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x,
         g[(size_t)r * (m + 1)] = beta[r];
       }
     }
-    for (int k = 0; k < m && count(inner); ++k) {
+    // The Arnoldi steps run one ahead of the host: step k + 1 is enqueued
+    // before the host waits for the Hessenberg column of step k, so the GPU
+    // computes while the host applies the Givens rotations.  Step k + 1 runs
+    // under the mask the host held before reading step k; a right-hand side
+    // that stops at step k computes it needlessly and its results are never
+    // read.  The device results of step k reach the host (in buffer k & 1)
+    // before step k + 1 overwrites them, by stream order.
+    std::vector<char> uploaded;  // mask in `act`; the cycle's end reuses `act`
+    auto arnoldi = [&](int k) {
       const int na = count(inner);
-      upload_mask(inner, nullptr);
+      if (inner != uploaded) {
+        upload_mask(inner, nullptr);
+        uploaded = inner;
+      }
       schur(Vb + (long)k * cv, vstr, na);
       double* d1 = dd;
       double* d2 = dd + 2 * (k + 1);
@@ -685,14 +700,23 @@ std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x,
         launch_scale_copy_bp<T>(w, cv, Vb + (long)(k + 1) * cv, vstr, part, nrm, nc, nrhs, act, h->st);
         CKL();
       }
-      CK(cudaMemcpy2DAsync(hb, 4 * (k + 1) * sizeof(double), dd, ds * sizeof(double), 4 * (k + 1) * sizeof(double),
+      double* hk = hpipe + (size_t)(k & 1) * (ds + 1) * nrhs;
+      CK(cudaMemcpy2DAsync(hk, 4 * (k + 1) * sizeof(double), dd, ds * sizeof(double), 4 * (k + 1) * sizeof(double),
                            nrhs, cudaMemcpyDeviceToHost, h->st));
-      read_norms();
+      CK(cudaMemcpyAsync(hk + (size_t)ds * nrhs, nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaEventRecord(h->pipe_ev[k & 1], h->st));
+    };
+    arnoldi(0);
+    for (int k = 0;; ++k) {
+      if (k + 1 < m) arnoldi(k + 1);
+      CK(cudaEventSynchronize(h->pipe_ev[k & 1]));
+      const double* hk = hpipe + (size_t)(k & 1) * (ds + 1) * nrhs;
+      const double* hnk = hk + (size_t)ds * nrhs;
       for (int r = 0; r < nrhs; ++r) {
         if (!inner[r]) continue;
-        const double hn = std::sqrt(hn_h[r]);
+        const double hn = std::sqrt(hnk[r]);
         if (!std::isfinite(hn)) raise(TM_ERR_NONFINITE, "non-finite coarse Arnoldi vector");
-        const double* hr = hb + (size_t)r * 4 * (k + 1);
+        const double* hr = hk + (size_t)r * 4 * (k + 1);
         cd* Hr = H.data() + (size_t)r * (m + 1) * m;
         cd* gr = g.data() + (size_t)r * (m + 1);
         cd* snr = sn.data() + (size_t)r * m;
@@ -720,6 +744,7 @@ std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x,
         kk[r] = k + 1;
         if (hn == 0 || std::abs(gr[k + 1]) <= tol * bnorm[r] || iters[r] >= maxit) inner[r] = 0;
       }
+      if (k + 1 >= m || !count(inner)) break;
     }
     // x_r += V_r y_r with R y = g for this cycle's right-hand sides
     int kmax = 0;
@@ -1693,6 +1718,8 @@ void tm_destroy(tm_handle* h) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->pipe_ev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 
