@@ -479,9 +479,21 @@ void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, con
   const int nv = ag.nv;
   const size_t per_site = (size_t)(build_row_stride(nv) + build_row_stride(2 * nv)) * sizeof(cx<T>);  // Ps + Us
   const size_t budget = 100 * 1024;  // two CTAs per SM
-  int TS = (int)(budget / per_site);
-  if (TS > 16) TS = 16;
-  if (TS < 1) TS = 1;
+  int ts_max = (int)(budget / per_site);
+  if (ts_max > 16) ts_max = 16;
+  if (ts_max < 1) ts_max = 1;
+  // tile size whose TS * N_v staging items fill the CTA's rounds best (the
+  // projection work does not depend on it); ties go to the larger tile
+  int TS = 1;
+  double best = 0;
+  for (int ts = 1; ts <= ts_max; ++ts) {
+    const int items = ts * nv, rounds = (items + kBuildThreads - 1) / kBuildThreads;
+    const double fill = (double)items / (rounds * kBuildThreads);
+    if (fill >= best) {
+      best = fill;
+      TS = ts;
+    }
+  }
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_coarse_build<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
