@@ -205,6 +205,22 @@ tm_status tm_setup_from_vectors(tm_handle* h, const double* test_vectors);
  * (no gauge field, or no earlier setup on this handle). */
 tm_status tm_setup_update(tm_handle* h, int fine_iters, int coarse_iters);
 
+/* Autotune the tile shape of the D_c build (the Galerkin projection
+ * P^dagger D P of Sec. 1) for this handle's N_v, aggregate and cycle
+ * precision.  Each candidate (sites staged per tile, columns per register
+ * tile) first rebuilds D_c into a scratch buffer that must equal the default
+ * shape's D_c bit for bit (every shape sums each entry in the same order),
+ * then is timed with CUDA events over `reps` (1..100) builds; the fastest is
+ * kept for the handle's later builds.  cache_path (may be NULL): a JSON file
+ * of earlier choices keyed by device name, kernel, precision, N_v and
+ * aggregate; a hit takes the stored shape without timing, a miss adds the
+ * new choice (the file is rewritten through a temporary file beside it).
+ * out (may be NULL): 4 doubles = sites per tile, columns per register tile,
+ * microseconds per build, candidates timed (0 for a cache hit).  The D_c in
+ * use is unchanged.  Errors: TM_ERR_STATE (no setup, or a candidate whose D_c
+ * differs), TM_ERR_ARG (reps out of range, cache not writable). */
+tm_status tm_autotune_build(tm_handle* h, const char* cache_path, int reps, double* out);
+
 /* Change mu and delta without a new setup (Sec. 1: D_c(mu) = D_c +
  * i mu Gamma5_c, so only the diagonal shift and the odd-site inverses of the
  * coarse Schur complement change; one setup serves D(+mu) and D(-mu)). */

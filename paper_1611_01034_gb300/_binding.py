@@ -59,6 +59,7 @@ _SIGS = {
     "tm_setup": (c_int, [c_void_p, c_void_p]),
     "tm_setup_from_vectors": (c_int, [c_void_p, c_void_p]),
     "tm_set_mu": (c_int, [c_void_p, c_double, c_double]),
+    "tm_autotune_build": (c_int, [c_void_p, c_char_p, c_int, POINTER(c_double)]),
     "tm_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
     "tm_solve_squared": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
     "tm_field_bytes": (c_size_t, [c_void_p, c_int, c_int, c_int]),
@@ -192,6 +193,13 @@ def tm_setup_from_vectors(h, test_vectors) -> None:
 
 def tm_set_mu(h, mu: float, delta: float) -> None:
     _check(lib().tm_set_mu(h, mu, delta), h)
+
+
+def tm_autotune_build(h, cache_path=None, reps: int = 3) -> dict:
+    out = (c_double * 4)()
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(lib().tm_autotune_build(h, path, reps, out), h)
+    return {"ts": int(out[0]), "ktc": int(out[1]), "us": out[2], "timed": int(out[3])}
 
 
 def tm_solve(h, b, x, nrhs: int, tol: float):

@@ -473,26 +473,54 @@ __global__ void __launch_bounds__(kBuildThreads, sizeof(T) == 4 ? 2 : 1) k_coars
   }
 }
 
-template <typename T>
-void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, const AggGeom& ag, double bc_t,
-                         cudaStream_t st) {
-  const int nv = ag.nv;
-  const size_t per_site = (size_t)(build_row_stride(nv) + build_row_stride(2 * nv)) * sizeof(cx<T>);  // Ps + Us
-  const size_t budget = 100 * 1024;  // two CTAs per SM
+// largest staged tile (sites) that keeps two CTAs per SM
+static int build_ts_max(int nv, size_t real_bytes) {
+  const size_t per_site = (size_t)(build_row_stride(nv) + build_row_stride(2 * nv)) * 2 * real_bytes;
+  const size_t budget = 100 * 1024;
   int ts_max = (int)(budget / per_site);
   if (ts_max > 16) ts_max = 16;
-  if (ts_max < 1) ts_max = 1;
+  return ts_max < 1 ? 1 : ts_max;
+}
+
+BuildShape coarse_build_default(int nv, size_t real_bytes) {
+  BuildShape b;
   // tile size whose TS * N_v staging items fill the CTA's rounds best (the
   // projection work does not depend on it); ties go to the larger tile
-  int TS = 1;
   double best = 0;
-  for (int ts = 1; ts <= ts_max; ++ts) {
+  for (int ts = 1; ts <= build_ts_max(nv, real_bytes); ++ts) {
     const int items = ts * nv, rounds = (items + kBuildThreads - 1) / kBuildThreads;
     const double fill = (double)items / (rounds * kBuildThreads);
     if (fill >= best) {
       best = fill;
-      TS = ts;
+      b.ts = ts;
     }
+  }
+  b.ktc = build_tiles(nv, 2) <= kBuildThreads ? 2 : build_tiles(nv, 3) <= kBuildThreads ? 3 : 4;
+  return b;
+}
+
+std::vector<BuildShape> coarse_build_candidates(int nv, size_t real_bytes) {
+  std::vector<BuildShape> out;
+  for (int ktc = 2; ktc <= 4; ++ktc) {
+    if (build_tiles(nv, ktc) > kBuildThreads) continue;
+    for (int ts = 1; ts <= build_ts_max(nv, real_bytes); ++ts) out.push_back(BuildShape{ts, ktc});
+  }
+  return out;
+}
+
+// Every shape sums each D_c entry over the same sites and components in the
+// same order, so all shapes give bit-identical blocks.
+template <typename T>
+void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, const AggGeom& ag, double bc_t,
+                         cudaStream_t st, BuildShape shape) {
+  const int nv = ag.nv;
+  const size_t per_site = (size_t)(build_row_stride(nv) + build_row_stride(2 * nv)) * sizeof(cx<T>);  // Ps + Us
+  const BuildShape def = coarse_build_default(nv, sizeof(T));
+  int TS = shape.ts > 0 ? shape.ts : def.ts;
+  int ktc = shape.ktc > 0 ? shape.ktc : def.ktc;
+  if (TS > build_ts_max(nv, sizeof(T)) || ktc < 2 || ktc > 4 || build_tiles(nv, ktc) > kBuildThreads) {
+    TS = def.ts;  // a shape outside the candidate set falls back to the default
+    ktc = def.ktc;
   }
   static bool attr = false;
   if (!attr) {
@@ -503,12 +531,30 @@ void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, con
   }
   dim3 grid(9, ag.gc.V);
   const size_t smem = TS * per_site;
-  if (build_tiles(nv, 2) <= kBuildThreads)
+  if (ktc == 2)
     k_coarse_build<T, 2><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
-  else if (build_tiles(nv, 3) <= kBuildThreads)
+  else if (ktc == 3)
     k_coarse_build<T, 3><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
   else
     k_coarse_build<T, 4><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
+}
+
+// number of 32-bit words in which a and b differ, added to *count
+__global__ void k_count_mismatch(const unsigned* __restrict__ a, const unsigned* __restrict__ b, long n,
+                                 unsigned long long* count) {
+  unsigned long long c = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    c += a[i] != b[i];
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+void launch_count_mismatch(const void* a, const void* b, long words, unsigned long long* count, cudaStream_t st) {
+  long blocks = (words + 255) / 256;
+  if (blocks > 152L * 8) blocks = 152L * 8;
+  if (blocks < 1) blocks = 1;
+  k_count_mismatch<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const unsigned*>(a), static_cast<const unsigned*>(b),
+                                                     words, count);
 }
 
 static_assert(build_tiles(21, 2) <= kBuildThreads && build_tiles(27, 3) <= kBuildThreads &&
@@ -944,7 +990,8 @@ TM_INST_B(float)
   template void launch_orthonormalise<T>(T*, const AggGeom&, int*, cudaStream_t);                              \
   template void launch_restrict<T>(const T*, const T*, T*, const AggGeom&, int, cudaStream_t);                 \
   template void launch_prolong<T>(const T*, const T*, T*, const AggGeom&, int, bool, cudaStream_t);            \
-  template void launch_coarse_build<T>(const T*, const T*, const T*, T*, const AggGeom&, double, cudaStream_t); \
+  template void launch_coarse_build<T>(const T*, const T*, const T*, T*, const AggGeom&, double, cudaStream_t,   \
+                                       BuildShape);                                                           \
   template void launch_coarse_apply<T>(const T*, const T*, T*, const Lat&, int, double, int, cudaStream_t);    \
   template void launch_oe_invert<T>(const T*, T*, const OEGeom&, double, int*, cudaStream_t);                  \
   template void launch_oe_hop_inv<T>(const T*, const T*, const T*, T*, const OEGeom&, cudaStream_t);           \

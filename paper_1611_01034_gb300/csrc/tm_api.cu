@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdio>
 #include <cstring>
 #include <type_traits>
 
@@ -121,6 +122,7 @@ struct tm_handle {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> evpool;
   cudaEvent_t pipe_ev[2] = {nullptr, nullptr};  // the coarse GMRES's double-buffered step results
+  BuildShape build_shape{};                     // tile shape of the D_c build (autotuned or default)
   long long prof_launch[16] = {};
   long long prof_units[16] = {};
   double prof_ms[16] = {};
@@ -497,7 +499,8 @@ void build_coarse(tm_handle* h) {
   Prof pf(h, PK_BUILD, 1, nk);
   launch_orthonormalise<T>(P, h->ag, h->d_err, h->st);
   CKL();
-  launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, static_cast<T*>(h->Dc), h->ag, h->p.bc_t, h->st);
+  launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, static_cast<T*>(h->Dc), h->ag, h->p.bc_t, h->st,
+                         h->build_shape);
   CKL();
   if constexpr (std::is_same<T, float>::value) {
     if (h->Dc1h) {  // FP16 blocks for the level-1 SAP
@@ -1643,6 +1646,130 @@ void apply_mu(tm_handle* h, double mu, double delta) {
   if (h) h->err.clear();                         \
   return TM_OK;
 
+// ---------------------------------------------------------------------------
+// autotuner of the D_c build's tile shape
+// ---------------------------------------------------------------------------
+// The cache is a JSON object with one entry per line,
+//   "<device>/k_coarse_build/<fp32|fp64>/nv<N_v>/agg<a_T>x<a_Z>x<a_Y>x<a_X>": {"ts": 12, "ktc": 2, "us": 512.30},
+// read back line by line; entries of other keys are kept when it is rewritten.
+struct TuneEntry {
+  int ts = 0, ktc = 0;
+  double us = 0;
+};
+
+static std::map<std::string, TuneEntry> read_tune_cache(const char* path) {
+  std::map<std::string, TuneEntry> m;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return m;
+  char line[1024];
+  while (std::fgets(line, sizeof line, f)) {
+    char key[512];
+    TuneEntry e;
+    if (std::sscanf(line, " \"%511[^\"]\": {\"ts\": %d, \"ktc\": %d, \"us\": %lf}", key, &e.ts, &e.ktc, &e.us) == 4)
+      m[key] = e;
+  }
+  std::fclose(f);
+  return m;
+}
+
+static void write_tune_cache(const char* path, const std::map<std::string, TuneEntry>& m) {
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) raise(TM_ERR_ARG, "cannot write the tuning cache");
+  std::fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& kv : m)
+    std::fprintf(f, "  \"%s\": {\"ts\": %d, \"ktc\": %d, \"us\": %.2f}%s\n", kv.first.c_str(), kv.second.ts,
+                 kv.second.ktc, kv.second.us, ++i < m.size() ? "," : "");
+  std::fprintf(f, "}\n");
+  const bool ok = std::fclose(f) == 0;
+  if (!ok || std::rename(tmp.c_str(), path) != 0) raise(TM_ERR_ARG, "cannot write the tuning cache");
+}
+
+template <typename T>
+void autotune_build(tm_handle* h, const char* cache_path, int reps, double* out) {
+  const AggGeom& ag = h->ag;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  const std::string key = std::string(prop.name) + "/k_coarse_build/" + (sizeof(T) == 4 ? "fp32" : "fp64") + "/nv" +
+                          std::to_string(ag.nv) + "/agg" + std::to_string(ag.agg[0]) + "x" +
+                          std::to_string(ag.agg[1]) + "x" + std::to_string(ag.agg[2]) + "x" +
+                          std::to_string(ag.agg[3]);
+  const std::vector<BuildShape> cand = coarse_build_candidates(ag.nv, sizeof(T));
+  auto listed = [&](int ts, int ktc) {
+    for (const BuildShape& b : cand)
+      if (b.ts == ts && b.ktc == ktc) return true;
+    return false;
+  };
+  std::map<std::string, TuneEntry> cache;
+  if (cache_path) {
+    cache = read_tune_cache(cache_path);
+    auto it = cache.find(key);
+    if (it != cache.end() && listed(it->second.ts, it->second.ktc)) {
+      h->build_shape = BuildShape{it->second.ts, it->second.ktc};
+      if (out) {
+        out[0] = it->second.ts;
+        out[1] = it->second.ktc;
+        out[2] = it->second.us;
+        out[3] = 0;  // from the cache: nothing timed
+      }
+      return;
+    }
+  }
+  const T* P = static_cast<const T*>(h->P);
+  const size_t n = (size_t)h->gc.V * 9 * h->n * h->n * 2;  // reals of D_c
+  T* ref = W<T>(h, "tune_ref", n);
+  T* trial = W<T>(h, "tune_dc", n);
+  unsigned long long* bad_d = W<unsigned long long>(h, "tune_bad", 1);
+  launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, ref, ag, h->p.bc_t, h->st, BuildShape{});
+  CKL();
+  cudaEvent_t e0 = take_event(h), e1 = take_event(h);
+  BuildShape best{};
+  double best_us = 0;
+  for (const BuildShape& b : cand) {
+    // parity first: the candidate's D_c must equal the default's bit for bit
+    launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, trial, ag, h->p.bc_t, h->st, b);
+    CKL();
+    CK(cudaMemsetAsync(bad_d, 0, sizeof(unsigned long long), h->st));
+    launch_count_mismatch(ref, trial, (long)(n * sizeof(T) / 4), bad_d, h->st);
+    CKL();
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bad, bad_d, sizeof bad, cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    if (bad)
+      raise(TM_ERR_STATE, "build shape ts=" + std::to_string(b.ts) + " ktc=" + std::to_string(b.ktc) +
+                              " differs from the default D_c in " + std::to_string(bad) + " words");
+    CK(cudaEventRecord(e0, h->st));
+    for (int r = 0; r < reps; ++r)
+      launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, trial, ag, h->p.bc_t, h->st, b);
+    CKL();
+    CK(cudaEventRecord(e1, h->st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    const double us = 1000.0 * ms / reps;
+    if (best.ts == 0 || us < best_us) {
+      best = b;
+      best_us = us;
+    }
+  }
+  h->evpool.push_back(e0);
+  h->evpool.push_back(e1);
+  h->build_shape = best;
+  if (cache_path) {
+    cache[key] = TuneEntry{best.ts, best.ktc, best_us};
+    write_tune_cache(cache_path, cache);
+  }
+  if (out) {
+    out[0] = best.ts;
+    out[1] = best.ktc;
+    out[2] = best_us;
+    out[3] = (double)cand.size();
+  }
+}
+
 extern "C" {
 
 void tm_params_default(tm_params* p) {
@@ -1931,6 +2058,17 @@ tm_status tm_setup_update(tm_handle* h, int fine_iters, int coarse_iters) {
 tm_status tm_setup(tm_handle* h, const double* test_vectors) { return setup_common(h, test_vectors, true); }
 tm_status tm_setup_from_vectors(tm_handle* h, const double* test_vectors) {
   return setup_common(h, test_vectors, false);
+}
+
+tm_status tm_autotune_build(tm_handle* h, const char* cache_path, int reps, double* out) {
+  if (!h || reps < 1 || reps > 100) return TM_ERR_ARG;
+  API_BEGIN
+  if (!h->setup_ok) raise(TM_ERR_STATE, "tm_setup must come first");
+  if (h->p.cycle_prec == TM_F64)
+    autotune_build<double>(h, cache_path, reps, out);
+  else
+    autotune_build<float>(h, cache_path, reps, out);
+  API_END
 }
 
 tm_status tm_set_mu(tm_handle* h, double mu, double delta) {

@@ -3,6 +3,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <vector>
+
 #include "tm_internal.cuh"
 
 namespace tmamg {
@@ -39,6 +42,11 @@ void launch_sap_colour(const T* gauge, const T* clover, const T* b, T* x, const 
                        double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st);
 
 // ---- aggregation and coarse operator (coarse.cu) ---------------------------
+// tile shape of the coarse-operator build kernel (0 = default heuristic)
+struct BuildShape {
+  int ts = 0, ktc = 0;
+};
+
 struct AggGeom {
   Lat g;        // fine lattice
   Lat gc;       // coarse lattice
@@ -59,7 +67,13 @@ void launch_prolong(const T* P, const T* coarse, T* fine, const AggGeom& ag, int
 // Dc blocks [Vc][9][2Nv col][2Nv row] = local Galerkin projection (mu-free)
 template <typename T>
 void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, const AggGeom& ag,
-                         double bc_t, cudaStream_t st);
+                         double bc_t, cudaStream_t st, BuildShape shape = BuildShape{});
+// tile shape of the build: ts fine sites staged per tile, ktc columns per
+// register tile (0 = the default heuristic); the candidates an autotuner may try
+BuildShape coarse_build_default(int nv, size_t real_bytes);
+std::vector<BuildShape> coarse_build_candidates(int nv, size_t real_bytes);
+// adds to *count the number of 32-bit words in which a and b differ
+void launch_count_mismatch(const void* a, const void* b, long words, unsigned long long* count, cudaStream_t st);
 // y = D_c(mu_c) v on the full coarse lattice
 template <typename T>
 void launch_coarse_apply(const T* Dc, const T* v, T* y, const Lat& gc, int nv, double mu_c, int nrhs,
