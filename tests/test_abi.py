@@ -79,4 +79,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert L.tm_solve(None, None, None, 1, 1e-10, None) == tm.TM_ERR_ARG
     assert L.tm_apply(None, 0, 0, None, None, 1) == tm.TM_ERR_ARG
     assert L.tm_synchronize(None) == tm.TM_ERR_ARG
+    assert L.tm_autotune_build(None, None, 3, None) == tm.TM_ERR_ARG
+    assert L.tm_set_mu(None, 0.01, 2.0) == tm.TM_ERR_ARG
+    assert L.tm_setup_update(None, 1, 0) == tm.TM_ERR_ARG
     L.tm_destroy(None)
