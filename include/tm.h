@@ -217,7 +217,9 @@ tm_status tm_setup_update(tm_handle* h, int fine_iters, int coarse_iters);
  * new choice (the file is rewritten through a temporary file beside it).
  * out (may be NULL): 4 doubles = sites per tile, columns per register tile,
  * microseconds per build, candidates timed (0 for a cache hit).  The D_c in
- * use is unchanged.  Errors: TM_ERR_STATE (no setup, or a candidate whose D_c
+ * use is unchanged; timing takes two D_c-sized scratch buffers in the
+ * handle's workspace, held until tm_destroy.  Synchronises the handle's
+ * stream.  Errors: TM_ERR_STATE (no setup, or a candidate whose D_c
  * differs), TM_ERR_ARG (reps out of range, cache not writable). */
 tm_status tm_autotune_build(tm_handle* h, const char* cache_path, int reps, double* out);
 
