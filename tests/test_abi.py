@@ -63,6 +63,18 @@ def test_defaults_and_status_strings(lib):
     dict(L=(16, 16, 16, 16), levels=3, nv2=29),
     dict(L=(16, 16, 16, 16), levels=3, sap_block1=(4, 2, 2, 2)),  # one level-1 SAP block in T
     dict(L=(16, 16, 16, 16), levels=3, nv=20, agg2=(4, 2, 2, 2), sap_block1=(2, 2, 2, 2)),  # not divisible
+    dict(L=(8, 8, 8, 8), coarse_mma=4),
+    dict(L=(8, 8, 8, 8), coarse_mma=1, cycle_prec=0),     # tensor cores need the FP32 cycle
+    dict(L=(8, 8, 8, 8), nn_mode=3),
+    dict(L=(8, 8, 8, 8), nn_mode=1, cycle_prec=0),        # learned layer needs the FP32 cycle
+    dict(L=(8, 8, 8, 8), nn_prec=7),
+    dict(L=(8, 8, 8, 8), sap1_prec=2),                    # FP16 level-1 blocks need three levels
+    dict(L=(8, 8, 8, 8), restart=0),
+    dict(L=(8, 8, 8, 8), restart=127),                    # Hessenberg column beyond the fixed bound
+    dict(L=(8, 8, 8, 8), coarse_restart=200),
+    dict(L=(8, 8, 8, 8), maxit=0),
+    dict(L=(8, 8, 8, 8), max_rhs=0),
+    dict(L=(8, 8, 8, 8), mr_iters=-1),
 ])
 def test_invalid_parameters_rejected_before_any_device_call(lib, bad):
     import paper_1611_01034_gb300 as tm
