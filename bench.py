@@ -303,6 +303,29 @@ def run_oracle_worker(wl_name: str) -> dict:
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
+# multi-rank pieces of the contract (N GPUs = N independent replicas)
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of rank `rank`'s replica: every rank solves its own system."""
+    return base + rank
+
+
+def max_over_ranks(sec: float, world: int, device) -> float:
+    """The slowest rank's timed region (all ranks have passed a barrier)."""
+    if world <= 1:
+        return sec
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([sec], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_seconds_per_step(sec_max: float, world: int, steps: int) -> float:
+    """Whole-job value: the slowest rank's time over the steps all ranks ran."""
+    return sec_max / (world * steps)
+
+
+# ---------------------------------------------------------------------------
 def main_native(args):
     import numpy as np
     import torch
@@ -318,7 +341,7 @@ def main_native(args):
     torch.cuda.set_device(local)
     wl = WORKLOADS[args.workload]
     m0, m0_src = (args.m0, "command line") if args.m0 is not None else workload_m0(wl)
-    L, nv, seed = wl["L"], wl["nv"], wl["seed"] + rank  # one independent replica per rank
+    L, nv, seed = wl["L"], wl["nv"], replica_seed(wl["seed"], rank)  # one independent replica per rank
     U = inputs.gauge_field(L, wl["eps"], seed)
     levels = wl.get("levels", 2)
     nrhs = wl.get("nrhs", 1)
@@ -396,12 +419,7 @@ def main_native(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        sec = e0.elapsed_time(e1) / 1000.0
-        if world > 1:
-            t = torch.tensor([sec], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            sec = float(t.item())
-        return sec
+        return max_over_ranks(e0.elapsed_time(e1) / 1000.0, world, "cuda")
 
     for _ in range(max(0, args.warmup - 1)):
         step(Ud, tvd, bd, xd)
@@ -439,8 +457,7 @@ def main_native(args):
             dist.destroy_process_group()
         return
     K = args.steps
-    units_total = world * K
-    value = sec / units_total
+    value = job_seconds_per_step(sec, world, K)
     # per-step unit counts (per rhs unit) from the profile
     per_step = {k: v["units"] / K for k, v in prof.items()}
     launches = sum(v["launches"] for v in prof.values())
@@ -544,7 +561,7 @@ def main_native(args):
             "coarse_iters": [i["coarse_iters"] for i in step_infos],
             "true_relres": max(i["true_relres"] for i in step_infos),
         },
-        "e2e": ({"value": round(sec_e2e / units_total, 5), "unit": "s",
+        "e2e": ({"value": round(job_seconds_per_step(sec_e2e, world, K), 5), "unit": "s",
                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h} if sec_e2e is not None else
                 {"value": None, "reason": "inputs generated on the device: pinned host copies of the FP64 "
                                           "test vectors would not fit the host memory twice"}),
