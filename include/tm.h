@@ -63,8 +63,11 @@ typedef enum {
   TM_ERR_STATE = -8          /* call out of order (e.g. solve before setup) */
 } tm_status;
 
-/* storage/arithmetic precision of a field (TM_F16: learned-layer inference only) */
-enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2 };
+/* storage/arithmetic precision of a field (TM_F16: learned-layer inference and
+   level-1 SAP blocks only).  TM_F32X2: FP32 storage of the input, arithmetic in
+   pairs of FP32 numbers (an unevaluated sum hi + lo, about 2^-46 relative)
+   with an FP64 result; see tm_params.outer_apply and tm_apply. */
+enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2, TM_F32X2 = 4 };
 
 /* what tm_export copies out */
 enum {
@@ -130,6 +133,14 @@ typedef struct {
      (three levels, cycle_prec = TM_F32): TM_F32, or TM_F16 for an FP16 copy
      (half the bytes; FP32 arithmetic).  The level-1 Krylov solve keeps FP32. */
   int sap1_prec;
+  /* Arithmetic of the outer FGMRES's products w = D(mu) z_k with the
+     preconditioned vectors z_k (which the FP32 K-cycle returns in FP32):
+     TM_F64 (z_k converted to FP64, FP64 stencil) or TM_F32X2 (FP32 pairs on
+     the FP32 z_k, FP64 result, about 2^-46 relative; GB300's FP64 rate is
+     1/64 of its FP32 rate).  TM_F32X2 needs cycle_prec = TM_F32 and keeps
+     the links and the clover term once more as FP32 pairs (288 B per site
+     each).  The true residual b - D x stays FP64 either way. */
+  int outer_apply;
 } tm_params;
 
 typedef struct {
@@ -148,7 +159,7 @@ typedef struct {
  * agg2 = sap_block1 = 2^4, mr_iters1 = 4, pre_smooth1 = 0, post_smooth1 = 2,
  * init_sweeps1 = 3, coarse_setup_iters = 3, coarsest_tol = 5e-2,
  * coarsest_maxit = 200, coarse_mma = 0, nn_mode = 0, nn_prec = TM_F32,
- * sap1_prec = TM_F32.
+ * sap1_prec = TM_F32, outer_apply = TM_F64.
  * L, m0, c_sw, mu are 0. */
 void tm_params_default(tm_params* p);
 
@@ -187,6 +198,8 @@ tm_status tm_load_gauge(tm_handle* h, const double* gauge);
  * w_j, and finally coarse_setup_iters times every w_j <- B1(w_j) with the
  * level-1 K-cycle, normalised, P2 and D_c2 rebuilt (Sec. 3: the fine and the
  * coarse setup iteration counts).
+ * The setup's own work buffers (N_v fine fields for the iterated vectors) are
+ * freed before it returns.
  * Errors: TM_ERR_STATE (no gauge), TM_ERR_ARG (rank-deficient aggregate),
  * TM_ERR_NONFINITE. */
 tm_status tm_setup(tm_handle* h, const double* test_vectors);
@@ -217,8 +230,8 @@ tm_status tm_setup_update(tm_handle* h, int fine_iters, int coarse_iters);
  * new choice (the file is rewritten through a temporary file beside it).
  * out (may be NULL): 4 doubles = sites per tile, columns per register tile,
  * microseconds per build, candidates timed (0 for a cache hit).  The D_c in
- * use is unchanged; timing takes two D_c-sized scratch buffers in the
- * handle's workspace, held until tm_destroy.  Synchronises the handle's
+ * use is unchanged; timing takes two D_c-sized scratch buffers, released
+ * before the call returns (on errors too).  Synchronises the handle's
  * stream.  Errors: TM_ERR_STATE (no setup, or a candidate whose D_c
  * differs), TM_ERR_ARG (reps out of range, cache not writable). */
 tm_status tm_autotune_build(tm_handle* h, const char* cache_path, int reps, double* out);
@@ -255,7 +268,9 @@ size_t tm_field_bytes(const tm_handle* h, int level, int prec, int nrhs);
 tm_status tm_pack(tm_handle* h, int level, int prec, const double* natural, void* field, int nrhs);
 tm_status tm_unpack(tm_handle* h, int level, int prec, const void* field, double* natural, int nrhs);
 
-/* A1 (level 0): out = D(mu) in, fine fields, prec TM_F64 or TM_F32.
+/* A1 (level 0): out = D(mu) in, fine fields, prec TM_F64 or TM_F32; with
+ * prec TM_F32X2 (handles created with outer_apply = TM_F32X2) in is an FP32
+ * field and out an FP64 field, computed in FP32-pair arithmetic.
  * A4 (level 1): out = D_c(delta mu) in, coarse fields, prec = cycle_prec,
  * after a setup.  in and out are distinct device fields of nrhs vectors. */
 tm_status tm_apply(tm_handle* h, int level, int prec, const void* in, void* out, int nrhs);

@@ -73,12 +73,53 @@ def _expi_hermitian(H: np.ndarray, eps: float) -> np.ndarray:
     return np.einsum("...ik,...k,...jk->...ij", W, ph, W.conj())
 
 
-def gauge_field(L, eps: float, seed: int) -> np.ndarray:
-    """Random SU(3) links U_mu(x) = exp(i*eps*H_mu(x)), shape [T,Z,Y,X,4,3,3]."""
+def _gauge_chunk(args):
+    """Worker of gauge_field: links lo..hi from the shared normals."""
+    from multiprocessing import shared_memory
+    name_h, name_u, n, lo, hi, eps = args
+    sh = shared_memory.SharedMemory(name=name_h)
+    su = shared_memory.SharedMemory(name=name_u)
+    try:
+        h = np.ndarray((n, 8), dtype=np.float64, buffer=sh.buf)
+        u = np.ndarray((n, 3, 3), dtype=np.complex128, buffer=su.buf)
+        H = np.einsum("...a,aij->...ij", h[lo:hi], gell_mann() / 2)
+        u[lo:hi] = _expi_hermitian(H, eps)
+        del h, u
+    finally:
+        sh.close()
+        su.close()
+
+
+def gauge_field(L, eps: float, seed: int, workers: int = 1) -> np.ndarray:
+    """Random SU(3) links U_mu(x) = exp(i*eps*H_mu(x)), shape [T,Z,Y,X,4,3,3].
+
+    ``workers`` > 1 evaluates the exponentials in that many spawned processes
+    (same random numbers, same per-link arithmetic); for large lattices."""
     T, Z, Y, X = (int(v) for v in L)
     rng = np.random.Generator(np.random.PCG64(seed))
-    H = random_hermitian_traceless(rng, (T, Z, Y, X, 4))
-    return _expi_hermitian(H, eps)
+    if workers <= 1:
+        H = random_hermitian_traceless(rng, (T, Z, Y, X, 4))
+        return _expi_hermitian(H, eps)
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    n = T * Z * Y * X * 4
+    sh = shared_memory.SharedMemory(create=True, size=n * 8 * 8)
+    su = shared_memory.SharedMemory(create=True, size=n * 9 * 16)
+    try:
+        h = np.ndarray((n, 8), dtype=np.float64, buffer=sh.buf)
+        h[...] = rng.standard_normal((n, 8))
+        step = -(-n // (4 * workers))
+        jobs = [(sh.name, su.name, n, lo, min(n, lo + step), eps) for lo in range(0, n, step)]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pool.map(_gauge_chunk, jobs)
+        U = np.ndarray((n, 3, 3), dtype=np.complex128, buffer=su.buf).copy()
+        del h
+    finally:
+        sh.close()
+        sh.unlink()
+        su.close()
+        su.unlink()
+    return U.reshape(T, Z, Y, X, 4, 3, 3)
 
 
 def evolve_gauge(U: np.ndarray, eta: float, seed: int) -> np.ndarray:

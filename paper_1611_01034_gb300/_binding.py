@@ -11,7 +11,7 @@ library_path = os.path.join(_HERE, "libtmamg.so")
 TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_OOM = 0, -1, -2, -3
 TM_ERR_NOT_CONVERGED, TM_ERR_TIMEOUT, TM_ERR_NOT_SU3 = -4, -5, -6
 TM_ERR_NONFINITE, TM_ERR_STATE = -7, -8
-TM_F64, TM_F32, TM_F16 = 0, 1, 2
+TM_F64, TM_F32, TM_F16, TM_F32X2 = 0, 1, 2, 4
 TM_EXPORT_P, TM_EXPORT_DC, TM_EXPORT_CLOVER, TM_EXPORT_TV = 0, 1, 2, 3
 TM_EXPORT_P2, TM_EXPORT_DC2, TM_EXPORT_TV1 = 4, 5, 6
 
@@ -28,6 +28,7 @@ class tm_params(ctypes.Structure):
         ("mr_iters1", c_int), ("pre_smooth1", c_int), ("post_smooth1", c_int), ("init_sweeps1", c_int),
         ("coarse_setup_iters", c_int), ("coarsest_tol", c_double), ("coarsest_maxit", c_int),
         ("coarse_mma", c_int), ("nn_mode", c_int), ("nn_prec", c_int), ("sap1_prec", c_int),
+        ("outer_apply", c_int),
     ]
 
 

@@ -97,6 +97,9 @@ struct tm_handle {
   int* d_odd2 = nullptr;
   int* d_cidx2 = nullptr;
   void* Dc1h = nullptr;  // FP16 copy of D_c1 for the level-1 SAP (sap1_prec = TM_F16)
+  // links and clover as FP32 pairs for the outer D(mu) z_k (outer_apply = TM_F32X2)
+  void* gdf = nullptr;
+  void* cdf = nullptr;
   // odd-even Schur complement of the coarsest level on the tensor cores
   bool tc_on = false;
   TcGeom tc{};
@@ -161,6 +164,14 @@ T* W(tm_handle* h, const std::string& name, size_t count) {
 
 void sync(tm_handle* h) { CK(cudaStreamSynchronize(h->st)); }
 
+// free a named work buffer (cudaFree waits for the work in flight); never throws
+void release(tm_handle* h, const std::string& name) noexcept {
+  auto it = h->work.find(name);
+  if (it == h->work.end()) return;
+  if (it->second.p) cudaFree(it->second.p);
+  h->work.erase(it);
+}
+
 // like W, but zero-filled when (re)allocated: batched solvers run finished
 // right-hand sides through shared launches, so their slots must hold finite data
 template <typename T>
@@ -177,12 +188,12 @@ T* Wz(tm_handle* h, const std::string& name, size_t count) {
 // ---------------------------------------------------------------------------
 enum ProfKind {
   PK_DSLASH64 = 0, PK_DSLASH32, PK_SAP, PK_RESTRICT, PK_PROLONG, PK_COARSE_OE, PK_BLAS_FINE, PK_BLAS_COARSE,
-  PK_BUILD, PK_OTHER, PK_CSAP, PK_LEVEL1, PK_NN, PK_N
+  PK_BUILD, PK_OTHER, PK_CSAP, PK_LEVEL1, PK_NN, PK_DSLASHDF, PK_N
 };
 const char* const kProfNames[PK_N] = {"dslash_f64", "dslash_f32",   "sap",          "restrict",
                                       "prolong",    "coarse_oe",    "blas_fine",    "blas_coarse",
                                       "coarse_build", "other",      "coarse_sap",   "level1",
-                                      "nn"};
+                                      "nn",           "dslash_f32x2"};
 
 cudaEvent_t take_event(tm_handle* h) {
   if (!h->evpool.empty()) {
@@ -276,6 +287,13 @@ template <typename T>
 void dslash(tm_handle* h, const T* in, T* out, const T* b, int nrhs) {
   Prof pf(h, std::is_same<T, double>::value ? PK_DSLASH64 : PK_DSLASH32, nrhs);
   launch_dslash<T>(gaugeT<T>(h), cloverT<T>(h), in, out, b, h->g, h->p.mu, h->p.bc_t, nrhs, h->st);
+  CKL();
+}
+
+// out (FP64) = D(mu) in (FP32) in FP32-pair arithmetic
+void dslash_df(tm_handle* h, const float* in, double* out, int nrhs) {
+  Prof pf(h, PK_DSLASHDF, nrhs);
+  launch_dslash_df(h->gdf, h->cdf, in, out, h->g, h->p.mu, h->p.bc_t, nrhs, h->st);
   CKL();
 }
 
@@ -1063,6 +1081,8 @@ void setup_iterate(tm_handle* h, int fine, int coarse) {
     }
   }
   sync(h);
+  release(h, "setup_z");  // setup-only work: N_v fine fields (tens of GB at 48^3 x 96)
+  release(h, "setup_z1");
 }
 
 // ---------------------------------------------------------------------------
@@ -1201,13 +1221,17 @@ void precond(tm_handle* h, const T* v, T* z, int nrhs) {
 template <typename T>
 KrylovOut solve_one(tm_handle* h, const double* b, double* x, double tol) {
   const long fr = fine_reals(h);
-  double* zt = W<double>(h, "s_z64", fr);
+  double* zt = std::is_same<T, double>::value || h->gdf ? nullptr : W<double>(h, "s_z64", fr);
   T* vt = std::is_same<T, double>::value ? nullptr : W<T>(h, "s_vT", fr);
   auto A = [&](const double* in, double* out) { dslash<double>(h, in, out, nullptr, 1); };
   auto AZ = [&](const T* z, double* out) {
     if constexpr (std::is_same<T, double>::value) {
       dslash<double>(h, z, out, nullptr, 1);
     } else {
+      if (h->gdf) {
+        dslash_df(h, z, out, 1);
+        return;
+      }
       {
         Prof pf(h, PK_OTHER);
         launch_convert<T, double>(z, zt, fr, h->st);
@@ -1447,7 +1471,7 @@ template <typename T>
 std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int nb, double tol) {
   const long fr = fine_reals(h);
   const long blk = fr * nb;
-  double* zt = std::is_same<T, double>::value ? nullptr : W<double>(h, "sb_z64", blk);
+  double* zt = std::is_same<T, double>::value || h->gdf ? nullptr : W<double>(h, "sb_z64", blk);
   T* vt = std::is_same<T, double>::value ? nullptr : W<T>(h, "sb_vT", blk);
   auto resid = [&](const double* xx, double* r) { dslash<double>(h, xx, r, b, nb); };
   auto M = [&](const double* v, T* z) {
@@ -1466,6 +1490,10 @@ std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int
     if constexpr (std::is_same<T, double>::value) {
       dslash<double>(h, z, o, nullptr, nb);
     } else {
+      if (h->gdf) {
+        dslash_df(h, z, o, nb);
+        return;
+      }
       {
         Prof pf(h, PK_OTHER, nb);
         launch_convert<T, double>(z, zt, blk, h->st);
@@ -1516,6 +1544,8 @@ void validate(const tm_params* p) {
   if (p->sap1_prec != TM_F32 && p->sap1_prec != TM_F16) bad("sap1_prec must be TM_F32 or TM_F16");
   if (p->sap1_prec == TM_F16 && (p->levels != 3 || p->cycle_prec != TM_F32))
     bad("sap1_prec = TM_F16 needs levels = 3 and cycle_prec = TM_F32");
+  if (p->outer_apply != TM_F64 && p->outer_apply != TM_F32X2) bad("outer_apply must be TM_F64 or TM_F32X2");
+  if (p->outer_apply == TM_F32X2 && p->cycle_prec != TM_F32) bad("outer_apply = TM_F32X2 needs cycle_prec = TM_F32");
   if (p->bc_t != 1.0 && p->bc_t != -1.0) bad("bc_t must be +1 or -1");
   if (!(p->delta >= 1.0)) bad("delta must be >= 1");
   if (p->max_rhs < 1) bad("max_rhs must be >= 1");
@@ -1720,12 +1750,25 @@ void autotune_build(tm_handle* h, const char* cache_path, int reps, double* out)
   }
   const T* P = static_cast<const T*>(h->P);
   const size_t n = (size_t)h->gc.V * 9 * h->n * h->n * 2;  // reals of D_c
+  // the scratch D_c copies and the events go back on every exit, errors included
+  struct Scratch {
+    tm_handle* h;
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~Scratch() {
+      for (cudaEvent_t ev : e)
+        if (ev) h->evpool.push_back(ev);
+      release(h, "tune_ref");
+      release(h, "tune_dc");
+      release(h, "tune_bad");
+    }
+  } scratch{h};
   T* ref = W<T>(h, "tune_ref", n);
   T* trial = W<T>(h, "tune_dc", n);
   unsigned long long* bad_d = W<unsigned long long>(h, "tune_bad", 1);
   launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, ref, ag, h->p.bc_t, h->st, BuildShape{});
   CKL();
-  cudaEvent_t e0 = take_event(h), e1 = take_event(h);
+  cudaEvent_t e0 = scratch.e[0] = take_event(h);
+  cudaEvent_t e1 = scratch.e[1] = take_event(h);
   BuildShape best{};
   double best_us = 0;
   for (const BuildShape& b : cand) {
@@ -1755,8 +1798,6 @@ void autotune_build(tm_handle* h, const char* cache_path, int reps, double* out)
       best_us = us;
     }
   }
-  h->evpool.push_back(e0);
-  h->evpool.push_back(e1);
   h->build_shape = best;
   if (cache_path) {
     cache[key] = TuneEntry{best.ts, best.ktc, best_us};
@@ -1805,6 +1846,7 @@ void tm_params_default(tm_params* p) {
   p->nn_mode = 0;
   p->nn_prec = TM_F32;
   p->sap1_prec = TM_F32;
+  p->outer_apply = TM_F64;
 }
 
 const char* tm_status_string(int s) {
@@ -1837,7 +1879,7 @@ void tm_destroy(tm_handle* h) {
     if (kv.second.first) cudaFreeHost(kv.second.first);
   void* p3[] = {h->tv1, h->P2, h->Dc2, h->Dinv2, h->d_even2, h->d_odd2, h->d_cidx2,
                 h->tc.even, h->tc.even_lo, h->tc.odd, h->tc.odd_lo, h->tc.nbr_e, h->tc.nbr_o,
-                h->d_nnw, h->d_nngrad, h->Dc1h};
+                h->d_nnw, h->d_nngrad, h->Dc1h, h->gdf, h->cdf};
   for (void* q : p3)
     if (q) cudaFree(q);
   for (auto& r : h->recs) {
@@ -1913,6 +1955,10 @@ tm_status tm_create(tm_handle** out, const tm_params* p, void* stream) {
     h->g32 = static_cast<float*>(dalloc(4L * NR_LINK * V * sizeof(float)));
     h->c64 = static_cast<double*>(dalloc((long)NR_CLOVER * V * sizeof(double)));
     h->c32 = static_cast<float*>(dalloc((long)NR_CLOVER * V * sizeof(float)));
+    if (p->outer_apply == TM_F32X2) {
+      h->gdf = dalloc((size_t)4 * 9 * V * 4 * sizeof(float));
+      h->cdf = dalloc((size_t)36 * V * 4 * sizeof(float));
+    }
     const size_t cs = csize(p->cycle_prec);
     h->tv = dalloc((size_t)p->nv * NR_SPINOR * V * cs);
     h->P = dalloc((size_t)p->nv * NR_SPINOR * V * cs);
@@ -2011,9 +2057,17 @@ tm_status tm_load_gauge(tm_handle* h, const double* gauge) {
     launch_clover(gd, h->c64, h->c32, h->g, h->p.m0, h->p.c_sw, h->st);
     CKL();
   }
+  if (h->gdf) {
+    Prof pf(h, PK_OTHER, 1, 2);
+    launch_pack_gauge_df(gd, h->gdf, h->g, h->st);
+    CKL();
+    launch_clover_df(h->c64, h->cdf, h->g, h->st);
+    CKL();
+  }
   h->gauge_ok = false;
   h->setup_ok = false;
   check_flags(h);
+  release(h, "stage_gauge");  // a host field's device copy is not needed any more
   h->gauge_ok = true;
   API_END
 }
@@ -2032,6 +2086,7 @@ static tm_status setup_common(tm_handle* h, const double* tv, bool adaptive) {
     setup_impl<double>(h, d, adaptive);
   else
     setup_impl<float>(h, d, adaptive);
+  release(h, "stage_tv");  // a host array's device copy is not needed any more
   h->setup_ok = true;
   h->tv_ok = true;
   API_END
@@ -2251,6 +2306,8 @@ tm_status tm_apply(tm_handle* h, int level, int prec, const void* in, void* out,
       dslash<double>(h, static_cast<const double*>(in), static_cast<double*>(out), nullptr, nrhs);
     else if (prec == TM_F32)
       dslash<float>(h, static_cast<const float*>(in), static_cast<float*>(out), nullptr, nrhs);
+    else if (prec == TM_F32X2 && h->gdf)
+      dslash_df(h, static_cast<const float*>(in), static_cast<double*>(out), nrhs);
     else
       raise(TM_ERR_ARG, "bad precision");
   } else if (level == 1) {

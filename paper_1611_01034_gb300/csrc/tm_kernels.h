@@ -29,6 +29,15 @@ template <typename T>
 void launch_dslash(const T* gauge, const T* clover, const T* in, T* out, const T* b, const Lat& g,
                    double mu, double bc_t, int nrhs, cudaStream_t st);
 
+// ---- FP32-pair D(mu) (dirac_df.cu) -------------------------------------------
+// links as [4][9][V] float4 (re.h, im.h, re.l, im.l) of entry 3a + b; clover as
+// [36][V] float4 (r[2j].h, r[2j+1].h, r[2j].l, r[2j+1].l) of the packed 72 reals
+void launch_pack_gauge_df(const double* nat, void* gdf, const Lat& g, cudaStream_t st);
+void launch_clover_df(const double* c64, void* cdf, const Lat& g, cudaStream_t st);
+// out (FP64 field) = D(mu) in (FP32 field) to about 2^-46 relative, FP32 pairs
+void launch_dslash_df(const void* gdf, const void* cdf, const float* in, double* out, const Lat& g, double mu,
+                      double bc_t, int nrhs, cudaStream_t st);
+
 // ---- SAP (sap.cu) ------------------------------------------------------------
 struct SapGeom {
   Lat g;

@@ -45,6 +45,7 @@ def test_defaults_and_status_strings(lib):
     assert p.cycle_prec == tm.TM_F32 and p.delta == 1.0
     assert p.levels == 2 and p.nv2 == 28 and list(p.agg2) == [2, 2, 2, 2] and list(p.sap_block1) == [2, 2, 2, 2]
     assert (p.pre_smooth1, p.post_smooth1, p.coarse_setup_iters, p.coarsest_maxit) == (0, 2, 3, 200)
+    assert p.outer_apply == tm.TM_F64
     assert tm.tm_status_string(tm.TM_ERR_NOT_CONVERGED) == "not converged"
     assert tm.tm_status_string(12345) == "unknown status"
 
@@ -75,6 +76,8 @@ def test_defaults_and_status_strings(lib):
     dict(L=(8, 8, 8, 8), maxit=0),
     dict(L=(8, 8, 8, 8), max_rhs=0),
     dict(L=(8, 8, 8, 8), mr_iters=-1),
+    dict(L=(8, 8, 8, 8), outer_apply=1),                  # only TM_F64 or TM_F32X2
+    dict(L=(8, 8, 8, 8), outer_apply=4, cycle_prec=0),    # FP32 pairs need the FP32 cycle
 ])
 def test_invalid_parameters_rejected_before_any_device_call(lib, bad):
     import paper_1611_01034_gb300 as tm

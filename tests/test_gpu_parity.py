@@ -65,6 +65,28 @@ def test_dirac_apply(name, prec, tol):
         assert rel(got[r], op.apply(psi[r])) <= tol
 
 
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("bc_t", [-1.0, 1.0])
+def test_dirac_apply_fp32_pairs(name, bc_t):
+    """D(mu) on an FP32 field in FP32-pair arithmetic, FP64 result: against the
+    oracle's FP64 D(mu) of the same FP32-rounded input within 1e-13 (pairs keep
+    about 46 significant bits; the stencil's sums cancel by less than 2^6)."""
+    L, eps, seed, m0, csw, mu, delta, nv, blk = CASES[name]
+    U = inputs.gauge_field(L, eps, seed)
+    g = GPU(U, m0=m0, c_sw=csw, mu=mu, delta=delta, nv=nv, agg=blk, sap_block=blk, cycle_prec=F32,
+            max_rhs=3, bc_t=bc_t, outer_apply=tm.TM_F32X2)
+    op = Operator(U, m0, csw, mu, bc_t=bc_t)
+    psi = inputs.gaussian_spinor(L, seed + 1000, nrhs=3).astype(np.complex64).astype(np.complex128)
+    fi = g.pack(0, F32, psi, 3)
+    fo = g.field(0, F64, 3)
+    tm.tm_apply(g.h, 0, tm.TM_F32X2, fi, fo, 3)
+    got = g.unpack(0, F64, fo, psi.shape, 3)
+    for r in range(3):
+        assert rel(got[r], op.apply(psi[r])) <= 1e-13
+    # the plain FP32 stencil is ~1e6 times further off
+    assert rel(g.apply_fine(psi, F32, nrhs=3), op.apply(psi)) > 1e-9
+
+
 def test_dirac_periodic_and_free_field():
     L = (4, 6, 4, 10)
     U = inputs.unit_gauge(L)
@@ -213,6 +235,26 @@ def test_solve_true_residual(name, prec):
     for r in range(2):
         assert np.linalg.norm(b[r] - op.apply(x[r])) / np.linalg.norm(b[r]) <= 1e-10
     assert info.true_relres <= 1e-10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_with_fp32_pair_outer_apply(name):
+    """FGMRES whose D(mu) z_k products run in FP32 pairs: same outer iteration
+    count as the FP64 products (the two Arnoldi relations agree to ~1e-14) and
+    the oracle's FP64 true residual of the solution <= 1e-10."""
+    iters = {}
+    for oa in (tm.TM_F64, tm.TM_F32X2):
+        U, g, op, seed = _case(name, F32, setup_iters=2, outer_apply=oa)
+        tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+        tm.tm_setup(g.h, tv)
+        b = inputs.gaussian_spinor(g.L, seed + 1000, nrhs=2)
+        x = np.zeros_like(b)
+        st, info = tm.tm_solve(g.h, b, x, 2, 1e-10)
+        assert st == tm.TM_OK and info.converged
+        for r in range(2):
+            assert np.linalg.norm(b[r] - op.apply(x[r])) / np.linalg.norm(b[r]) <= 1e-10
+        iters[oa] = info.iters
+    assert abs(iters[tm.TM_F64] - iters[tm.TM_F32X2]) <= 1, iters
 
 
 def test_solve_iterations_match_oracle_fp64():
