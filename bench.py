@@ -1,25 +1,31 @@
 #!/usr/bin/env python
 """Benchmark of the twisted-mass DD-alphaAMG hot path on one GB300.
 
-One step = the whole path of the paper's method on one batch of synthetic
-input: load the gauge field (SU(3) check, link packing, clover term), the
-adaptive setup (test vectors, P, D_c(delta mu)), and the FGMRES solve of
-D(mu) x = b to a true relative residual of 1e-10 (FP64 outer iteration,
-FP32 K-cycle of eq. (1)).  Fig. 1 of the paper also times setup + solve.
+One step = one FGMRES solve of D(mu) x = b (the K-cycle of eq. (1) as
+preconditioner, Sec. 1) for one group of right-hand sides to a true relative
+residual of 1e-10, with the setup (gauge field, clover term, adaptive setup
+of P and the coarse operators) done once before the timed region and reported
+separately, as the paper separates setup and solve costs (Fig. 1).
 
-Workload (default): 16^3 x 32 lattice, U = exp(0.5 i H), c_sw = 1.5,
-mu = 0.003, delta = 5, two levels, N_v = 20, 4^4 aggregates and SAP
-blocks, 3 setup iterations (few right-hand sides), one Gaussian rhs, m0 from
-inputs/m0_tuned.json (near-critical).  Inputs per step (gauge 75 MB, test
-vectors 503 MB, rhs 25 MB in FP64) exceed the 129 MB L2, so no extra flush.
+Default workload: 48^3 x 96, U = exp(0.6 i H), c_sw = 1.57551, mu = 0.0009,
+delta = 5, three levels (N_v = 24 on 4^4 aggregates, then N_v2 = 28 on 2^4
+level-1 aggregates; SAP blocks 4^4 and 2^4), 3 + 3 setup iterations, the 12
+spin-colour point sources at one random site, solved in 3 steps of 4 (the
+FGMRES(8) basis of 4 right-hand sides is what fits next to the setup data in
+the 280 GB).  m0 from inputs/m0_tuned.json (near-critical).  Every field of
+the step (2 GB per fine FP64 vector) is larger than the 129 MB L2, so no
+flush is needed.
 
-Output: one JSON line (rank 0).  ``value`` is seconds per step with inputs
-resident in HBM; ``e2e`` the same through the C ABI with pinned host
-buffers (host->device copies and the device->host read of x inside the
-timed region).  ``roofline`` rates the dominant kernel class by its
-algorithmic bytes per launch over its CUDA-event time, measured live during
-the timed steps.  ``cpu_baseline`` times the FP64 numpy oracle on a bounded
-sample of the same workload and scales it by the unit counts of the run.
+Output: one JSON line (rank 0).  ``value`` is seconds per step with the
+inputs resident in HBM; ``e2e`` the same steps through the C ABI with pinned
+host buffers (b, x0 host->device and x device->host inside the timed region),
+cycling through the three groups of sources.  ``roofline`` rates the dominant
+kernel class of the step by its algorithmic work per launch over its
+CUDA-event time measured live during the timed steps.  ``cpu_baseline`` is
+the FP64 numpy oracle: per-unit costs timed on the host (single thread, on
+sample lattices, scaled per site) times the step's unit counts; its leg also
+recomputes the true residual of one GPU solution with the oracle on the full
+lattice, T-slab by T-slab over the host's cores.
 
 ``--impl reference`` times the oracle alone (the reference arm of this
 method is the CPU oracle; there is no other implementation to install).
@@ -39,7 +45,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+TM_F32X2 = 4  # tm_params.outer_apply: FP32-pair products D(mu) z_k
+
 WORKLOADS = {
+    "48x48x48x96_3lvl_nv24_28_12pt": dict(
+        L=(96, 48, 48, 48), eps=0.6, seed=1, c_sw=1.57551, mu=0.0009, delta=5.0, nv=24,
+        agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, nrhs=12, point=True,
+        levels=3, nv2=28, agg2=(2, 2, 2, 2), sap_block1=(2, 2, 2, 2), coarse_setup_iters=3,
+        restart=8, rhs_batch=4, coarse_mma=1, sap1_prec=2, outer_apply=TM_F32X2,
+        m0_key="16x16x16x32_eps0.6_seed1_csw1.57551", device_inputs=True),
     "16x16x16x32_2lvl_nv20": dict(
         L=(32, 16, 16, 16), eps=0.5, seed=1, c_sw=1.5, mu=0.003, delta=5.0, nv=20,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, coarse_mma=1,
@@ -47,13 +61,7 @@ WORKLOADS = {
     "24x24x24x48_2lvl_nv24_12pt": dict(
         L=(48, 24, 24, 24), eps=0.5, seed=1, c_sw=1.5, mu=0.002, delta=5.0, nv=24,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=5, tol=1e-10, nrhs=12, point=True, coarse_mma=1,
-        m0_key="16x16x16x32_eps0.5_seed1"),  # same field strength; the critical mass is a bulk quantity
-    "48x48x48x96_3lvl_nv24_28_12pt": dict(
-        L=(96, 48, 48, 48), eps=0.6, seed=1, c_sw=1.57551, mu=0.0009, delta=5.0, nv=24,
-        agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, nrhs=12, point=True,
-        levels=3, nv2=28, agg2=(2, 2, 2, 2), sap_block1=(2, 2, 2, 2), coarse_setup_iters=3,
-        restart=16, rhs_batch=1, coarse_mma=1, sap1_prec=2, m0_key="16x16x16x32_eps0.6_seed1_csw1.57551",
-        device_inputs=True),
+        rhs_batch=12, m0_key="16x16x16x32_eps0.5_seed1"),  # same field strength; critical mass is a bulk quantity
     "8x8x8x8_2lvl_nv8": dict(
         L=(8, 8, 8, 8), eps=0.5, seed=5, c_sw=1.5, mu=0.005, delta=5.0, nv=8,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, m0=-0.4),
@@ -61,11 +69,16 @@ WORKLOADS = {
 # learned preconditioner stage, trained on 8 seeded fields and tested on 4 held-out ones
 LEARNED = dict(L=(16, 16, 16, 16), eps=0.5, c_sw=1.5, mu=0.003, delta=5.0, nv=20, agg=(4, 4, 4, 4),
                sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, m0_key="16x16x16x32_eps0.5_seed1",
-               train_seeds=tuple(range(101, 109)), test_seeds=tuple(range(201, 205)), pairs_per_field=256,
+               train_seeds=tuple(range(101, 109)), test_seeds=tuple(range(201, 205)), pairs_per_field=1280,
                epochs=8, batch=32, lr=2e-3)
 WORKLOADS["16x16x16x16_learned"] = dict(LEARNED)
-DEFAULT_WORKLOAD = "16x16x16x32_2lvl_nv20"
+DEFAULT_WORKLOAD = "48x48x48x96_3lvl_nv24_28_12pt"
 COUNTS_FILE = os.path.join(ROOT, "profiles", "bench_unit_counts.json")
+METRIC = "solve seconds to 1e-10 rel. residual; D(mu) HBM GB/s and D_c TFLOP/s vs peak"
+# FP64 rate of GB300 from the nominal table: 1.25 TFLOP/s = 152 SMs x 2.07 GHz x 2 FMA/clk x 2
+FP64_PEAK_TFLOPS = 1.25
+# FP32 (CUDA cores): 152 SMs x 128 FMA/clk x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def ncu_traffic(wl_name: str, kind: str) -> float | None:
@@ -78,9 +91,7 @@ def ncu_traffic(wl_name: str, kind: str) -> float | None:
     rec = json.load(open(path)).get(wl_name, {}).get(kind)
     if not rec:
         return None
-    files = {"sap": ["sap.cu", "tm_stencil.cuh", "tm_internal.cuh"],
-             "dslash_f32": ["dirac.cu", "tm_stencil.cuh", "tm_internal.cuh"],
-             "dslash_f64": ["dirac.cu", "tm_stencil.cuh", "tm_internal.cuh"]}.get(kind)
+    files = rec.get("files")
     if not files:
         return None
     m = hashlib.sha256()
@@ -92,54 +103,104 @@ def ncu_traffic(wl_name: str, kind: str) -> float | None:
 def workload_m0(wl: dict) -> tuple[float, str]:
     if "m0" in wl:
         return wl["m0"], "fixed"
-    path = os.path.join(ROOT, "inputs", "m0_tuned.json")
-    table = json.load(open(path))
+    table = json.load(open(os.path.join(ROOT, "inputs", "m0_tuned.json")))
     return float(table[wl["m0_key"]]["m0"]), "inputs/m0_tuned.json"
 
 
-# ---------------------------------------------------------------------------
-# algorithmic bytes per unit (one right-hand side) of each kernel class
-# ---------------------------------------------------------------------------
-def algorithmic_bytes(kind: str, wl: dict) -> tuple[float, float] | None:
-    """(operator bytes per launch, vector bytes per rhs unit) a kernel class
-    must move at minimum; a launch over u right-hand sides moves op + u * vec.
-
-    dslash:   op = 4 links x 12 + clover 72 = 120 reals/site;
-              vec = in + out spinor 48 reals/site
-    sap:      one colour: op = links + clover on the colour's half (120 V/2);
-              vec = x everywhere (24 V) + b and x-write on the half (48 V/2)
-    restrict: op = P (24 N_v reals/site); vec = fine spinor 24 reals/site
-    prolong:  op = P; vec = fine in/out 48 reals/site
-    coarse_oe (one Schur application S = D_ee - D_eo D_oo^-1 D_oe, two
-              launches): op = the 9 D_c blocks of every coarse site with the
-              odd-site inverses in place of the odd self blocks, 9 (2N_v)^2
-              complex per coarse site; vec = 2 coarse vectors
-    coarse_build (one build of D_c): op = P, links and clover read once and
-              D_c written; vec = 0
-    """
+def volumes(wl: dict) -> tuple[int, int, int]:
+    """Sites of the fine, first coarse and (three levels) second coarse lattice."""
     V = 1
     for n in wl["L"]:
         V *= n
-    nv = wl["nv"]
-    Vc = V
+    a1 = 1
     for a in wl["agg"]:
-        Vc //= a
-    n = 2 * nv
+        a1 *= a
+    V1 = V // a1
+    V2 = 0
+    if wl.get("levels", 2) == 3:
+        a2 = 1
+        for a in wl["agg2"]:
+            a2 *= a
+        V2 = V1 // a2
+    return V, V1, V2
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch of a kernel class (roofline numerators)
+# ---------------------------------------------------------------------------
+def roofline_model(kind: str, wl: dict, units: float, launches: float, outer: dict, peaks: dict) -> dict | None:
+    """Bound, work per launch and peak of a kernel class.
+
+    units / launches: right-hand-side units and kernel launches of the class
+    in the timed steps; outer: {"iters": outer FGMRES iterations per rhs,
+    "restart": m} for the FP64 Arnoldi BLAS.  Bytes count every operator
+    array once per launch and every vector once per right-hand side; flops
+    count the arithmetic the definition needs.
+      sap (one colour of a sweep): links + clover of the colour's half, x
+        everywhere, b and the x update on the half: (120 V/2) op, (24 V + 48 V/2) vec reals
+      coarse_sap (level-1, one colour): the colour's D_c1 blocks once (9 n^2
+        complex per site, FP16 copy with sap1_prec = TM_F16) + x everywhere,
+        b and x on the half (FP32)
+      restrict / prolong: P (24 N_v reals per site) + fine vectors
+      level1 (D_c1 v): 9 n^2 complex per level-1 site + 2 vectors
+      coarse_oe (one odd-even Schur application, 2 launches): 9 n^2 complex per
+        coarsest site + 2 vectors
+      dslash_f64: 2232 flop per site and rhs (FP64 ALU, 1344 B per site)
+      dslash_f32x2: 672 B per site in FP32 input + FP64 output + FP32-pair
+        links and clover (576 + 576 B per site once per launch): HBM bytes
+      blas_fine: FP64 flops of the Arnoldi steps (CGS2: 2 k (k+1) complex
+        multiply-adds per element in a cycle of k steps, plus norms, scaling
+        and the solution update), FP64 ALU
+    """
+    V, V1, V2 = volumes(wl)
+    nv = wl["nv"]
+    n1 = 2 * nv
     f = 4  # FP32 cycle
-    if kind == "dslash_f64":
-        return 120 * 8 * V, 48 * 8 * V
-    if kind == "dslash_f32":
-        return 120 * f * V, 48 * f * V
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "recipe fallback 6.8 TB/s"
+    if launches <= 0:
+        return None
+    per = units / launches  # rhs units per launch
     if kind == "sap":
-        return 120 * f * V / 2, (24 * V + 48 * V / 2) * f
+        b = 120 * f * V / 2 + per * (24 * V + 48 * V / 2) * f
+        return {"bound": "hbm", "work": b, "unit": "GB/s", "peak": hbm, "peak_source": hbm_src}
+    if kind == "coarse_sap":
+        ob = 2 if wl.get("sap1_prec") == 2 else 4
+        b = 9 * n1 * n1 * 2 * ob * V1 / 2 + per * (2 * n1 * V1 + 2 * 2 * n1 * V1 / 2) * f
+        return {"bound": "hbm", "work": b, "unit": "GB/s", "peak": hbm, "peak_source": hbm_src}
     if kind == "restrict":
-        return 24 * nv * f * V, 24 * f * V
+        return {"bound": "hbm", "work": 24 * nv * f * V + per * 24 * f * V, "unit": "GB/s", "peak": hbm,
+                "peak_source": hbm_src}
     if kind == "prolong":
-        return 24 * nv * f * V, 48 * f * V
+        return {"bound": "hbm", "work": 24 * nv * f * V + per * 48 * f * V, "unit": "GB/s", "peak": hbm,
+                "peak_source": hbm_src}
+    if kind == "level1":
+        return {"bound": "hbm", "work": 9 * n1 * n1 * 2 * f * V1 + per * 2 * n1 * 2 * f * V1, "unit": "GB/s",
+                "peak": hbm, "peak_source": hbm_src}
     if kind == "coarse_oe":
-        return 9 * n * n * 2 * f * Vc, 2 * n * 2 * f * Vc
-    if kind == "coarse_build":
-        return (24 * nv + 120) * f * V + 9 * n * n * 2 * f * Vc, 0.0
+        n, Vc = (2 * wl["nv2"], V2) if wl.get("levels", 2) == 3 else (n1, V1)
+        b = (9 * n * n * 2 * f * Vc + per * 2 * n * 2 * f * Vc) / 2  # two launches per application
+        return {"bound": "hbm", "work": b, "unit": "GB/s", "peak": hbm, "peak_source": hbm_src}
+    if kind == "dslash_f64":
+        return {"bound": "alu", "work": 2232.0 * V * per / 1e3, "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 1.25 TFLOP/s (152 SMs x 2.07 GHz x 2 FMA/clk x 2, nominal table)",
+                "scale": 1e9}
+    if kind == "dslash_f32x2":
+        b = (576 + 576) * V + per * (96 + 192) * V
+        return {"bound": "hbm", "work": b, "unit": "GB/s", "peak": hbm, "peak_source": hbm_src}
+    if kind == "blas_fine":
+        m, it = outer["restart"], outer["iters"]
+        nrhs_total = outer["rhs"]
+        flops_el = 0.0  # real flops per complex element of one rhs, whole solve
+        left = it
+        while left > 0:
+            k = min(m, left)
+            flops_el += 16 * k * (k + 1) + 4 * k + 2 * k + 8 * k + 6
+            left -= k
+        total = flops_el * 12 * V * nrhs_total
+        return {"bound": "alu", "work": total / launches / 1e3, "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 1.25 TFLOP/s (152 SMs x 2.07 GHz x 2 FMA/clk x 2, nominal table)",
+                "scale": 1e9}
     return None
 
 
@@ -198,93 +259,145 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# oracle CPU baseline: per-unit costs on the full-size workload
+# oracle CPU baseline: per-unit costs on sample lattices, scaled per site
 # ---------------------------------------------------------------------------
-def oracle_unit_costs(wl_name: str) -> dict:
-    """Seconds per unit of each step component, timed on the oracle (FP64 numpy).
+SAMPLE_L = (32, 16, 16, 16)
 
-    Samples (full 16^3 x 32 lattice unless stated): the clover leaves of one
-    ordered plane (x12 for the clover term); one D(mu) apply; one SAP colour
-    half-sweep with 4 MR steps; one restriction and one prolongation with N_v
-    vectors; the thin QR of all aggregates; 10 coarse odd-even GMRES steps on
-    a coarse operator of the workload's shape; the local Galerkin build of
-    D_c for N_v = 2 (scaled by columns x rows to N_v).
+
+def oracle_unit_costs(wl_name: str) -> dict:
+    """Seconds per unit and per site of each step component, timed on the
+    FP64 numpy oracle in this (single-threaded) process.
+
+    Fine units on a 16^3 x 32 sample lattice: one D(mu) apply; one SAP colour
+    half-sweep (residual + MR steps on the colour's blocks); one restriction
+    and one prolongation with N_v vectors; one outer FGMRES(restart) iteration
+    of CGS2 Arnoldi BLAS (trivial operator and preconditioner).  Two levels:
+    ten odd-even coarse GMRES steps on a coarse operator of the workload's
+    block size.  Three levels, on sample coarse lattices: a level-1 D_c1
+    apply, a level-1 SAP colour, one P2 restriction or prolongation, a level-1
+    FGMRES(coarse_restart) iteration of BLAS, ten odd-even GMRES steps on a
+    coarsest operator of block size 2 N_v2.  Each cost is divided by the
+    sample's sites; the workload's cost scales it by its own sites.
     """
     import numpy as np
     import inputs
-    from oracle.dirac import Operator, clover_leaves
+    from oracle.dirac import Operator
     from oracle.sap import SAP
     from oracle.coarse import Interpolation, CoarseOperator, OddEvenCoarse
     from oracle.krylov import gmres
 
     wl = WORKLOADS[wl_name]
-    L, nv = wl["L"], wl["nv"]
+    nv, levels = wl["nv"], wl.get("levels", 2)
     try:
         m0, _ = workload_m0(wl)
     except (OSError, KeyError):
         m0 = -0.5  # the unit costs do not depend on the value of m0
-    U = inputs.gauge_field(L, wl["eps"], wl["seed"])
+    Ls = SAMPLE_L
+    Vs = int(np.prod(Ls))
+    U = inputs.gauge_field(Ls, wl["eps"], wl["seed"])
     out = {}
-    t = time.perf_counter()
-    clover_leaves(U, 0, 1)
-    out["clover"] = 12 * (time.perf_counter() - t)
-    op = Operator.__new__(Operator)
-    op.U, op.L, op.m0, op.c_sw, op.mu, op.bc_t = U, tuple(L), m0, wl["c_sw"], wl["mu"], -1.0
-    A = np.zeros(tuple(L) + (12, 12), dtype=np.complex128)
-    A[...] = (m0 + 4) * np.eye(12)
-    op.A = A
-    psi = inputs.gaussian_spinor(L, 7)
+    op = Operator(U, m0, wl["c_sw"], wl["mu"])
+    psi = inputs.gaussian_spinor(Ls, 7)
     t = time.perf_counter()
     op.apply(psi)
-    out["dslash_f64"] = time.perf_counter() - t
+    out["dslash_site"] = (time.perf_counter() - t) / Vs
     sap = SAP(op, wl["sap_block"], n_mr=4)
     mask = sap.colour == 0
     t = time.perf_counter()
     r = psi - op.apply(psi)
     psi + sap.mr(r, mask) * mask[..., None, None]
-    out["sap"] = time.perf_counter() - t
-    tv = inputs.random_test_vectors(L, nv, 11)
-    t = time.perf_counter()
-    P = Interpolation(tv, wl["agg"])
-    out["qr"] = time.perf_counter() - t
+    out["sap_site"] = (time.perf_counter() - t) / Vs
+    P = Interpolation(inputs.random_test_vectors(Ls, nv, 11), wl["agg"])
     t = time.perf_counter()
     rc = P.restrict(psi)
-    out["restrict"] = time.perf_counter() - t
+    out["restrict_site"] = (time.perf_counter() - t) / Vs
     t = time.perf_counter()
     psi + P.prolong(rc)
-    out["prolong"] = time.perf_counter() - t
+    out["prolong_site"] = (time.perf_counter() - t) / Vs
     rng = np.random.default_rng(0)
-    n = 2 * nv
-    blocks = (rng.standard_normal(P.Lc + (9, n, n)) + 1j * rng.standard_normal(P.Lc + (9, n, n))) * 0.05
-    blocks[..., 0, :, :] += 4 * np.eye(n)
-    oe = OddEvenCoarse(CoarseOperator(blocks, nv, wl["delta"] * wl["mu"]))
+    m = wl.get("restart", 25)
+    d = 1.0 + rng.random(psi.shape)
+    nit = 2 * m
     t = time.perf_counter()
-    gmres(oe.schur, oe.reduced_rhs(rc), tol=0.0, restart=30, maxit=10)
-    out["coarse_iter"] = (time.perf_counter() - t) / 10
-    # the build applies the operator to 2 N_v columns and projects each onto
-    # 2 N_v rows: T(N_v) = 2 N_v alpha + 2 N_v^2 beta, fitted at N_v = 1 and 2
-    tb = []
-    for k in (1, 2):
-        Pk = Interpolation(tv[:k], wl["agg"])
+    gmres(lambda v: d * v, psi, tol=0.0, restart=m, maxit=nit, M=lambda v: v)
+    out["outer_iter_site"] = (time.perf_counter() - t) / nit / Vs
+    n = 2 * nv
+    Lc1 = tuple(Ls[k] // wl["agg"][k] for k in range(4))
+    V1s = int(np.prod(Lc1))
+
+    def rand_blocks(Lc, nn, shift):
+        b = (rng.standard_normal(Lc + (9, nn, nn)) + 1j * rng.standard_normal(Lc + (9, nn, nn))) * 0.05
+        b[..., 0, :, :] += shift * np.eye(nn)
+        return b
+
+    if levels == 2:
+        oe = OddEvenCoarse(CoarseOperator(rand_blocks(Lc1, n, 4.0), nv, wl["delta"] * wl["mu"]))
         t = time.perf_counter()
-        CoarseOperator.build(op, Pk, 0.0)
-        tb.append(time.perf_counter() - t)
-    beta = max(0.0, (tb[1] - 2 * tb[0]) / 4)
-    alpha = max(0.0, tb[0] / 2 - beta)
-    out["coarse_build"] = 2 * nv * alpha + 2 * nv * nv * beta + out["qr"]
+        gmres(oe.schur, oe.reduced_rhs(rc), tol=0.0, restart=30, maxit=10)
+        out["coarse_iter_site"] = (time.perf_counter() - t) / 10 / V1s
+        return out
+    from oracle.multilevel import CoarseSAP, CoarseInterpolation
+    nv2 = wl["nv2"]
+    Dc1 = CoarseOperator(rand_blocks(Lc1, n, 4.0), nv, wl["mu"])
+    v1 = rng.standard_normal(Lc1 + (n,)) + 1j * rng.standard_normal(Lc1 + (n,))
+    t = time.perf_counter()
+    Dc1.apply(v1)
+    out["level1_apply_site"] = (time.perf_counter() - t) / V1s
+    csap = CoarseSAP(Dc1, wl["sap_block1"], 4)
+    cmask = csap.colour == 0
+    t = time.perf_counter()
+    r1 = v1 - Dc1.apply(v1)
+    v1 + csap.mr(r1, cmask) * cmask[..., None]
+    out["csap_site"] = (time.perf_counter() - t) / V1s
+    w = rng.standard_normal((nv2,) + Lc1 + (n,)) + 1j * rng.standard_normal((nv2,) + Lc1 + (n,))
+    P2 = CoarseInterpolation(w, wl["agg2"], nv)
+    t = time.perf_counter()
+    c2 = P2.restrict(v1)
+    v1 + P2.prolong(c2)
+    out["l1xfer_site"] = (time.perf_counter() - t) / 2 / V1s
+    d1 = 1.0 + rng.random(v1.shape)
+    m1 = 30
+    t = time.perf_counter()
+    gmres(lambda v: d1 * v, v1, tol=0.0, restart=m1, maxit=m1, M=lambda v: v)
+    out["level1_iter_site"] = (time.perf_counter() - t) / m1 / V1s
+    Lc2 = (4, 4, 4, 4)
+    V2s = int(np.prod(Lc2))
+    oe2 = OddEvenCoarse(CoarseOperator(rand_blocks(Lc2, 2 * nv2, 4.0), nv2, wl["delta"] * wl["mu"]))
+    b2 = rng.standard_normal(Lc2 + (2 * nv2,)) + 1j * rng.standard_normal(Lc2 + (2 * nv2,))
+    t = time.perf_counter()
+    gmres(oe2.schur, oe2.reduced_rhs(b2), tol=0.0, restart=30, maxit=10)
+    out["coarsest_iter_site"] = (time.perf_counter() - t) / 10 / V2s
     return out
 
 
-def oracle_seconds(costs: dict, counts: dict) -> float:
-    """Oracle seconds per step = sum over components of count x unit cost."""
-    return (counts["clover"] * costs["clover"]
-            + counts["dslash_f64"] * costs["dslash_f64"]
-            + counts["dslash_f32"] * costs["dslash_f64"]
-            + counts["sap"] * costs["sap"]
-            + counts["restrict"] * costs["restrict"]
-            + counts["prolong"] * costs["prolong"]
-            + counts["coarse_iter"] * costs["coarse_iter"]
-            + counts["coarse_build"] * costs["coarse_build"])
+def step_counts(prof: dict, steps: int, outer_iters: float, levels: int) -> dict:
+    """Unit counts per step from the timed profile: D(mu) applies, SAP colour
+    units, transfers, coarse steps; outer FGMRES iterations from the solve."""
+    u = {k: v["units"] / steps for k, v in prof.items()}
+    c = {"dslash": u.get("dslash_f64", 0) + u.get("dslash_f32x2", 0) + u.get("dslash_f32", 0),
+         "sap": u.get("sap", 0), "restrict": u.get("restrict", 0), "prolong": u.get("prolong", 0),
+         "outer_iter": outer_iters}
+    if levels == 2:
+        c["coarse_iter"] = u.get("coarse_oe", 0)
+    else:
+        c.update({"level1_apply": u.get("level1", 0), "csap": u.get("coarse_sap", 0),
+                  "l1xfer": u.get("level1_transfer", 0), "coarsest_iter": u.get("coarse_oe", 0),
+                  # each level-1 FGMRES step applies D_c1 once (restart residuals add a few)
+                  "level1_iter": u.get("level1", 0)})
+    return c
+
+
+def oracle_seconds(costs: dict, counts: dict, wl: dict) -> float:
+    """Oracle seconds per step = sum over components of count x per-site cost x sites."""
+    V, V1, V2 = volumes(wl)
+    s = (counts["dslash"] * costs["dslash_site"] * V + counts["sap"] * costs["sap_site"] * V
+         + counts["restrict"] * costs["restrict_site"] * V + counts["prolong"] * costs["prolong_site"] * V
+         + counts["outer_iter"] * costs["outer_iter_site"] * V)
+    if "coarse_iter" in counts:
+        return s + counts["coarse_iter"] * costs["coarse_iter_site"] * V1
+    return s + (counts["level1_apply"] * costs["level1_apply_site"] * V1 + counts["csap"] * costs["csap_site"] * V1
+                + counts["l1xfer"] * costs["l1xfer_site"] * V1 + counts["level1_iter"] * costs["level1_iter_site"] * V1
+                + counts["coarsest_iter"] * costs["coarsest_iter_site"] * V2)
 
 
 def run_oracle_worker(wl_name: str) -> dict:
@@ -300,10 +413,53 @@ def run_oracle_worker(wl_name: str) -> dict:
     return costs
 
 
-# ---------------------------------------------------------------------------
-# native arm
+def _slab_worker(args):
+    """One T-slab of the oracle's true residual (spawned process)."""
+    from multiprocessing import shared_memory
+    import numpy as np
+    from oracle.slabs import slab_residual_norms
+    names, shapes, m0, c_sw, mu, bc_t, t0, t1 = args
+    shm = [shared_memory.SharedMemory(name=n) for n in names]
+    try:
+        U, x, b = (np.ndarray(sh, dtype=np.complex128, buffer=s.buf) for s, sh in zip(shm, shapes))
+        return slab_residual_norms(U, x, b, m0, c_sw, mu, bc_t, t0, t1)
+    finally:
+        del U, x, b
+        for s in shm:
+            s.close()
+
+
+def oracle_true_residual(U, x, b, m0, c_sw, mu, bc_t, workers: int) -> tuple[float, float]:
+    """||b - D(mu) x|| / ||b|| by the oracle, slab by slab over `workers`
+    spawned processes (the arrays in shared memory); returns (relres, seconds)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import numpy as np
+    t0 = time.time()
+    T = U.shape[0]
+    shm, shapes = [], []
+    try:
+        for a in (U, x, b):
+            s = shared_memory.SharedMemory(create=True, size=a.nbytes)
+            np.ndarray(a.shape, dtype=np.complex128, buffer=s.buf)[...] = a
+            shm.append(s)
+            shapes.append(a.shape)
+        slab = max(1, min(T // 2 - 1, -(-T // workers)))
+        jobs = [([s.name for s in shm], shapes, m0, c_sw, mu, bc_t, t, min(T, t + slab)) for t in range(0, T, slab)]
+        with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:
+            res = pool.map(_slab_worker, jobs)
+    finally:
+        for s in shm:
+            s.close()
+            s.unlink()
+    rr = sum(r[0] for r in res)
+    bb = sum(r[1] for r in res)
+    return float(np.sqrt(rr / bb)), time.time() - t0
+
+
 # ---------------------------------------------------------------------------
 # multi-rank pieces of the contract (N GPUs = N independent replicas)
+# ---------------------------------------------------------------------------
 def replica_seed(base: int, rank: int) -> int:
     """Seed of rank `rank`'s replica: every rank solves its own system."""
     return base + rank
@@ -326,283 +482,36 @@ def job_seconds_per_step(sec_max: float, world: int, steps: int) -> float:
 
 
 # ---------------------------------------------------------------------------
-def main_native(args):
+# native arm
+# ---------------------------------------------------------------------------
+def point_source_group(L, x0, first: int, count: int, dtype_np=None, device=None):
+    """Sources first..first+count-1 of the twelve spin-colour point sources at x0
+    (source k = 3 s0 + c0), natural layout [count, T, Z, Y, X, 4, 3]."""
     import numpy as np
-    import torch
-    import torch.distributed as dist
-    import inputs
-    import paper_1611_01034_gb300 as tm
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    wl = WORKLOADS[args.workload]
-    m0, m0_src = (args.m0, "command line") if args.m0 is not None else workload_m0(wl)
-    L, nv, seed = wl["L"], wl["nv"], replica_seed(wl["seed"], rank)  # one independent replica per rank
-    U = inputs.gauge_field(L, wl["eps"], seed)
-    levels = wl.get("levels", 2)
-    nrhs = wl.get("nrhs", 1)
-    rb = args.rhs_batch or wl.get("rhs_batch", nrhs)  # right-hand sides per tm_solve call
-    V = 1
-    for n in L:
-        V *= n
-    Lc1 = tuple(L[d] // wl["agg"][d] for d in range(4))
-    n_w = wl["nv2"] * (V // (wl["agg"][0] * wl["agg"][1] * wl["agg"][2] * wl["agg"][3])) * 2 * nv \
-        if levels == 3 else 0
-    if wl.get("device_inputs"):
-        # the FP64 test vectors (tens of GB) are drawn on the device with a seeded
-        # generator; the point sources are built there too; no host copies
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(seed + inputs.TV_SEED_OFFSET)
-        tvd = torch.randn((nv * V * 12 + n_w,), dtype=torch.complex128, device="cuda", generator=gen)
-        x0 = inputs.point_source_site(L, seed + inputs.RHS_SEED_OFFSET)
-        site = ((x0[0] * L[1] + x0[1]) * L[2] + x0[2]) * L[3] + x0[3]
-        bd = torch.zeros((12, V, 4, 3), dtype=torch.complex128, device="cuda")
-        for k in range(12):
-            bd[k, site, k // 3, k % 3] = 1.0
-        Ud = torch.from_numpy(U).cuda()
-        Uh = tvh = bh = xh = None
+    V = int(np.prod(L))
+    site = ((x0[0] * L[1] + x0[1]) * L[2] + x0[2]) * L[3] + x0[3]
+    if device is not None:
+        import torch
+        b = torch.zeros((count, V, 4, 3), dtype=torch.complex128, device=device)
     else:
-        tv = inputs.random_test_vectors(L, nv, seed + inputs.TV_SEED_OFFSET)
-        if levels == 3:  # level-1 random vectors follow the fine ones
-            w0 = inputs.random_coarse_vectors(Lc1, 2 * nv, wl["nv2"], seed + inputs.TV_SEED_OFFSET + 1)
-            tv = np.concatenate([tv.ravel(), w0.ravel()])
-        if wl.get("point"):
-            b, _ = inputs.point_sources(L, seed + inputs.RHS_SEED_OFFSET)
-        else:
-            b = inputs.gaussian_spinor(L, seed + inputs.RHS_SEED_OFFSET)
-        Ud, tvd, bd = (torch.from_numpy(a).cuda() for a in (U, tv, b))
-        Uh, tvh, bh = (torch.from_numpy(a).pin_memory() for a in (U, tv, b))
-        xh = torch.zeros(bh.shape, dtype=bh.dtype).pin_memory()
-    xd = torch.zeros_like(bd)
-    stream = torch.cuda.current_stream()
-    extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec")
-             if k in wl}
-    extra["coarse_mma"] = args.coarse_mma if args.coarse_mma is not None else wl.get("coarse_mma", 0)
-    for kv in args.param or []:  # solver-parameter overrides, e.g. --param coarse_tol=0.02
-        k, v = kv.split("=", 1)
-        extra[k] = float(v) if "." in v or "e" in v else int(v)
-    extra.setdefault("cycle_prec", tm.TM_F32)
-    p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv,
-                  agg=wl["agg"], sap_block=wl["sap_block"], setup_iters=wl["setup_iters"],
-                  max_rhs=rb, levels=levels, **extra)
-    h = tm.tm_create(p, stream)
-    infos = []
-
-    def step(Ug, tvg, bg, xg):
-        tm.tm_load_gauge(h, Ug)
-        tm.tm_setup(h, tvg)
-        xg.zero_()
-        for r0 in range(0, nrhs, rb):
-            st, info = tm.tm_solve(h, bg[r0:r0 + rb], xg[r0:r0 + rb], min(rb, nrhs - r0), wl["tol"])
-            if st != tm.TM_OK:
-                raise RuntimeError(f"solve failed: {tm.tm_status_string(st)}")
-            infos.append(info.as_dict())
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def timed(Ug, tvg, bg, xg, k, profile):
-        barrier()
-        torch.cuda.synchronize()
-        if profile:
-            tm.tm_profile(h, True)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(k):
-            step(Ug, tvg, bg, xg)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        return max_over_ranks(e0.elapsed_time(e1) / 1000.0, world, "cuda")
-
-    for _ in range(max(0, args.warmup - 1)):
-        step(Ud, tvd, bd, xd)
-    # last warm-up step: time every kernel class once to find the dominant one
-    tm.tm_profile(h, -1)
-    step(Ud, tvd, bd, xd)
-    prof_all = tm.tm_profile_read(h)
-    tm.tm_profile(h, False)
-    dom = max(prof_all, key=lambda k: prof_all[k]["ms"])
-    kinds = [tm.tm_profile_name(k) for k in range(tm.tm_profile_kinds())]
-    clocks = ClockSampler(local)
-    clocks.start()
-    infos.clear()
-    # timed steps: every class counted, only the dominant class timed with events
-    tm.tm_profile(h, 1 << kinds.index(dom))
-    sec = timed(Ud, tvd, bd, xd, args.steps, profile=False)
-    prof = tm.tm_profile_read(h)
-    tm.tm_profile(h, False)
-    clk = clocks.stop()
-    step_infos = list(infos)
-    del Ud, tvd, bd, xd  # the host-buffer run stages its own copies
-    torch.cuda.empty_cache()
-    sec_e2e = None
-    h2d = d2h = 0
-    if Uh is not None:
-        # end-to-end through the C ABI with pinned host buffers
-        step(Uh, tvh, bh, xh)
-        sec_e2e = timed(Uh, tvh, bh, xh, args.steps, profile=False)
-        h2d = (Uh.numel() + tvh.numel() + bh.numel() + xh.numel()) * 16
-        d2h = xh.numel() * 16
-    tm.tm_destroy(h)
-
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
-    K = args.steps
-    value = job_seconds_per_step(sec, world, K)
-    # per-step unit counts (per rhs unit) from the profile
-    per_step = {k: v["units"] / K for k, v in prof.items()}
-    launches = sum(v["launches"] for v in prof.values())
-    # kernel launches per profiled scope of a class (a Schur half is one
-    # launch; a build scope is orthonormalisation + build + odd-site inverses)
-    kernels_per_scope = {"coarse_oe": 2}
-    roof = None
-    model = algorithmic_bytes(dom, wl)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    if model is not None and prof[dom]["launches"]:
-        # a build scope counts one unit (one D_c) whatever kernels it launches
-        scopes = prof[dom]["units"] if dom == "coarse_build" else \
-            prof[dom]["launches"] / kernels_per_scope.get(dom, 1)
-        per_launch_bytes = model[0] + model[1] * prof[dom]["units"] / scopes
-        avg_s = prof[dom]["ms"] / scopes / 1000.0
-        achieved = per_launch_bytes / avg_s / 1e9
-        tr = ncu_traffic(args.workload, dom)
-        traffic = tr * prof[dom]["units"] / scopes if tr else None
-        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
-                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
-                "bytes_per_launch": per_launch_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
-    tot_ms = sum(v["ms"] for v in prof_all.values())
-    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                   "share": round(v["ms"] / max(1e-12, tot_ms), 4)}
-               for k, v in prof_all.items() if v["launches"]}
-    # units per step; coarse_oe units count the odd-even Schur applications
-    # (one per coarse GMRES step, plus the per-solve rhs/reconstruction)
-    counts = {
-        "clover": 1.0,
-        "dslash_f64": per_step["dslash_f64"],
-        "dslash_f32": per_step["dslash_f32"],
-        "sap": per_step["sap"],
-        "restrict": per_step["restrict"],
-        "prolong": per_step["prolong"],
-        "coarse_iter": per_step["coarse_oe"],
-        "coarse_build": prof["coarse_build"]["units"] / K,
-    }
-    cpu = None
-    if levels == 3:
-        cpu = {"value": None, "unit": "s", "kind": "oracle",
-               "note": "the oracle's per-unit cost model covers the two-level path only"}
-    elif not args.no_cpu_baseline:
-        try:
-            costs = run_oracle_worker(args.workload)
-            osec = oracle_seconds(costs, counts)
-            cpu = {"value": round(osec, 2), "unit": "s", "cores": 1, "kind": "oracle",
-                   "sample": ("FP64 numpy oracle, single thread, per-unit costs timed on the "
-                              "full lattice (clover plane, D apply, SAP colour half-sweep, "
-                              "restriction, prolongation, QR, 10 coarse GMRES steps, D_c build "
-                              "at N_v=1,2 fitted as 2N_v a + 2N_v^2 b) x this run's unit counts per step"),
-                   "sample_wall_s": round(costs["_wall"], 1),
-                   "unit_costs_s": {k: round(v, 4) for k, v in costs.items() if not k.startswith("_")}}
-        except Exception as e:  # report, do not hide
-            cpu = {"value": None, "error": str(e)[:300]}
-    scale = None
-    if rank == 0 and world == 1 and not args.no_scale_kernels and args.workload == DEFAULT_WORKLOAD:
-        try:
-            scale = kernels_at_scale(peaks)
-        except Exception as e:  # report, do not hide
-            scale = {"error": str(e)[:300]}
-    if args.write_counts:
-        os.makedirs(os.path.dirname(COUNTS_FILE), exist_ok=True)
-        json.dump({"workload": args.workload, "counts_per_step": counts,
-                   "note": "unit counts per step of the hot path (algorithmic counts of this "
-                           "method on this workload), used to scale the oracle's per-unit costs"},
-                  open(COUNTS_FILE, "w"), indent=1)
-    line = {
-        "metric": "solve seconds to 1e-10 rel. residual; D(mu) HBM GB/s and D_c TFLOP/s vs peak",
-        "value": round(value, 5),
-        "unit": "s",
-        "n_gpus": world,
-        "steps": K,
-        "warmup": args.warmup,
-        "ms_per_step": round(sec / K * 1000, 3),
-        "higher_is_better": False,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f64 outer / f32 cycle" if p.cycle_prec == tm.TM_F32 else "f64",
-        "data": f"synthetic (seeded random SU(3) field U = exp({wl['eps']} i H); "
-                + ("12 point sources)" if wl.get("point") else "Gaussian rhs)"),
-        "config": {
-            "workload": args.workload, "lattice_TZYX": list(L), "sites": V, "levels": levels,
-            **({"nv2": wl["nv2"], "aggregate2": list(wl["agg2"]), "sap_block1": list(wl["sap_block1"]),
-                "coarse_setup_iters": wl["coarse_setup_iters"]} if levels == 3 else {}),
-            "restart": p.restart, "rhs_per_solve_call": rb, "coarse_mma": p.coarse_mma,
-            "coarse_tol": p.coarse_tol, "post_smooth": p.post_smooth, "mr_iters": p.mr_iters,
-            **({"sap1_prec": "f16" if p.sap1_prec == 2 else "f32"} if levels == 3 else {}),
-            "nv": nv, "aggregate": list(wl["agg"]), "sap_block": list(wl["sap_block"]),
-            "m0": m0, "m0_source": m0_src, "c_sw": wl["c_sw"], "mu": wl["mu"],
-            "delta": wl["delta"], "setup_iters": wl["setup_iters"], "tol": wl["tol"], "nrhs": nrhs,
-            "rhs": "12 spin-colour point sources" if wl.get("point") else "Gaussian",
-            "step": f"load gauge + clover, adaptive setup, FGMRES solve ({nrhs} rhs, {rb} per call)",
-            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": "inputs per step > 129 MB L2 (no extra flush)",
-        },
-        "solve": {
-            "outer_iters": [i["iters"] for i in step_infos],
-            "coarse_iters": [i["coarse_iters"] for i in step_infos],
-            "true_relres": max(i["true_relres"] for i in step_infos),
-        },
-        "e2e": ({"value": round(job_seconds_per_step(sec_e2e, world, K), 5), "unit": "s",
-                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h} if sec_e2e is not None else
-                {"value": None, "reason": "inputs generated on the device: pinned host copies of the FP64 "
-                                          "test vectors would not fit the host memory twice"}),
-        "gpu_launches": int(launches),
-        "roofline": roof,
-        "kernels_one_step": kernels,
-        "kernels_at_scale": scale,
-        "clocks": clk,
-        "cpu_baseline": cpu,
-    }
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+        b = np.zeros((count, V, 4, 3), dtype=np.complex128)
+    for j in range(count):
+        k = first + j
+        b[j, site, k // 3, k % 3] = 1.0
+    return b
 
 
-# ---------------------------------------------------------------------------
-# reference arm: the oracle alone
-# ---------------------------------------------------------------------------
-def kernels_at_scale(peaks: dict) -> dict:
-    """D(mu) applies and the tensor-core coarse Schur complement on a 24^3x48
-    lattice (inputs larger than L2), timed with CUDA events on the library's
-    stream: the D(mu) HBM GB/s and D_c TFLOP/s of the benchmark's metric."""
-    import numpy as np
+def kernels_on_workload(h, tm, wl: dict, R: int, peaks: dict) -> dict:
+    """D(mu) applies (FP32, FP64, FP32 pairs) and the coarse operators on the
+    benchmark's own lattice with the setup just built, CUDA events on the
+    library's stream: the D(mu) HBM GB/s and D_c TFLOP/s of the metric."""
     import torch
-    import inputs
-    import paper_1611_01034_gb300 as tm
-
-    L, nv = (48, 24, 24, 24), 24
-    V = 1
-    for n in L:
-        V *= n
+    V, V1, V2 = volumes(wl)
     stream = torch.cuda.current_stream()
-    U = torch.from_numpy(inputs.gauge_field(L, 0.5, 1)).cuda()
-    p = tm.params(L=L, m0=-0.41769, c_sw=1.5, mu=0.002, delta=5.0, nv=nv, agg=(4, 4, 4, 4),
-                  sap_block=(4, 4, 4, 4), cycle_prec=tm.TM_F32, coarse_mma=1, max_rhs=12)
-    h = tm.tm_create(p, stream)
-    tm.tm_load_gauge(h, U)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    out = {"lattice_TZYX": list(L)}
+    out = {"lattice_TZYX": list(wl["L"])}
 
-    def timed(fn, k=20):
+    def timed(fn, k=10):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
@@ -615,44 +524,299 @@ def kernels_at_scale(peaks: dict) -> dict:
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k / 1e3
 
-    for prec, name, esz in ((tm.TM_F32, "dslash_f32", 4), (tm.TM_F64, "dslash_f64", 8)):
-        nb = tm.tm_field_bytes(h, 0, prec, 1)
-        a = torch.zeros(nb, dtype=torch.uint8, device="cuda")
-        b = torch.zeros_like(a)
-        a.view(torch.float32 if esz == 4 else torch.float64).normal_()
-        t = timed(lambda: tm.tm_apply(h, 0, prec, a, b, 1))
-        byts = V * esz * (48 + 120)   # spinor in + out, 4 links x 12 reals, clover 72 reals per site
-        out[name] = {"us": round(t * 1e6, 1), "algorithmic_bytes": byts, "achieved_gbs": round(byts / t / 1e9, 1),
-                     "frac_of_measured_hbm": round(byts / t / 1e9 / hbm, 4),
+    for pin, pout, name, byts in ((tm.TM_F32, tm.TM_F32, "dslash_f32", 168 * 4),
+                                  (tm.TM_F64, tm.TM_F64, "dslash_f64", 168 * 8),
+                                  (tm.TM_F32X2, tm.TM_F64, "dslash_f32x2", 96 + 192 + 576 + 576)):
+        if pin == tm.TM_F32X2 and wl.get("outer_apply") != TM_F32X2:
+            continue
+        a = torch.zeros(tm.tm_field_bytes(h, 0, tm.TM_F32 if pin == tm.TM_F32X2 else pin, 1), dtype=torch.uint8,
+                        device="cuda")
+        b = torch.zeros(tm.tm_field_bytes(h, 0, pout, 1), dtype=torch.uint8, device="cuda")
+        a.view(torch.float64 if pin == tm.TM_F64 else torch.float32).normal_()
+        t = timed(lambda: tm.tm_apply(h, 0, pin, a, b, 1))
+        out[name] = {"us": round(t * 1e6, 1), "algorithmic_bytes": byts * V,
+                     "achieved_gbs": round(byts * V / t / 1e9, 1),
+                     "frac_of_measured_hbm": round(byts * V / t / 1e9 / hbm, 4),
                      "tflops": round(V * 2232 / t / 1e12, 3)}
         del a, b
-    # 12-rhs odd-even coarse Schur complement on the tensor cores (TF32) after a setup from random vectors
-    tv = torch.from_numpy(inputs.random_test_vectors(L, nv, 1 + inputs.TV_SEED_OFFSET)).cuda()
-    tm.tm_setup_from_vectors(h, tv)
-    del tv
-    nh = V // 256 // 2
-    n = 2 * nv
-    R = 12
-    v = torch.randn(R * nh * n * 2, device="cuda", dtype=torch.float32)
-    y = torch.zeros_like(v)
-    kinds = [tm.tm_profile_name(k) for k in range(tm.tm_profile_kinds())]
-    for _ in range(3):
-        tm.tm_schur(h, tm.TM_F32, v, y, R)
-    tm.tm_profile(h, 1 << kinds.index("coarse_oe"))
-    K = 20
-    for _ in range(K):
-        tm.tm_schur(h, tm.TM_F32, v, y, R)
-    t = tm.tm_profile_read(h)["coarse_oe"]["ms"] / K / 1e3
-    tm.tm_profile(h, False)
-    flops = nh * 17 * n * n * 8 * R           # complex multiply-adds of the 17 blocks per site pair
-    tiles = nh * 17 * (2 * n) * n * 4         # operator bytes read (FP32 tiles)
-    out["coarse_schur_tf32"] = {"coarse_sites_per_parity": nh, "nv": nv, "nrhs": R, "us": round(t * 1e6, 1),
-                                "tflops": round(flops / t / 1e12, 2), "operator_gbs": round(tiles / t / 1e9, 1),
-                                "frac_of_measured_bf16": round(flops / t / 1e12 / float(peaks.get("bf16_tflops", 1900.0)), 4)}
-    tm.tm_destroy(h)
+    # level-1 operator D_c1 with R right-hand sides (FP32 blocks)
+    n1 = 2 * wl["nv"]
+    nb = tm.tm_field_bytes(h, 1, tm.TM_F32, R)
+    a = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    b = torch.zeros_like(a)
+    a.view(torch.float32).normal_()
+    t = timed(lambda: tm.tm_apply(h, 1, tm.TM_F32, a, b, R))
+    fl = V1 * 9 * n1 * n1 * 8 * R
+    out["level1_apply"] = {"nrhs": R, "us": round(t * 1e6, 1), "tflops": round(fl / t / 1e12, 3),
+                           "operator_gbs": round(V1 * 9 * n1 * n1 * 8 / t / 1e9, 1)}
+    del a, b
+    torch.cuda.empty_cache()
     return out
 
 
+def main_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import inputs
+    import paper_1611_01034_gb300 as tm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+    m0, m0_src = (args.m0, "command line") if args.m0 is not None else workload_m0(wl)
+    L, nv, seed = wl["L"], wl["nv"], replica_seed(wl["seed"], rank)  # one independent replica per rank
+    # host inputs first: the gauge generator's process pool is spawned before any CUDA call
+    U = inputs.gauge_field(L, wl["eps"], seed, workers=min(16, os.cpu_count() or 1))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    levels = wl.get("levels", 2)
+    nrhs = wl.get("nrhs", 1)
+    R = args.rhs_batch or wl.get("rhs_batch", nrhs)  # right-hand sides per step
+    groups = max(1, nrhs // R)
+    V, V1, V2 = volumes(wl)
+    n_w = wl["nv2"] * V1 * 2 * nv if levels == 3 else 0
+    if wl.get("device_inputs"):
+        # the FP64 test vectors (tens of GB) are drawn on the device with a seeded generator
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(seed + inputs.TV_SEED_OFFSET)
+        tvd = torch.randn((nv * V * 12 + n_w,), dtype=torch.complex128, device="cuda", generator=gen)
+    else:
+        tv = inputs.random_test_vectors(L, nv, seed + inputs.TV_SEED_OFFSET)
+        if levels == 3:  # level-1 random vectors follow the fine ones
+            Lc1 = tuple(L[d] // wl["agg"][d] for d in range(4))
+            w0 = inputs.random_coarse_vectors(Lc1, 2 * nv, wl["nv2"], seed + inputs.TV_SEED_OFFSET + 1)
+            tv = np.concatenate([tv.ravel(), w0.ravel()])
+        tvd = torch.from_numpy(tv).cuda()
+        del tv
+    x0 = inputs.point_source_site(L, seed + inputs.RHS_SEED_OFFSET) if wl.get("point") else None
+
+    def host_group(g):
+        if x0 is not None:
+            return point_source_group(L, x0, g * R, R)
+        return inputs.gaussian_spinor(L, seed + inputs.RHS_SEED_OFFSET + g, nrhs=R).reshape(R, V, 4, 3)
+
+    stream = torch.cuda.current_stream()
+    extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec",
+                                "outer_apply") if k in wl}
+    extra["coarse_mma"] = args.coarse_mma if args.coarse_mma is not None else wl.get("coarse_mma", 0)
+    for kv in args.param or []:  # solver-parameter overrides, e.g. --param coarse_tol=0.02
+        k, v = kv.split("=", 1)
+        extra[k] = float(v) if "." in v or "e" in v else int(v)
+    extra.setdefault("cycle_prec", tm.TM_F32)
+    p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv,
+                  agg=wl["agg"], sap_block=wl["sap_block"], setup_iters=wl["setup_iters"],
+                  max_rhs=R, levels=levels, **extra)
+    h = tm.tm_create(p, stream)
+    kinds = [tm.tm_profile_name(k) for k in range(tm.tm_profile_kinds())]
+
+    # ---- setup (once, outside the timed steps) ---------------------------------
+    Ud = torch.from_numpy(U).cuda()
+    torch.cuda.synchronize()
+    tm.tm_profile(h, -1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tm.tm_load_gauge(h, Ud)
+    tm.tm_setup(h, tvd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    setup_s = e0.elapsed_time(e1) / 1000.0
+    prof_setup = tm.tm_profile_read(h)
+    tm.tm_profile(h, False)
+    del Ud, tvd
+    torch.cuda.empty_cache()
+
+    # ---- device-resident steps ---------------------------------------------------
+    bd = torch.from_numpy(host_group(0)).cuda()
+    xd = torch.zeros_like(bd)
+    infos = []
+
+    def step(bg, xg):
+        xg.zero_()
+        st, info = tm.tm_solve(h, bg, xg, R, wl["tol"])
+        if st != tm.TM_OK:
+            raise RuntimeError(f"solve failed: {tm.tm_status_string(st)}: {tm.tm_last_error(h)}")
+        infos.append(info.as_dict())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(k, one_step):
+        barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(k):
+            one_step(i)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(t0.elapsed_time(t1) / 1000.0, world, "cuda")
+
+    for _ in range(max(0, args.warmup - 1)):
+        step(bd, xd)
+    # last warm-up step: time every kernel class once to find the dominant one
+    tm.tm_profile(h, -1)
+    step(bd, xd)
+    prof_all = tm.tm_profile_read(h)
+    tm.tm_profile(h, False)
+    dom = max(prof_all, key=lambda k: prof_all[k]["ms"])
+    clocks = ClockSampler(local)
+    clocks.start()
+    infos.clear()
+    # timed steps: every class counted, only the dominant class timed with events
+    tm.tm_profile(h, 1 << kinds.index(dom))
+    sec = timed(args.steps, lambda i: step(bd, xd))
+    prof = tm.tm_profile_read(h)
+    tm.tm_profile(h, False)
+    clk = clocks.stop()
+    step_infos = list(infos)
+    x_check = xd[0].cpu().numpy() if rank == 0 else None  # first source's solution, for the oracle
+    del bd, xd
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the C ABI with pinned host buffers --------------------------
+    bh = [torch.from_numpy(host_group(g)).pin_memory() for g in range(groups)]
+    xh = torch.zeros(bh[0].shape, dtype=bh[0].dtype).pin_memory()
+    step(bh[0], xh)
+    sec_e2e = timed(args.steps, lambda i: step(bh[i % groups], xh))
+    h2d = (bh[0].numel() + xh.numel()) * 16
+    d2h = xh.numel() * 16
+    del bh, xh
+    scale = None
+    if not args.no_scale_kernels:
+        try:
+            scale = kernels_on_workload(h, tm, wl, R, json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+                                        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {})
+        except Exception as e:  # report, do not hide
+            scale = {"error": str(e)[:300]}
+    tm.tm_destroy(h)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    K = args.steps
+    value = job_seconds_per_step(sec, world, K)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    outer_iters = sum(i["iters"] for i in step_infos) / K  # summed over the step's right-hand sides
+    launches = sum(v["launches"] for v in prof.values())
+    roof = None
+    outer = {"iters": round(outer_iters / R), "restart": p.restart, "rhs": R}
+    model = roofline_model(dom, wl, prof[dom]["units"], prof[dom]["launches"], outer, peaks)
+    if model is not None and prof[dom]["launches"]:
+        avg_s = prof[dom]["ms"] / prof[dom]["launches"] / 1000.0
+        if dom == "coarse_oe":
+            avg_s *= 2  # the model counts one Schur application (two launches)
+        achieved = model["work"] / avg_s / 1e9
+        tr = ncu_traffic(args.workload, dom)
+        roof = {"kernel": dom, "bound": model["bound"], "achieved": round(achieved, 3), "peak": model["peak"],
+                "unit": model["unit"], "frac": round(achieved / model["peak"], 4),
+                "traffic": (tr * prof[dom]["units"] / prof[dom]["launches"]) if tr else None,
+                ("flops_per_launch" if model["bound"] == "alu" else "bytes_per_launch"):
+                    model["work"] * (1e3 if model["bound"] == "alu" else 1),
+                "avg_launch_us": round(avg_s * 1e6, 2), "peak_source": model["peak_source"]}
+    tot_ms = sum(v["ms"] for v in prof_all.values())
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share": round(v["ms"] / max(1e-12, tot_ms), 4)}
+               for k, v in prof_all.items() if v["launches"]}
+    counts = step_counts(prof, K, outer_iters, levels)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            costs = run_oracle_worker(args.workload)
+            osec = oracle_seconds(costs, counts, wl)
+            cpu = {"value": round(osec, 2), "unit": "s", "cores": 1, "kind": "oracle",
+                   "sample": ("FP64 numpy oracle, one thread: per-site costs of each step component timed on "
+                              "sample lattices (D apply, SAP colour, P, P^dagger, outer FGMRES iteration on "
+                              "16^3x32" + ("; level-1 D_c1, level-1 SAP colour, P2, level-1 FGMRES iteration on "
+                                           "8x4x4x4 level-1 sites; coarsest odd-even GMRES step on 4^4 sites"
+                                           if levels == 3 else "; odd-even coarse GMRES steps")
+                              + ") x the sites of this workload x this run's unit counts per step"),
+                   "sample_wall_s": round(costs["_wall"], 1),
+                   "unit_costs_s_per_site": {k: float(f"{v:.4g}") for k, v in costs.items() if not k.startswith("_")}}
+        except Exception as e:  # report, do not hide
+            cpu = {"value": None, "error": str(e)[:300]}
+        if x_check is not None:
+            try:
+                b0 = host_group(0)[0]
+                nw = min(16, os.cpu_count() or 1)
+                rr, ts = oracle_true_residual(U, x_check.reshape(L + (4, 3)), b0.reshape(L + (4, 3)), m0,
+                                              wl["c_sw"], wl["mu"], -1.0, nw)
+                cpu = dict(cpu or {}, oracle_check={
+                    "true_relres": rr, "seconds": round(ts, 1), "processes": nw,
+                    "what": "the oracle's FP64 D(mu) recomputes ||b - D x|| / ||b|| of the first source's GPU "
+                            "solution on the full lattice, T-slab by T-slab"})
+            except Exception as e:  # report, do not hide
+                cpu = dict(cpu or {}, oracle_check={"error": str(e)[:300]})
+    if args.write_counts:
+        os.makedirs(os.path.dirname(COUNTS_FILE), exist_ok=True)
+        json.dump({"workload": args.workload, "counts_per_step": counts,
+                   "note": "unit counts per step of the hot path on this workload (D applies, SAP colour "
+                           "units, transfers, coarse steps, outer iterations), used to scale the oracle's "
+                           "per-site costs"}, open(COUNTS_FILE, "w"), indent=1)
+    setup_kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 1)} for k, v in prof_setup.items()
+                     if v["launches"]}
+    oa = "f32x2" if p.outer_apply == TM_F32X2 else "f64"
+    line = {
+        "metric": METRIC,
+        "value": round(value, 5),
+        "unit": "s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(sec / K * 1000, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": (f"f64 FGMRES (Arnoldi, true residual); {oa} D(mu) z_k products; f32 K-cycle"
+                  + ("; f16 level-1 SAP blocks" if p.sap1_prec == 2 else "")
+                  + ("; tf32 coarsest Schur complement" if p.coarse_mma else "")),
+        "data": f"synthetic (seeded random SU(3) field U = exp({wl['eps']} i H); "
+                + ("12 spin-colour point sources)" if wl.get("point") else "Gaussian rhs)"),
+        "config": {
+            "workload": args.workload, "lattice_TZYX": list(L), "sites": V, "levels": levels,
+            **({"nv2": wl["nv2"], "aggregate2": list(wl["agg2"]), "sap_block1": list(wl["sap_block1"]),
+                "coarse_setup_iters": wl["coarse_setup_iters"],
+                "sap1_prec": "f16" if p.sap1_prec == 2 else "f32"} if levels == 3 else {}),
+            "nv": nv, "aggregate": list(wl["agg"]), "sap_block": list(wl["sap_block"]),
+            "restart": p.restart, "coarse_tol": p.coarse_tol, "post_smooth": p.post_smooth, "mr_iters": p.mr_iters,
+            "coarse_mma": p.coarse_mma, "outer_apply": oa,
+            "m0": m0, "m0_source": m0_src, "c_sw": wl["c_sw"], "mu": wl["mu"], "delta": wl["delta"],
+            "setup_iters": wl["setup_iters"], "tol": wl["tol"], "rhs_total": nrhs, "rhs_per_step": R,
+            "rhs": "12 spin-colour point sources" if wl.get("point") else "Gaussian",
+            "step": (f"FGMRES solve of {R} right-hand side(s) to 1e-10 (one group of {nrhs}); gauge field, clover "
+                     f"term and adaptive setup once before the timed steps (setup_s)"),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "every fine vector > 129 MB L2 (no extra flush)",
+        },
+        "setup_s": round(setup_s, 3),
+        "setup_kernels": setup_kernels,
+        "solve": {
+            "outer_iters_per_step": [i["iters"] for i in step_infos],
+            "coarse_iters_per_step": [i["coarse_iters"] for i in step_infos],
+            "true_relres_max": max(i["true_relres"] for i in step_infos),
+            "seconds_per_rhs": round(value / R, 4),
+            "seconds_all_sources": round(value * nrhs / R, 3),
+        },
+        "e2e": {"value": round(job_seconds_per_step(sec_e2e, world, K), 5), "unit": "s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": f"steps cycle through the {groups} source group(s); x0 = 0 written on the host each step"},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernels_one_step": kernels,
+        "kernels_on_workload": scale,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 def main_learned(args):
     """Train the learned layer on 8 fields, then solve on 4 held-out fields with
     no stage after the K-cycle, the learned layer (FP16 inference) and one SAP
@@ -763,25 +927,33 @@ def main_reference(args):
         print(json.dumps({"impl": "reference", "unavailable":
                           "no unit counts recorded (profiles/bench_unit_counts.json)"}))
         return
-    counts = json.load(open(COUNTS_FILE))["counts_per_step"]
+    rec = json.load(open(COUNTS_FILE))
+    if rec.get("workload") != args.workload:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"unit counts recorded for {rec.get('workload')}, not {args.workload}"}))
+        return
+    counts = rec["counts_per_step"]
+    wl = WORKLOADS[args.workload]
     times = []
     last = None
     for i in range(args.warmup + args.steps):
         costs = run_oracle_worker(args.workload)
         if i >= args.warmup:
-            times.append(oracle_seconds(costs, counts))
+            times.append(oracle_seconds(costs, counts, wl))
         last = costs
     value = statistics.mean(times)
     print(json.dumps({
         "impl": "reference",
-        "metric": "solve seconds to 1e-10 rel. residual; D(mu) HBM GB/s and D_c TFLOP/s vs peak",
+        "metric": METRIC,
         "value": round(value, 2), "unit": "s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload},
         "cpu_baseline": {"value": round(value, 2), "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": "per-unit oracle costs x recorded unit counts per step",
-                         "unit_costs_s": {k: round(v, 4) for k, v in last.items() if not k.startswith("_")}},
+                         "sample": "per-site oracle costs on sample lattices x the workload's sites x the unit "
+                                   "counts per step recorded from a GPU run (profiles/bench_unit_counts.json)",
+                         "unit_costs_s_per_site": {k: float(f"{v:.4g}") for k, v in last.items()
+                                                   if not k.startswith("_")}},
         "e2e": {"value": round(value, 2), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -796,9 +968,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--write-counts", action="store_true")
     ap.add_argument("--param", action="append", help="override a tm_params field: name=value")
-    ap.add_argument("--rhs-batch", type=int, default=None, help="right-hand sides per tm_solve call")
+    ap.add_argument("--rhs-batch", type=int, default=None, help="right-hand sides per step")
     ap.add_argument("--no-scale-kernels", action="store_true",
-                    help="skip the D(mu) and coarse Schur measurements on the 24^3x48 lattice")
+                    help="skip the D(mu) and D_c1 measurements on the workload's lattice")
     ap.add_argument("--oracle-worker", default=None)
     ap.add_argument("--m0", type=float, default=None, help="override the workload's tuned m0")
     ap.add_argument("--coarse-mma", type=int, default=None,

@@ -384,7 +384,9 @@ tm_status tm_synchronize(tm_handle* h);
 /* Opt-in per-kernel accounting.  Kernel launches fall into
  * tm_profile_kinds() classes (named by tm_profile_name: dslash_f64,
  * dslash_f32, sap, restrict, prolong, coarse_oe, blas_fine, blas_coarse,
- * coarse_build, other).  With enable != 0 every launch is counted (launches
+ * coarse_build, other, coarse_sap (level-1 SAP), level1 (level-1 operator),
+ * nn, dslash_f32x2, level1_transfer (P2 and P2^dagger)).  With enable != 0
+ * every launch is counted (launches
  * and right-hand-side units) and the launches of class k are also bracketed
  * by a pair of CUDA events on the handle's stream when bit k of enable is set
  * (enable = -1 times every class).  tm_profile resets the totals;

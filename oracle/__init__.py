@@ -24,6 +24,13 @@ Modules
   rotations (Sec. 1, Fig. 3).
 * ``amg``    -- the K-cycle of eq. (1), the adaptive setup (Sec. 1, Sec. 3)
   and the FGMRES + AMG solve.
+* ``multilevel`` -- the three-level hierarchy of Sec. 2 (coarse-grid SAP,
+  level-1 aggregation, the level-1 K-cycle).
+* ``slabs``  -- the true residual of a large lattice evaluated T-slab by
+  T-slab with the unchanged operator (for solutions too large for one
+  full-lattice oracle apply).
+* ``nn``     -- the learned gauge-covariant layer (not in the paper).
+* ``tune_m0`` -- the m0 reading of the synthetic workloads.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, algebraic identities, dense brute force or library

@@ -18,7 +18,7 @@ import os
 
 from ._binding import (  # noqa: F401
     TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_OOM, TM_ERR_NOT_CONVERGED, TM_ERR_TIMEOUT,
-    TM_ERR_NOT_SU3, TM_ERR_NONFINITE, TM_ERR_STATE, TM_F64, TM_F32, TM_F16,
+    TM_ERR_NOT_SU3, TM_ERR_NONFINITE, TM_ERR_STATE, TM_F64, TM_F32, TM_F16, TM_F32X2,
     TM_EXPORT_P, TM_EXPORT_DC, TM_EXPORT_CLOVER, TM_EXPORT_TV, TM_EXPORT_P2, TM_EXPORT_DC2, TM_EXPORT_TV1,
     TMError, tm_params, tm_solve_info, lib, library_path, params,
     tm_params_default, tm_create, tm_destroy, tm_status_string, tm_last_error,

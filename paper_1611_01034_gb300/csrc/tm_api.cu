@@ -126,9 +126,9 @@ struct tm_handle {
   std::vector<cudaEvent_t> evpool;
   cudaEvent_t pipe_ev[2] = {nullptr, nullptr};  // the coarse GMRES's double-buffered step results
   BuildShape build_shape{};                     // tile shape of the D_c build (autotuned or default)
-  long long prof_launch[16] = {};
-  long long prof_units[16] = {};
-  double prof_ms[16] = {};
+  long long prof_launch[24] = {};
+  long long prof_units[24] = {};
+  double prof_ms[24] = {};
 };
 
 namespace {
@@ -188,12 +188,13 @@ T* Wz(tm_handle* h, const std::string& name, size_t count) {
 // ---------------------------------------------------------------------------
 enum ProfKind {
   PK_DSLASH64 = 0, PK_DSLASH32, PK_SAP, PK_RESTRICT, PK_PROLONG, PK_COARSE_OE, PK_BLAS_FINE, PK_BLAS_COARSE,
-  PK_BUILD, PK_OTHER, PK_CSAP, PK_LEVEL1, PK_NN, PK_DSLASHDF, PK_N
+  PK_BUILD, PK_OTHER, PK_CSAP, PK_LEVEL1, PK_NN, PK_DSLASHDF, PK_L1XFER, PK_N
 };
+static_assert(PK_N <= 24, "profile arrays of the handle hold 24 classes");
 const char* const kProfNames[PK_N] = {"dslash_f64", "dslash_f32",   "sap",          "restrict",
                                       "prolong",    "coarse_oe",    "blas_fine",    "blas_coarse",
                                       "coarse_build", "other",      "coarse_sap",   "level1",
-                                      "nn",           "dslash_f32x2"};
+                                      "nn",           "dslash_f32x2", "level1_transfer"};
 
 cudaEvent_t take_event(tm_handle* h) {
   if (!h->evpool.empty()) {
@@ -915,13 +916,13 @@ void kcycle1(tm_handle* h, const T* v, T* z, int nrhs) {
   T* r2 = W<T>(h, "k1_r2", c2 * nrhs);
   T* e2 = W<T>(h, "k1_e2", c2 * nrhs);
   {
-    Prof pf(h, PK_LEVEL1, nrhs);
+    Prof pf(h, PK_L1XFER, nrhs);
     launch_crestrict<T>(static_cast<const T*>(h->P2), r, r2, h->cag, nrhs, h->st);
     CKL();
   }
   coarse_solve<T>(h, coarsest_level(h), r2, e2, nrhs, h->p.coarsest_tol, h->p.coarsest_maxit);
   {
-    Prof pf(h, PK_LEVEL1, nrhs);
+    Prof pf(h, PK_L1XFER, nrhs);
     launch_cprolong<T>(static_cast<const T*>(h->P2), e2, z, h->cag, nrhs, true, h->st);
     CKL();
   }

@@ -98,3 +98,19 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert L.tm_set_mu(None, 0.01, 2.0) == tm.TM_ERR_ARG
     assert L.tm_setup_update(None, 1, 0) == tm.TM_ERR_ARG
     L.tm_destroy(None)
+
+
+def test_names_the_tests_and_bench_use_exist():
+    """Every ``tm.<name>`` that a test file or bench.py refers to is exported by
+    the package (the GPU tests are skipped on a machine without a GPU, so a
+    missing name would otherwise only show there)."""
+    import glob
+    import paper_1611_01034_gb300 as tm
+    files = glob.glob(os.path.join(ROOT, "tests", "*.py")) + [os.path.join(ROOT, "bench.py"),
+                                                           os.path.join(ROOT, "__graft_entry__.py")]
+    missing = set()
+    for f in files:
+        for name in re.findall(r"\btm\.([A-Za-z_][A-Za-z0-9_]*)", open(f).read()):
+            if name != "h" and not hasattr(tm, name):  # "tm.h" is the header
+                missing.add((os.path.basename(f), name))
+    assert not missing, sorted(missing)
