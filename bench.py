@@ -133,7 +133,8 @@ def roofline_model(kind: str, wl: dict, units: float, launches: float, outer: di
 
     units / launches: right-hand-side units and kernel launches of the class
     in the timed steps; outer: {"iters": outer FGMRES iterations per rhs,
-    "restart": m} for the FP64 Arnoldi BLAS.  Bytes count every operator
+    "restart": m, "rhs": right-hand sides per step, "steps": timed steps}
+    for the FP64 Arnoldi BLAS.  Bytes count every operator
     array once per launch and every vector once per right-hand side; flops
     count the arithmetic the definition needs.
       sap (one colour of a sweep): links + clover of the colour's half, x
@@ -190,7 +191,7 @@ def roofline_model(kind: str, wl: dict, units: float, launches: float, outer: di
         return {"bound": "hbm", "work": b, "unit": "GB/s", "peak": hbm, "peak_source": hbm_src}
     if kind == "blas_fine":
         m, it = outer["restart"], outer["iters"]
-        nrhs_total = outer["rhs"]
+        nrhs_total = outer["rhs"] * outer["steps"]  # right-hand sides solved in the timed steps
         flops_el = 0.0  # real flops per complex element of one rhs, whole solve
         left = it
         while left > 0:
@@ -708,7 +709,7 @@ def main_native(args):
     outer_iters = sum(i["iters"] for i in step_infos) / K  # summed over the step's right-hand sides
     launches = sum(v["launches"] for v in prof.values())
     roof = None
-    outer = {"iters": round(outer_iters / R), "restart": p.restart, "rhs": R}
+    outer = {"iters": round(outer_iters / R), "restart": p.restart, "rhs": R, "steps": K}
     model = roofline_model(dom, wl, prof[dom]["units"], prof[dom]["launches"], outer, peaks)
     if model is not None and prof[dom]["launches"]:
         avg_s = prof[dom]["ms"] / prof[dom]["launches"] / 1000.0
