@@ -141,6 +141,13 @@ typedef struct {
      the links and the clover term once more as FP32 pairs (288 B per site
      each).  The true residual b - D x stays FP64 either way. */
   int outer_apply;
+  /* SAP block solves (Sec. 3: odd-even preconditioning in the smoother):
+     0 = mr_iters MR steps on the block operator D_B; 1 = mr_iters MR steps on
+     the block's odd-even Schur complement D_ee - D_eo D_oo^-1 D_oe over its
+     even sites, odd sites recovered afterwards.  1 needs even sap_block dims
+     and keeps (A(x) + i mu gamma5)^-1 of every odd site (144 reals per odd
+     site in cycle_prec); SAP then runs in cycle_prec only. */
+  int block_oe;
 } tm_params;
 
 typedef struct {
@@ -159,7 +166,7 @@ typedef struct {
  * agg2 = sap_block1 = 2^4, mr_iters1 = 4, pre_smooth1 = 0, post_smooth1 = 2,
  * init_sweeps1 = 3, coarse_setup_iters = 3, coarsest_tol = 5e-2,
  * coarsest_maxit = 200, coarse_mma = 0, nn_mode = 0, nn_prec = TM_F32,
- * sap1_prec = TM_F32, outer_apply = TM_F64.
+ * sap1_prec = TM_F32, outer_apply = TM_F64, block_oe = 0.
  * L, m0, c_sw, mu are 0. */
 void tm_params_default(tm_params* p);
 
@@ -276,8 +283,10 @@ tm_status tm_unpack(tm_handle* h, int level, int prec, const void* field, double
 tm_status tm_apply(tm_handle* h, int level, int prec, const void* in, void* out, int nrhs);
 
 /* A2: sweeps SAP sweeps (red blocks, then black) on D x = b with mr_iters MR
- * steps per block solve (Sec. 1: the smoother M).  b may be NULL (b = 0).
- * Fine fields, prec TM_F64 or TM_F32; x is updated in place. */
+ * steps per block solve (Sec. 1: the smoother M; with block_oe = 1 on the
+ * block's odd-even Schur complement, Sec. 3).  b may be NULL (b = 0).
+ * Fine fields, prec TM_F64 or TM_F32 (cycle_prec with block_oe = 1); x is
+ * updated in place. */
 tm_status tm_sap(tm_handle* h, int prec, const void* b, void* x, int sweeps, int nrhs);
 
 /* A3: coarse = P^dagger fine.  A6: fine = P coarse (accumulate = 0) or

@@ -190,4 +190,375 @@ template void launch_sap_colour<double>(const double*, const double*, const doub
 template void launch_sap_colour<float>(const float*, const float*, const float*, float*, const SapGeom&, double,
                                        double, int, int, int, cudaStream_t);
 
+// ===========================================================================
+// Odd-even block solve (Sec. 3: odd-even preconditioning is used in the
+// smoother).  Within a block B (all dims even, origin on an even site, so the
+// site parity (t+z+y+x) mod 2 splits it into two halves of BS/2 sites),
+//   D_B = [[D_ee, D_eo], [D_oe, D_oo]],
+// D_ee, D_oo the site-diagonal A(x) + i mu gamma5, D_eo, D_oe the Dirichlet
+// intra-block hops.  The MR steps run on the Schur complement
+//   S = D_ee - D_eo D_oo^-1 D_oe  over the even sites,
+// with right-hand side r_e - D_eo D_oo^-1 r_o; afterwards
+//   e_o = D_oo^-1 (r_o - D_oe e_e).
+// One CTA owns one block and one right-hand side; thread j owns the j-th even
+// and the j-th odd site (same t, z, y; x = 2 j_x + parity offset), so no lane
+// idles in either half-step.  D_oo^-1 comes precomputed per odd site
+// (launch_clover_inverse).
+// ===========================================================================
+namespace {
+
+// index of a site within its parity class, from block-local coordinates
+__device__ __forceinline__ int half_index(const int lc[4], const int blk[4]) {
+  return ((lc[0] * blk[1] + lc[1]) * blk[2] + lc[2]) * (blk[3] / 2) + (lc[3] >> 1);
+}
+
+// acc += hops (Dirichlet, without the -1/2) from the neighbours of a site inside
+// the block, whose values of the other parity are in shared memory src [12][HB]
+template <typename T>
+__device__ __forceinline__ void oe_block_hops(const cx<T>* __restrict__ src, int HB, const int lc[4],
+                                              const int blk[4], const T* __restrict__ gauge, const Lat& g, int s,
+                                              const int c[4], cx<T> (&acc)[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = cx<T>{0, 0};
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    if (lc[mu] < blk[mu] - 1) {
+      int ln[4] = {lc[0], lc[1], lc[2], lc[3]};
+      ln[mu] += 1;
+      const int j = half_index(ln, blk);
+      cx<T> p[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) p[k] = src[k * HB + j];
+      switch (mu) {
+        case 0: hop_fwd_p<T, 0>(p, gauge, g.V, s, T(1), acc); break;
+        case 1: hop_fwd_p<T, 1>(p, gauge, g.V, s, T(1), acc); break;
+        case 2: hop_fwd_p<T, 2>(p, gauge, g.V, s, T(1), acc); break;
+        default: hop_fwd_p<T, 3>(p, gauge, g.V, s, T(1), acc); break;
+      }
+    }
+    if (lc[mu] > 0) {
+      int ln[4] = {lc[0], lc[1], lc[2], lc[3]};
+      ln[mu] -= 1;
+      const int j = half_index(ln, blk);
+      cx<T> p[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) p[k] = src[k * HB + j];
+      const int sb = nb_bwd(g, s, c, mu);
+      switch (mu) {
+        case 0: hop_bwd_p<T, 0>(p, gauge, g.V, sb, T(1), acc); break;
+        case 1: hop_bwd_p<T, 1>(p, gauge, g.V, sb, T(1), acc); break;
+        case 2: hop_bwd_p<T, 2>(p, gauge, g.V, sb, T(1), acc); break;
+        default: hop_bwd_p<T, 3>(p, gauge, g.V, sb, T(1), acc); break;
+      }
+    }
+  }
+}
+
+// y = D_oo^-1 p at odd site s: two general 6x6 complex blocks, 36 float4 /
+// double2-pair chunks per odd site, compact odd index s >> 1
+template <typename T>
+__device__ __forceinline__ void apply_dinv(const T* __restrict__ dinv, long Vh, int s, const cx<T> (&p)[12],
+                                           cx<T> (&y)[12]) {
+  const long so = s >> 1;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      cx<T> m[6];
+      ld_cx<T, 6>(dinv + (long)(h * 6 + i) * 12 * Vh, Vh, so, m);  // row i of block h: 6 complex
+      cx<T> acc = m[0] * p[6 * h];
+#pragma unroll
+      for (int j = 1; j < 6; ++j) cfma(acc, m[j], p[6 * h + j]);
+      y[6 * h + i] = acc;
+    }
+  }
+}
+
+// r = b - D x at site s (full operator, neighbours from global memory; b may be null)
+template <typename T>
+__device__ __forceinline__ void sap_residual_site(const T* __restrict__ x, const T* __restrict__ b,
+                                                  const T* __restrict__ gauge, const T* __restrict__ clover,
+                                                  const Lat& g, int s, const int c[4], T bc, T mu, cx<T> (&r)[12]) {
+  cx<T> acc[12], p[12];
+  all_hops_global<T>(x, gauge, g, s, c, bc, acc);
+  ld_cx<T, 12>(x, g.V, s, p);
+  site_diag<T>(clover, g.V, s, mu, p, r);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) r[i] = T(0.5) * acc[i] - r[i];
+  if (b) {
+    ld_cx<T, 12>(b, g.V, s, p);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) r[i] = r[i] + p[i];
+  }
+}
+
+}  // namespace
+
+template <typename T>
+struct SapOeArgs {
+  const T* gauge;
+  const T* clover;
+  const T* dinv;
+  const T* b;
+  T* x;
+  SapGeom sg;
+  T mu;
+  T bc;
+  int n_mr;
+  int colour;
+  int nrhs;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SapGeom& sg = a.sg;
+  const Lat& g = sg.g;
+  const int HB = sg.bsites / 2;
+  cx<T>* ev = reinterpret_cast<cx<T>*>(smem_raw);  // [12][HB] even-site values (Schur residual, then e_e)
+  cx<T>* od = ev + 12 * HB;                         // [12][HB] odd-site values (D_oo^-1 ...)
+  cx<T>* ro = od + 12 * HB;                         // [12][HB] r_o
+  T* red = reinterpret_cast<T*>(ro + 12 * HB);      // [32 * 3]
+  const int rhs = blockIdx.x % a.nrhs;
+  const long off = (long)rhs * NR_SPINOR * g.V;
+  T* x = a.x + off;
+  const long Vh = g.V / 2;
+
+  int k = blockIdx.x / a.nrhs;
+  const int nbxh = sg.nb[3] / 2;
+  int bc4[4];
+  const int bxh = k % nbxh;
+  k /= nbxh;
+  bc4[2] = k % sg.nb[2];
+  k /= sg.nb[2];
+  bc4[1] = k % sg.nb[1];
+  bc4[0] = k / sg.nb[1];
+  bc4[3] = 2 * bxh + ((bc4[0] + bc4[1] + bc4[2] + a.colour) & 1);
+
+  const int j = threadIdx.x;
+  const bool act = j < HB;
+  // local coordinates of the j-th even (P = 0) and odd (P = 1) site
+  int lce[4], lco[4], ce[4], co[4];
+  int se = 0, so = 0;
+  {
+    int q = act ? j : 0;
+    const int bxh2 = sg.blk[3] / 2;
+    const int xh = q % bxh2;
+    q /= bxh2;
+    lce[2] = q % sg.blk[2];
+    q /= sg.blk[2];
+    lce[1] = q % sg.blk[1];
+    lce[0] = q / sg.blk[1];
+    const int pr = (lce[0] + lce[1] + lce[2]) & 1;
+    lce[3] = 2 * xh + pr;
+    lco[0] = lce[0];
+    lco[1] = lce[1];
+    lco[2] = lce[2];
+    lco[3] = 2 * xh + (pr ^ 1);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      ce[d] = bc4[d] * sg.blk[d] + lce[d];
+      co[d] = bc4[d] * sg.blk[d] + lco[d];
+    }
+    se = ((ce[0] * g.L[1] + ce[1]) * g.L[2] + ce[2]) * g.L[3] + ce[3];
+    so = ((co[0] * g.L[1] + co[1]) * g.L[2] + co[2]) * g.L[3] + co[3];
+  }
+  const T half = T(0.5);
+
+  // r = b - D x on both sites; r_o -> shared, u_o = D_oo^-1 r_o -> shared
+  cx<T> re[12];
+  if (act) {
+    cx<T> p[12], ro_[12];
+    sap_residual_site<T>(x, a.b ? a.b + off : nullptr, a.gauge, a.clover, g, se, ce, a.bc, a.mu, re);
+    sap_residual_site<T>(x, a.b ? a.b + off : nullptr, a.gauge, a.clover, g, so, co, a.bc, a.mu, ro_);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) ro[i * HB + j] = ro_[i];
+    apply_dinv<T>(a.dinv, Vh, so, ro_, p);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) od[i * HB + j] = p[i];
+  }
+  __syncthreads();
+  // Schur right-hand side rho = r_e - D_eo u_o  (D_eo = -1/2 hops)
+  if (act) {
+    cx<T> acc[12];
+    oe_block_hops<T>(od, HB, lce, sg.blk, a.gauge, g, se, ce, acc);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      re[i] = re[i] + half * acc[i];
+      ev[i * HB + j] = re[i];
+    }
+  }
+  cx<T> e[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) e[i] = cx<T>{0, 0};
+  for (int it = 0; it < a.n_mr; ++it) {
+    __syncthreads();
+    // t_o = D_oo^-1 D_oe rho
+    if (act) {
+      cx<T> acc[12], t[12];
+      oe_block_hops<T>(ev, HB, lco, sg.blk, a.gauge, g, so, co, acc);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) acc[i] = -half * acc[i];
+      apply_dinv<T>(a.dinv, Vh, so, acc, t);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) od[i * HB + j] = t[i];
+    }
+    __syncthreads();
+    // q = D_ee rho - D_eo t_o
+    cx<T> q[12];
+    T dots[3] = {0, 0, 0};
+    if (act) {
+      cx<T> acc[12];
+      oe_block_hops<T>(od, HB, lce, sg.blk, a.gauge, g, se, ce, acc);
+      site_diag<T>(a.clover, g.V, se, a.mu, re, q);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) {
+        q[i] = q[i] + half * acc[i];
+        dots[0] = fma(q[i].r, re[i].r, fma(q[i].i, re[i].i, dots[0]));   // Re <q, rho>
+        dots[1] = fma(q[i].r, re[i].i, fma(-q[i].i, re[i].r, dots[1]));  // Im <q, rho>
+        dots[2] = fma(q[i].r, q[i].r, fma(q[i].i, q[i].i, dots[2]));     // <q, q>
+      }
+    }
+    block_allreduce<T, 3>(dots, red);
+    const cx<T> alpha = dots[2] > T(0) ? cx<T>{dots[0] / dots[2], dots[1] / dots[2]} : cx<T>{0, 0};
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < 12; ++i) {
+        cfma(e[i], alpha, re[i]);
+        cfma(re[i], -alpha, q[i]);
+      }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < 12; ++i) ev[i * HB + j] = re[i];
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) ev[i * HB + j] = e[i];
+  }
+  __syncthreads();
+  if (act) {
+    // e_o = D_oo^-1 (r_o - D_oe e_e); x += e
+    cx<T> acc[12], t[12], p[12];
+    oe_block_hops<T>(ev, HB, lco, sg.blk, a.gauge, g, so, co, acc);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) t[i] = ro[i * HB + j] + half * acc[i];
+    apply_dinv<T>(a.dinv, Vh, so, t, acc);
+    ld_cx<T, 12>(x, g.V, so, p);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p[i] = p[i] + acc[i];
+    st_cx<T, 12>(x, g.V, so, p);
+    ld_cx<T, 12>(x, g.V, se, p);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p[i] = p[i] + e[i];
+    st_cx<T, 12>(x, g.V, se, p);
+  }
+}
+
+template <typename T>
+void launch_sap_oe_colour(const T* gauge, const T* clover, const T* dinv, const T* b, T* x, const SapGeom& sg,
+                          double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st) {
+  const int HB = sg.bsites / 2;
+  const int threads = (HB + 31) / 32 * 32;
+  const size_t smem = 3 * 12 * (size_t)HB * sizeof(cx<T>) + 32 * 3 * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_sap_oe<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  const int nblk_colour = sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2;
+  SapOeArgs<T> a{gauge, clover, dinv, b, x, sg, (T)mu, (T)bc_t, n_mr, colour, nrhs};
+  k_sap_oe<T><<<dim3(nblk_colour * nrhs), threads, smem, st>>>(a);
+}
+
+template void launch_sap_oe_colour<double>(const double*, const double*, const double*, const double*, double*,
+                                           const SapGeom&, double, double, int, int, int, cudaStream_t);
+template void launch_sap_oe_colour<float>(const float*, const float*, const float*, const float*, float*,
+                                          const SapGeom&, double, double, int, int, int, cudaStream_t);
+
+// ===========================================================================
+// D_oo^-1 for the odd-even block solve: per odd site the inverses of the two
+// chiral 6x6 blocks A_h(x) + i s_h mu (s_0 = -1, s_1 = +1: gamma5 of the
+// chirality), Gauss-Jordan with partial pivoting in FP64, stored row-major
+// per block as 12 rows of 6 complex, chunked SoA over the V/2 odd sites
+// (compact index s >> 1).
+// ===========================================================================
+namespace {
+template <typename T>
+__global__ void k_clover_inverse(const double* __restrict__ c64, T* __restrict__ dinv, Lat g, double mu, int* err) {
+  const long so = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long Vh = g.V / 2;
+  if (so >= Vh) return;
+  // odd site with compact index so: x-row so / (X/2), x = 2 (so % (X/2)) + parity offset
+  const long row = so / (g.L[3] / 2);
+  const int xh = (int)(so % (g.L[3] / 2));
+  int c[4];
+  c[2] = (int)(row % g.L[2]);
+  c[1] = (int)((row / g.L[2]) % g.L[1]);
+  c[0] = (int)(row / ((long)g.L[2] * g.L[1]));
+  c[3] = 2 * xh + (((c[0] + c[1] + c[2]) & 1) ^ 1);
+  const int s = ((c[0] * g.L[1] + c[1]) * g.L[2] + c[2]) * g.L[3] + c[3];
+  double m72[72];
+  ld_re<double, 72>(c64, g.V, s, m72);
+  for (int h = 0; h < 2; ++h) {
+    cx<double> M[6][12];
+    const double* m = m72 + 36 * h;
+    for (int i = 0; i < 6; ++i)
+      for (int jj = 0; jj < 12; ++jj) M[i][jj] = cx<double>{jj - 6 == i ? 1.0 : 0.0, 0.0};
+    for (int i = 0; i < 6; ++i) M[i][i] = cx<double>{m[i], (h == 0 ? -mu : mu)};
+    int kk = 6;
+    for (int i = 0; i < 6; ++i)
+      for (int jj = i + 1; jj < 6; ++jj) {
+        M[i][jj] = cx<double>{m[kk], m[kk + 1]};
+        M[jj][i] = cx<double>{m[kk], -m[kk + 1]};
+        kk += 2;
+      }
+    for (int col = 0; col < 6; ++col) {
+      int piv = col;
+      double best = norm2(M[col][col]);
+      for (int i = col + 1; i < 6; ++i)
+        if (norm2(M[i][col]) > best) {
+          best = norm2(M[i][col]);
+          piv = i;
+        }
+      if (!(best > 0)) {
+        atomicOr(err, ERRF_SINGULAR);
+        return;
+      }
+      if (piv != col)
+        for (int jj = 0; jj < 12; ++jj) {
+          const cx<double> t = M[col][jj];
+          M[col][jj] = M[piv][jj];
+          M[piv][jj] = t;
+        }
+      const cx<double> pv = M[col][col];
+      const double pn = norm2(pv);
+      const cx<double> inv{pv.r / pn, -pv.i / pn};
+      for (int jj = 0; jj < 12; ++jj) M[col][jj] = inv * M[col][jj];
+      for (int i = 0; i < 6; ++i) {
+        if (i == col) continue;
+        const cx<double> f = M[i][col];
+        for (int jj = 0; jj < 12; ++jj) M[i][jj] = M[i][jj] - f * M[col][jj];
+      }
+    }
+    for (int i = 0; i < 6; ++i) {
+      cx<T> row6[6];
+      for (int jj = 0; jj < 6; ++jj) row6[jj] = cx<T>{(T)M[i][6 + jj].r, (T)M[i][6 + jj].i};
+      st_cx<T, 6>(dinv + (long)(h * 6 + i) * 12 * Vh, Vh, so, row6);
+    }
+  }
+}
+}  // namespace
+
+template <typename T>
+void launch_clover_inverse(const double* c64, T* dinv, const Lat& g, double mu, int* err, cudaStream_t st) {
+  const long Vh = g.V / 2;
+  k_clover_inverse<T><<<(unsigned)((Vh + 63) / 64), 64, 0, st>>>(c64, dinv, g, mu, err);
+}
+template void launch_clover_inverse<double>(const double*, double*, const Lat&, double, int*, cudaStream_t);
+template void launch_clover_inverse<float>(const double*, float*, const Lat&, double, int*, cudaStream_t);
+
 }  // namespace tmamg

@@ -100,6 +100,8 @@ struct tm_handle {
   // links and clover as FP32 pairs for the outer D(mu) z_k (outer_apply = TM_F32X2)
   void* gdf = nullptr;
   void* cdf = nullptr;
+  // (A(x) + i mu gamma5)^-1 at the odd sites for the odd-even SAP block solves (block_oe = 1)
+  void* dinv_sap = nullptr;
   // odd-even Schur complement of the coarsest level on the tensor cores
   bool tc_on = false;
   TcGeom tc{};
@@ -300,13 +302,31 @@ void dslash_df(tm_handle* h, const float* in, double* out, int nrhs) {
 
 template <typename T>
 void sap_sweeps(tm_handle* h, const T* b, T* x, int sweeps, int nrhs) {
+  if (h->p.block_oe && (sizeof(T) == 8) != (h->p.cycle_prec == TM_F64))
+    raise(TM_ERR_ARG, "with block_oe = 1 the SAP smoother runs in cycle_prec");
   for (int s = 0; s < sweeps; ++s)
     for (int colour = 0; colour < 2; ++colour) {
       Prof pf(h, PK_SAP, nrhs);
-      launch_sap_colour<T>(gaugeT<T>(h), cloverT<T>(h), b, x, h->sg, h->p.mu, h->p.bc_t, h->p.mr_iters, colour, nrhs,
-                           h->st);
+      if (h->p.block_oe)
+        launch_sap_oe_colour<T>(gaugeT<T>(h), cloverT<T>(h), static_cast<const T*>(h->dinv_sap), b, x, h->sg,
+                                h->p.mu, h->p.bc_t, h->p.mr_iters, colour, nrhs, h->st);
+      else
+        launch_sap_colour<T>(gaugeT<T>(h), cloverT<T>(h), b, x, h->sg, h->p.mu, h->p.bc_t, h->p.mr_iters, colour,
+                             nrhs, h->st);
       CKL();
     }
+}
+
+// (A(x) + i mu gamma5)^-1 at the odd sites for the odd-even SAP (after a new
+// clover term or a new mu)
+void build_sap_inverse(tm_handle* h) {
+  if (!h->dinv_sap) return;
+  Prof pf(h, PK_OTHER);
+  if (h->p.cycle_prec == TM_F64)
+    launch_clover_inverse<double>(h->c64, static_cast<double*>(h->dinv_sap), h->g, h->p.mu, h->d_err, h->st);
+  else
+    launch_clover_inverse<float>(h->c64, static_cast<float*>(h->dinv_sap), h->g, h->p.mu, h->d_err, h->st);
+  CKL();
 }
 
 // ||x_r||^2 for nrhs vectors -> host
@@ -1547,6 +1567,10 @@ void validate(const tm_params* p) {
     bad("sap1_prec = TM_F16 needs levels = 3 and cycle_prec = TM_F32");
   if (p->outer_apply != TM_F64 && p->outer_apply != TM_F32X2) bad("outer_apply must be TM_F64 or TM_F32X2");
   if (p->outer_apply == TM_F32X2 && p->cycle_prec != TM_F32) bad("outer_apply = TM_F32X2 needs cycle_prec = TM_F32");
+  if (p->block_oe != 0 && p->block_oe != 1) bad("block_oe must be 0 or 1");
+  if (p->block_oe)
+    for (int d = 0; d < 4; ++d)
+      if (p->sap_block[d] % 2) bad("block_oe = 1 needs even SAP block dims");
   if (p->bc_t != 1.0 && p->bc_t != -1.0) bad("bc_t must be +1 or -1");
   if (!(p->delta >= 1.0)) bad("delta must be >= 1");
   if (p->max_rhs < 1) bad("max_rhs must be >= 1");
@@ -1643,6 +1667,10 @@ void solve_core(tm_handle* h, const double* bd, double* xd, int nrhs, double tol
 void apply_mu(tm_handle* h, double mu, double delta) {
   h->p.mu = mu;
   h->p.delta = delta;
+  if (h->gauge_ok) {
+    build_sap_inverse(h);
+    check_flags(h);
+  }
   if (h->setup_ok) {
     Prof pf(h, PK_BUILD, 0, h->tc_on ? 2 : 1);  // no new D_c: zero build units
     void* Dc = h->three ? h->Dc2 : h->Dc;
@@ -1880,7 +1908,7 @@ void tm_destroy(tm_handle* h) {
     if (kv.second.first) cudaFreeHost(kv.second.first);
   void* p3[] = {h->tv1, h->P2, h->Dc2, h->Dinv2, h->d_even2, h->d_odd2, h->d_cidx2,
                 h->tc.even, h->tc.even_lo, h->tc.odd, h->tc.odd_lo, h->tc.nbr_e, h->tc.nbr_o,
-                h->d_nnw, h->d_nngrad, h->Dc1h, h->gdf, h->cdf};
+                h->d_nnw, h->d_nngrad, h->Dc1h, h->gdf, h->cdf, h->dinv_sap};
   for (void* q : p3)
     if (q) cudaFree(q);
   for (auto& r : h->recs) {
@@ -1956,6 +1984,7 @@ tm_status tm_create(tm_handle** out, const tm_params* p, void* stream) {
     h->g32 = static_cast<float*>(dalloc(4L * NR_LINK * V * sizeof(float)));
     h->c64 = static_cast<double*>(dalloc((long)NR_CLOVER * V * sizeof(double)));
     h->c32 = static_cast<float*>(dalloc((long)NR_CLOVER * V * sizeof(float)));
+    if (p->block_oe) h->dinv_sap = dalloc((size_t)(V / 2) * 144 * csize(p->cycle_prec));
     if (p->outer_apply == TM_F32X2) {
       h->gdf = dalloc((size_t)4 * 9 * V * 4 * sizeof(float));
       h->cdf = dalloc((size_t)36 * V * 4 * sizeof(float));
@@ -2065,6 +2094,7 @@ tm_status tm_load_gauge(tm_handle* h, const double* gauge) {
     launch_clover_df(h->c64, h->cdf, h->g, h->st);
     CKL();
   }
+  build_sap_inverse(h);
   h->gauge_ok = false;
   h->setup_ok = false;
   check_flags(h);

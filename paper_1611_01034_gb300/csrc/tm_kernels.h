@@ -50,6 +50,16 @@ template <typename T>
 void launch_sap_colour(const T* gauge, const T* clover, const T* b, T* x, const SapGeom& sg,
                        double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st);
 
+// the same with the block solves on the odd-even Schur complement (Sec. 3);
+// all block dims even; dinv from launch_clover_inverse
+template <typename T>
+void launch_sap_oe_colour(const T* gauge, const T* clover, const T* dinv, const T* b, T* x, const SapGeom& sg,
+                          double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st);
+// dinv [12 rows x 6 complex chunks][V/2] = (A(x) + i mu gamma5)^-1 of the two
+// chiral blocks at every odd site (compact index s >> 1; X even)
+template <typename T>
+void launch_clover_inverse(const double* c64, T* dinv, const Lat& g, double mu, int* err, cudaStream_t st);
+
 // ---- aggregation and coarse operator (coarse.cu) ---------------------------
 // tile shape of the coarse-operator build kernel (0 = default heuristic)
 struct BuildShape {

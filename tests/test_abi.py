@@ -78,6 +78,8 @@ def test_defaults_and_status_strings(lib):
     dict(L=(8, 8, 8, 8), mr_iters=-1),
     dict(L=(8, 8, 8, 8), outer_apply=1),                  # only TM_F64 or TM_F32X2
     dict(L=(8, 8, 8, 8), outer_apply=4, cycle_prec=0),    # FP32 pairs need the FP32 cycle
+    dict(L=(8, 8, 8, 8), block_oe=2),
+    dict(L=(6, 6, 6, 6), agg=(3, 3, 3, 3), sap_block=(3, 3, 3, 3), block_oe=1),  # odd SAP block dims
 ])
 def test_invalid_parameters_rejected_before_any_device_call(lib, bad):
     import paper_1611_01034_gb300 as tm

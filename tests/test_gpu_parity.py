@@ -114,6 +114,27 @@ def test_sap_sweeps(name, prec, tol):
     assert rel(got0, expect0) <= tol
 
 
+OE_CASES = ["c1_4x4x4x4", "8x8x8x8"]  # even SAP block dims
+
+
+@pytest.mark.parametrize("name", OE_CASES)
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-10), (F32, 5e-5)])
+def test_sap_sweeps_odd_even_blocks(name, prec, tol):
+    """SAP with the block solves on the odd-even Schur complement (Sec. 3)
+    against the oracle's SAP.mr_oe; the handle's cycle precision is prec."""
+    U, g, op, seed = _case(name, prec, block_oe=1)
+    blk = CASES[name][8]
+    sap = SAP(op, blk, n_mr=4, block_oe=True)
+    b = inputs.gaussian_spinor(g.L, seed + 11)
+    x0 = 0.1 * inputs.gaussian_spinor(g.L, seed + 12)
+    assert rel(g.sap(b, x0, 2, prec), sap.smooth(b, x0, 2)) <= tol
+    assert rel(g.sap(None, x0, 1, prec), sap.smooth(np.zeros_like(b), x0, 1)) <= tol
+    # the sign of mu reaches the odd-site inverses (tm_set_mu rebuilds them)
+    tm.tm_set_mu(g.h, -op.mu, g.p.delta)
+    sapm = SAP(op.with_mu(-op.mu), blk, n_mr=4, block_oe=True)
+    assert rel(g.sap(b, x0, 1, prec), sapm.smooth(b, x0, 1)) <= tol
+
+
 def _from_vectors(name, prec=F64):
     U, g, op, seed = _case(name, prec)
     tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
@@ -208,6 +229,36 @@ def test_kcycle_fixed_coarse_steps(name, pre):
     got = g.unpack(0, F64, fz, v.shape, 2)
     for r in range(2):
         assert rel(got[r], tl.kcycle(v[r])) <= 1e-10
+
+
+@pytest.mark.parametrize("name", OE_CASES)
+def test_kcycle_odd_even_smoother_fixed_coarse_steps(name):
+    U, g, op, seed = _case(name, F64, coarse_tol=0.0, coarse_maxit=9, pre_smooth=1, post_smooth=2, block_oe=1)
+    tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+    tm.tm_setup_from_vectors(g.h, tv)
+    tl = _oracle_two_level(g, U, name, block_oe=True)
+    tl.sap = SAP(tl.op, tl.prm.sap_block, tl.prm.mr_iters, True)
+    tl.build_coarse(tv)
+    v = inputs.gaussian_spinor(g.L, seed + 31, nrhs=2)
+    fv = g.pack(0, F64, v, 2)
+    fz = g.field(0, F64, 2)
+    tm.tm_kcycle(g.h, F64, fv, fz, 2)
+    got = g.unpack(0, F64, fz, v.shape, 2)
+    for r in range(2):
+        assert rel(got[r], tl.kcycle(v[r])) <= 1e-10
+
+
+@pytest.mark.parametrize("name", OE_CASES)
+def test_solve_with_odd_even_smoother(name):
+    U, g, op, seed = _case(name, F32, setup_iters=2, block_oe=1)
+    tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+    tm.tm_setup(g.h, tv)
+    b = inputs.gaussian_spinor(g.L, seed + 1000, nrhs=2)
+    x = np.zeros_like(b)
+    st, info = tm.tm_solve(g.h, b, x, 2, 1e-10)
+    assert st == tm.TM_OK and info.converged
+    for r in range(2):
+        assert np.linalg.norm(b[r] - op.apply(x[r])) / np.linalg.norm(b[r]) <= 1e-10
 
 
 @pytest.mark.parametrize("name", ["c1_4x4x4x4", "ragged_4x6x4x10"])
