@@ -309,14 +309,23 @@ struct SapOeArgs {
   int nrhs;
 };
 
+// The kernel walks 2 n_MR + 3 half-steps, odd and even alternating, so that the
+// hop gather, D_oo^-1 and the site-diagonal term each appear once in the code
+// (the instruction cache holds the loop):
+//   step 0 (odd):            u_o = D_oo^-1 r_o
+//   step 1 (even):           rho = r_e - D_eo u_o
+//   step 2k (odd, k >= 1):   t_o = D_oo^-1 D_oe rho
+//   step 2k+1 (even):        q = D_ee rho - D_eo t_o; MR update of e_e, rho
+//   step 2 n_MR + 2 (odd):   e_o = D_oo^-1 (r_o - D_oe e_e); x += e
+// (D_eo, D_oe = -1/2 times the intra-block hops.)
 template <typename T>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SapGeom& sg = a.sg;
   const Lat& g = sg.g;
   const int HB = sg.bsites / 2;
-  cx<T>* ev = reinterpret_cast<cx<T>*>(smem_raw);  // [12][HB] even-site values (Schur residual, then e_e)
-  cx<T>* od = ev + 12 * HB;                         // [12][HB] odd-site values (D_oo^-1 ...)
+  cx<T>* ev = reinterpret_cast<cx<T>*>(smem_raw);  // [12][HB] even-site values (rho, then e_e)
+  cx<T>* od = ev + 12 * HB;                         // [12][HB] odd-site values (u_o, t_o)
   cx<T>* ro = od + 12 * HB;                         // [12][HB] r_o
   T* red = reinterpret_cast<T*>(ro + 12 * HB);      // [32 * 3]
   const int rhs = blockIdx.x % a.nrhs;
@@ -337,9 +346,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArg
 
   const int j = threadIdx.x;
   const bool act = j < HB;
-  // local coordinates of the j-th even (P = 0) and odd (P = 1) site
-  int lce[4], lco[4], ce[4], co[4];
-  int se = 0, so = 0;
+  // block-local coordinates of the j-th even site; the j-th odd site differs in x only
+  int lce[4];
+  int pr;
   {
     int q = act ? j : 0;
     const int bxh2 = sg.blk[3] / 2;
@@ -349,112 +358,116 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArg
     q /= sg.blk[2];
     lce[1] = q % sg.blk[1];
     lce[0] = q / sg.blk[1];
-    const int pr = (lce[0] + lce[1] + lce[2]) & 1;
+    pr = (lce[0] + lce[1] + lce[2]) & 1;
     lce[3] = 2 * xh + pr;
-    lco[0] = lce[0];
-    lco[1] = lce[1];
-    lco[2] = lce[2];
-    lco[3] = 2 * xh + (pr ^ 1);
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      ce[d] = bc4[d] * sg.blk[d] + lce[d];
-      co[d] = bc4[d] * sg.blk[d] + lco[d];
-    }
-    se = ((ce[0] * g.L[1] + ce[1]) * g.L[2] + ce[2]) * g.L[3] + ce[3];
-    so = ((co[0] * g.L[1] + co[1]) * g.L[2] + co[2]) * g.L[3] + co[3];
   }
+  auto site_of = [&](int parity, int (&lc)[4], int (&c)[4]) {
+    lc[0] = lce[0];
+    lc[1] = lce[1];
+    lc[2] = lce[2];
+    lc[3] = lce[3] - pr + (pr ^ parity);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) c[d] = bc4[d] * sg.blk[d] + lc[d];
+    return ((c[0] * g.L[1] + c[1]) * g.L[2] + c[2]) * g.L[3] + c[3];
+  };
   const T half = T(0.5);
 
-  // r = b - D x on both sites; r_o -> shared, u_o = D_oo^-1 r_o -> shared
-  cx<T> re[12];
-  if (act) {
-    cx<T> p[12], ro_[12];
-    sap_residual_site<T>(x, a.b ? a.b + off : nullptr, a.gauge, a.clover, g, se, ce, a.bc, a.mu, re);
-    sap_residual_site<T>(x, a.b ? a.b + off : nullptr, a.gauge, a.clover, g, so, co, a.bc, a.mu, ro_);
+  // r = b - D x on the odd (pass 0, -> shared r_o) and the even site (pass 1, -> rho)
+  cx<T> rho[12];
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    if (act) {
+      int lc[4], c[4];
+      const int s = site_of(pass ^ 1, lc, c);
+      sap_residual_site<T>(x, a.b ? a.b + off : nullptr, a.gauge, a.clover, g, s, c, a.bc, a.mu, rho);
+      if (pass == 0) {
 #pragma unroll
-    for (int i = 0; i < 12; ++i) ro[i * HB + j] = ro_[i];
-    apply_dinv<T>(a.dinv, Vh, so, ro_, p);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) od[i * HB + j] = p[i];
-  }
-  __syncthreads();
-  // Schur right-hand side rho = r_e - D_eo u_o  (D_eo = -1/2 hops)
-  if (act) {
-    cx<T> acc[12];
-    oe_block_hops<T>(od, HB, lce, sg.blk, a.gauge, g, se, ce, acc);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      re[i] = re[i] + half * acc[i];
-      ev[i * HB + j] = re[i];
+        for (int i = 0; i < 12; ++i) ro[i * HB + j] = rho[i];
+      }
     }
   }
   cx<T> e[12];
 #pragma unroll
   for (int i = 0; i < 12; ++i) e[i] = cx<T>{0, 0};
-  for (int it = 0; it < a.n_mr; ++it) {
+  const int nsteps = 2 * a.n_mr + 3;
+#pragma unroll 1
+  for (int st = 0; st < nsteps; ++st) {
+    const int parity = (st & 1) ^ 1;  // even steps work on odd sites
     __syncthreads();
-    // t_o = D_oo^-1 D_oe rho
-    if (act) {
-      cx<T> acc[12], t[12];
-      oe_block_hops<T>(ev, HB, lco, sg.blk, a.gauge, g, so, co, acc);
+    cx<T> acc[12];
+    int lc[4], c[4];
+    const int s = site_of(parity, lc, c);
+    if (act && st > 0) oe_block_hops<T>(parity ? ev : od, HB, lc, sg.blk, a.gauge, g, s, c, acc);
+    if (parity) {
+      // odd site: y = D_oo^-1 in
+      if (act) {
+        cx<T> in[12], y[12];
+        const bool last = st == nsteps - 1;
 #pragma unroll
-      for (int i = 0; i < 12; ++i) acc[i] = -half * acc[i];
-      apply_dinv<T>(a.dinv, Vh, so, acc, t);
+        for (int i = 0; i < 12; ++i) {
+          if (st == 0)
+            in[i] = ro[i * HB + j];
+          else if (last)
+            in[i] = ro[i * HB + j] + half * acc[i];
+          else
+            in[i] = -half * acc[i];
+        }
+        apply_dinv<T>(a.dinv, Vh, s, in, y);
+        if (!last) {
 #pragma unroll
-      for (int i = 0; i < 12; ++i) od[i * HB + j] = t[i];
-    }
-    __syncthreads();
-    // q = D_ee rho - D_eo t_o
-    cx<T> q[12];
-    T dots[3] = {0, 0, 0};
-    if (act) {
-      cx<T> acc[12];
-      oe_block_hops<T>(od, HB, lce, sg.blk, a.gauge, g, se, ce, acc);
-      site_diag<T>(a.clover, g.V, se, a.mu, re, q);
+          for (int i = 0; i < 12; ++i) od[i * HB + j] = y[i];
+        } else {
+          // x_o += e_o, x_e += e_e
+          cx<T> p[12];
+          ld_cx<T, 12>(x, g.V, s, p);
 #pragma unroll
-      for (int i = 0; i < 12; ++i) {
-        q[i] = q[i] + half * acc[i];
-        dots[0] = fma(q[i].r, re[i].r, fma(q[i].i, re[i].i, dots[0]));   // Re <q, rho>
-        dots[1] = fma(q[i].r, re[i].i, fma(-q[i].i, re[i].r, dots[1]));  // Im <q, rho>
-        dots[2] = fma(q[i].r, q[i].r, fma(q[i].i, q[i].i, dots[2]));     // <q, q>
+          for (int i = 0; i < 12; ++i) p[i] = p[i] + y[i];
+          st_cx<T, 12>(x, g.V, s, p);
+          int lc2[4], c2[4];
+          const int s2 = site_of(0, lc2, c2);
+          ld_cx<T, 12>(x, g.V, s2, p);
+#pragma unroll
+          for (int i = 0; i < 12; ++i) p[i] = p[i] + e[i];
+          st_cx<T, 12>(x, g.V, s2, p);
+        }
+      }
+    } else {
+      const int kk = (st - 1) / 2;  // MR steps done before this one
+      if (st == 1) {
+        if (act) {
+#pragma unroll
+          for (int i = 0; i < 12; ++i) rho[i] = rho[i] + half * acc[i];
+        }
+      } else {
+        cx<T> q[12];
+        T dots[3] = {0, 0, 0};
+        if (act) {
+          site_diag<T>(a.clover, g.V, s, a.mu, rho, q);
+#pragma unroll
+          for (int i = 0; i < 12; ++i) {
+            q[i] = q[i] + half * acc[i];
+            dots[0] = fma(q[i].r, rho[i].r, fma(q[i].i, rho[i].i, dots[0]));   // Re <q, rho>
+            dots[1] = fma(q[i].r, rho[i].i, fma(-q[i].i, rho[i].r, dots[1]));  // Im <q, rho>
+            dots[2] = fma(q[i].r, q[i].r, fma(q[i].i, q[i].i, dots[2]));       // <q, q>
+          }
+        }
+        block_allreduce<T, 3>(dots, red);
+        const cx<T> alpha = dots[2] > T(0) ? cx<T>{dots[0] / dots[2], dots[1] / dots[2]} : cx<T>{0, 0};
+        if (act) {
+#pragma unroll
+          for (int i = 0; i < 12; ++i) {
+            cfma(e[i], alpha, rho[i]);
+            cfma(rho[i], -alpha, q[i]);
+          }
+        }
+      }
+      // the next odd step gathers rho, or e_e after the last MR step (step 2 n_MR + 1)
+      if (act) {
+        const bool store_e = kk == a.n_mr;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) ev[i * HB + j] = store_e ? e[i] : rho[i];
       }
     }
-    block_allreduce<T, 3>(dots, red);
-    const cx<T> alpha = dots[2] > T(0) ? cx<T>{dots[0] / dots[2], dots[1] / dots[2]} : cx<T>{0, 0};
-    if (act) {
-#pragma unroll
-      for (int i = 0; i < 12; ++i) {
-        cfma(e[i], alpha, re[i]);
-        cfma(re[i], -alpha, q[i]);
-      }
-    }
-    __syncthreads();
-    if (act) {
-#pragma unroll
-      for (int i = 0; i < 12; ++i) ev[i * HB + j] = re[i];
-    }
-  }
-  __syncthreads();
-  if (act) {
-#pragma unroll
-    for (int i = 0; i < 12; ++i) ev[i * HB + j] = e[i];
-  }
-  __syncthreads();
-  if (act) {
-    // e_o = D_oo^-1 (r_o - D_oe e_e); x += e
-    cx<T> acc[12], t[12], p[12];
-    oe_block_hops<T>(ev, HB, lco, sg.blk, a.gauge, g, so, co, acc);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) t[i] = ro[i * HB + j] + half * acc[i];
-    apply_dinv<T>(a.dinv, Vh, so, t, acc);
-    ld_cx<T, 12>(x, g.V, so, p);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) p[i] = p[i] + acc[i];
-    st_cx<T, 12>(x, g.V, so, p);
-    ld_cx<T, 12>(x, g.V, se, p);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) p[i] = p[i] + e[i];
-    st_cx<T, 12>(x, g.V, se, p);
   }
 }
 
