@@ -9,7 +9,8 @@ separately, as the paper separates setup and solve costs (Fig. 1).
 
 Default workload: 48^3 x 96, U = exp(0.6 i H), c_sw = 1.57551, mu = 0.0009,
 delta = 5, three levels (N_v = 24 on 4^4 aggregates, then N_v2 = 28 on 2^4
-level-1 aggregates; SAP blocks 4^4 and 2^4), 3 + 3 setup iterations, the 12
+level-1 aggregates; SAP blocks 4^4 with odd-even block solves as in Sec. 3,
+and 2^4 on level 1), 3 + 3 setup iterations, the 12
 spin-colour point sources at one random site, solved in 3 steps of 4 (the
 FGMRES(8) basis of 4 right-hand sides is what fits next to the setup data in
 the 280 GB).  m0 from inputs/m0_tuned.json (near-critical).  Every field of
@@ -52,7 +53,7 @@ WORKLOADS = {
         L=(96, 48, 48, 48), eps=0.6, seed=1, c_sw=1.57551, mu=0.0009, delta=5.0, nv=24,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, nrhs=12, point=True,
         levels=3, nv2=28, agg2=(2, 2, 2, 2), sap_block1=(2, 2, 2, 2), coarse_setup_iters=3,
-        restart=8, rhs_batch=4, coarse_mma=1, sap1_prec=2, outer_apply=TM_F32X2,
+        restart=8, rhs_batch=4, coarse_mma=1, sap1_prec=2, outer_apply=TM_F32X2, block_oe=1,
         m0_key="16x16x16x32_eps0.6_seed1_csw1.57551", device_inputs=True),
     "16x16x16x32_2lvl_nv20": dict(
         L=(32, 16, 16, 16), eps=0.5, seed=1, c_sw=1.5, mu=0.003, delta=5.0, nv=20,
@@ -601,7 +602,7 @@ def main_native(args):
 
     stream = torch.cuda.current_stream()
     extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec",
-                                "outer_apply") if k in wl}
+                                "outer_apply", "block_oe") if k in wl}
     extra["coarse_mma"] = args.coarse_mma if args.coarse_mma is not None else wl.get("coarse_mma", 0)
     for kv in args.param or []:  # solver-parameter overrides, e.g. --param coarse_tol=0.02
         k, v = kv.split("=", 1)
@@ -787,7 +788,7 @@ def main_native(args):
                 "sap1_prec": "f16" if p.sap1_prec == 2 else "f32"} if levels == 3 else {}),
             "nv": nv, "aggregate": list(wl["agg"]), "sap_block": list(wl["sap_block"]),
             "restart": p.restart, "coarse_tol": p.coarse_tol, "post_smooth": p.post_smooth, "mr_iters": p.mr_iters,
-            "coarse_mma": p.coarse_mma, "outer_apply": oa,
+            "coarse_mma": p.coarse_mma, "outer_apply": oa, "block_oe": p.block_oe,
             "m0": m0, "m0_source": m0_src, "c_sw": wl["c_sw"], "mu": wl["mu"], "delta": wl["delta"],
             "setup_iters": wl["setup_iters"], "tol": wl["tol"], "rhs_total": nrhs, "rhs_per_step": R,
             "rhs": "12 spin-colour point sources" if wl.get("point") else "Gaussian",
