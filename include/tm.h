@@ -148,6 +148,12 @@ typedef struct {
      and keeps (A(x) + i mu gamma5)^-1 of every odd site (144 reals per odd
      site in cycle_prec); SAP then runs in cycle_prec only. */
   int block_oe;
+  /* Polls of each pipeline mbarrier wait in the tensor-core kernel before it
+     gives up (0 = the default, 2^22).  On a timeout the kernel drains its
+     copies and MMAs, frees its tensor memory and the call returns
+     TM_ERR_TIMEOUT; the context stays usable.  Small values exist to test that
+     path. */
+  int tc_spin_limit;
 } tm_params;
 
 typedef struct {
@@ -166,7 +172,7 @@ typedef struct {
  * agg2 = sap_block1 = 2^4, mr_iters1 = 4, pre_smooth1 = 0, post_smooth1 = 2,
  * init_sweeps1 = 3, coarse_setup_iters = 3, coarsest_tol = 5e-2,
  * coarsest_maxit = 200, coarse_mma = 0, nn_mode = 0, nn_prec = TM_F32,
- * sap1_prec = TM_F32, outer_apply = TM_F64, block_oe = 0.
+ * sap1_prec = TM_F32, outer_apply = TM_F64, block_oe = 0, tc_spin_limit = 0.
  * L, m0, c_sw, mu are 0. */
 void tm_params_default(tm_params* p);
 

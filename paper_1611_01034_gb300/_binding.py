@@ -28,7 +28,7 @@ class tm_params(ctypes.Structure):
         ("mr_iters1", c_int), ("pre_smooth1", c_int), ("post_smooth1", c_int), ("init_sweeps1", c_int),
         ("coarse_setup_iters", c_int), ("coarsest_tol", c_double), ("coarsest_maxit", c_int),
         ("coarse_mma", c_int), ("nn_mode", c_int), ("nn_prec", c_int), ("sap1_prec", c_int),
-        ("outer_apply", c_int), ("block_oe", c_int),
+        ("outer_apply", c_int), ("block_oe", c_int), ("tc_spin_limit", c_int),
     ]
 
 

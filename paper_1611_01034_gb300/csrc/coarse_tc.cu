@@ -70,9 +70,11 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait on phase `parity`; false on timeout or when another warp aborted
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+// bounded wait on phase `parity` (at most `limit` polls); false on timeout or
+// when another warp aborted
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort,
+                                          uint32_t limit = kSpinLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_test(b, parity)) return true;
     if ((it & 255u) == 255u && *abort) return false;
   }
@@ -164,6 +166,7 @@ struct TcArgs {
   const int* active;      // rhs mask (null: all)
   int ntgt, nt, n, nv, kp, mp, R, rp, split, stages;
   int* err;
+  uint32_t spin;          // polls per pipeline wait before giving up (the drain waits use kSpinLimit)
 };
 
 struct TcShared {
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
       for (int k = blockIdx.x; k < a.ntgt && ok; k += gridDim.x)
         for (int t = 0; t < a.nt && ok; ++t, ++g) {
           const int s = (int)(g % S);
-          if (!mbar_wait(&sh.empty[s], (uint32_t)((g / S) & 1) ^ 1u, abort)) {
+          if (!mbar_wait(&sh.empty[s], (uint32_t)((g / S) & 1) ^ 1u, abort, a.spin)) {
             ok = false;
             break;
           }
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
       bool ok = true;
       for (int k = blockIdx.x; k < a.ntgt && ok; k += gridDim.x, ++j) {
         const int slot = j & 1;
-        if (!mbar_wait(&sh.tempty[slot], (uint32_t)((j >> 1) & 1) ^ 1u, abort)) {
+        if (!mbar_wait(&sh.tempty[slot], (uint32_t)((j >> 1) & 1) ^ 1u, abort, a.spin)) {
           ok = false;
           break;
         }
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
         for (int t = 0; t < a.nt; ++t, ++g) {
           const int s = (int)(g % S);
           const uint32_t par = (uint32_t)((g / S) & 1);
-          if (!mbar_wait(&sh.full_b[s], par, abort)) {  // the gather warp saw the tile land
+          if (!mbar_wait(&sh.full_b[s], par, abort, a.spin)) {  // the gather warp saw the tile land
             ok = false;
             break;
           }
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
       const int k = blockIdx.x + jl * gridDim.x;
       const int j = a.nbr[(long)k * a.nt + t];
       const int s = (int)(g % S);
-      if (!mbar_wait(&sh.empty[s], (uint32_t)((g / S) & 1) ^ 1u, abort)) {
+      if (!mbar_wait(&sh.empty[s], (uint32_t)((g / S) & 1) ^ 1u, abort, a.spin)) {
         ok = false;
         break;
       }
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
       __syncwarp();
       if (lane == 0) {
         // the stage is ready once its operator tile has landed as well
-        if (!mbar_wait(&sh.full_a[s], (uint32_t)((g / S) & 1), abort)) ok = false;
+        if (!mbar_wait(&sh.full_a[s], (uint32_t)((g / S) & 1), abort, a.spin)) ok = false;
         else mbar_arrive(&sh.full_b[s]);
       }
       if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs a) {
     bool ok = true;
     for (int k = blockIdx.x; k < a.ntgt; k += gridDim.x, ++j) {
       const int slot = j & 1;
-      if (!mbar_wait(&sh.tfull[slot], (uint32_t)((j >> 1) & 1), abort)) {
+      if (!mbar_wait(&sh.tfull[slot], (uint32_t)((j >> 1) & 1), abort, a.spin)) {
         ok = false;
         break;
       }
@@ -559,8 +562,9 @@ void tc_build_odd(const float* Dc, const float* Dinv, const OEGeom& oe, const Tc
 
 void launch_tc_schur(const TcGeom& tg, const OEGeom& oe, const float* ve, float* uo, float* ye, double mu_c,
                      int nrhs, long vstr, long ustr, long ystr, const int* active, int split, int* err,
-                     cudaStream_t st) {
+                     cudaStream_t st, unsigned spin) {
   TcArgs a{};
+  a.spin = spin ? spin : kSpinLimit;
   a.n = 2 * oe.nv;
   a.nv = oe.nv;
   a.kp = tg.kp;

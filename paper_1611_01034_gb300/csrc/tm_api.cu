@@ -658,7 +658,8 @@ std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x,
     Prof pf(h, PK_COARSE_OE, units, 2);
     if constexpr (std::is_same<T, float>::value) {
       if (use_tc) {
-        launch_tc_schur(*lv.tc, lv.oe, v, uo, w, mc, nrhs, vs, cv, cv, act, h->p.coarse_mma, h->d_err, h->st);
+        launch_tc_schur(*lv.tc, lv.oe, v, uo, w, mc, nrhs, vs, cv, cv, act, h->p.coarse_mma, h->d_err, h->st,
+                        (unsigned)h->p.tc_spin_limit);
         CKL();
         return;
       }
@@ -1567,6 +1568,7 @@ void validate(const tm_params* p) {
     bad("sap1_prec = TM_F16 needs levels = 3 and cycle_prec = TM_F32");
   if (p->outer_apply != TM_F64 && p->outer_apply != TM_F32X2) bad("outer_apply must be TM_F64 or TM_F32X2");
   if (p->outer_apply == TM_F32X2 && p->cycle_prec != TM_F32) bad("outer_apply = TM_F32X2 needs cycle_prec = TM_F32");
+  if (p->tc_spin_limit < 0) bad("tc_spin_limit must be >= 0");
   if (p->block_oe != 0 && p->block_oe != 1) bad("block_oe must be 0 or 1");
   if (p->block_oe)
     for (int d = 0; d < 4; ++d)
@@ -2591,7 +2593,8 @@ tm_status tm_schur(tm_handle* h, int prec, const void* ve, void* ye, int nrhs) {
     float* uo = W<float>(h, "sch_uo", cv * nrhs);
     if (lv.tc && tc_supported(lv.oe.nv, nrhs, h->p.coarse_mma))
       launch_tc_schur(*lv.tc, lv.oe, static_cast<const float*>(ve), uo, static_cast<float*>(ye), lv.mu_c, nrhs, cv, cv,
-                      cv, nullptr, h->p.coarse_mma, h->d_err, h->st);
+                      cv, nullptr, h->p.coarse_mma, h->d_err, h->st,
+                      (unsigned)h->p.tc_spin_limit);
     else
       launch_oe_schur_b<float>(static_cast<const float*>(lv.Dc), static_cast<const float*>(lv.Dinv),
                                static_cast<const float*>(ve), uo, static_cast<float*>(ye), lv.oe, lv.mu_c, nrhs, cv,

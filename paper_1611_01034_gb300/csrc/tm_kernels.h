@@ -196,10 +196,11 @@ bool tc_supported(int nv, int nrhs, int split);
 void tc_build(const float* Dc, const float* Dinv, const OEGeom& oe, const TcGeom& tg, cudaStream_t st);
 // odd tiles only (they carry D_oo^-1, so they follow mu)
 void tc_build_odd(const float* Dc, const float* Dinv, const OEGeom& oe, const TcGeom& tg, cudaStream_t st);
-// ye = S ve for nrhs compact even vectors (uo: odd work vectors); `split` TF32 products
+// ye = S ve for nrhs compact even vectors (uo: odd work vectors); `split` TF32 products;
+// `spin` polls per pipeline wait before the kernel gives up (0: the default limit)
 void launch_tc_schur(const TcGeom& tg, const OEGeom& oe, const float* ve, float* uo, float* ye, double mu_c,
                      int nrhs, long vstr, long ustr, long ystr, const int* active, int split, int* err,
-                     cudaStream_t st);
+                     cudaStream_t st, unsigned spin = 0);
 
 // ---- learned gauge-covariant layer (nn.cu) ------------------------------------
 // weights: complex float2 [Cout][Cin][9 directions][4][4]; hidden fields

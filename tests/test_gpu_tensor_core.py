@@ -134,3 +134,23 @@ def test_solves_with_tensor_core_coarse_solve(mma):
     st0, info0 = tm.tm_solve(g0.h, b, x0, 3, 1e-10)
     assert st0 == tm.TM_OK
     assert info.iters <= 1.5 * info0.iters + 3
+
+
+def test_bounded_waits_time_out_cleanly():
+    """A tensor-core Schur application whose pipeline waits may poll only once
+    gives up: the call returns TM_ERR_TIMEOUT (the kernel drained its copies and
+    MMAs and freed its tensor memory), the handle keeps working, and a fresh
+    handle on the same GPU still matches the oracle on the tensor cores."""
+    g, U, op, tv, oe, seed = _two_level("8x8x8x8_nv24", 1, tc_spin_limit=1)
+    n = 2 * g.nv
+    with pytest.raises(tm.TMError) as e:
+        _schur_case(g, oe, g.Lc, n, 12, seed + 700)
+    assert e.value.status == tm.TM_ERR_TIMEOUT
+    # the handle keeps working: the coarse operator on the CUDA cores
+    v = inputs.random_coarse_vectors(g.Lc, n, 1, seed + 701).reshape(g.Lc + (n,))
+    fo = g.field(1, F32)
+    tm.tm_apply(g.h, 1, F32, g.pack(1, F32, v), fo, 1)
+    assert rel(g.unpack(1, F32, fo, v.shape), oe.Dc.apply(v)) <= 1e-5
+    g2, *_ = _two_level("8x8x8x8_nv24", 1)
+    got, expect = _schur_case(g2, oe, g2.Lc, n, 12, seed + 702)
+    assert max(rel(got[r], expect[r]) for r in range(12)) <= TOL[1]
