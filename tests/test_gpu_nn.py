@@ -163,3 +163,45 @@ def test_solve_with_stage_after_kcycle(mode, prec):
     op = Operator(U, -0.3, 1.5, 0.01)
     for k in range(2):
         assert np.linalg.norm(b[k] - op.apply(x[k])) / np.linalg.norm(b[k]) <= 1e-10
+
+
+def test_adam_steps_match_numpy_restatement():
+    """tm_nn_train's update, restated in numpy: Adam (beta1 0.9, beta2 0.999,
+    eps 1e-8, bias-corrected) on the real and imaginary parts of every weight
+    with the steepest-descent direction 2 dL/d conj(W) of each minibatch, in
+    order.  The restatement is fed the library's own minibatch gradients
+    (tm_nn_grad at the restated weights; those gradients are checked against
+    the oracle above), so the comparison isolates the update rule."""
+    L = (4, 4, 4, 4)
+    U, g = _handle(L, 61)
+    _, g_ref = _handle(L, 61)
+    W1, W2 = _weights(62, 0.05)
+    w = nn.pack_weights(W1, W2)
+    npairs, batch, epochs, lr = 8, 3, 2, 2e-3
+    R = _fields(L, npairs, 63)
+    E = _fields(L, npairs, 64)
+    fr, fe = g.pack(0, F32, R, npairs), g.pack(0, F32, E, npairs)
+    tm.tm_nn_set_weights(g.h, w)
+    tm.tm_nn_train(g.h, fr, fe, npairs, epochs, batch, lr)
+    got = tm.tm_nn_get_weights(g.h)
+    fb = tm.tm_field_bytes(g.h, 0, F32, 1)
+    m = np.zeros(2 * w.size)
+    v = np.zeros(2 * w.size)
+    t = 0
+    b1, b2, eps = 0.9, 0.999, 1e-8
+    for _ in range(epochs):
+        for p0 in range(0, npairs, batch):
+            nb = min(batch, npairs - p0)
+            tm.tm_nn_set_weights(g_ref.h, w)
+            _, G = tm.tm_nn_grad(g_ref.h, fr[p0 * fb:(p0 + nb) * fb], fe[p0 * fb:(p0 + nb) * fb], nb)
+            gr = np.empty(2 * w.size)
+            gr[0::2], gr[1::2] = 2 * G.real, 2 * G.imag
+            t += 1
+            m = b1 * m + (1 - b1) * gr
+            v = b2 * v + (1 - b2) * gr * gr
+            upd = lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+            w = w - (upd[0::2] + 1j * upd[1::2])
+    assert t == 6
+    assert rel(got, w) <= 1e-12
+    # and the update moved the weights by about lr per component and step
+    assert rel(got, nn.pack_weights(W1, W2)) > 1e-3

@@ -48,6 +48,29 @@ def test_noalloc_coarse_solve_matches_existing(prec, tol):
     g.close()
 
 
+def test_noalloc_coarse_solve_allocates_no_device_memory():
+    """After a first call (which may load kernels and looks up the array's
+    address), further calls leave the device's free memory unchanged: no
+    workspace of the handle grows and nothing else is allocated."""
+    L = (8, 8, 8, 8)
+    U = inputs.gauge_field(L, 0.5, 5)
+    g = GPU(U, m0=-0.4, c_sw=1.5, mu=0.005, delta=5.0, nv=8, agg=(4, 4, 4, 4),
+            sap_block=(4, 4, 4, 4), cycle_prec=tm.TM_F32, coarse_restart=10)
+    tm.tm_setup_from_vectors(g.h, inputs.random_test_vectors(L, 8, 2005))
+    rng = np.random.default_rng(19)
+    b = rng.standard_normal(g.coarse_shape()) + 1j * rng.standard_normal(g.coarse_shape())
+    fb = g.pack(1, tm.TM_F32, b)
+    fx = g.field(1, tm.TM_F32)
+    tm.tm_coarse_solve_noalloc(g.h, tm.TM_F32, fb, fx, 1e-8, 200)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        tm.tm_coarse_solve_noalloc(g.h, tm.TM_F32, fb, fx, 1e-8, 200)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    g.close()
+
+
 def test_noalloc_rejects_systems_beyond_its_array():
     # 16^3 x 32 with N_v = 28, restart 120, FP64: the Krylov basis alone is ~28 MB
     p = tm.params(L=(32, 16, 16, 16), nv=28, agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4),
