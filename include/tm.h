@@ -272,6 +272,33 @@ tm_status tm_solve(tm_handle* h, const double* b, double* x, int nrhs, double to
  * handle is left at +mu. */
 tm_status tm_solve_squared(tm_handle* h, const double* b, double* x, int nrhs, double tol, tm_solve_info* info);
 
+/* Device memory a handle with parameters p needs, in bytes: what tm_create
+ * allocates, plus the larger of the adaptive setup's work (with device
+ * test vectors) and the work of tm_solve with nrhs right-hand sides (batched
+ * up to max_rhs).  For planning before anything is allocated (a 48^3 x 96
+ * three-level handle needs well over 100 GB); inputs passed as host arrays
+ * add a device copy of their size.  0 for invalid parameters. */
+size_t tm_workspace_bytes(const tm_params* p, int nrhs);
+
+/* Save the setup of a handle (test vectors, P and D_c; with three levels also
+ * the level-1 test vectors, P2 and D_c2, in the handle's device layout and
+ * cycle precision) to a file, with a header of the lattice, aggregates, N_v,
+ * levels and precision; the file is written through `path`.tmp and renamed.
+ * Sec. 3: one setup serves many inversions and, updated, the next gauge
+ * fields of an HMC trajectory.  Errors: TM_ERR_STATE (no setup), TM_ERR_ARG
+ * (file not writable). */
+tm_status tm_save_setup(tm_handle* h, const char* path);
+
+/* Load a saved setup into a handle created with the same lattice, aggregates,
+ * N_v (N_v2, agg2) and cycle_prec, after tm_load_gauge.  The odd-site
+ * inverses (current mu and delta), the FP16 level-1 blocks and the
+ * tensor-core tiles are rebuilt from the loaded D_c.  A solve after loading
+ * reproduces a solve with the saved handle's setup bit for bit on the same
+ * gauge field; with another field follow with tm_setup_update.  Errors:
+ * TM_ERR_STATE (no gauge field), TM_ERR_ARG (unreadable or foreign file,
+ * other sizes). */
+tm_status tm_load_setup(tm_handle* h, const char* path);
+
 /* Bytes of one field of nrhs vectors: level 0 = fine spinors, level 1 =
  * coarse vectors; prec TM_F64 or TM_F32.  0 for invalid arguments. */
 size_t tm_field_bytes(const tm_handle* h, int level, int prec, int nrhs);

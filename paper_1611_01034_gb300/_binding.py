@@ -64,6 +64,9 @@ _SIGS = {
     "tm_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
     "tm_solve_squared": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
     "tm_field_bytes": (c_size_t, [c_void_p, c_int, c_int, c_int]),
+    "tm_workspace_bytes": (c_size_t, [POINTER(tm_params), c_int]),
+    "tm_save_setup": (c_int, [c_void_p, c_char_p]),
+    "tm_load_setup": (c_int, [c_void_p, c_char_p]),
     "tm_pack": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
     "tm_unpack": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
     "tm_apply": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),
@@ -221,6 +224,18 @@ def tm_solve_squared(h, b, x, nrhs: int, tol: float):
 
 def tm_field_bytes(h, level: int, prec: int, nrhs: int) -> int:
     return int(lib().tm_field_bytes(h, level, prec, nrhs))
+
+
+def tm_workspace_bytes(p: tm_params, nrhs: int = 1) -> int:
+    return int(lib().tm_workspace_bytes(ctypes.byref(p), nrhs))
+
+
+def tm_save_setup(h, path: str) -> None:
+    _check(lib().tm_save_setup(h, os.fsencode(path)), h)
+
+
+def tm_load_setup(h, path: str) -> None:
+    _check(lib().tm_load_setup(h, os.fsencode(path)), h)
 
 
 def tm_pack(h, level, prec, natural, field, nrhs) -> None:

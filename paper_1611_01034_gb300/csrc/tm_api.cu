@@ -1691,6 +1691,80 @@ void apply_mu(tm_handle* h, double mu, double delta) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// memory plan (tm_workspace_bytes): what tm_create, tm_setup and tm_solve
+// allocate on the device for given parameters
+// ---------------------------------------------------------------------------
+struct MemPlan {
+  double persistent = 0, setup = 0, solve = 0;
+};
+
+MemPlan memory_plan(const tm_params* p, int nrhs) {
+  MemPlan m;
+  const double V = (double)p->L[0] * p->L[1] * p->L[2] * p->L[3];
+  double a1 = 1, a2 = 1;
+  for (int d = 0; d < 4; ++d) a1 *= p->agg[d];
+  const double Vc = V / a1;
+  const double n = 2.0 * p->nv;
+  const double cs = p->cycle_prec == TM_F64 ? 8 : 4;
+  const double fr = 24 * V;  // reals of a fine field
+  const bool three = p->levels == 3;
+  double V2 = 0, n2 = 0;
+  if (three) {
+    for (int d = 0; d < 4; ++d) a2 *= p->agg2[d];
+    V2 = Vc / a2;
+    n2 = 2.0 * p->nv2;
+  }
+  // persistent (tm_create)
+  double& P = m.persistent;
+  P += 3 * Vc * 4 + (three ? 3 * V2 * 4 : 0);           // odd-even index maps
+  P += 48 * V * (8 + 4) + 72 * V * (8 + 4);             // links and clover, FP64 and FP32
+  if (p->outer_apply == TM_F32X2) P += 1152 * V;         // links and clover as FP32 pairs
+  if (p->block_oe) P += V / 2 * 144 * cs;                // odd-site clover inverses
+  P += 2 * p->nv * fr * cs;                              // test vectors, P
+  P += Vc * 9 * n * n * 2 * cs + Vc / 2 * n * n * 2 * cs;  // D_c, odd-site inverses
+  if (three) {
+    P += 2 * p->nv2 * Vc * n * 2 * cs;                   // level-1 test vectors, P2
+    P += V2 * 9 * n2 * n2 * 2 * cs + V2 / 2 * n2 * n2 * 2 * cs;
+    if (p->sap1_prec == TM_F16) P += Vc * 9 * n * n * 4;
+  }
+  const double nvc = three ? p->nv2 : p->nv, nh = (three ? V2 : Vc) / 2;
+  double cvc = 2 * (three ? V2 : Vc) * (three ? n2 : n);  // reals of a coarsest vector
+  if (p->coarse_mma > 0) {
+    const double kp = std::ceil(2 * nvc / 16) * 16, mp = std::ceil(4 * nvc / 8) * 8;
+    P += nh * 17 * kp * mp * 4 * (p->coarse_mma == 3 ? 2 : 1) + nh * 17 * 4;
+  }
+  P += (double)kScratchBlocks * kMaxDots * 2 * 8 + kSmall * 8;
+  // work of one K-cycle over r right-hand sides
+  auto kcycle_work = [&](double r) {
+    double w = (p->pre_smooth > 0 ? fr * r * cs : 0) + 2 * (2 * Vc * n) * r * cs;  // k_r, k_rc, k_ec
+    const double mc = p->coarse_restart;
+    const double coarse = (5 + (mc + 1)) * (cvc / 2) * r * cs;                        // odd-even GMRES vectors
+    w += coarse;
+    if (three) {
+      const double c1 = 2 * Vc * n;
+      w += ((mc + 1) + mc + 1) * c1 * r * cs;                                         // level-1 FGMRES basis
+      w += (p->pre_smooth1 > 0 ? c1 * r * cs : 0) + 2 * (2 * V2 * n2) * r * cs;       // k1_r, k1_r2, k1_e2
+    }
+    return w;
+  };
+  const double nb = std::max(1, std::min(nrhs, p->max_rhs));
+  // the K-cycle's work buffers stay allocated, sized for the larger of the
+  // setup's N_v test vectors and the solve's batch
+  m.persistent += kcycle_work(std::max((double)p->nv, nb));
+  // setup: the iterated test vectors (released when the setup returns)
+  m.setup = p->nv * fr * cs + (three ? p->nv2 * 2 * Vc * n * cs : 0);
+  // solve: FP64 FGMRES(restart) over a batch of nb right-hand sides
+  const double mo = p->restart;
+  double sv = 2 * fr * nb * 8                           // packed b and x
+              + (mo + 1) * fr * nb * 8 + fr * nb * 8   // Krylov basis V and w
+              + mo * fr * nb * cs + fr * nb * cs;      // preconditioned basis Z, FP32 copy of v
+  if (p->cycle_prec != TM_F64 && p->outer_apply != TM_F32X2) sv += fr * nb * 8;  // FP64 copy of z
+  if (p->nn_mode) sv += 2 * fr * nb * cs;
+  m.solve = sv;
+  return m;
+}
+
 }  // namespace
 
 #define API_BEGIN try {
@@ -1841,6 +1915,95 @@ void autotune_build(tm_handle* h, const char* cache_path, int reps, double* out)
     out[3] = (double)cand.size();
   }
 }
+
+// ---------------------------------------------------------------------------
+// saving and loading a setup
+// ---------------------------------------------------------------------------
+namespace {
+constexpr char kSetupMagic[8] = {'T', 'M', 'A', 'M', 'G', 'S', 'U', '1'};
+struct SetupHeader {
+  char magic[8];
+  int version;
+  int L[4], nv, agg[4], levels, nv2, agg2[4], cycle_prec;
+  double m0, c_sw, bc_t;
+  long long nbytes[6];  // tv, P, Dc, tv1, P2, Dc2
+};
+
+// the saved arrays in the handle's device layout
+void setup_arrays(tm_handle* h, void* ptr[6], size_t bytes[6]) {
+  const size_t cs = csize(h->p.cycle_prec);
+  const size_t fr = (size_t)NR_SPINOR * h->g.V;
+  ptr[0] = h->tv;
+  bytes[0] = h->p.nv * fr * cs;
+  ptr[1] = h->P;
+  bytes[1] = bytes[0];
+  ptr[2] = h->Dc;
+  bytes[2] = (size_t)h->gc.V * 9 * h->n * h->n * 2 * cs;
+  for (int k = 3; k < 6; ++k) {
+    ptr[k] = nullptr;
+    bytes[k] = 0;
+  }
+  if (h->three) {
+    ptr[3] = h->tv1;
+    bytes[3] = (size_t)h->p.nv2 * h->gc.V * h->n * 2 * cs;
+    ptr[4] = h->P2;
+    bytes[4] = bytes[3];
+    ptr[5] = h->Dc2;
+    bytes[5] = (size_t)h->gc2.V * 9 * h->n2 * h->n2 * 2 * cs;
+  }
+}
+
+// device <-> file through a pinned staging buffer
+void copy_through(tm_handle* h, FILE* f, void* dev, size_t bytes, bool to_file) {
+  constexpr size_t kChunk = 64ull << 20;
+  double* hb = host_scratch(h, "io", kChunk / sizeof(double));
+  char* d = static_cast<char*>(dev);
+  for (size_t o = 0; o < bytes; o += kChunk) {
+    const size_t c = std::min(kChunk, bytes - o);
+    if (to_file) {
+      CK(cudaMemcpyAsync(hb, d + o, c, cudaMemcpyDeviceToHost, h->st));
+      sync(h);
+      if (std::fwrite(hb, 1, c, f) != c) raise(TM_ERR_ARG, "short write to the setup file");
+    } else {
+      if (std::fread(hb, 1, c, f) != c) raise(TM_ERR_ARG, "setup file is truncated");
+      CK(cudaMemcpyAsync(d + o, hb, c, cudaMemcpyHostToDevice, h->st));
+      sync(h);
+    }
+  }
+}
+
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() {
+    if (f) std::fclose(f);
+  }
+};
+
+template <typename T>
+void rebuild_derived(tm_handle* h) {
+  // everything the build derives from D_c (and D_c2): FP16 blocks, odd-site
+  // inverses with the current mu, tensor-core tiles
+  Prof pf(h, PK_BUILD, 0, 1);
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->Dc1h) {
+      launch_blocks_to_half(static_cast<const float*>(h->Dc), h->Dc1h, (long)h->gc.V * 9 * h->n * h->n, h->st);
+      CKL();
+    }
+  }
+  void* Dc = h->three ? h->Dc2 : h->Dc;
+  void* Di = h->three ? h->Dinv2 : h->Dinv;
+  const OEGeom& oe = h->three ? h->oe2 : h->oe;
+  launch_oe_invert<T>(static_cast<T*>(Dc), static_cast<T*>(Di), oe, mu_c(h), h->d_err, h->st);
+  CKL();
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->tc_on) {
+      tc_build(static_cast<const float*>(Dc), static_cast<const float*>(Di), oe, h->tc, h->st);
+      CKL();
+    }
+  }
+  check_flags(h);
+}
+}  // namespace
 
 extern "C" {
 
@@ -2822,6 +2985,89 @@ tm_status tm_profile_read(tm_handle* h, long long* launches, long long* units, d
   API_END
 }
 
+
+size_t tm_workspace_bytes(const tm_params* p, int nrhs) {
+  if (!p || nrhs < 1) return 0;
+  try {
+    validate(p);
+  } catch (...) {
+    return 0;
+  }
+  const MemPlan m = memory_plan(p, nrhs);
+  return (size_t)(m.persistent + std::max(m.setup, m.solve));
+}
+
+
+tm_status tm_save_setup(tm_handle* h, const char* path) {
+  if (!h || !path) return TM_ERR_ARG;
+  API_BEGIN
+  if (!h->setup_ok) raise(TM_ERR_STATE, "no setup to save");
+  SetupHeader hd{};
+  std::memcpy(hd.magic, kSetupMagic, 8);
+  hd.version = 1;
+  for (int d = 0; d < 4; ++d) {
+    hd.L[d] = h->p.L[d];
+    hd.agg[d] = h->p.agg[d];
+    hd.agg2[d] = h->three ? h->p.agg2[d] : 0;
+  }
+  hd.nv = h->p.nv;
+  hd.levels = h->p.levels;
+  hd.nv2 = h->three ? h->p.nv2 : 0;
+  hd.cycle_prec = h->p.cycle_prec;
+  hd.m0 = h->p.m0;
+  hd.c_sw = h->p.c_sw;
+  hd.bc_t = h->p.bc_t;
+  void* ptr[6];
+  size_t bytes[6];
+  setup_arrays(h, ptr, bytes);
+  for (int k = 0; k < 6; ++k) hd.nbytes[k] = (long long)bytes[k];
+  const std::string tmp = std::string(path) + ".tmp";
+  {
+    FileCloser fc{std::fopen(tmp.c_str(), "wb")};
+    if (!fc.f) raise(TM_ERR_ARG, "cannot write " + tmp);
+    if (std::fwrite(&hd, sizeof hd, 1, fc.f) != 1) raise(TM_ERR_ARG, "short write to the setup file");
+    sync(h);
+    for (int k = 0; k < 6; ++k)
+      if (bytes[k]) copy_through(h, fc.f, ptr[k], bytes[k], true);
+    if (std::fflush(fc.f) != 0) raise(TM_ERR_ARG, "cannot flush the setup file");
+  }
+  if (std::rename(tmp.c_str(), path) != 0) raise(TM_ERR_ARG, std::string("cannot rename to ") + path);
+  API_END
+}
+
+tm_status tm_load_setup(tm_handle* h, const char* path) {
+  if (!h || !path) return TM_ERR_ARG;
+  API_BEGIN
+  if (!h->gauge_ok) raise(TM_ERR_STATE, "tm_load_gauge must come first");
+  FileCloser fc{std::fopen(path, "rb")};
+  if (!fc.f) raise(TM_ERR_ARG, std::string("cannot open ") + path);
+  SetupHeader hd{};
+  if (std::fread(&hd, sizeof hd, 1, fc.f) != 1 || std::memcmp(hd.magic, kSetupMagic, 8) != 0 || hd.version != 1)
+    raise(TM_ERR_ARG, "not a setup file of this library");
+  bool same = hd.nv == h->p.nv && hd.levels == h->p.levels && hd.cycle_prec == h->p.cycle_prec;
+  for (int d = 0; d < 4; ++d) {
+    same = same && hd.L[d] == h->p.L[d] && hd.agg[d] == h->p.agg[d];
+    if (h->three) same = same && hd.agg2[d] == h->p.agg2[d];
+  }
+  if (h->three) same = same && hd.nv2 == h->p.nv2;
+  if (!same) raise(TM_ERR_ARG, "the setup file was saved with other lattice, aggregate, N_v, level or precision");
+  void* ptr[6];
+  size_t bytes[6];
+  setup_arrays(h, ptr, bytes);
+  for (int k = 0; k < 6; ++k)
+    if ((long long)bytes[k] != hd.nbytes[k]) raise(TM_ERR_ARG, "setup file sizes do not match the handle");
+  h->setup_ok = false;
+  sync(h);
+  for (int k = 0; k < 6; ++k)
+    if (bytes[k]) copy_through(h, fc.f, ptr[k], bytes[k], false);
+  if (h->p.cycle_prec == TM_F64)
+    rebuild_derived<double>(h);
+  else
+    rebuild_derived<float>(h);
+  h->setup_ok = true;
+  h->tv_ok = true;
+  API_END
+}
 }  // extern "C"
 
 // ===========================================================================

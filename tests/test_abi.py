@@ -116,3 +116,24 @@ def test_names_the_tests_and_bench_use_exist():
             if name != "h" and not hasattr(tm, name):  # "tm.h" is the header
                 missing.add((os.path.basename(f), name))
     assert not missing, sorted(missing)
+
+
+def test_workspace_bytes_plan(lib):
+    """The memory calculator needs no GPU: the 48^3 x 96 three-level benchmark
+    handle with 4 right-hand sides per solve fits one GB300 (280 GB), one
+    right-hand side needs less, more than max_rhs changes nothing, and
+    invalid parameters give 0."""
+    import paper_1611_01034_gb300 as tm
+    kw = dict(L=(96, 48, 48, 48), m0=-0.59, c_sw=1.57551, mu=0.0009, delta=5.0, nv=24, agg=(4, 4, 4, 4),
+              sap_block=(4, 4, 4, 4), levels=3, nv2=28, agg2=(2, 2, 2, 2), sap_block1=(2, 2, 2, 2), restart=8,
+              max_rhs=4, coarse_mma=1, sap1_prec=tm.TM_F16, outer_apply=tm.TM_F32X2, block_oe=1,
+              cycle_prec=tm.TM_F32)
+    p = tm.params(**kw)
+    b1, b4, b8 = (tm.tm_workspace_bytes(p, r) for r in (1, 4, 8))
+    assert 100e9 < b1 < b4 <= 280e9
+    assert b8 == b4
+    # FP64 cycle: the smoother, P and D_c double
+    assert tm.tm_workspace_bytes(tm.params(**dict(kw, cycle_prec=tm.TM_F64, coarse_mma=0, sap1_prec=tm.TM_F32,
+                                                  outer_apply=tm.TM_F64)), 4) > b4
+    assert tm.tm_workspace_bytes(tm.params(**dict(kw, nv=40)), 1) == 0
+    assert tm.tm_workspace_bytes(p, 0) == 0
