@@ -62,8 +62,9 @@ def test_saved_setup_reproduces_the_solve(name, tmp_path):
     path = os.path.join(tmp_path, "setup.bin")
     tm.tm_save_setup(g1.h, path)
     g2 = GPU(U, **kw)
-    st, _ = tm.tm_solve(g2.h, b, np.zeros_like(b), 2, 1e-10)  # no setup yet
-    assert st == tm.TM_ERR_STATE
+    with pytest.raises(tm.TMError) as e:  # no setup yet
+        tm.tm_solve(g2.h, b, np.zeros_like(b), 2, 1e-10)
+    assert e.value.status == tm.TM_ERR_STATE
     tm.tm_load_setup(g2.h, path)
     assert np.array_equal(g2.P_columns(), g1.P_columns())
     assert np.array_equal(g2.Dc_blocks(), g1.Dc_blocks())
