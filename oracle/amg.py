@@ -25,6 +25,10 @@ Readings (choices where the paper is silent)
 * Coarse solve: GMRES(coarse_restart) on the odd-even Schur complement of
   D_c(delta*mu) from zero, to a residual ``coarse_tol`` relative to the
   reduced right-hand side, at most ``coarse_maxit`` steps.
+* Odd-site twisted-mass shift rho (Sec. 2): the fine operator carries mu on
+  even and mu + rho on odd sites; the coarse operator is the Galerkin
+  projection P^dagger (D_W + i rho Pi_odd Gamma5) P with i delta mu Gamma5_c
+  added, i.e. delta raises the common twisted mass only.
 * Setup: each random v_i gets ``init_sweeps`` SAP sweeps on D v = 0 (i.e.
   v_i <- (I - M D) v_i) and is normalised; P and D_c are built; then
   ``setup_iters`` times: every v_i <- B(v_i) with the current P, D_c,
@@ -63,6 +67,7 @@ class AMGParams:
     coarse_maxit: int = 200
     restart: int = 25
     maxit: int = 1000
+    rho: float = 0.0          # odd-site twisted-mass shift (Sec. 2): mu + rho on odd sites
     extra: dict = field(default_factory=dict)
 
 
@@ -77,7 +82,7 @@ class TwoLevel:
 
     def __init__(self, U: np.ndarray, prm: AMGParams):
         self.prm = prm
-        self.op = Operator(U, prm.m0, prm.c_sw, prm.mu, prm.bc_t)
+        self.op = Operator(U, prm.m0, prm.c_sw, prm.mu, prm.bc_t, rho=prm.rho)
         self.sap = SAP(self.op, prm.sap_block, prm.mr_iters, prm.block_oe)
         self.P = None
         self.Dc = None
@@ -157,6 +162,17 @@ class TwoLevel:
         self.sap = SAP(self.op, self.prm.sap_block, self.prm.mr_iters, self.prm.block_oe)
         if self.Dc is not None:
             self.Dc = self.Dc.with_mu(self.prm.delta * mu)
+            self.oe = OddEvenCoarse(self.Dc)
+
+    def set_mu_eo(self, mu_even: float, mu_odd: float) -> None:
+        """Twisted mass mu_even on the even and mu_odd on the odd sites (Sec. 2)
+        with the same P; the odd shift enters D_c through the Galerkin
+        projection, so D_c is projected again from the kept P."""
+        self.prm.mu, self.prm.rho = mu_even, mu_odd - mu_even
+        self.op = self.op.with_mu_eo(mu_even, mu_odd)
+        self.sap = SAP(self.op, self.prm.sap_block, self.prm.mr_iters, self.prm.block_oe)
+        if self.P is not None:
+            self.Dc = CoarseOperator.build(self.op, self.P, self.prm.delta * mu_even)
             self.oe = OddEvenCoarse(self.Dc)
 
     def solve_squared(self, b: np.ndarray, tol: float = 1e-10):

@@ -164,30 +164,55 @@ def clover_blocks(A: np.ndarray) -> np.ndarray:
 # the operator
 # ----------------------------------------------------------------------------
 
+def site_parity(L) -> np.ndarray:
+    """(t + z + y + x) mod 2 per site, [T, Z, Y, X]: the even (0) and odd (1)
+    sites of the odd-even decomposition."""
+    c = np.indices(tuple(L))
+    return c.sum(axis=0) % 2
+
+
 class Operator:
-    """D(mu) on a fixed gauge field: diagonal A(x) + i mu gamma5, Wilson hops."""
+    """D(mu) on a fixed gauge field: diagonal A(x) + i mu gamma5, Wilson hops.
+
+    ``rho`` (Sec. 2: a different twisted mass on the even and the odd sites)
+    adds i rho gamma5 on the odd sites only: the twisted mass is mu on even
+    and mu + rho on odd sites."""
 
     def __init__(self, U: np.ndarray, m0: float, c_sw: float, mu: float,
-                 bc_t: float = -1.0):
+                 bc_t: float = -1.0, rho: float = 0.0):
         self.U = U
         self.L = tuple(U.shape[:4])
         self.m0, self.c_sw, self.mu, self.bc_t = m0, c_sw, mu, bc_t
+        self.rho = rho
+        self.odd = site_parity(self.L) == 1
         self.A = clover_matrix(U, m0, c_sw)
 
     def with_mu(self, mu: float) -> "Operator":
+        """The same operator with twisted mass mu on even sites (and mu + rho on odd)."""
         other = object.__new__(Operator)
         other.__dict__.update(self.__dict__)
         other.mu = mu
         return other
 
+    def with_mu_eo(self, mu_even: float, mu_odd: float) -> "Operator":
+        """Twisted mass mu_even on the even and mu_odd on the odd sites."""
+        other = self.with_mu(mu_even)
+        other.rho = mu_odd - mu_even
+        return other
+
+    def mu_field(self, mu: float | None = None) -> np.ndarray:
+        """The twisted mass per site, [T, Z, Y, X] (mu of the even sites
+        overridden by ``mu`` if given; the odd shift rho is kept)."""
+        mu = self.mu if mu is None else mu
+        return mu + self.rho * self.odd
+
     # -- pieces --------------------------------------------------------------
     def diag(self, psi: np.ndarray, mu: float | None = None) -> np.ndarray:
-        """A(x) psi(x) + i mu gamma5 psi(x)."""
-        mu = self.mu if mu is None else mu
+        """A(x) psi(x) + i mu(x) gamma5 psi(x), mu(x) = mu (+ rho on odd sites)."""
         sh = psi.shape
         y = np.einsum("...ij,...j->...i", self.A, psi.reshape(sh[:-2] + (12,)))
         y = y.reshape(sh)
-        return y + 1j * mu * spin_mul(GAMMA5, psi)
+        return y + 1j * self.mu_field(mu)[..., None, None] * spin_mul(GAMMA5, psi)
 
     def hop_term(self, psi: np.ndarray, mu: int, direction: int) -> np.ndarray:
         """-1/2 (1 - gamma_mu) U psi(x+mu) (direction +1) or
@@ -220,7 +245,7 @@ class Operator:
         for s in sites:
             s = tuple(int(v) for v in s)
             y = (self.A[s] @ psi[s].reshape(12)).reshape(4, 3)
-            y = y + 1j * self.mu * (GAMMA5 @ psi[s])
+            y = y + 1j * (self.mu + self.rho * (sum(s) % 2)) * (GAMMA5 @ psi[s])
             for d in range(4):
                 f = list(s)
                 f[d] = (s[d] + 1) % L[d]

@@ -239,7 +239,7 @@ class ThreeLevel:
 
     def __init__(self, U: np.ndarray, prm: ThreeLevelParams):
         self.prm = prm
-        self.op = Operator(U, prm.m0, prm.c_sw, prm.mu, prm.bc_t)
+        self.op = Operator(U, prm.m0, prm.c_sw, prm.mu, prm.bc_t, rho=prm.rho)
         self.sap = SAP(self.op, prm.sap_block, prm.mr_iters, prm.block_oe)
         self.coarse_iters = []
         self.coarsest_iters = []

@@ -141,11 +141,12 @@ class SAP:
 
     # odd-even block solve ------------------------------------------------------
     def _diag_inverse(self):
-        """Per-site inverse of A(x) + i mu gamma5 (12x12), computed once."""
-        if getattr(self, "_dinv_mu", None) != self.op.mu:
-            D = self.op.A + 1j * self.op.mu * np.kron(GAMMA5, np.eye(3))
+        """Per-site inverse of A(x) + i mu(x) gamma5 (12x12), computed once per mu."""
+        key = (self.op.mu, self.op.rho)
+        if getattr(self, "_dinv_mu", None) != key:
+            D = self.op.A + 1j * self.op.mu_field()[..., None, None] * np.kron(GAMMA5, np.eye(3))
             self._dinv = np.linalg.inv(D)
-            self._dinv_mu = self.op.mu
+            self._dinv_mu = key
         return self._dinv
 
     def _diag_solve(self, psi):
