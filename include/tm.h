@@ -251,8 +251,40 @@ tm_status tm_autotune_build(tm_handle* h, const char* cache_path, int reps, doub
 
 /* Change mu and delta without a new setup (Sec. 1: D_c(mu) = D_c +
  * i mu Gamma5_c, so only the diagonal shift and the odd-site inverses of the
- * coarse Schur complement change; one setup serves D(+mu) and D(-mu)). */
+ * coarse Schur complement change; one setup serves D(+mu) and D(-mu)).  The
+ * twisted mass becomes mu on all sites (see tm_set_mu_eo). */
 tm_status tm_set_mu(tm_handle* h, double mu, double delta);
+
+/* A different twisted mass on the even and the odd sites (Sec. 2, needed for
+ * Hasenbusch preconditioning with odd-even preconditioning): D = D_W +
+ * i Gamma5 mu(x), mu(x) = mu_even on sites with (t+z+y+x) even, mu_odd on odd
+ * ones.  The coarse operators are the Galerkin projections of
+ * D_W + i (mu_odd - mu_even) Pi_odd Gamma5 plus i mu_even Gamma5_c (times
+ * delta on the coarsest level): a change of mu_odd - mu_even projects D_c
+ * (and D_c2) again from the current P (and P2), without a new setup.
+ * Errors: TM_ERR_ARG (non-finite masses, delta < 1). */
+tm_status tm_set_mu_eo(tm_handle* h, double mu_even, double mu_odd, double delta);
+
+/* The odd-even reduced system D^ x_o = b_o, D^ = D_oo - D_oe D_ee^-1 D_eo on
+ * the odd sites of the handle's current operator, solved through the full
+ * operator (Sec. 3: DD-alphaAMG inverts the full operator even when the
+ * reduced one is wanted): D x = (0 on even sites, b_o on odd sites) to tol,
+ * x_o the odd part.  b, x natural spinors (host or device) of which only the
+ * odd sites count; x holds a start vector and returns x_o with zeros on the
+ * even sites.  info as tm_solve (the residual is that of the full system). */
+tm_status tm_solve_odd(tm_handle* h, const double* b, double* x, int nrhs, double tol, tm_solve_info* info);
+
+/* The two inversions of a Hasenbusch-preconditioned HMC force term (Sec. 3),
+ * in the order the paper lists them, on the odd sites:
+ *   y = (D^(mu) + i rho G^5)^-1 b,   x = (G^5 D^(-mu) G^5 - i rho G^5)^-1 y,
+ * G^5 = Gamma5 on the odd sites, with one setup.  The first operator is the
+ * odd Schur complement of D(mu on even, mu + rho on odd sites); the second is
+ * its adjoint, inverted as G^5 (D^(-mu) - i rho G^5)^-1 G^5 with D(-mu,
+ * -mu - rho): x = (A A^dagger)^-1 b, A = D^(mu) + i rho G^5.  b, x as
+ * tm_solve_odd (x is overwritten, no start vector); info sums both solves.
+ * The handle is left at mu on even and mu + rho on odd sites. */
+tm_status tm_solve_hasenbusch(tm_handle* h, const double* b, double* x, int nrhs, double mu, double rho, double tol,
+                              tm_solve_info* info);
 
 /* A7: solve D(mu) x_r = b_r for nrhs right-hand sides to ||b - D x|| <=
  * tol ||b|| by FGMRES(restart) preconditioned with the K-cycle of eq. (1).
@@ -266,7 +298,8 @@ tm_status tm_solve(tm_handle* h, const double* b, double* x, int nrhs, double to
 /* Squared-operator solve with one setup (Sec. 1: the same setup serves
  * D(+mu) and D(-mu); Sec. 3: the squared operator is inverted by two solves
  * of the non-squared operator): x = (D(mu)^dagger D(mu))^-1 b computed as
- * D(mu)^-1 Gamma5 D(-mu)^-1 Gamma5 b, using D(mu)^dagger = Gamma5 D(-mu) Gamma5.
+ * D(mu)^-1 Gamma5 D(-mu)^-1 Gamma5 b, using D(mu)^dagger = Gamma5 D(-mu) Gamma5
+ * (with an odd-site shift the adjoint flips it too: D(-mu, -mu - rho)).
  * The D(-mu) solve starts from zero, the D(mu) solve from x; both run to tol.
  * Arguments, layouts and errors as tm_solve; info sums both solves.  The
  * handle is left at +mu. */

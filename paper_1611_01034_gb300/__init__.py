@@ -22,7 +22,8 @@ from ._binding import (  # noqa: F401
     TM_EXPORT_P, TM_EXPORT_DC, TM_EXPORT_CLOVER, TM_EXPORT_TV, TM_EXPORT_P2, TM_EXPORT_DC2, TM_EXPORT_TV1,
     TMError, tm_params, tm_solve_info, lib, library_path, params,
     tm_params_default, tm_create, tm_destroy, tm_status_string, tm_last_error,
-    tm_load_gauge, tm_setup, tm_setup_from_vectors, tm_set_mu, tm_autotune_build, tm_solve, tm_solve_squared,
+    tm_load_gauge, tm_setup, tm_setup_from_vectors, tm_set_mu, tm_set_mu_eo, tm_autotune_build, tm_solve, tm_solve_squared, tm_solve_odd,
+    tm_solve_hasenbusch,
     tm_field_bytes, tm_workspace_bytes, tm_save_setup, tm_load_setup, tm_pack, tm_unpack, tm_apply, tm_sap, tm_restrict, tm_prolong,
     tm_coarse_solve, tm_coarse_solve_noalloc, tm_kcycle, tm_setup_update, tm_schur, tm_nn_set_weights, tm_nn_get_weights, tm_nn_apply, tm_nn_pairs,
     tm_nn_grad, tm_nn_train, tm_sap1, tm_restrict1, tm_prolong1, tm_kcycle1,

@@ -60,6 +60,10 @@ _SIGS = {
     "tm_setup": (c_int, [c_void_p, c_void_p]),
     "tm_setup_from_vectors": (c_int, [c_void_p, c_void_p]),
     "tm_set_mu": (c_int, [c_void_p, c_double, c_double]),
+    "tm_set_mu_eo": (c_int, [c_void_p, c_double, c_double, c_double]),
+    "tm_solve_odd": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
+    "tm_solve_hasenbusch": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_double,
+                                    POINTER(tm_solve_info)]),
     "tm_autotune_build": (c_int, [c_void_p, c_char_p, c_int, POINTER(c_double)]),
     "tm_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
     "tm_solve_squared": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
@@ -209,6 +213,26 @@ def tm_autotune_build(h, cache_path=None, reps: int = 3) -> dict:
 def tm_solve(h, b, x, nrhs: int, tol: float):
     info = tm_solve_info()
     st = lib().tm_solve(h, _ptr(b), _ptr(x), nrhs, tol, ctypes.byref(info))
+    if st not in (TM_OK, TM_ERR_NOT_CONVERGED):
+        _check(st, h)
+    return st, info
+
+
+def tm_set_mu_eo(h, mu_even: float, mu_odd: float, delta: float) -> None:
+    _check(lib().tm_set_mu_eo(h, mu_even, mu_odd, delta), h)
+
+
+def tm_solve_odd(h, b, x, nrhs: int, tol: float):
+    info = tm_solve_info()
+    st = lib().tm_solve_odd(h, _ptr(b), _ptr(x), nrhs, tol, ctypes.byref(info))
+    if st not in (TM_OK, TM_ERR_NOT_CONVERGED):
+        _check(st, h)
+    return st, info
+
+
+def tm_solve_hasenbusch(h, b, x, nrhs: int, mu: float, rho: float, tol: float):
+    info = tm_solve_info()
+    st = lib().tm_solve_hasenbusch(h, _ptr(b), _ptr(x), nrhs, mu, rho, tol, ctypes.byref(info))
     if st not in (TM_OK, TM_ERR_NOT_CONVERGED):
         _check(st, h)
     return st, info

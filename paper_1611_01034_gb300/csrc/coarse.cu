@@ -309,7 +309,7 @@ __device__ __forceinline__ void build_hops_pair(const T* __restrict__ P, const T
 template <typename T>
 __device__ __forceinline__ void column_op_pair(const T* __restrict__ gauge, const T* __restrict__ clover,
                                                const T* __restrict__ P, const AggGeom& ag, int s, const int c[4],
-                                               const int lc[4], int j, int t, T bc, cx<T> (&u0)[12],
+                                               const int lc[4], int j, int t, T bc, T rho, cx<T> (&u0)[12],
                                                cx<T> (&u1)[12]) {
   cx<T> acc0[12], acc1[12];
 #pragma unroll
@@ -320,10 +320,12 @@ __device__ __forceinline__ void column_op_pair(const T* __restrict__ gauge, cons
   build_hops_pair<T, 3>(P, gauge, ag, s, c, lc, j, t, bc, acc0, acc1);
   if (t == 0) {
     // the clover term is block diagonal in chirality: A P_j splits into the
-    // chirality-0 rows of column j and the chirality-1 rows of column Nv + j
+    // chirality-0 rows of column j and the chirality-1 rows of column Nv + j;
+    // an odd-site twisted-mass shift rho (i rho gamma5, also chirality
+    // diagonal) is projected with it, the common twisted mass is added at apply
     cx<T> p[12], y[12];
     ld_cx<T, 12>(P + (long)j * NR_SPINOR * ag.g.V, ag.g.V, s, p);
-    site_diag<T>(clover, ag.g.V, s, T(0), p, y);
+    site_diag<T>(clover, ag.g.V, s, ((c[0] + c[1] + c[2] + c[3]) & 1) ? rho : T(0), p, y);
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       u0[q] = y[q];
@@ -391,7 +393,7 @@ template <typename T, int KTC>
 __global__ void __launch_bounds__(kBuildThreads, sizeof(T) == 4 ? 2 : 1) k_coarse_build(const T* __restrict__ gauge,
                                                                 const T* __restrict__ clover,
                                                                 const T* __restrict__ P, T* __restrict__ Dc,
-                                                                AggGeom ag, T bc, int TS) {
+                                                                AggGeom ag, T bc, int TS, T rho) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nv = ag.nv, n = 2 * nv;
   const int LP = build_row_stride(nv), LU = build_row_stride(n);
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(kBuildThreads, sizeof(T) == 4 ? 2 : 1) k_coars
       int lc[4], c[4];
       const int s = agg_site(ag, a, block_site(ag, t, f0 + l), lc, c);
       cx<T> u0[12], u1[12];
-      column_op_pair<T>(gauge, clover, P, ag, s, c, lc, j, t, bc, u0, u1);
+      column_op_pair<T>(gauge, clover, P, ag, s, c, lc, j, t, bc, rho, u0, u1);
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
         Us[(size_t)l * LU + q * n + j] = u0[q];
@@ -512,7 +514,7 @@ std::vector<BuildShape> coarse_build_candidates(int nv, size_t real_bytes) {
 // same order, so all shapes give bit-identical blocks.
 template <typename T>
 void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, const AggGeom& ag, double bc_t,
-                         cudaStream_t st, BuildShape shape) {
+                         cudaStream_t st, BuildShape shape, double rho) {
   const int nv = ag.nv;
   const size_t per_site = (size_t)(build_row_stride(nv) + build_row_stride(2 * nv)) * sizeof(cx<T>);  // Ps + Us
   const BuildShape def = coarse_build_default(nv, sizeof(T));
@@ -532,11 +534,11 @@ void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, con
   dim3 grid(9, ag.gc.V);
   const size_t smem = TS * per_site;
   if (ktc == 2)
-    k_coarse_build<T, 2><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
+    k_coarse_build<T, 2><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS, (T)rho);
   else if (ktc == 3)
-    k_coarse_build<T, 3><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
+    k_coarse_build<T, 3><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS, (T)rho);
   else
-    k_coarse_build<T, 4><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS);
+    k_coarse_build<T, 4><<<grid, kBuildThreads, smem, st>>>(gauge, clover, P, Dc, ag, (T)bc_t, TS, (T)rho);
 }
 
 // number of 32-bit words in which a and b differ, added to *count
@@ -991,7 +993,7 @@ TM_INST_B(float)
   template void launch_restrict<T>(const T*, const T*, T*, const AggGeom&, int, cudaStream_t);                 \
   template void launch_prolong<T>(const T*, const T*, T*, const AggGeom&, int, bool, cudaStream_t);            \
   template void launch_coarse_build<T>(const T*, const T*, const T*, T*, const AggGeom&, double, cudaStream_t,   \
-                                       BuildShape);                                                           \
+                                       BuildShape, double);                                                   \
   template void launch_coarse_apply<T>(const T*, const T*, T*, const Lat&, int, double, int, cudaStream_t);    \
   template void launch_oe_invert<T>(const T*, T*, const OEGeom&, double, int*, cudaStream_t);                  \
   template void launch_oe_hop_inv<T>(const T*, const T*, const T*, T*, const OEGeom&, cudaStream_t);           \

@@ -68,6 +68,24 @@ __global__ void k_gamma5_nat(const double* __restrict__ in, double* __restrict__
     out[i] = (i % 24) < 12 ? -in[i] : in[i];
 }
 
+// zero the sites of one parity ((t + z + y + x) mod 2) of natural spinor arrays
+__global__ void k_zero_parity_nat(double* __restrict__ nat, Lat g, int parity, int nrhs) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;  // site of one rhs
+  if (i >= (long)g.V * nrhs) return;
+  const int s = (int)(i % g.V);
+  int c[4];
+  site_coords(g, s, c);
+  if (((c[0] + c[1] + c[2] + c[3]) & 1) != parity) return;
+  double2* p = reinterpret_cast<double2*>(nat) + i * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) p[k] = make_double2(0.0, 0.0);
+}
+
+void launch_zero_parity_nat(double* nat, const Lat& g, int parity, int nrhs, cudaStream_t st) {
+  const long n = (long)g.V * nrhs;
+  k_zero_parity_nat<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nat, g, parity, nrhs);
+}
+
 void launch_gamma5_nat(const double* in, double* out, long nsites, cudaStream_t st) {
   long blocks = (nsites * 24 + 255) / 256;
   if (blocks > 152L * 16) blocks = 152L * 16;
@@ -272,6 +290,7 @@ struct DslashArgs {
   T mu;
   T bc;
   int nrhs;
+  T rho;  // odd sites carry mu + rho (Sec. 2: a different twisted mass on even and odd sites)
 };
 
 // right-hand sides vary fastest over the CTAs so the links and clover of a site
@@ -289,7 +308,7 @@ __global__ void __launch_bounds__(128) k_dslash(DslashArgs<T> a) {
   all_hops_global<T>(in, a.gauge, a.g, s, c, a.bc, acc);
   cx<T> p[12], y[12];
   ld_cx<T, 12>(in, a.g.V, s, p);
-  site_diag<T>(a.clover, a.g.V, s, a.mu, p, y);
+  site_diag<T>(a.clover, a.g.V, s, ((c[0] + c[1] + c[2] + c[3]) & 1) ? a.mu + a.rho : a.mu, p, y);
   const T half = T(0.5);
 #pragma unroll
   for (int k = 0; k < 12; ++k) y[k] = y[k] - half * acc[k];
@@ -304,8 +323,8 @@ __global__ void __launch_bounds__(128) k_dslash(DslashArgs<T> a) {
 
 template <typename T>
 void launch_dslash(const T* gauge, const T* clover, const T* in, T* out, const T* b, const Lat& g, double mu,
-                   double bc_t, int nrhs, cudaStream_t st) {
-  DslashArgs<T> a{gauge, clover, in, out, b, g, (T)mu, (T)bc_t, nrhs};
+                   double bc_t, int nrhs, cudaStream_t st, double rho) {
+  DslashArgs<T> a{gauge, clover, in, out, b, g, (T)mu, (T)bc_t, nrhs, (T)rho};
   dim3 grid((unsigned)((g.V + 127) / 128) * (unsigned)nrhs);
   if (b)
     k_dslash<T, true><<<grid, 128, 0, st>>>(a);
@@ -313,8 +332,8 @@ void launch_dslash(const T* gauge, const T* clover, const T* in, T* out, const T
     k_dslash<T, false><<<grid, 128, 0, st>>>(a);
 }
 template void launch_dslash<double>(const double*, const double*, const double*, double*, const double*,
-                                    const Lat&, double, double, int, cudaStream_t);
+                                    const Lat&, double, double, int, cudaStream_t, double);
 template void launch_dslash<float>(const float*, const float*, const float*, float*, const float*, const Lat&,
-                                   double, double, int, cudaStream_t);
+                                   double, double, int, cudaStream_t, double);
 
 }  // namespace tmamg

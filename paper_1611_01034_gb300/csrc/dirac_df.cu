@@ -206,7 +206,7 @@ struct DfArgs {
   const float* in;
   double* out;
   Lat g;
-  dfl mu;
+  dfl mu, mu_odd;  // twisted mass on even and on odd sites
   float bc;
   int nrhs;
 };
@@ -267,7 +267,8 @@ __global__ void __launch_bounds__(128) k_dslash_df(DfArgs a) {
         cfmac_pf(y[j], u, p[6 * h + i]);
       }
     // i mu gamma5 p, gamma5 = -1 on spins 0, 1 (h = 0), +1 on spins 2, 3
-    const dfl m = h == 0 ? neg(a.mu) : a.mu;
+    const dfl mus = ((c[0] + c[1] + c[2] + c[3]) & 1) ? a.mu_odd : a.mu;
+    const dfl m = h == 0 ? neg(mus) : mus;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       fma_pf(y[i].r, neg(m), p[6 * h + i].i);
@@ -330,10 +331,11 @@ void launch_clover_df(const double* c64, void* cdf, const Lat& g, cudaStream_t s
 }
 
 void launch_dslash_df(const void* gdf, const void* cdf, const float* in, double* out, const Lat& g, double mu,
-                      double bc_t, int nrhs, cudaStream_t st) {
-  const float mh = (float)mu;
+                      double bc_t, int nrhs, cudaStream_t st, double rho) {
+  const double muo = mu + rho;
+  const float mh = (float)mu, moh = (float)muo;
   DfArgs a{static_cast<const float4*>(gdf), static_cast<const float4*>(cdf), in, out, g,
-           dfl{mh, (float)(mu - (double)mh)}, (float)bc_t, nrhs};
+           dfl{mh, (float)(mu - (double)mh)}, dfl{moh, (float)(muo - (double)moh)}, (float)bc_t, nrhs};
   dim3 grid((unsigned)((g.V + 127) / 128) * (unsigned)nrhs);
   k_dslash_df<<<grid, 128, 0, st>>>(a);
 }

@@ -32,6 +32,7 @@ struct SapArgs {
   int n_mr;
   int colour;
   int nrhs;
+  T rho;  // odd sites carry mu + rho
 };
 
 template <typename T, int MU>
@@ -104,11 +105,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sap(SapArgs<T> 
 
   cx<T> r[12], e[12];
   const T half = T(0.5);
+  const T mus = ((c[0] + c[1] + c[2] + c[3]) & 1) ? a.mu + a.rho : a.mu;
   if (act) {
     cx<T> acc[12], p[12];
     all_hops_global<T>(x, a.gauge, g, s, c, a.bc, acc);
     ld_cx<T, 12>(x, g.V, s, p);
-    site_diag<T>(a.clover, g.V, s, a.mu, p, r);
+    site_diag<T>(a.clover, g.V, s, mus, p, r);
 #pragma unroll
     for (int i = 0; i < 12; ++i) r[i] = half * acc[i] - r[i];  // -D x
     if (a.b) {
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sap(SapArgs<T> 
       block_hops<T, 1>(rs, BS, l, lc, lst, a.gauge, g, s, c, sg.blk, acc);
       block_hops<T, 2>(rs, BS, l, lc, lst, a.gauge, g, s, c, sg.blk, acc);
       block_hops<T, 3>(rs, BS, l, lc, lst, a.gauge, g, s, c, sg.blk, acc);
-      site_diag<T>(a.clover, g.V, s, a.mu, r, q);
+      site_diag<T>(a.clover, g.V, s, mus, r, q);
 #pragma unroll
       for (int i = 0; i < 12; ++i) {
         q[i] = q[i] - half * acc[i];
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sap(SapArgs<T> 
 
 template <typename T>
 void launch_sap_colour(const T* gauge, const T* clover, const T* b, T* x, const SapGeom& sg, double mu,
-                       double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st) {
+                       double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st, double rho) {
   const int threads = (sg.bsites + 31) / 32 * 32;
   const size_t smem = 12 * sg.bsites * sizeof(cx<T>) + 32 * 3 * sizeof(T);
   static bool attr_set = false;
@@ -180,15 +182,15 @@ void launch_sap_colour(const T* gauge, const T* clover, const T* b, T* x, const 
     attr_set = true;
   }
   const int nblk_colour = sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2;
-  SapArgs<T> a{gauge, clover, b, x, sg, (T)mu, (T)bc_t, n_mr, colour, nrhs};
+  SapArgs<T> a{gauge, clover, b, x, sg, (T)mu, (T)bc_t, n_mr, colour, nrhs, (T)rho};
   dim3 grid(nblk_colour * nrhs);
   k_sap<T><<<grid, threads, smem, st>>>(a);
 }
 
 template void launch_sap_colour<double>(const double*, const double*, const double*, double*, const SapGeom&,
-                                        double, double, int, int, int, cudaStream_t);
+                                        double, double, int, int, int, cudaStream_t, double);
 template void launch_sap_colour<float>(const float*, const float*, const float*, float*, const SapGeom&, double,
-                                       double, int, int, int, cudaStream_t);
+                                       double, int, int, int, cudaStream_t, double);
 
 // ===========================================================================
 // Odd-even block solve (Sec. 3: odd-even preconditioning is used in the
@@ -307,6 +309,7 @@ struct SapOeArgs {
   int n_mr;
   int colour;
   int nrhs;
+  T rho;  // odd sites carry mu + rho (D_oo^-1 is built with it)
 };
 
 // The kernel walks 2 n_MR + 3 half-steps, odd and even alternating, so that the
@@ -379,7 +382,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArg
     if (act) {
       int lc[4], c[4];
       const int s = site_of(pass ^ 1, lc, c);
-      sap_residual_site<T>(x, a.b ? a.b + off : nullptr, a.gauge, a.clover, g, s, c, a.bc, a.mu, rho);
+      sap_residual_site<T>(x, a.b ? a.b + off : nullptr, a.gauge, a.clover, g, s, c, a.bc,
+                           pass == 0 ? a.mu + a.rho : a.mu, rho);
       if (pass == 0) {
 #pragma unroll
         for (int i = 0; i < 12; ++i) ro[i * HB + j] = rho[i];
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArg
 
 template <typename T>
 void launch_sap_oe_colour(const T* gauge, const T* clover, const T* dinv, const T* b, T* x, const SapGeom& sg,
-                          double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st) {
+                          double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st, double rho) {
   const int HB = sg.bsites / 2;
   const int threads = (HB + 31) / 32 * 32;
   const size_t smem = 3 * 12 * (size_t)HB * sizeof(cx<T>) + 32 * 3 * sizeof(T);
@@ -483,14 +487,14 @@ void launch_sap_oe_colour(const T* gauge, const T* clover, const T* dinv, const 
     attr_set = true;
   }
   const int nblk_colour = sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2;
-  SapOeArgs<T> a{gauge, clover, dinv, b, x, sg, (T)mu, (T)bc_t, n_mr, colour, nrhs};
+  SapOeArgs<T> a{gauge, clover, dinv, b, x, sg, (T)mu, (T)bc_t, n_mr, colour, nrhs, (T)rho};
   k_sap_oe<T><<<dim3(nblk_colour * nrhs), threads, smem, st>>>(a);
 }
 
 template void launch_sap_oe_colour<double>(const double*, const double*, const double*, const double*, double*,
-                                           const SapGeom&, double, double, int, int, int, cudaStream_t);
+                                           const SapGeom&, double, double, int, int, int, cudaStream_t, double);
 template void launch_sap_oe_colour<float>(const float*, const float*, const float*, const float*, float*,
-                                          const SapGeom&, double, double, int, int, int, cudaStream_t);
+                                          const SapGeom&, double, double, int, int, int, cudaStream_t, double);
 
 // ===========================================================================
 // D_oo^-1 for the odd-even block solve: per odd site the inverses of the two

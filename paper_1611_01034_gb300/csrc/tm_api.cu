@@ -102,6 +102,8 @@ struct tm_handle {
   void* cdf = nullptr;
   // (A(x) + i mu gamma5)^-1 at the odd sites for the odd-even SAP block solves (block_oe = 1)
   void* dinv_sap = nullptr;
+  // twisted-mass shift of the odd sites (Sec. 2): mu on even, mu + rho on odd sites
+  double rho = 0;
   // odd-even Schur complement of the coarsest level on the tensor cores
   bool tc_on = false;
   TcGeom tc{};
@@ -289,14 +291,14 @@ double mu_c(tm_handle* h) { return h->p.delta * h->p.mu; }
 template <typename T>
 void dslash(tm_handle* h, const T* in, T* out, const T* b, int nrhs) {
   Prof pf(h, std::is_same<T, double>::value ? PK_DSLASH64 : PK_DSLASH32, nrhs);
-  launch_dslash<T>(gaugeT<T>(h), cloverT<T>(h), in, out, b, h->g, h->p.mu, h->p.bc_t, nrhs, h->st);
+  launch_dslash<T>(gaugeT<T>(h), cloverT<T>(h), in, out, b, h->g, h->p.mu, h->p.bc_t, nrhs, h->st, h->rho);
   CKL();
 }
 
 // out (FP64) = D(mu) in (FP32) in FP32-pair arithmetic
 void dslash_df(tm_handle* h, const float* in, double* out, int nrhs) {
   Prof pf(h, PK_DSLASHDF, nrhs);
-  launch_dslash_df(h->gdf, h->cdf, in, out, h->g, h->p.mu, h->p.bc_t, nrhs, h->st);
+  launch_dslash_df(h->gdf, h->cdf, in, out, h->g, h->p.mu, h->p.bc_t, nrhs, h->st, h->rho);
   CKL();
 }
 
@@ -309,10 +311,10 @@ void sap_sweeps(tm_handle* h, const T* b, T* x, int sweeps, int nrhs) {
       Prof pf(h, PK_SAP, nrhs);
       if (h->p.block_oe)
         launch_sap_oe_colour<T>(gaugeT<T>(h), cloverT<T>(h), static_cast<const T*>(h->dinv_sap), b, x, h->sg,
-                                h->p.mu, h->p.bc_t, h->p.mr_iters, colour, nrhs, h->st);
+                                h->p.mu, h->p.bc_t, h->p.mr_iters, colour, nrhs, h->st, h->rho);
       else
         launch_sap_colour<T>(gaugeT<T>(h), cloverT<T>(h), b, x, h->sg, h->p.mu, h->p.bc_t, h->p.mr_iters, colour,
-                             nrhs, h->st);
+                             nrhs, h->st, h->rho);
       CKL();
     }
 }
@@ -323,9 +325,11 @@ void build_sap_inverse(tm_handle* h) {
   if (!h->dinv_sap) return;
   Prof pf(h, PK_OTHER);
   if (h->p.cycle_prec == TM_F64)
-    launch_clover_inverse<double>(h->c64, static_cast<double*>(h->dinv_sap), h->g, h->p.mu, h->d_err, h->st);
+    launch_clover_inverse<double>(h->c64, static_cast<double*>(h->dinv_sap), h->g, h->p.mu + h->rho, h->d_err,
+                                  h->st);
   else
-    launch_clover_inverse<float>(h->c64, static_cast<float*>(h->dinv_sap), h->g, h->p.mu, h->d_err, h->st);
+    launch_clover_inverse<float>(h->c64, static_cast<float*>(h->dinv_sap), h->g, h->p.mu + h->rho, h->d_err,
+                                 h->st);
   CKL();
 }
 
@@ -528,18 +532,23 @@ KrylovOut krylov(tm_handle* h, const std::string& tag, FA A, FAZ AZ, FM M, bool 
 // ---------------------------------------------------------------------------
 // coarse level
 // ---------------------------------------------------------------------------
+// orth = false: D_c projected again from the current (orthonormal) P, e.g.
+// after a change of the odd-site twisted-mass shift
 template <typename T>
-void build_coarse(tm_handle* h) {
+void build_coarse(tm_handle* h, bool orth = true) {
   T* P = static_cast<T*>(h->P);
   constexpr bool f32 = std::is_same<T, float>::value;
   // orthonormalisation + build, the FP16 copy, the odd-site inverses and the
   // three tensor-core tile kernels
-  const int nk = 2 + (f32 && h->Dc1h ? 1 : 0) + (h->three ? 0 : 1) + (f32 && h->tc_on && !h->three ? 3 : 0);
+  const int nk = (orth ? 2 : 1) + (f32 && h->Dc1h ? 1 : 0) + (h->three ? 0 : 1) +
+                 (f32 && h->tc_on && !h->three ? 3 : 0);
   Prof pf(h, PK_BUILD, 1, nk);
-  launch_orthonormalise<T>(P, h->ag, h->d_err, h->st);
-  CKL();
+  if (orth) {
+    launch_orthonormalise<T>(P, h->ag, h->d_err, h->st);
+    CKL();
+  }
   launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, static_cast<T*>(h->Dc), h->ag, h->p.bc_t, h->st,
-                         h->build_shape);
+                         h->build_shape, h->rho);
   CKL();
   if constexpr (std::is_same<T, float>::value) {
     if (h->Dc1h) {  // FP16 blocks for the level-1 SAP
@@ -974,10 +983,12 @@ void level1_solve(tm_handle* h, const T* b1, T* x1, int nrhs, double tol, int ma
 
 // P2 (holding the level-1 test vectors) -> orthonormal P2, D_c2, odd-site inverses
 template <typename T>
-void build_level2(tm_handle* h) {
-  Prof pf(h, PK_BUILD, 1, 3 + (std::is_same<T, float>::value && h->tc_on ? 3 : 0));
-  launch_corth<T>(static_cast<T*>(h->P2), h->cag, h->d_err, h->st);
-  CKL();
+void build_level2(tm_handle* h, bool orth = true) {
+  Prof pf(h, PK_BUILD, 1, (orth ? 3 : 2) + (std::is_same<T, float>::value && h->tc_on ? 3 : 0));
+  if (orth) {
+    launch_corth<T>(static_cast<T*>(h->P2), h->cag, h->d_err, h->st);
+    CKL();
+  }
   launch_cbuild<T>(static_cast<const T*>(h->Dc), static_cast<const T*>(h->P2), static_cast<T*>(h->Dc2), h->cag,
                    h->st);
   CKL();
@@ -1691,6 +1702,33 @@ void apply_mu(tm_handle* h, double mu, double delta) {
   }
 }
 
+// twisted mass mu_even on the even and mu_odd on the odd sites (Sec. 2); a new
+// odd shift enters D_c (and D_c2) through the Galerkin projection, so they are
+// projected again from the current P (and P2) without a new setup
+void apply_mu_eo(tm_handle* h, double mu_even, double mu_odd, double delta) {
+  const double rho = mu_odd - mu_even;
+  if (rho == h->rho) {
+    apply_mu(h, mu_even, delta);
+    return;
+  }
+  h->rho = rho;
+  h->p.mu = mu_even;
+  h->p.delta = delta;
+  if (h->gauge_ok) {
+    build_sap_inverse(h);
+    check_flags(h);
+  }
+  if (!h->setup_ok) return;
+  if (h->p.cycle_prec == TM_F64) {
+    build_coarse<double>(h, false);
+    if (h->three) build_level2<double>(h, false);
+  } else {
+    build_coarse<float>(h, false);
+    if (h->three) build_level2<float>(h, false);
+  }
+  check_flags(h);
+}
+
 // ---------------------------------------------------------------------------
 // memory plan (tm_workspace_bytes): what tm_create, tm_setup and tm_solve
 // allocate on the device for given parameters
@@ -1870,7 +1908,7 @@ void autotune_build(tm_handle* h, const char* cache_path, int reps, double* out)
   T* ref = W<T>(h, "tune_ref", n);
   T* trial = W<T>(h, "tune_dc", n);
   unsigned long long* bad_d = W<unsigned long long>(h, "tune_bad", 1);
-  launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, ref, ag, h->p.bc_t, h->st, BuildShape{});
+  launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, ref, ag, h->p.bc_t, h->st, BuildShape{}, h->rho);
   CKL();
   cudaEvent_t e0 = scratch.e[0] = take_event(h);
   cudaEvent_t e1 = scratch.e[1] = take_event(h);
@@ -1878,7 +1916,7 @@ void autotune_build(tm_handle* h, const char* cache_path, int reps, double* out)
   double best_us = 0;
   for (const BuildShape& b : cand) {
     // parity first: the candidate's D_c must equal the default's bit for bit
-    launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, trial, ag, h->p.bc_t, h->st, b);
+    launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, trial, ag, h->p.bc_t, h->st, b, h->rho);
     CKL();
     CK(cudaMemsetAsync(bad_d, 0, sizeof(unsigned long long), h->st));
     launch_count_mismatch(ref, trial, (long)(n * sizeof(T) / 4), bad_d, h->st);
@@ -1891,7 +1929,7 @@ void autotune_build(tm_handle* h, const char* cache_path, int reps, double* out)
                               " differs from the default D_c in " + std::to_string(bad) + " words");
     CK(cudaEventRecord(e0, h->st));
     for (int r = 0; r < reps; ++r)
-      launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, trial, ag, h->p.bc_t, h->st, b);
+      launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, trial, ag, h->p.bc_t, h->st, b, h->rho);
     CKL();
     CK(cudaEventRecord(e1, h->st));
     CK(cudaEventSynchronize(e1));
@@ -1925,7 +1963,7 @@ struct SetupHeader {
   char magic[8];
   int version;
   int L[4], nv, agg[4], levels, nv2, agg2[4], cycle_prec;
-  double m0, c_sw, bc_t;
+  double m0, c_sw, bc_t, rho;  // rho: odd-site twisted-mass shift projected into D_c
   long long nbytes[6];  // tv, P, Dc, tv1, P2, Dc2
 };
 
@@ -2326,7 +2364,16 @@ tm_status tm_set_mu(tm_handle* h, double mu, double delta) {
   if (!h) return TM_ERR_ARG;
   API_BEGIN
   if (!(delta >= 1.0) || !std::isfinite(mu)) raise(TM_ERR_ARG, "need finite mu and delta >= 1");
-  apply_mu(h, mu, delta);
+  apply_mu_eo(h, mu, mu, delta);
+  API_END
+}
+
+tm_status tm_set_mu_eo(tm_handle* h, double mu_even, double mu_odd, double delta) {
+  if (!h) return TM_ERR_ARG;
+  API_BEGIN
+  if (!(delta >= 1.0) || !std::isfinite(mu_even) || !std::isfinite(mu_odd))
+    raise(TM_ERR_ARG, "need finite twisted masses and delta >= 1");
+  apply_mu_eo(h, mu_even, mu_odd, delta);
   API_END
 }
 
@@ -2372,7 +2419,7 @@ tm_status tm_solve_squared(tm_handle* h, const double* b, double* x, int nrhs, d
   tm_solve_info loc{};
   loc.converged = 1;
   tm_status st = TM_OK;
-  const double mu = h->p.mu;
+  const double mu = h->p.mu, rho = h->rho;
   try {
     if (!h->setup_ok) raise(TM_ERR_STATE, "tm_setup must come first");
     const long V = h->g.V;
@@ -2388,11 +2435,11 @@ tm_status tm_solve_squared(tm_handle* h, const double* b, double* x, int nrhs, d
     launch_gamma5_nat(bd, y, (long)V * nrhs, h->st);  // y = Gamma5 b
     CKL();
     CK(cudaMemsetAsync(z, 0, one * nrhs, h->st));
-    apply_mu(h, -mu, h->p.delta);  // D(-mu) z = Gamma5 b, same setup
+    apply_mu_eo(h, -mu, -mu - rho, h->p.delta);  // D(mu)^dagger = Gamma5 D(-mu) Gamma5: same setup
     solve_core(h, y, z, nrhs, tol, loc);
     launch_gamma5_nat(z, y, (long)V * nrhs, h->st);  // y = Gamma5 z
     CKL();
-    apply_mu(h, mu, h->p.delta);  // D(mu) x = Gamma5 z
+    apply_mu_eo(h, mu, mu + rho, h->p.delta);  // D(mu) x = Gamma5 z
     solve_core(h, y, xd, nrhs, tol, loc);
     if (!xdev) CK(cudaMemcpyAsync(x, xd, one * nrhs, cudaMemcpyDeviceToHost, h->st));
     sync(h);
@@ -2411,11 +2458,112 @@ tm_status tm_solve_squared(tm_handle* h, const double* b, double* x, int nrhs, d
     h->err = e.what();
     st = TM_ERR_CUDA;
   }
-  if (h->p.mu != mu) {  // leave the handle at +mu even after an error
+  if (h->p.mu != mu || h->rho != rho) {  // leave the handle at +mu even after an error
     try {
-      apply_mu(h, mu, h->p.delta);
+      apply_mu_eo(h, mu, mu + rho, h->p.delta);
     } catch (...) {
     }
+  }
+  if (info) *info = loc;
+  return st;
+}
+
+// the odd-site reduced system through the full operator: b's even sites are
+// dropped, x's even sites are zeroed on return (Sec. 3)
+static void solve_odd_core(tm_handle* h, const double* bd, double* xd, int nrhs, double tol, tm_solve_info& loc) {
+  const long V = h->g.V;
+  const size_t one = (size_t)V * 12 * 2 * sizeof(double);
+  double* bw = W<double>(h, "odd_b", one * nrhs / sizeof(double));
+  CK(cudaMemcpyAsync(bw, bd, one * nrhs, cudaMemcpyDeviceToDevice, h->st));
+  launch_zero_parity_nat(bw, h->g, 0, nrhs, h->st);
+  CKL();
+  solve_core(h, bw, xd, nrhs, tol, loc);
+  launch_zero_parity_nat(xd, h->g, 0, nrhs, h->st);
+  CKL();
+}
+
+static tm_status finish_solve(tm_handle* h, tm_solve_info& loc) {
+  loc.coarse_iters = h->coarse_iters;
+  loc.kcycles = h->kcycles;
+  if (!loc.converged) {
+    h->err = "solver reached maxit";
+    return TM_ERR_NOT_CONVERGED;
+  }
+  h->err.clear();
+  return TM_OK;
+}
+
+tm_status tm_solve_odd(tm_handle* h, const double* b, double* x, int nrhs, double tol, tm_solve_info* info) {
+  if (!h || !b || !x || nrhs < 1 || !(tol > 0)) return TM_ERR_ARG;
+  tm_solve_info loc{};
+  loc.converged = 1;
+  tm_status st = TM_OK;
+  try {
+    if (!h->setup_ok) raise(TM_ERR_STATE, "tm_setup must come first");
+    const size_t one = (size_t)h->g.V * 12 * 2 * sizeof(double);
+    const bool xdev = is_device_ptr(x);
+    const double* bd = stage_in(h, b, one * nrhs, "stage_b");
+    double* xd = xdev ? x : W<double>(h, "stage_x", one * nrhs / sizeof(double));
+    if (!xdev) CK(cudaMemcpyAsync(xd, x, one * nrhs, cudaMemcpyHostToDevice, h->st));
+    h->coarse_iters = 0;
+    h->kcycles = 0;
+    solve_odd_core(h, bd, xd, nrhs, tol, loc);
+    if (!xdev) CK(cudaMemcpyAsync(x, xd, one * nrhs, cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    st = finish_solve(h, loc);
+  } catch (const TmError& e) {
+    h->err = e.m;
+    st = e.s;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    st = TM_ERR_CUDA;
+  }
+  if (info) *info = loc;
+  return st;
+}
+
+tm_status tm_solve_hasenbusch(tm_handle* h, const double* b, double* x, int nrhs, double mu, double rho, double tol,
+                              tm_solve_info* info) {
+  if (!h || !b || !x || nrhs < 1 || !(tol > 0) || !std::isfinite(mu) || !std::isfinite(rho)) return TM_ERR_ARG;
+  tm_solve_info loc{};
+  loc.converged = 1;
+  tm_status st = TM_OK;
+  try {
+    if (!h->setup_ok) raise(TM_ERR_STATE, "tm_setup must come first");
+    const long V = h->g.V;
+    const size_t one = (size_t)V * 12 * 2 * sizeof(double);
+    const bool xdev = is_device_ptr(x);
+    const double* bd = stage_in(h, b, one * nrhs, "stage_b");
+    double* xd = xdev ? x : W<double>(h, "stage_x", one * nrhs / sizeof(double));
+    double* y = W<double>(h, "hb_y", one * nrhs / sizeof(double));
+    double* z = W<double>(h, "hb_z", one * nrhs / sizeof(double));
+    h->coarse_iters = 0;
+    h->kcycles = 0;
+    // y = (D^(mu) + i rho G^5)^-1 b: the odd Schur complement of D(mu, mu + rho)
+    apply_mu_eo(h, mu, mu + rho, h->p.delta);
+    CK(cudaMemsetAsync(y, 0, one * nrhs, h->st));
+    solve_odd_core(h, bd, y, nrhs, tol, loc);
+    // x = (G^5 D^(-mu) G^5 - i rho G^5)^-1 y = G^5 (D^(-mu) - i rho G^5)^-1 G^5 y
+    launch_gamma5_nat(y, z, (long)V * nrhs, h->st);
+    CKL();
+    apply_mu_eo(h, -mu, -mu - rho, h->p.delta);
+    CK(cudaMemsetAsync(y, 0, one * nrhs, h->st));
+    solve_odd_core(h, z, y, nrhs, tol, loc);
+    launch_gamma5_nat(y, xd, (long)V * nrhs, h->st);
+    CKL();
+    if (!xdev) CK(cudaMemcpyAsync(x, xd, one * nrhs, cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    st = finish_solve(h, loc);
+  } catch (const TmError& e) {
+    h->err = e.m;
+    st = e.s;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    st = TM_ERR_CUDA;
+  }
+  try {  // leave the handle at the first operator, D(mu) on even and mu + rho on odd sites
+    apply_mu_eo(h, mu, mu + rho, h->p.delta);
+  } catch (...) {
   }
   if (info) *info = loc;
   return st;
@@ -3017,6 +3165,7 @@ tm_status tm_save_setup(tm_handle* h, const char* path) {
   hd.m0 = h->p.m0;
   hd.c_sw = h->p.c_sw;
   hd.bc_t = h->p.bc_t;
+  hd.rho = h->rho;
   void* ptr[6];
   size_t bytes[6];
   setup_arrays(h, ptr, bytes);
@@ -3060,10 +3209,20 @@ tm_status tm_load_setup(tm_handle* h, const char* path) {
   sync(h);
   for (int k = 0; k < 6; ++k)
     if (bytes[k]) copy_through(h, fc.f, ptr[k], bytes[k], false);
-  if (h->p.cycle_prec == TM_F64)
+  if (hd.rho != h->rho) {  // the saved D_c carries another odd-site shift: project again from P
+    if (h->p.cycle_prec == TM_F64) {
+      build_coarse<double>(h, false);
+      if (h->three) build_level2<double>(h, false);
+    } else {
+      build_coarse<float>(h, false);
+      if (h->three) build_level2<float>(h, false);
+    }
+    check_flags(h);
+  } else if (h->p.cycle_prec == TM_F64) {
     rebuild_derived<double>(h);
-  else
+  } else {
     rebuild_derived<float>(h);
+  }
   h->setup_ok = true;
   h->tv_ok = true;
   API_END

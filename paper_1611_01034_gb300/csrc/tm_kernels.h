@@ -22,12 +22,14 @@ void launch_pack_gauge(const double* nat, double* g64, float* g32, const Lat& g,
 // clover blocks (m0 + 4 included, mu-free) from the natural gauge field
 void launch_clover(const double* nat, double* c64, float* c32, const Lat& g, double m0, double c_sw,
                    cudaStream_t st);
+// zero the sites of the given parity of nrhs natural spinor arrays
+void launch_zero_parity_nat(double* nat, const Lat& g, int parity, int nrhs, cudaStream_t st);
 // out = Gamma5 in on natural spinor arrays of nsites sites (in may equal out)
 void launch_gamma5_nat(const double* in, double* out, long nsites, cudaStream_t st);
-// out = D(mu) in (res == nullptr) or out = b - D(mu) in
+// out = D(mu) in (res == nullptr) or out = b - D(mu) in; odd sites carry mu + rho
 template <typename T>
 void launch_dslash(const T* gauge, const T* clover, const T* in, T* out, const T* b, const Lat& g,
-                   double mu, double bc_t, int nrhs, cudaStream_t st);
+                   double mu, double bc_t, int nrhs, cudaStream_t st, double rho = 0.0);
 
 // ---- FP32-pair D(mu) (dirac_df.cu) -------------------------------------------
 // links as [4][9][V] float4 (re.h, im.h, re.l, im.l) of entry 3a + b; clover as
@@ -36,7 +38,7 @@ void launch_pack_gauge_df(const double* nat, void* gdf, const Lat& g, cudaStream
 void launch_clover_df(const double* c64, void* cdf, const Lat& g, cudaStream_t st);
 // out (FP64 field) = D(mu) in (FP32 field) to about 2^-46 relative, FP32 pairs
 void launch_dslash_df(const void* gdf, const void* cdf, const float* in, double* out, const Lat& g, double mu,
-                      double bc_t, int nrhs, cudaStream_t st);
+                      double bc_t, int nrhs, cudaStream_t st, double rho = 0.0);
 
 // ---- SAP (sap.cu) ------------------------------------------------------------
 struct SapGeom {
@@ -48,15 +50,16 @@ struct SapGeom {
 // one colour of one sweep on D x = b (b may be null: b = 0)
 template <typename T>
 void launch_sap_colour(const T* gauge, const T* clover, const T* b, T* x, const SapGeom& sg,
-                       double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st);
+                       double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st, double rho = 0.0);
 
 // the same with the block solves on the odd-even Schur complement (Sec. 3);
 // all block dims even; dinv from launch_clover_inverse
 template <typename T>
 void launch_sap_oe_colour(const T* gauge, const T* clover, const T* dinv, const T* b, T* x, const SapGeom& sg,
-                          double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st);
+                          double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st, double rho = 0.0);
 // dinv [12 rows x 6 complex chunks][V/2] = (A(x) + i mu gamma5)^-1 of the two
-// chiral blocks at every odd site (compact index s >> 1; X even)
+// chiral blocks at every odd site (compact index s >> 1; X even); mu = the
+// odd sites' twisted mass
 template <typename T>
 void launch_clover_inverse(const double* c64, T* dinv, const Lat& g, double mu, int* err, cudaStream_t st);
 
@@ -86,7 +89,7 @@ void launch_prolong(const T* P, const T* coarse, T* fine, const AggGeom& ag, int
 // Dc blocks [Vc][9][2Nv col][2Nv row] = local Galerkin projection (mu-free)
 template <typename T>
 void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, const AggGeom& ag,
-                         double bc_t, cudaStream_t st, BuildShape shape = BuildShape{});
+                         double bc_t, cudaStream_t st, BuildShape shape = BuildShape{}, double rho = 0.0);
 // tile shape of the build: ts fine sites staged per tile, ktc columns per
 // register tile (0 = the default heuristic); the candidates an autotuner may try
 BuildShape coarse_build_default(int nv, size_t real_bytes);
