@@ -11,9 +11,9 @@ Default workload: 48^3 x 96, U = exp(0.6 i H), c_sw = 1.57551, mu = 0.0009,
 delta = 5, three levels (N_v = 24 on 4^4 aggregates, then N_v2 = 28 on 2^4
 level-1 aggregates; SAP blocks 4^4 with odd-even block solves as in Sec. 3,
 and 2^4 on level 1), 3 + 3 setup iterations, the 12
-spin-colour point sources at one random site, solved in 3 steps of 4 (the
-FGMRES(8) basis of 4 right-hand sides is what fits next to the setup data in
-the 280 GB).  m0 from inputs/m0_tuned.json (near-critical).  Every field of
+spin-colour point sources at one random site, solved in 2 steps of 6 (the
+FGMRES(4) basis of 6 right-hand sides is what fits next to the setup data in
+the 280 GB; restart 4 needs no more outer iterations than 8 or 16 here).  m0 from inputs/m0_tuned.json (near-critical).  Every field of
 the step (2 GB per fine FP64 vector) is larger than the 129 MB L2, so no
 flush is needed.
 
@@ -53,7 +53,7 @@ WORKLOADS = {
         L=(96, 48, 48, 48), eps=0.6, seed=1, c_sw=1.57551, mu=0.0009, delta=5.0, nv=24,
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, nrhs=12, point=True,
         levels=3, nv2=28, agg2=(2, 2, 2, 2), sap_block1=(2, 2, 2, 2), coarse_setup_iters=3,
-        restart=8, rhs_batch=4, coarse_mma=1, sap1_prec=2, outer_apply=TM_F32X2, block_oe=1,
+        restart=4, rhs_batch=6, coarse_mma=1, sap1_prec=2, outer_apply=TM_F32X2, block_oe=1,
         m0_key="16x16x16x32_eps0.6_seed1_csw1.57551", device_inputs=True),
     "16x16x16x32_2lvl_nv20": dict(
         L=(32, 16, 16, 16), eps=0.5, seed=1, c_sw=1.5, mu=0.003, delta=5.0, nv=20,
