@@ -139,7 +139,8 @@ def roofline_model(kind: str, wl: dict, units: float, launches: float, outer: di
     array once per launch and every vector once per right-hand side; flops
     count the arithmetic the definition needs.
       sap (one colour of a sweep): links + clover of the colour's half, x
-        everywhere, b and the x update on the half: (120 V/2) op, (24 V + 48 V/2) vec reals
+        everywhere, b and the x update on the half: (120 V/2) op, (24 V + 48 V/2) vec reals;
+        with odd-even block solves also D_oo^-1 of the half's odd sites (144 V/4 reals)
       coarse_sap (level-1, one colour): the colour's D_c1 blocks once (9 n^2
         complex per site, FP16 copy with sap1_prec = TM_F16) + x everywhere,
         b and x on the half (FP32)
@@ -165,6 +166,8 @@ def roofline_model(kind: str, wl: dict, units: float, launches: float, outer: di
     per = units / launches  # rhs units per launch
     if kind == "sap":
         b = 120 * f * V / 2 + per * (24 * V + 48 * V / 2) * f
+        if wl.get("block_oe"):
+            b += 144 * f * V / 4
         return {"bound": "hbm", "work": b, "unit": "GB/s", "peak": hbm, "peak_source": hbm_src}
     if kind == "coarse_sap":
         ob = 2 if wl.get("sap1_prec") == 2 else 4
@@ -711,7 +714,8 @@ def main_native(args):
     launches = sum(v["launches"] for v in prof.values())
     roof = None
     outer = {"iters": round(outer_iters / R), "restart": p.restart, "rhs": R, "steps": K}
-    model = roofline_model(dom, wl, prof[dom]["units"], prof[dom]["launches"], outer, peaks)
+    model = roofline_model(dom, dict(wl, block_oe=p.block_oe, sap1_prec=p.sap1_prec), prof[dom]["units"],
+                           prof[dom]["launches"], outer, peaks)
     if model is not None and prof[dom]["launches"]:
         avg_s = prof[dom]["ms"] / prof[dom]["launches"] / 1000.0
         if dom == "coarse_oe":
