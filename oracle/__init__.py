@@ -26,6 +26,10 @@ Modules
   and the FGMRES + AMG solve.
 * ``multilevel`` -- the three-level hierarchy of Sec. 2 (coarse-grid SAP,
   level-1 aggregation, the level-1 K-cycle).
+* ``evenodd`` -- the odd-site reduced operator with even/odd twisted masses
+  and the Hasenbusch two-solve sequence (Sec. 2, Sec. 3).
+* ``oecg``   -- odd-even CG on the normal equations, the comparison solver of
+  Fig. 1 (Sec. 1).
 * ``slabs``  -- the true residual of a large lattice evaluated T-slab by
   T-slab with the unchanged operator (for solutions too large for one
   full-lattice oracle apply).
