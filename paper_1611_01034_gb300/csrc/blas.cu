@@ -214,6 +214,7 @@ static inline int dot_grid(long ncx) {
 }
 
 long multidot_scratch_doubles(long ncx, int k, int nrhs) { return 2L * dot_grid(ncx) * k * nrhs; }
+int dot_grid_for(long ncx) { return dot_grid(ncx); }
 
 template <typename T>
 __global__ void k_multidot_partial_b(const T* __restrict__ X, long xstr, long ldx, int k, const T* __restrict__ y,

@@ -16,52 +16,11 @@
 //   (D psi)(x) = A(x) psi(x) + i mu gamma5 psi(x)
 //       - 1/2 sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu) ]
 #include "tm_kernels.h"
+#include "tm_pair.cuh"
 
 namespace tmamg {
 
 namespace {
-
-// a value h + l
-struct dfl {
-  float h, l;
-};
-
-// error-free transforms (the _rn intrinsics are never contracted into FMAs)
-__device__ __forceinline__ dfl two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-// acc += a * b, a a pair, b an exact FP32 number
-__device__ __forceinline__ void fma_pf(dfl& acc, dfl a, float b) {
-  const float p = __fmul_rn(a.h, b);
-  float e = __fmaf_rn(a.h, b, -p);
-  e = __fmaf_rn(a.l, b, e);
-  const dfl s = two_sum(acc.h, p);
-  acc.h = s.h;
-  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
-}
-// acc += a * b, both pairs (the l * l term, 2^-48 relative, is dropped)
-__device__ __forceinline__ void fma_pp(dfl& acc, dfl a, dfl b) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, e);
-  e = __fmaf_rn(a.l, b.h, e);
-  const dfl s = two_sum(acc.h, p);
-  acc.h = s.h;
-  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
-}
-__device__ __forceinline__ dfl neg(dfl a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ void add_to(dfl& acc, dfl a) {
-  const dfl s = two_sum(acc.h, a.h);
-  acc.h = s.h;
-  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, a.l));
-}
-
-struct cdf {
-  dfl r, i;
-};
 
 // multiply by a phase from {+1, +i, -1, -i} (exact)
 __device__ __forceinline__ cdf mulp(cdf z, int p) {
@@ -85,34 +44,6 @@ __device__ __forceinline__ cx<float> mulph_rt(cx<float> z, int p) {
 
 // exact difference / sum of two FP32 complex numbers as a pair
 __device__ __forceinline__ cdf exact_sum(cx<float> a, cx<float> b) { return cdf{two_sum(a.r, b.r), two_sum(a.i, b.i)}; }
-
-// acc += u * x (pairs)
-__device__ __forceinline__ void cfma_pp(cdf& acc, cdf u, cdf x) {
-  fma_pp(acc.r, u.r, x.r);
-  fma_pp(acc.r, neg(u.i), x.i);
-  fma_pp(acc.i, u.r, x.i);
-  fma_pp(acc.i, u.i, x.r);
-}
-// acc += conj(u) * x (pairs)
-__device__ __forceinline__ void cfmac_pp(cdf& acc, cdf u, cdf x) {
-  fma_pp(acc.r, u.r, x.r);
-  fma_pp(acc.r, u.i, x.i);
-  fma_pp(acc.i, u.r, x.i);
-  fma_pp(acc.i, neg(u.i), x.r);
-}
-// acc += u * x, x exact FP32
-__device__ __forceinline__ void cfma_pf(cdf& acc, cdf u, cx<float> x) {
-  fma_pf(acc.r, u.r, x.r);
-  fma_pf(acc.r, neg(u.i), x.i);
-  fma_pf(acc.i, u.r, x.i);
-  fma_pf(acc.i, u.i, x.r);
-}
-__device__ __forceinline__ void cfmac_pf(cdf& acc, cdf u, cx<float> x) {
-  fma_pf(acc.r, u.r, x.r);
-  fma_pf(acc.r, u.i, x.i);
-  fma_pf(acc.i, u.r, x.i);
-  fma_pf(acc.i, neg(u.i), x.r);
-}
 
 // link entry e = 3 a + b of direction mu at site s: float4 (re.h, im.h, re.l, im.l)
 __device__ __forceinline__ cdf ld_link_entry(const float4* __restrict__ gdf, long V, int mu, int e, long s) {
@@ -186,18 +117,6 @@ __device__ __forceinline__ void hops_df(const float* __restrict__ in, const floa
     const float sign = (MU == 0 && c[0] == 0) ? bc : 1.f;
     hop_df<MU, false>(p, gdf, g.V, sb, sign, acc);
   }
-}
-
-// FP32 bits -> FP64 with integer operations (exact for normal numbers; FP32
-// subnormals, below 1.2e-38, become zero)
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned mag = u & 0x7fffffffu;
-  if (mag < 0x00800000u) return __longlong_as_double((long long)sgn);
-  if (mag >= 0x7f800000u) return (double)f;  // Inf, NaN
-  const unsigned long long bits = sgn | (((unsigned long long)mag << 29) + (896ull << 52));
-  return __longlong_as_double((long long)bits);
 }
 
 struct DfArgs {

@@ -1325,6 +1325,9 @@ std::vector<KrylovOut> fgmres_b(tm_handle* h, const std::string& tag, int pk, FR
   std::vector<char> active(nb), inner(nb);
   std::vector<cd> H((size_t)nb * (m + 1) * m), g((size_t)nb * (m + 1)), sn((size_t)nb * m);
   std::vector<double> cs((size_t)nb * m);
+  // the fine FP64 FGMRES with FP32-pair outer products also runs its Arnoldi
+  // steps and solution update in pair arithmetic
+  const bool pair_blas = std::is_same<Tv, double>::value && pk == PK_BLAS_FINE && h->p.outer_apply == TM_F32X2;
   auto count = [&](const std::vector<char>& msk) {
     int c = 0;
     for (char v : msk) c += v ? 1 : 0;
@@ -1389,7 +1392,20 @@ std::vector<KrylovOut> fgmres_b(tm_handle* h, const std::string& tag, int pk, FR
       upload_mask(inner, nullptr);
       double* d1 = dd;
       double* d2 = dd + 2 * (k + 1);
-      if (nc <= kFuseMaxCx) {  // short vectors: the launches dominate, fuse the reductions
+      if (pair_blas) {  // FP64 basis, CGS2 in FP32-pair arithmetic with fused reductions
+        Prof pf(h, pk, na, 7);
+        if constexpr (std::is_same<Tv, double>::value) {
+          launch_pdot_b(Vb, fr, blk, k + 1, w, fr, nc, d1, ds, part, nb, act, h->st);
+          CKL();
+          const int nl = launch_pcaxpy_dot_b(Vb, fr, blk, k + 1, d1, ds, w, fr, nc, d2, ds, part, nb, act, h->st);
+          CKL();
+          launch_pcaxpy_norm_b(Vb, fr, blk, k + 1, d2, ds, w, fr, nc, nrm, part, nb, act, h->st);
+          CKL();
+          launch_scale_copy_b<Tv>(w, fr, Vb + (long)(k + 1) * blk, fr, nrm, nc, nb, act, h->st);
+          CKL();
+          if (nl == 3 && h->prof) h->prof_launch[pk] += 1;
+        }
+      } else if (nc <= kFuseMaxCx) {  // short vectors: the launches dominate, fuse the reductions
         Prof pf(h, pk, na, 6);
         launch_multidot_b_partials<Tv>(Vb, fr, blk, k + 1, w, fr, nc, part, nb, act, h->st);
         CKL();
@@ -1478,7 +1494,14 @@ std::vector<KrylovOut> fgmres_b(tm_handle* h, const std::string& tag, int pk, FR
     upload_mask(active, &kk);
     {
       Prof pf(h, pk, count(active));
-      launch_lincomb_b<Tz, Tv>(Z, fr, blk, kmax, dd, ds, x, fr, nc, nb, act, h->st);
+      if constexpr (std::is_same<Tz, float>::value && std::is_same<Tv, double>::value) {
+        if (pair_blas)
+          launch_plincomb_b(Z, fr, blk, kmax, dd, ds, x, fr, nc, nb, act, h->st);
+        else
+          launch_lincomb_b<Tz, Tv>(Z, fr, blk, kmax, dd, ds, x, fr, nc, nb, act, h->st);
+      } else {
+        launch_lincomb_b<Tz, Tv>(Z, fr, blk, kmax, dd, ds, x, fr, nc, nb, act, h->st);
+      }
       CKL();
     }
     resid(x, Vb);  // true residuals

@@ -279,6 +279,19 @@ template <typename T>
 void launch_sub_b(const T* x, long xstr, T* y, long ystr, long ncx, int nrhs, const int* active, cudaStream_t st);
 // scratch doubles that launch_multidot_b / launch_norm2_b need
 long multidot_scratch_doubles(long ncx, int k, int nrhs);
+int dot_grid_for(long ncx);  // partial-sum CTAs per right-hand side of the batched reductions
+// Arnoldi steps of the FP64 FGMRES in FP32-pair arithmetic (blas_pair.cu); the
+// reductions write FP64 results like launch_multidot_b / launch_norm2_b
+void launch_pdot_b(const double* X, long xstr, long ldx, int k, const double* y, long ystr, long ncx, double* out,
+                   long ostr, double* scratch, int nrhs, const int* active, cudaStream_t st);
+int launch_pcaxpy_dot_b(const double* X, long xstr, long ldx, int k, const double* c, long cstr, double* y, long ystr,
+                        long ncx, double* out, long ostr, double* scratch, int nrhs, const int* active,
+                        cudaStream_t st);  // returns the launches made
+void launch_pcaxpy_norm_b(const double* X, long xstr, long ldx, int k, const double* c, long cstr, double* y,
+                          long ystr, long ncx, double* nrm, double* scratch, int nrhs, const int* active,
+                          cudaStream_t st);
+void launch_plincomb_b(const float* Z, long zstr, long ldz, int k, const double* c, long cstr, double* x, long xstr,
+                       long ncx, int nrhs, const int* active, cudaStream_t st);
 // fused pairs: the partial sums of a multidot / norm go straight into the next
 // step, which reduces them itself (the final values are also written to c / nrm):
 //   multidot partials -> y_r -= sum_j c_rj X_rj;   norm partials -> dst_r = src_r / ||src_r||
