@@ -47,6 +47,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 TM_F32X2 = 4  # tm_params.outer_apply: FP32-pair products D(mu) z_k
+PREC_NAMES = {0: "f64", 1: "f32", 2: "f16", 3: "bf16", 4: "f32x2"}
 
 WORKLOADS = {
     "48x48x48x96_3lvl_nv24_28_12pt": dict(
@@ -54,6 +55,7 @@ WORKLOADS = {
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, nrhs=12, point=True,
         levels=3, nv2=28, agg2=(2, 2, 2, 2), sap_block1=(2, 2, 2, 2), coarse_setup_iters=3,
         restart=4, rhs_batch=6, coarse_mma=1, sap1_prec=2, outer_apply=TM_F32X2, block_oe=1,
+        sap_prec=2, transfer_prec=2,
         m0_key="16x16x16x32_eps0.6_seed1_csw1.57551", device_inputs=True),
     "16x16x16x32_2lvl_nv20": dict(
         L=(32, 16, 16, 16), eps=0.5, seed=1, c_sw=1.5, mu=0.003, delta=5.0, nv=20,
@@ -605,7 +607,7 @@ def main_native(args):
 
     stream = torch.cuda.current_stream()
     extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec",
-                                "outer_apply", "block_oe") if k in wl}
+                                "outer_apply", "block_oe", "sap_prec", "transfer_prec") if k in wl}
     extra["coarse_mma"] = args.coarse_mma if args.coarse_mma is not None else wl.get("coarse_mma", 0)
     for kv in args.param or []:  # solver-parameter overrides, e.g. --param coarse_tol=0.02
         k, v = kv.split("=", 1)
@@ -780,8 +782,11 @@ def main_native(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": (f"f64 FGMRES (Arnoldi, true residual); {oa} D(mu) z_k products; f32 K-cycle"
-                  + ("; f16 level-1 SAP blocks" if p.sap1_prec == 2 else "")
+        "dtype": (f"f64 FGMRES vectors and true residual; {oa} D(mu) z_k products"
+                  + (" and Arnoldi arithmetic" if oa == "f32x2" else "") + "; f32 K-cycle"
+                  + (f"; {PREC_NAMES[p.sap_prec]} SAP links/clover/D_oo^-1" if p.sap_prec in (2, 3) else "")
+                  + (f"; {PREC_NAMES[p.transfer_prec]} P for the transfers" if p.transfer_prec in (2, 3) else "")
+                  + (f"; {PREC_NAMES[p.sap1_prec]} level-1 SAP blocks" if p.sap1_prec in (2, 3) else "")
                   + ("; tf32 coarsest Schur complement" if p.coarse_mma else "")),
         "data": f"synthetic (seeded random SU(3) field U = exp({wl['eps']} i H); "
                 + ("12 spin-colour point sources)" if wl.get("point") else "Gaussian rhs)"),
@@ -789,7 +794,8 @@ def main_native(args):
             "workload": args.workload, "lattice_TZYX": list(L), "sites": V, "levels": levels,
             **({"nv2": wl["nv2"], "aggregate2": list(wl["agg2"]), "sap_block1": list(wl["sap_block1"]),
                 "coarse_setup_iters": wl["coarse_setup_iters"],
-                "sap1_prec": "f16" if p.sap1_prec == 2 else "f32"} if levels == 3 else {}),
+                "sap1_prec": PREC_NAMES[p.sap1_prec]} if levels == 3 else {}),
+            "sap_prec": PREC_NAMES[p.sap_prec], "transfer_prec": PREC_NAMES[p.transfer_prec],
             "nv": nv, "aggregate": list(wl["agg"]), "sap_block": list(wl["sap_block"]),
             "restart": p.restart, "coarse_tol": p.coarse_tol, "post_smooth": p.post_smooth, "mr_iters": p.mr_iters,
             "coarse_mma": p.coarse_mma, "outer_apply": oa, "block_oe": p.block_oe,
@@ -964,13 +970,213 @@ def main_reference(args):
     }), flush=True)
 
 
+def main_compare(args):
+    """Fig. 1 shape (Sec. 1): time to solution of DD-alphaAMG, setup included,
+    against oeCG for 1 and for all right-hand sides of the workload.  oeCG
+    solves one right-hand side after another (FP32 CG inside FP64 defect
+    correction); its time for n sources is n times the measured mean of the
+    first sources.  One JSON line, not the bench line."""
+    import numpy as np
+    import torch
+    import inputs
+    import paper_1611_01034_gb300 as tm
+
+    name = args.workload or "24x24x24x48_2lvl_nv24_12pt"
+    wl = WORKLOADS[name]
+    m0, m0_src = (args.m0, "command line") if args.m0 is not None else workload_m0(wl)
+    L, nv, seed = wl["L"], wl["nv"], wl["seed"]
+    U = inputs.gauge_field(L, wl["eps"], seed, workers=min(16, os.cpu_count() or 1))
+    torch.cuda.set_device(0)
+    levels = wl.get("levels", 2)
+    nrhs = wl.get("nrhs", 1)
+    R = args.rhs_batch or wl.get("rhs_batch", nrhs)
+    V, V1, V2 = volumes(wl)
+    n_w = wl["nv2"] * V1 * 2 * nv if levels == 3 else 0
+    tv_host = None
+    if not wl.get("device_inputs"):
+        tv_host = inputs.random_test_vectors(L, nv, seed + inputs.TV_SEED_OFFSET)
+        if levels == 3:
+            Lc1 = tuple(L[d] // wl["agg"][d] for d in range(4))
+            w0 = inputs.random_coarse_vectors(Lc1, 2 * nv, wl["nv2"], seed + inputs.TV_SEED_OFFSET + 1)
+            tv_host = np.concatenate([tv_host.ravel(), w0.ravel()])
+
+    def make_tv():  # as in the benchmark: the 48^3 x 96 test vectors are drawn on the device
+        if tv_host is not None:
+            return torch.from_numpy(tv_host).cuda()
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(seed + inputs.TV_SEED_OFFSET)
+        return torch.randn((nv * V * 12 + n_w,), dtype=torch.complex128, device="cuda", generator=gen)
+
+    x0 = inputs.point_source_site(L, seed + inputs.RHS_SEED_OFFSET) if wl.get("point") else None
+
+    def sources(first, n):
+        if x0 is not None:
+            return point_source_group(L, x0, first, n)
+        return inputs.gaussian_spinor(L, seed + inputs.RHS_SEED_OFFSET + first, nrhs=n).reshape(n, V, 4, 3)
+
+    stream = torch.cuda.current_stream()
+    extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec",
+                                "outer_apply", "block_oe", "sap_prec", "transfer_prec") if k in wl}
+    extra["coarse_mma"] = wl.get("coarse_mma", 0)
+    for kv in args.param or []:
+        k, v = kv.split("=", 1)
+        extra[k] = float(v) if "." in v or "e" in v else int(v)
+    extra.setdefault("cycle_prec", tm.TM_F32)
+    p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv, agg=wl["agg"],
+                  sap_block=wl["sap_block"], setup_iters=wl["setup_iters"], max_rhs=R, levels=levels, **extra)
+    Ud = torch.from_numpy(U).cuda()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    def new_setup():  # a handle with the gauge field and the adaptive setup; returns (handle, seconds)
+        hh = tm.tm_create(p, stream)
+        tvd = make_tv()
+        t, _ = timed(lambda: (tm.tm_load_gauge(hh, Ud), tm.tm_setup(hh, tvd)))
+        del tvd
+        torch.cuda.empty_cache()
+        return hh, t
+
+    # DD-alphaAMG, all sources R at a time (the handle's batch), inputs resident on the device
+    h, t_setup_a = new_setup()
+    t_amgn, it_n, res_n = 0.0, 0, 0.0
+    for g0 in range(0, nrhs, R):
+        n = min(R, nrhs - g0)
+        bg = torch.from_numpy(sources(g0, n)).cuda()
+        xg = torch.zeros_like(bg)
+        t, (st, info) = timed(lambda: tm.tm_solve(h, bg, xg, n, wl["tol"]))
+        if st != tm.TM_OK:
+            raise RuntimeError(tm.tm_last_error(h))
+        t_amgn += t
+        it_n += info.iters
+        res_n = max(res_n, info.true_relres)
+        del bg, xg
+    tm.tm_destroy(h)
+    torch.cuda.empty_cache()
+    # DD-alphaAMG, one source, on a fresh handle (its single-rhs work buffers would not fit next to the batch's)
+    h, t_setup = new_setup()
+    b1 = torch.from_numpy(sources(0, 1)).cuda()
+    x1 = torch.zeros_like(b1)
+    t_amg1, (st, info1) = timed(lambda: tm.tm_solve(h, b1, x1, 1, wl["tol"]))
+    if st != tm.TM_OK:
+        raise RuntimeError(tm.tm_last_error(h))
+    del b1, x1
+    tm.tm_destroy(h)
+    torch.cuda.empty_cache()
+    # oeCG needs only the gauge field: a handle without a hierarchy worth the name
+    pc = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=1.0, nv=1, agg=wl["agg"],
+                   sap_block=wl["sap_block"], max_rhs=1, cycle_prec=tm.TM_F32)
+    h = tm.tm_create(pc, stream)
+    tm.tm_load_gauge(h, Ud)
+    n_cg = min(2, nrhs)
+    t_cg = []
+    cg_iters = []
+    cg_res = 0.0
+    for r in range(n_cg):
+        br = torch.from_numpy(sources(r, 1)).cuda()
+        xr = torch.zeros_like(br)
+        t, (st, info) = timed(lambda: tm.tm_solve_oecg(h, br, xr, 1, wl["tol"]))
+        if st != tm.TM_OK:
+            raise RuntimeError(tm.tm_last_error(h))
+        t_cg.append(t)
+        cg_iters.append(info.iters)
+        cg_res = max(cg_res, info.true_relres)
+    cg_per_rhs = statistics.mean(t_cg)
+    rows = []
+    for n, t_solve in ((1, t_amg1), (nrhs, t_amgn)):
+        amg = t_setup + t_solve
+        rows.append({"nrhs": n, "amg_s": round(amg, 4), "oecg_s": round(n * cg_per_rhs, 4),
+                     "speedup": round(n * cg_per_rhs / amg, 2)})
+    print(json.dumps({
+        "metric": "time to solution to 1e-10: DD-alphaAMG (setup included) vs oeCG, Fig. 1 shape",
+        "unit": "s", "workload": name, "m0": m0, "m0_source": m0_src, "mu": wl["mu"],
+        "amg_setup_s": round(t_setup, 4), "amg_setup_first_s": round(t_setup_a, 4),
+        "amg_solve_1_s": round(t_amg1, 4),
+        "amg_solve_all_s": round(t_amgn, 4), "rhs_all": nrhs,
+        "amg_outer_iters_per_rhs": round(it_n / nrhs, 2),
+        "oecg_s_per_rhs": [round(t, 4) for t in t_cg], "oecg_cg_iters_per_rhs": cg_iters,
+        "true_relres": {"amg": res_n, "oecg": cg_res},
+        "rows": rows,
+        "timing": "wall clock around each call with a device synchronisation on both sides",
+    }), flush=True)
+    tm.tm_destroy(h)
+
+
+def main_check_m0(args):
+    """Check of the near-critical m0 on the workload's own lattice: inverse
+    iteration with the library's squared solve, y = (D(mu)^dagger D(mu))^-1 x,
+    which shares its low modes with D_W^dagger D_W (D^dagger D = D_W^dagger D_W
+    + mu^2).  After k steps 1 / |y| (x normalised) bounds the lowest eigenvalue
+    lambda of D^dagger D from above, hence sigma_min(D_W) <= sqrt(1/|y| - mu^2).
+    One JSON line, not the bench line."""
+    import numpy as np
+    import torch
+    import inputs
+    import paper_1611_01034_gb300 as tm
+
+    name = args.workload or DEFAULT_WORKLOAD
+    wl = WORKLOADS[name]
+    m0, m0_src = (args.m0, "command line") if args.m0 is not None else workload_m0(wl)
+    L, nv, seed = wl["L"], wl["nv"], wl["seed"]
+    U = inputs.gauge_field(L, wl["eps"], seed, workers=min(16, os.cpu_count() or 1))
+    torch.cuda.set_device(0)
+    levels = wl.get("levels", 2)
+    V, V1, V2 = volumes(wl)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed + inputs.TV_SEED_OFFSET)
+    n_w = wl["nv2"] * V1 * 2 * nv if levels == 3 else 0
+    tvd = torch.randn((nv * V * 12 + n_w,), dtype=torch.complex128, device="cuda", generator=gen)
+    extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec",
+                                "outer_apply", "block_oe", "sap_prec", "transfer_prec") if k in wl}
+    extra["coarse_mma"] = wl.get("coarse_mma", 0)
+    extra.setdefault("cycle_prec", tm.TM_F32)
+    p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv, agg=wl["agg"],
+                  sap_block=wl["sap_block"], setup_iters=wl["setup_iters"], max_rhs=1, levels=levels, **extra)
+    stream = torch.cuda.current_stream()
+    h = tm.tm_create(p, stream)
+    tm.tm_load_gauge(h, torch.from_numpy(U).cuda())
+    tm.tm_setup(h, tvd)
+    del tvd
+    torch.cuda.empty_cache()
+    gen.manual_seed(seed + 7777)
+    x = torch.randn((1, V, 4, 3), dtype=torch.complex128, device="cuda", generator=gen)
+    x /= torch.linalg.vector_norm(x)
+    mu = wl["mu"]
+    rows = []
+    t0 = time.time()
+    for k in range(1, args.m0_iters + 1):
+        y = torch.zeros_like(x)
+        st, info = tm.tm_solve_squared(h, x, y, 1, 1e-8)
+        if st != tm.TM_OK:
+            raise RuntimeError(tm.tm_last_error(h))
+        ny = float(torch.linalg.vector_norm(y))
+        rq = float(torch.vdot(x.flatten(), y.flatten()).real)
+        lam = 1.0 / ny
+        rows.append({"k": k, "lambda_upper": lam, "sigma_w_upper": float(np.sqrt(max(lam - mu * mu, 0.0))),
+                     "rayleigh_inverse": rq, "outer_iters": info.iters})
+        x = y / ny
+    print(json.dumps({
+        "metric": "upper bound of sigma_min(D_W(m0)) by inverse iteration on D(mu)^dagger D(mu)",
+        "workload": name, "m0": m0, "m0_source": m0_src, "mu": mu, "target_sigma_min": 1e-3,
+        "iterations": rows, "seconds": round(time.time() - t0, 1),
+        "reading": "D^dagger D = D_W^dagger D_W + mu^2, so lambda_min(D^dagger D) <= 1/|y_k| gives "
+                   "sigma_min(D_W) <= sqrt(1/|y_k| - mu^2); the bound falls towards sigma_min as k grows"}),
+          flush=True)
+    tm.tm_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(WORKLOADS))
+    ap.add_argument("--workload", default=None, choices=list(WORKLOADS),
+                    help="default: the 48^3 x 96 three-level workload (24^3 x 48 with --compare-oecg)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--write-counts", action="store_true")
     ap.add_argument("--param", action="append", help="override a tm_params field: name=value")
@@ -979,12 +1185,24 @@ def main():
                     help="skip the D(mu) and D_c1 measurements on the workload's lattice")
     ap.add_argument("--oracle-worker", default=None)
     ap.add_argument("--m0", type=float, default=None, help="override the workload's tuned m0")
+    ap.add_argument("--compare-oecg", action="store_true",
+                    help="Fig. 1 shape: DD-alphaAMG (with setup) against oeCG on --workload (default 24^3 x 48)")
+    ap.add_argument("--check-m0", action="store_true",
+                    help="inverse iteration on D(mu)^dagger D(mu): an upper bound of sigma_min(D_W(m0))")
+    ap.add_argument("--m0-iters", type=int, default=6)
     ap.add_argument("--coarse-mma", type=int, default=None,
                     help="override the workload's coarse_mma (0 CUDA cores, 1..3 TF32 tensor-core products)")
     args = ap.parse_args()
     if args.oracle_worker:
         print(json.dumps(oracle_unit_costs(args.oracle_worker)))
         return
+    if args.compare_oecg:
+        main_compare(args)
+        return
+    if args.check_m0:
+        main_check_m0(args)
+        return
+    args.workload = args.workload or DEFAULT_WORKLOAD
     if args.impl == "reference":
         main_reference(args)
     elif args.workload == "16x16x16x16_learned":

@@ -63,11 +63,14 @@ typedef enum {
   TM_ERR_STATE = -8          /* call out of order (e.g. solve before setup) */
 } tm_status;
 
-/* storage/arithmetic precision of a field (TM_F16: learned-layer inference and
-   level-1 SAP blocks only).  TM_F32X2: FP32 storage of the input, arithmetic in
-   pairs of FP32 numbers (an unevaluated sum hi + lo, about 2^-46 relative)
-   with an FP64 result; see tm_params.outer_apply and tm_apply. */
-enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2, TM_F32X2 = 4 };
+/* storage/arithmetic precision of a field.  TM_F16 and TM_BF16 are storage
+   formats of operators read by the FP32 K-cycle (arithmetic stays FP32): the
+   interpolation P of the restriction and prolongation (tm_params.transfer_prec),
+   the level-1 SAP blocks (sap1_prec), and FP16 for learned-layer inference.
+   TM_F32X2: FP32 storage of the input, arithmetic in pairs of FP32 numbers (an
+   unevaluated sum hi + lo, about 2^-46 relative) with an FP64 result; see
+   tm_params.outer_apply and tm_apply. */
+enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2, TM_BF16 = 3, TM_F32X2 = 4 };
 
 /* what tm_export copies out */
 enum {
@@ -130,8 +133,9 @@ typedef struct {
   int nn_mode;
   int nn_prec;
   /* Storage of the level-1 operator blocks read by the level-1 SAP smoother
-     (three levels, cycle_prec = TM_F32): TM_F32, or TM_F16 for an FP16 copy
-     (half the bytes; FP32 arithmetic).  The level-1 Krylov solve keeps FP32. */
+     (three levels, cycle_prec = TM_F32): TM_F32, or TM_F16 / TM_BF16 for a
+     16-bit copy (half the bytes; FP32 arithmetic).  The level-1 Krylov solve
+     keeps FP32. */
   int sap1_prec;
   /* Arithmetic of the outer FGMRES's products w = D(mu) z_k with the
      preconditioned vectors z_k (which the FP32 K-cycle returns in FP32):
@@ -154,6 +158,22 @@ typedef struct {
      TM_ERR_TIMEOUT; the context stays usable.  Small values exist to test that
      path. */
   int tc_spin_limit;
+  /* Storage of P as read by the K-cycle's restriction P^dagger r and
+     prolongation P e between the fine and the first coarse level
+     (cycle_prec = TM_F32): TM_F32 (P itself), or TM_F16 / TM_BF16 for a 16-bit
+     copy made after every build of P (half the bytes of the largest operand
+     of both transfers; FP32 arithmetic and FP32 vectors).  The coarse
+     operator is built from the full-precision P.  tm_restrict / tm_prolong
+     with prec = TM_F32 use the same copy. */
+  int transfer_prec;
+  /* Storage of the links, the clover term and the odd-site inverses D_oo^-1
+     read by the fine SAP smoother with odd-even block solves (block_oe = 1,
+     cycle_prec = TM_F32): TM_F32, or TM_F16 / TM_BF16 for 16-bit copies made
+     with every gauge field and twisted mass (FP32 arithmetic and FP32
+     vectors; the smoother then works with the rounded operator, which the
+     flexible outer solver tolerates).  The outer D(mu), the coarse build and
+     the FP32 D apply keep the full-precision operator. */
+  int sap_prec;
 } tm_params;
 
 typedef struct {
@@ -172,7 +192,8 @@ typedef struct {
  * agg2 = sap_block1 = 2^4, mr_iters1 = 4, pre_smooth1 = 0, post_smooth1 = 2,
  * init_sweeps1 = 3, coarse_setup_iters = 3, coarsest_tol = 5e-2,
  * coarsest_maxit = 200, coarse_mma = 0, nn_mode = 0, nn_prec = TM_F32,
- * sap1_prec = TM_F32, outer_apply = TM_F64, block_oe = 0, tc_spin_limit = 0.
+ * sap1_prec = TM_F32, outer_apply = TM_F64, block_oe = 0, tc_spin_limit = 0,
+ * transfer_prec = sap_prec = TM_F32.
  * L, m0, c_sw, mu are 0. */
 void tm_params_default(tm_params* p);
 
@@ -286,6 +307,24 @@ tm_status tm_solve_odd(tm_handle* h, const double* b, double* x, int nrhs, doubl
 tm_status tm_solve_hasenbusch(tm_handle* h, const double* b, double* x, int nrhs, double mu, double rho, double tol,
                               tm_solve_info* info);
 
+/* f4: the comparison solver of Fig. 1 (Sec. 1): oeCG, conjugate gradient on
+ * D^dagger D^ x_o = D^dagger b^ for the odd-even reduced operator
+ * D^ = D_oo - D_oe D_ee^-1 D_eo of Sec. 3 (twisted mass mu on even and
+ * mu + rho on odd sites as set by tm_set_mu / tm_set_mu_eo), with
+ * b^ = b_o - D_oe D_ee^-1 b_e and x_e = D_ee^-1 (b_e - D_eo x_o) afterwards.
+ * CG iterates in FP32 (CGLS form, scalars on the device) inside FP64 defect
+ * correction: after each inner solve, which reduces the defect by 1e-5 or to
+ * the target, the reduced residual is recomputed in FP64 and the solve stops
+ * once |b^ - D^ x_o| = |b - D x| <= tol |b|.  Right-hand sides are solved
+ * one after another.  Needs tm_load_gauge only (no setup).  b, x as tm_solve
+ * (x holds the start vector; its odd sites are used).  maxit bounds the CG
+ * iterations per right-hand side.  info->iters = CG iterations in all,
+ * ->restarts = defect-correction cycles, ->true_relres = max FP64 relative
+ * residual, coarse_iters = kcycles = 0.  Errors: TM_ERR_STATE (no gauge
+ * field), TM_ERR_ARG (odd X extent), TM_ERR_NOT_CONVERGED. */
+tm_status tm_solve_oecg(tm_handle* h, const double* b, double* x, int nrhs, double tol, int maxit,
+                        tm_solve_info* info);
+
 /* A7: solve D(mu) x_r = b_r for nrhs right-hand sides to ||b - D x|| <=
  * tol ||b|| by FGMRES(restart) preconditioned with the K-cycle of eq. (1).
  * b, x natural spinors (host or device); x holds the start vector on entry
@@ -356,7 +395,8 @@ tm_status tm_apply(tm_handle* h, int level, int prec, const void* in, void* out,
 tm_status tm_sap(tm_handle* h, int prec, const void* b, void* x, int sweeps, int nrhs);
 
 /* A3: coarse = P^dagger fine.  A6: fine = P coarse (accumulate = 0) or
- * fine += P coarse (accumulate = 1).  prec = cycle_prec, after a setup. */
+ * fine += P coarse (accumulate = 1).  prec = cycle_prec, after a setup; with
+ * a 16-bit transfer_prec the FP32 transfers read the 16-bit copy of P. */
 tm_status tm_restrict(tm_handle* h, int prec, const void* fine, void* coarse, int nrhs);
 tm_status tm_prolong(tm_handle* h, int prec, const void* coarse, void* fine, int nrhs, int accumulate);
 

@@ -11,7 +11,7 @@ library_path = os.path.join(_HERE, "libtmamg.so")
 TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_OOM = 0, -1, -2, -3
 TM_ERR_NOT_CONVERGED, TM_ERR_TIMEOUT, TM_ERR_NOT_SU3 = -4, -5, -6
 TM_ERR_NONFINITE, TM_ERR_STATE = -7, -8
-TM_F64, TM_F32, TM_F16, TM_F32X2 = 0, 1, 2, 4
+TM_F64, TM_F32, TM_F16, TM_BF16, TM_F32X2 = 0, 1, 2, 3, 4
 TM_EXPORT_P, TM_EXPORT_DC, TM_EXPORT_CLOVER, TM_EXPORT_TV = 0, 1, 2, 3
 TM_EXPORT_P2, TM_EXPORT_DC2, TM_EXPORT_TV1 = 4, 5, 6
 
@@ -28,7 +28,8 @@ class tm_params(ctypes.Structure):
         ("mr_iters1", c_int), ("pre_smooth1", c_int), ("post_smooth1", c_int), ("init_sweeps1", c_int),
         ("coarse_setup_iters", c_int), ("coarsest_tol", c_double), ("coarsest_maxit", c_int),
         ("coarse_mma", c_int), ("nn_mode", c_int), ("nn_prec", c_int), ("sap1_prec", c_int),
-        ("outer_apply", c_int), ("block_oe", c_int), ("tc_spin_limit", c_int),
+        ("outer_apply", c_int), ("block_oe", c_int), ("tc_spin_limit", c_int), ("transfer_prec", c_int),
+        ("sap_prec", c_int),
     ]
 
 
@@ -64,6 +65,7 @@ _SIGS = {
     "tm_solve_odd": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
     "tm_solve_hasenbusch": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_double,
                                     POINTER(tm_solve_info)]),
+    "tm_solve_oecg": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_int, POINTER(tm_solve_info)]),
     "tm_autotune_build": (c_int, [c_void_p, c_char_p, c_int, POINTER(c_double)]),
     "tm_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
     "tm_solve_squared": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, POINTER(tm_solve_info)]),
@@ -233,6 +235,14 @@ def tm_solve_odd(h, b, x, nrhs: int, tol: float):
 def tm_solve_hasenbusch(h, b, x, nrhs: int, mu: float, rho: float, tol: float):
     info = tm_solve_info()
     st = lib().tm_solve_hasenbusch(h, _ptr(b), _ptr(x), nrhs, mu, rho, tol, ctypes.byref(info))
+    if st not in (TM_OK, TM_ERR_NOT_CONVERGED):
+        _check(st, h)
+    return st, info
+
+
+def tm_solve_oecg(h, b, x, nrhs: int, tol: float, maxit: int = 100000):
+    info = tm_solve_info()
+    st = lib().tm_solve_oecg(h, _ptr(b), _ptr(x), nrhs, tol, maxit, ctypes.byref(info))
     if st not in (TM_OK, TM_ERR_NOT_CONVERGED):
         _check(st, h)
     return st, info

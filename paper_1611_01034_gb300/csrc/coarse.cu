@@ -116,8 +116,17 @@ void launch_orthonormalise(T* P, const AggGeom& ag, int* err, cudaStream_t st) {
 // ===========================================================================
 // restriction  coarse(a, chi*Nv + i) = sum_{x in a, comp in chi} conj(P_i) fine
 // ===========================================================================
-template <typename T>
-__global__ void k_restrict(const T* __restrict__ P, const T* __restrict__ fine, T* __restrict__ coarse,
+// column i of P at site s, stored as T (S = ST_NATIVE) or in 16 bits
+template <typename T, int S>
+__device__ __forceinline__ void ld_pcol(const void* __restrict__ P, int i, long V, long s, cx<T> (&p)[12]) {
+  if constexpr (S == ST_NATIVE)
+    ld_cx<T, 12>(static_cast<const T*>(P) + (long)i * NR_SPINOR * V, V, s, p);
+  else
+    ld_cx16<T, S, 12>(static_cast<const unsigned short*>(P) + (long)i * NR_SPINOR * V, V, s, p);
+}
+
+template <typename T, int S>
+__global__ void k_restrict(const void* __restrict__ P, const T* __restrict__ fine, T* __restrict__ coarse,
                            AggGeom ag, int nrhs) {
   __shared__ T red[32 * 16];
   // right-hand sides fastest over the CTAs: an aggregate's P columns are reused from L2
@@ -139,7 +148,7 @@ __global__ void k_restrict(const T* __restrict__ P, const T* __restrict__ fine, 
       for (int ii = 0; ii < 4; ++ii) {
         if (i0 + ii < nv) {
           cx<T> p[12];
-          ld_cx<T, 12>(P + (long)(i0 + ii) * NR_SPINOR * V, V, s, p);
+          ld_pcol<T, S>(P, i0 + ii, V, s, p);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             cx<T> acc{0, 0};
@@ -160,17 +169,23 @@ __global__ void k_restrict(const T* __restrict__ P, const T* __restrict__ fine, 
 }
 
 template <typename T>
-void launch_restrict(const T* P, const T* fine, T* coarse, const AggGeom& ag, int nrhs, cudaStream_t st) {
+void launch_restrict(const T* P, const T* fine, T* coarse, const AggGeom& ag, int nrhs, cudaStream_t st,
+                     const void* P16, int p16) {
   const int threads = (ag.asites + 31) / 32 * 32;
   dim3 grid((unsigned)ag.gc.V * (unsigned)nrhs);
-  k_restrict<T><<<grid, threads, 0, st>>>(P, fine, coarse, ag, nrhs);
+  if (P16 && p16 == ST_F16)
+    k_restrict<T, ST_F16><<<grid, threads, 0, st>>>(P16, fine, coarse, ag, nrhs);
+  else if (P16 && p16 == ST_BF16)
+    k_restrict<T, ST_BF16><<<grid, threads, 0, st>>>(P16, fine, coarse, ag, nrhs);
+  else
+    k_restrict<T, ST_NATIVE><<<grid, threads, 0, st>>>(P, fine, coarse, ag, nrhs);
 }
 
 // ===========================================================================
 // prolongation  fine(x, comp in chi) (+)= sum_i P_i(x, comp) coarse(a(x), chi*Nv + i)
 // ===========================================================================
-template <typename T, bool ACC>
-__global__ void k_prolong(const T* __restrict__ P, const T* __restrict__ coarse, T* __restrict__ fine,
+template <typename T, bool ACC, int S>
+__global__ void k_prolong(const void* __restrict__ P, const T* __restrict__ coarse, T* __restrict__ fine,
                           AggGeom ag, int nrhs) {
   const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;  // right-hand sides fastest (P reuse)
   const int rhs = blockIdx.x % nrhs, nv = ag.nv;
@@ -188,7 +203,7 @@ __global__ void k_prolong(const T* __restrict__ P, const T* __restrict__ coarse,
     for (int k = 0; k < 12; ++k) out[k] = cx<T>{0, 0};
   for (int i = 0; i < nv; ++i) {
     cx<T> p[12];
-    ld_cx<T, 12>(P + (long)i * NR_SPINOR * V, V, s, p);
+    ld_pcol<T, S>(P, i, V, s, p);
     const cx<T> e0 = e[i], e1 = e[nv + i];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -199,14 +214,50 @@ __global__ void k_prolong(const T* __restrict__ P, const T* __restrict__ coarse,
   st_cx<T, 12>(f, V, s, out);
 }
 
-template <typename T>
-void launch_prolong(const T* P, const T* coarse, T* fine, const AggGeom& ag, int nrhs, bool accumulate,
-                    cudaStream_t st) {
+template <typename T, int S>
+void prolong_s(const void* P, const T* coarse, T* fine, const AggGeom& ag, int nrhs, bool accumulate,
+               cudaStream_t st) {
   dim3 grid((unsigned)((ag.g.V + 127) / 128) * (unsigned)nrhs);
   if (accumulate)
-    k_prolong<T, true><<<grid, 128, 0, st>>>(P, coarse, fine, ag, nrhs);
+    k_prolong<T, true, S><<<grid, 128, 0, st>>>(P, coarse, fine, ag, nrhs);
   else
-    k_prolong<T, false><<<grid, 128, 0, st>>>(P, coarse, fine, ag, nrhs);
+    k_prolong<T, false, S><<<grid, 128, 0, st>>>(P, coarse, fine, ag, nrhs);
+}
+
+template <typename T>
+void launch_prolong(const T* P, const T* coarse, T* fine, const AggGeom& ag, int nrhs, bool accumulate,
+                    cudaStream_t st, const void* P16, int p16) {
+  if (P16 && p16 == ST_F16)
+    prolong_s<T, ST_F16>(P16, coarse, fine, ag, nrhs, accumulate, st);
+  else if (P16 && p16 == ST_BF16)
+    prolong_s<T, ST_BF16>(P16, coarse, fine, ag, nrhs, accumulate, st);
+  else
+    prolong_s<T, ST_NATIVE>(P, coarse, fine, ag, nrhs, accumulate, st);
+}
+
+// 16-bit copy of n_cx FP32 complex numbers (element order kept)
+template <int S>
+__global__ void k_to16(const float2* __restrict__ in, unsigned* __restrict__ out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    unsigned u;
+    if constexpr (S == ST_F16) {
+      const __half2 v = __float22half2_rn(in[i]);
+      memcpy(&u, &v, 4);
+    } else {
+      const __nv_bfloat162 v = __float22bfloat162_rn(in[i]);
+      memcpy(&u, &v, 4);
+    }
+    out[i] = u;
+  }
+}
+
+void launch_to16(const float* in, void* out, long n_cx, int kind, cudaStream_t st) {
+  long b = (n_cx + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (kind == ST_F16)
+    k_to16<ST_F16><<<(int)b, 256, 0, st>>>(reinterpret_cast<const float2*>(in), static_cast<unsigned*>(out), n_cx);
+  else
+    k_to16<ST_BF16><<<(int)b, 256, 0, st>>>(reinterpret_cast<const float2*>(in), static_cast<unsigned*>(out), n_cx);
 }
 
 // ===========================================================================
@@ -990,8 +1041,9 @@ TM_INST_B(float)
 
 #define TM_INST(T)                                                                                               \
   template void launch_orthonormalise<T>(T*, const AggGeom&, int*, cudaStream_t);                              \
-  template void launch_restrict<T>(const T*, const T*, T*, const AggGeom&, int, cudaStream_t);                 \
-  template void launch_prolong<T>(const T*, const T*, T*, const AggGeom&, int, bool, cudaStream_t);            \
+  template void launch_restrict<T>(const T*, const T*, T*, const AggGeom&, int, cudaStream_t, const void*, int); \
+  template void launch_prolong<T>(const T*, const T*, T*, const AggGeom&, int, bool, cudaStream_t, const void*,  \
+                                  int);                                                                        \
   template void launch_coarse_build<T>(const T*, const T*, const T*, T*, const AggGeom&, double, cudaStream_t,   \
                                        BuildShape, double);                                                   \
   template void launch_coarse_apply<T>(const T*, const T*, T*, const Lat&, int, double, int, cudaStream_t);    \

@@ -14,11 +14,12 @@
 
 namespace tmamg {
 
-// D_c1 block entry: stored in T, or as FP16 (re, im) pairs when H (arithmetic stays in T)
-template <typename T, bool H>
+// D_c1 block entry: stored in T (S = ST_NATIVE), or as 16-bit (re, im) pairs
+// (ST_F16, ST_BF16; arithmetic stays in T)
+template <typename T, int S>
 __device__ __forceinline__ cx<T> ld_blk(const void* __restrict__ Dc, long idx) {
-  if constexpr (H) {
-    const float2 f = __half22float2(reinterpret_cast<const __half2*>(Dc)[idx]);
+  if constexpr (S != ST_NATIVE) {
+    const float2 f = unpack16x2<S>(__ldg(reinterpret_cast<const unsigned*>(Dc) + idx));
     return cx<T>{(T)f.x, (T)f.y};
   } else {
     return reinterpret_cast<const cx<T>*>(Dc)[idx];
@@ -36,7 +37,7 @@ __device__ __forceinline__ int c_nb(const Lat& g, int s, int t) {
 // ===========================================================================
 // coarse SAP: one colour; CTA = one block of level-1 sites, thread = (site, row)
 // ===========================================================================
-template <typename T, bool H>
+template <typename T, int H>
 __global__ void k_csap(const void* __restrict__ Dc, const T* __restrict__ b, T* __restrict__ x, CSapGeom sg, T mu,
                        int n_mr, int colour, int nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -131,26 +132,16 @@ __global__ void k_csap(const void* __restrict__ Dc, const T* __restrict__ b, T* 
 
 template <typename T>
 void launch_csap_colour(const T* Dc, const T* b, T* x, const CSapGeom& sg, double mu, int n_mr, int colour,
-                        int nrhs, cudaStream_t st, const void* Dc_half) {
+                        int nrhs, cudaStream_t st, const void* Dc_half, int half_kind) {
   const int threads = (sg.bsites * sg.n + 31) / 32 * 32;
   const size_t smem = (size_t)sg.bsites * sg.n * sizeof(cx<T>) + 32 * 3 * sizeof(T);
   dim3 grid((unsigned)(sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2) * (unsigned)nrhs);
-  if (Dc_half)
-    k_csap<T, true><<<grid, threads, smem, st>>>(Dc_half, b, x, sg, (T)mu, n_mr, colour, nrhs);
+  if (Dc_half && half_kind == ST_BF16)
+    k_csap<T, ST_BF16><<<grid, threads, smem, st>>>(Dc_half, b, x, sg, (T)mu, n_mr, colour, nrhs);
+  else if (Dc_half)
+    k_csap<T, ST_F16><<<grid, threads, smem, st>>>(Dc_half, b, x, sg, (T)mu, n_mr, colour, nrhs);
   else
-    k_csap<T, false><<<grid, threads, smem, st>>>(Dc, b, x, sg, (T)mu, n_mr, colour, nrhs);
-}
-
-// FP16 (re, im) copy of FP32 coarse blocks
-__global__ void k_to_half2(const float2* __restrict__ in, __half2* __restrict__ out, long n) {
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    out[i] = __float22half2_rn(in[i]);
-}
-
-void launch_blocks_to_half(const float* Dc, void* out, long ncx, cudaStream_t st) {
-  long b = (ncx + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
-  k_to_half2<<<(int)b, 256, 0, st>>>(reinterpret_cast<const float2*>(Dc), static_cast<__half2*>(out), ncx);
+    k_csap<T, ST_NATIVE><<<grid, threads, smem, st>>>(Dc, b, x, sg, (T)mu, n_mr, colour, nrhs);
 }
 
 // ===========================================================================
@@ -423,7 +414,7 @@ void launch_cbuild(const T* Dc1, const T* P2, T* Dc2, const CAggGeom& ag, cudaSt
 
 #define TM_INST(T)                                                                                           \
   template void launch_csap_colour<T>(const T*, const T*, T*, const CSapGeom&, double, int, int, int,       \
-                                      cudaStream_t, const void*);                                            \
+                                      cudaStream_t, const void*, int);                                       \
   template void launch_corth<T>(T*, const CAggGeom&, int*, cudaStream_t);                                   \
   template void launch_crestrict<T>(const T*, const T*, T*, const CAggGeom&, int, cudaStream_t);            \
   template void launch_cprolong<T>(const T*, const T*, T*, const CAggGeom&, int, bool, cudaStream_t);       \

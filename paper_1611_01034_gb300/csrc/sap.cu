@@ -15,6 +15,8 @@
 // Block colour = parity of the sum of block coordinates; every dimension has
 // an even number (>= 2) of blocks, so no block touches itself or a block of
 // its own colour.
+#include <type_traits>
+
 #include "tm_kernels.h"
 #include "tm_stencil.cuh"
 
@@ -216,9 +218,9 @@ __device__ __forceinline__ int half_index(const int lc[4], const int blk[4]) {
 
 // acc += hops (Dirichlet, without the -1/2) from the neighbours of a site inside
 // the block, whose values of the other parity are in shared memory src [12][HB]
-template <typename T>
+template <typename T, int S>
 __device__ __forceinline__ void oe_block_hops(const cx<T>* __restrict__ src, int HB, const int lc[4],
-                                              const int blk[4], const T* __restrict__ gauge, const Lat& g, int s,
+                                              const int blk[4], const void* __restrict__ gauge, const Lat& g, int s,
                                               const int c[4], cx<T> (&acc)[12]) {
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = cx<T>{0, 0};
@@ -232,10 +234,10 @@ __device__ __forceinline__ void oe_block_hops(const cx<T>* __restrict__ src, int
 #pragma unroll
       for (int k = 0; k < 12; ++k) p[k] = src[k * HB + j];
       switch (mu) {
-        case 0: hop_fwd_p<T, 0>(p, gauge, g.V, s, T(1), acc); break;
-        case 1: hop_fwd_p<T, 1>(p, gauge, g.V, s, T(1), acc); break;
-        case 2: hop_fwd_p<T, 2>(p, gauge, g.V, s, T(1), acc); break;
-        default: hop_fwd_p<T, 3>(p, gauge, g.V, s, T(1), acc); break;
+        case 0: hop_fwd_p<T, 0, S>(p, gauge, g.V, s, T(1), acc); break;
+        case 1: hop_fwd_p<T, 1, S>(p, gauge, g.V, s, T(1), acc); break;
+        case 2: hop_fwd_p<T, 2, S>(p, gauge, g.V, s, T(1), acc); break;
+        default: hop_fwd_p<T, 3, S>(p, gauge, g.V, s, T(1), acc); break;
       }
     }
     if (lc[mu] > 0) {
@@ -247,10 +249,10 @@ __device__ __forceinline__ void oe_block_hops(const cx<T>* __restrict__ src, int
       for (int k = 0; k < 12; ++k) p[k] = src[k * HB + j];
       const int sb = nb_bwd(g, s, c, mu);
       switch (mu) {
-        case 0: hop_bwd_p<T, 0>(p, gauge, g.V, sb, T(1), acc); break;
-        case 1: hop_bwd_p<T, 1>(p, gauge, g.V, sb, T(1), acc); break;
-        case 2: hop_bwd_p<T, 2>(p, gauge, g.V, sb, T(1), acc); break;
-        default: hop_bwd_p<T, 3>(p, gauge, g.V, sb, T(1), acc); break;
+        case 0: hop_bwd_p<T, 0, S>(p, gauge, g.V, sb, T(1), acc); break;
+        case 1: hop_bwd_p<T, 1, S>(p, gauge, g.V, sb, T(1), acc); break;
+        case 2: hop_bwd_p<T, 2, S>(p, gauge, g.V, sb, T(1), acc); break;
+        default: hop_bwd_p<T, 3, S>(p, gauge, g.V, sb, T(1), acc); break;
       }
     }
   }
@@ -258,8 +260,8 @@ __device__ __forceinline__ void oe_block_hops(const cx<T>* __restrict__ src, int
 
 // y = D_oo^-1 p at odd site s: two general 6x6 complex blocks, 36 float4 /
 // double2-pair chunks per odd site, compact odd index s >> 1
-template <typename T>
-__device__ __forceinline__ void apply_dinv(const T* __restrict__ dinv, long Vh, int s, const cx<T> (&p)[12],
+template <typename T, int S>
+__device__ __forceinline__ void apply_dinv(const void* __restrict__ dinv, long Vh, int s, const cx<T> (&p)[12],
                                            cx<T> (&y)[12]) {
   const long so = s >> 1;
 #pragma unroll
@@ -267,7 +269,11 @@ __device__ __forceinline__ void apply_dinv(const T* __restrict__ dinv, long Vh, 
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       cx<T> m[6];
-      ld_cx<T, 6>(dinv + (long)(h * 6 + i) * 12 * Vh, Vh, so, m);  // row i of block h: 6 complex
+      const long off = (long)(h * 6 + i) * 12 * Vh;  // row i of block h: 6 complex
+      if constexpr (S == ST_NATIVE)
+        ld_cx<T, 6>(static_cast<const T*>(dinv) + off, Vh, so, m);
+      else
+        ld_cx16<T, S, 6>(static_cast<const unsigned short*>(dinv) + off, Vh, so, m);
       cx<T> acc = m[0] * p[6 * h];
 #pragma unroll
       for (int j = 1; j < 6; ++j) cfma(acc, m[j], p[6 * h + j]);
@@ -277,14 +283,14 @@ __device__ __forceinline__ void apply_dinv(const T* __restrict__ dinv, long Vh, 
 }
 
 // r = b - D x at site s (full operator, neighbours from global memory; b may be null)
-template <typename T>
+template <typename T, int S = ST_NATIVE>
 __device__ __forceinline__ void sap_residual_site(const T* __restrict__ x, const T* __restrict__ b,
-                                                  const T* __restrict__ gauge, const T* __restrict__ clover,
+                                                  const void* __restrict__ gauge, const void* __restrict__ clover,
                                                   const Lat& g, int s, const int c[4], T bc, T mu, cx<T> (&r)[12]) {
   cx<T> acc[12], p[12];
-  all_hops_global<T>(x, gauge, g, s, c, bc, acc);
+  all_hops_global<T, S>(x, gauge, g, s, c, bc, acc);
   ld_cx<T, 12>(x, g.V, s, p);
-  site_diag<T>(clover, g.V, s, mu, p, r);
+  site_diag<T, S>(clover, g.V, s, mu, p, r);
 #pragma unroll
   for (int i = 0; i < 12; ++i) r[i] = T(0.5) * acc[i] - r[i];
   if (b) {
@@ -298,9 +304,9 @@ __device__ __forceinline__ void sap_residual_site(const T* __restrict__ x, const
 
 template <typename T>
 struct SapOeArgs {
-  const T* gauge;
-  const T* clover;
-  const T* dinv;
+  const void* gauge;  // links, clover and D_oo^-1 as T, or in 16 bits (kernel parameter S)
+  const void* clover;
+  const void* dinv;
   const T* b;
   T* x;
   SapGeom sg;
@@ -321,7 +327,7 @@ struct SapOeArgs {
 //   step 2k+1 (even):        q = D_ee rho - D_eo t_o; MR update of e_e, rho
 //   step 2 n_MR + 2 (odd):   e_o = D_oo^-1 (r_o - D_oe e_e); x += e
 // (D_eo, D_oe = -1/2 times the intra-block hops.)
-template <typename T>
+template <typename T, int S>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SapGeom& sg = a.sg;
@@ -382,8 +388,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArg
     if (act) {
       int lc[4], c[4];
       const int s = site_of(pass ^ 1, lc, c);
-      sap_residual_site<T>(x, a.b ? a.b + off : nullptr, a.gauge, a.clover, g, s, c, a.bc,
-                           pass == 0 ? a.mu + a.rho : a.mu, rho);
+      sap_residual_site<T, S>(x, a.b ? a.b + off : nullptr, a.gauge, a.clover, g, s, c, a.bc,
+                              pass == 0 ? a.mu + a.rho : a.mu, rho);
       if (pass == 0) {
 #pragma unroll
         for (int i = 0; i < 12; ++i) ro[i * HB + j] = rho[i];
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArg
     cx<T> acc[12];
     int lc[4], c[4];
     const int s = site_of(parity, lc, c);
-    if (act && st > 0) oe_block_hops<T>(parity ? ev : od, HB, lc, sg.blk, a.gauge, g, s, c, acc);
+    if (act && st > 0) oe_block_hops<T, S>(parity ? ev : od, HB, lc, sg.blk, a.gauge, g, s, c, acc);
     if (parity) {
       // odd site: y = D_oo^-1 in
       if (act) {
@@ -416,7 +422,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArg
           else
             in[i] = -half * acc[i];
         }
-        apply_dinv<T>(a.dinv, Vh, s, in, y);
+        apply_dinv<T, S>(a.dinv, Vh, s, in, y);
         if (!last) {
 #pragma unroll
           for (int i = 0; i < 12; ++i) od[i * HB + j] = y[i];
@@ -446,7 +452,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArg
         cx<T> q[12];
         T dots[3] = {0, 0, 0};
         if (act) {
-          site_diag<T>(a.clover, g.V, s, a.mu, rho, q);
+          site_diag<T, S>(a.clover, g.V, s, a.mu, rho, q);
 #pragma unroll
           for (int i = 0; i < 12; ++i) {
             q[i] = q[i] + half * acc[i];
@@ -475,26 +481,36 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_sap_oe(SapOeArg
   }
 }
 
+template <typename T, int S>
+void sap_oe_s(const SapOeArgs<T>& a, int nblocks, int threads, size_t smem, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_sap_oe<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  k_sap_oe<T, S><<<dim3(nblocks), threads, smem, st>>>(a);
+}
+
 template <typename T>
-void launch_sap_oe_colour(const T* gauge, const T* clover, const T* dinv, const T* b, T* x, const SapGeom& sg,
-                          double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st, double rho) {
+void launch_sap_oe_colour(const void* gauge, const void* clover, const void* dinv, const T* b, T* x,
+                          const SapGeom& sg, double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st,
+                          double rho, int s16) {
   const int HB = sg.bsites / 2;
   const int threads = (HB + 31) / 32 * 32;
   const size_t smem = 3 * 12 * (size_t)HB * sizeof(cx<T>) + 32 * 3 * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_sap_oe<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
   const int nblk_colour = sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2;
   SapOeArgs<T> a{gauge, clover, dinv, b, x, sg, (T)mu, (T)bc_t, n_mr, colour, nrhs, (T)rho};
-  k_sap_oe<T><<<dim3(nblk_colour * nrhs), threads, smem, st>>>(a);
+  if constexpr (std::is_same<T, float>::value) {
+    if (s16 == ST_F16) return sap_oe_s<T, ST_F16>(a, nblk_colour * nrhs, threads, smem, st);
+    if (s16 == ST_BF16) return sap_oe_s<T, ST_BF16>(a, nblk_colour * nrhs, threads, smem, st);
+  }
+  sap_oe_s<T, ST_NATIVE>(a, nblk_colour * nrhs, threads, smem, st);
 }
 
-template void launch_sap_oe_colour<double>(const double*, const double*, const double*, const double*, double*,
-                                           const SapGeom&, double, double, int, int, int, cudaStream_t, double);
-template void launch_sap_oe_colour<float>(const float*, const float*, const float*, const float*, float*,
-                                          const SapGeom&, double, double, int, int, int, cudaStream_t, double);
+template void launch_sap_oe_colour<double>(const void*, const void*, const void*, const double*, double*,
+                                           const SapGeom&, double, double, int, int, int, cudaStream_t, double, int);
+template void launch_sap_oe_colour<float>(const void*, const void*, const void*, const float*, float*,
+                                          const SapGeom&, double, double, int, int, int, cudaStream_t, double, int);
 
 // ===========================================================================
 // D_oo^-1 for the odd-even block solve: per odd site the inverses of the two
@@ -505,7 +521,8 @@ template void launch_sap_oe_colour<float>(const float*, const float*, const floa
 // ===========================================================================
 namespace {
 template <typename T>
-__global__ void k_clover_inverse(const double* __restrict__ c64, T* __restrict__ dinv, Lat g, double mu, int* err) {
+__global__ void k_clover_inverse(const double* __restrict__ c64, T* __restrict__ dinv, Lat g, double mu, int* err,
+                                 int parity) {
   const long so = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long Vh = g.V / 2;
   if (so >= Vh) return;
@@ -516,7 +533,7 @@ __global__ void k_clover_inverse(const double* __restrict__ c64, T* __restrict__
   c[2] = (int)(row % g.L[2]);
   c[1] = (int)((row / g.L[2]) % g.L[1]);
   c[0] = (int)(row / ((long)g.L[2] * g.L[1]));
-  c[3] = 2 * xh + (((c[0] + c[1] + c[2]) & 1) ^ 1);
+  c[3] = 2 * xh + (((c[0] + c[1] + c[2]) & 1) ^ parity);
   const int s = ((c[0] * g.L[1] + c[1]) * g.L[2] + c[2]) * g.L[3] + c[3];
   double m72[72];
   ld_re<double, 72>(c64, g.V, s, m72);
@@ -571,11 +588,12 @@ __global__ void k_clover_inverse(const double* __restrict__ c64, T* __restrict__
 }  // namespace
 
 template <typename T>
-void launch_clover_inverse(const double* c64, T* dinv, const Lat& g, double mu, int* err, cudaStream_t st) {
+void launch_clover_inverse(const double* c64, T* dinv, const Lat& g, double mu, int* err, cudaStream_t st,
+                           int parity) {
   const long Vh = g.V / 2;
-  k_clover_inverse<T><<<(unsigned)((Vh + 63) / 64), 64, 0, st>>>(c64, dinv, g, mu, err);
+  k_clover_inverse<T><<<(unsigned)((Vh + 63) / 64), 64, 0, st>>>(c64, dinv, g, mu, err, parity);
 }
-template void launch_clover_inverse<double>(const double*, double*, const Lat&, double, int*, cudaStream_t);
-template void launch_clover_inverse<float>(const double*, float*, const Lat&, double, int*, cudaStream_t);
+template void launch_clover_inverse<double>(const double*, double*, const Lat&, double, int*, cudaStream_t, int);
+template void launch_clover_inverse<float>(const double*, float*, const Lat&, double, int*, cudaStream_t, int);
 
 }  // namespace tmamg

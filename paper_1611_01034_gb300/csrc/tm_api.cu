@@ -96,7 +96,11 @@ struct tm_handle {
   int* d_even2 = nullptr;
   int* d_odd2 = nullptr;
   int* d_cidx2 = nullptr;
-  void* Dc1h = nullptr;  // FP16 copy of D_c1 for the level-1 SAP (sap1_prec = TM_F16)
+  void* Dc1h = nullptr;  // 16-bit copy of D_c1 for the level-1 SAP (sap1_prec = TM_F16 / TM_BF16)
+  void* P16 = nullptr;   // 16-bit copy of P for the transfers (transfer_prec = TM_F16 / TM_BF16)
+  void* g16 = nullptr;   // 16-bit links, clover and odd-site inverses of the fine SAP (sap_prec)
+  void* c16 = nullptr;
+  void* dinv16 = nullptr;
   // links and clover as FP32 pairs for the outer D(mu) z_k (outer_apply = TM_F32X2)
   void* gdf = nullptr;
   void* cdf = nullptr;
@@ -192,13 +196,14 @@ T* Wz(tm_handle* h, const std::string& name, size_t count) {
 // ---------------------------------------------------------------------------
 enum ProfKind {
   PK_DSLASH64 = 0, PK_DSLASH32, PK_SAP, PK_RESTRICT, PK_PROLONG, PK_COARSE_OE, PK_BLAS_FINE, PK_BLAS_COARSE,
-  PK_BUILD, PK_OTHER, PK_CSAP, PK_LEVEL1, PK_NN, PK_DSLASHDF, PK_L1XFER, PK_N
+  PK_BUILD, PK_OTHER, PK_CSAP, PK_LEVEL1, PK_NN, PK_DSLASHDF, PK_L1XFER, PK_OECG_OP, PK_OECG_BLAS, PK_N
 };
 static_assert(PK_N <= 24, "profile arrays of the handle hold 24 classes");
 const char* const kProfNames[PK_N] = {"dslash_f64", "dslash_f32",   "sap",          "restrict",
                                       "prolong",    "coarse_oe",    "blas_fine",    "blas_coarse",
                                       "coarse_build", "other",      "coarse_sap",   "level1",
-                                      "nn",           "dslash_f32x2", "level1_transfer"};
+                                      "nn",           "dslash_f32x2", "level1_transfer", "oecg_operator",
+                                      "oecg_blas"};
 
 cudaEvent_t take_event(tm_handle* h) {
   if (!h->evpool.empty()) {
@@ -309,9 +314,12 @@ void sap_sweeps(tm_handle* h, const T* b, T* x, int sweeps, int nrhs) {
   for (int s = 0; s < sweeps; ++s)
     for (int colour = 0; colour < 2; ++colour) {
       Prof pf(h, PK_SAP, nrhs);
-      if (h->p.block_oe)
-        launch_sap_oe_colour<T>(gaugeT<T>(h), cloverT<T>(h), static_cast<const T*>(h->dinv_sap), b, x, h->sg,
-                                h->p.mu, h->p.bc_t, h->p.mr_iters, colour, nrhs, h->st, h->rho);
+      if (h->p.block_oe && h->g16)  // 16-bit links, clover and D_oo^-1 (sap_prec)
+        launch_sap_oe_colour<T>(h->g16, h->c16, h->dinv16, b, x, h->sg, h->p.mu, h->p.bc_t, h->p.mr_iters, colour,
+                                nrhs, h->st, h->rho, h->p.sap_prec);
+      else if (h->p.block_oe)
+        launch_sap_oe_colour<T>(gaugeT<T>(h), cloverT<T>(h), h->dinv_sap, b, x, h->sg, h->p.mu, h->p.bc_t,
+                                h->p.mr_iters, colour, nrhs, h->st, h->rho);
       else
         launch_sap_colour<T>(gaugeT<T>(h), cloverT<T>(h), b, x, h->sg, h->p.mu, h->p.bc_t, h->p.mr_iters, colour,
                              nrhs, h->st, h->rho);
@@ -331,6 +339,10 @@ void build_sap_inverse(tm_handle* h) {
     launch_clover_inverse<float>(h->c64, static_cast<float*>(h->dinv_sap), h->g, h->p.mu + h->rho, h->d_err,
                                  h->st);
   CKL();
+  if (h->dinv16) {
+    launch_to16(static_cast<const float*>(h->dinv_sap), h->dinv16, (long)h->g.V / 2 * 72, h->p.sap_prec, h->st);
+    CKL();
+  }
 }
 
 // ||x_r||^2 for nrhs vectors -> host
@@ -531,6 +543,19 @@ KrylovOut krylov(tm_handle* h, const std::string& tag, FA A, FAZ AZ, FM M, bool 
 
 // ---------------------------------------------------------------------------
 // coarse level
+// 16-bit copies of FP32 operators read by the K-cycle: D_c1 for the level-1
+// SAP (sap1_prec) and P for the transfers (transfer_prec)
+void refresh_16bit(tm_handle* h) {
+  if (h->Dc1h) {
+    launch_to16(static_cast<const float*>(h->Dc), h->Dc1h, (long)h->gc.V * 9 * h->n * h->n, h->p.sap1_prec, h->st);
+    CKL();
+  }
+  if (h->P16) {
+    launch_to16(static_cast<const float*>(h->P), h->P16, (long)h->p.nv * h->g.V * 12, h->p.transfer_prec, h->st);
+    CKL();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // orth = false: D_c projected again from the current (orthonormal) P, e.g.
 // after a change of the odd-site twisted-mass shift
@@ -540,7 +565,7 @@ void build_coarse(tm_handle* h, bool orth = true) {
   constexpr bool f32 = std::is_same<T, float>::value;
   // orthonormalisation + build, the FP16 copy, the odd-site inverses and the
   // three tensor-core tile kernels
-  const int nk = (orth ? 2 : 1) + (f32 && h->Dc1h ? 1 : 0) + (h->three ? 0 : 1) +
+  const int nk = (orth ? 2 : 1) + (f32 && h->Dc1h ? 1 : 0) + (f32 && h->P16 ? 1 : 0) + (h->three ? 0 : 1) +
                  (f32 && h->tc_on && !h->three ? 3 : 0);
   Prof pf(h, PK_BUILD, 1, nk);
   if (orth) {
@@ -550,12 +575,7 @@ void build_coarse(tm_handle* h, bool orth = true) {
   launch_coarse_build<T>(gaugeT<T>(h), cloverT<T>(h), P, static_cast<T*>(h->Dc), h->ag, h->p.bc_t, h->st,
                          h->build_shape, h->rho);
   CKL();
-  if constexpr (std::is_same<T, float>::value) {
-    if (h->Dc1h) {  // FP16 blocks for the level-1 SAP
-      launch_blocks_to_half(static_cast<const float*>(h->Dc), h->Dc1h, (long)h->gc.V * 9 * h->n * h->n, h->st);
-      CKL();
-    }
-  }
+  if constexpr (std::is_same<T, float>::value) refresh_16bit(h);
   if (!h->three) {  // with three levels the odd-even solve runs on level 2
     launch_oe_invert<T>(static_cast<T*>(h->Dc), static_cast<T*>(h->Dinv), h->oe, mu_c(h), h->d_err, h->st);
     CKL();
@@ -882,7 +902,7 @@ void kcycle(tm_handle* h, const T* v, T* z, int nrhs) {
   T* ec = W<T>(h, "k_ec", 2 * cc * nrhs);
   {
     Prof pf(h, PK_RESTRICT, nrhs);
-    launch_restrict<T>(static_cast<const T*>(h->P), r, rc, h->ag, nrhs, h->st);
+    launch_restrict<T>(static_cast<const T*>(h->P), r, rc, h->ag, nrhs, h->st, h->P16, h->p.transfer_prec);
     CKL();
   }
   if (h->three)
@@ -891,7 +911,7 @@ void kcycle(tm_handle* h, const T* v, T* z, int nrhs) {
     coarse_solve<T>(h, coarsest_level(h), rc, ec, nrhs, h->p.coarse_tol, h->p.coarse_maxit);
   {
     Prof pf(h, PK_PROLONG, nrhs);
-    launch_prolong<T>(static_cast<const T*>(h->P), ec, z, h->ag, nrhs, true, h->st);
+    launch_prolong<T>(static_cast<const T*>(h->P), ec, z, h->ag, nrhs, true, h->st, h->P16, h->p.transfer_prec);
     CKL();
   }
   sap_sweeps<T>(h, v, z, h->p.post_smooth, nrhs);
@@ -919,7 +939,7 @@ void csap_sweeps(tm_handle* h, const T* b, T* x, int sweeps, int nrhs) {
     for (int colour = 0; colour < 2; ++colour) {
       Prof pf(h, PK_CSAP, nrhs);
       launch_csap_colour<T>(static_cast<const T*>(h->Dc), b, x, h->csg, h->p.mu, h->p.mr_iters1, colour, nrhs,
-                            h->st, std::is_same<T, float>::value ? h->Dc1h : nullptr);
+                            h->st, std::is_same<T, float>::value ? h->Dc1h : nullptr, h->p.sap1_prec);
       CKL();
     }
 }
@@ -1358,7 +1378,16 @@ std::vector<KrylovOut> fgmres_b(tm_handle* h, const std::string& tag, int pk, FR
     bnorm[r] = std::sqrt(hn_h[r]);
     if (!std::isfinite(bnorm[r])) raise(TM_ERR_NONFINITE, "non-finite right-hand side");
   }
-  resid(x, Vb);  // r = b - A x
+  norms(x, nullptr);  // a zero start vector (the usual case) needs no product: r = b
+  read_norms();
+  bool x_zero = true;
+  for (int r = 0; r < nb; ++r) x_zero = x_zero && hn_h[r] == 0;
+  if (x_zero) {
+    Prof pf(h, pk, nb);
+    CK(cudaMemcpyAsync(Vb, b, (size_t)blk * sizeof(Tv), cudaMemcpyDeviceToDevice, h->st));
+  } else {
+    resid(x, Vb);  // r = b - A x
+  }
   norms(Vb, nullptr);
   read_norms();
   for (int r = 0; r < nb; ++r) {
@@ -1597,9 +1626,16 @@ void validate(const tm_params* p) {
   if (p->nn_mode < 0 || p->nn_mode > 2) bad("nn_mode must be 0, 1 or 2");
   if (p->nn_mode == 1 && p->cycle_prec != TM_F32) bad("the learned layer needs cycle_prec = TM_F32");
   if (p->nn_prec != TM_F32 && p->nn_prec != TM_F16) bad("nn_prec must be TM_F32 or TM_F16");
-  if (p->sap1_prec != TM_F32 && p->sap1_prec != TM_F16) bad("sap1_prec must be TM_F32 or TM_F16");
-  if (p->sap1_prec == TM_F16 && (p->levels != 3 || p->cycle_prec != TM_F32))
-    bad("sap1_prec = TM_F16 needs levels = 3 and cycle_prec = TM_F32");
+  auto is16 = [](int v) { return v == TM_F16 || v == TM_BF16; };
+  if (p->sap1_prec != TM_F32 && !is16(p->sap1_prec)) bad("sap1_prec must be TM_F32, TM_F16 or TM_BF16");
+  if (is16(p->sap1_prec) && (p->levels != 3 || p->cycle_prec != TM_F32))
+    bad("a 16-bit sap1_prec needs levels = 3 and cycle_prec = TM_F32");
+  if (p->transfer_prec != TM_F32 && !is16(p->transfer_prec))
+    bad("transfer_prec must be TM_F32, TM_F16 or TM_BF16");
+  if (is16(p->transfer_prec) && p->cycle_prec != TM_F32) bad("a 16-bit transfer_prec needs cycle_prec = TM_F32");
+  if (p->sap_prec != TM_F32 && !is16(p->sap_prec)) bad("sap_prec must be TM_F32, TM_F16 or TM_BF16");
+  if (is16(p->sap_prec) && (p->cycle_prec != TM_F32 || !p->block_oe))
+    bad("a 16-bit sap_prec needs cycle_prec = TM_F32 and block_oe = 1");
   if (p->outer_apply != TM_F64 && p->outer_apply != TM_F32X2) bad("outer_apply must be TM_F64 or TM_F32X2");
   if (p->outer_apply == TM_F32X2 && p->cycle_prec != TM_F32) bad("outer_apply = TM_F32X2 needs cycle_prec = TM_F32");
   if (p->tc_spin_limit < 0) bad("tc_spin_limit must be >= 0");
@@ -1787,8 +1823,10 @@ MemPlan memory_plan(const tm_params* p, int nrhs) {
   if (three) {
     P += 2 * p->nv2 * Vc * n * 2 * cs;                   // level-1 test vectors, P2
     P += V2 * 9 * n2 * n2 * 2 * cs + V2 / 2 * n2 * n2 * 2 * cs;
-    if (p->sap1_prec == TM_F16) P += Vc * 9 * n * n * 4;
+    if (p->sap1_prec == TM_F16 || p->sap1_prec == TM_BF16) P += Vc * 9 * n * n * 4;
   }
+  if (p->transfer_prec == TM_F16 || p->transfer_prec == TM_BF16) P += p->nv * fr * 2;  // 16-bit copy of P
+  if (p->sap_prec == TM_F16 || p->sap_prec == TM_BF16) P += (48 + 72 + 72) * V * 2;  // 16-bit SAP operator
   const double nvc = three ? p->nv2 : p->nv, nh = (three ? V2 : Vc) / 2;
   double cvc = 2 * (three ? V2 : Vc) * (three ? n2 : n);  // reals of a coarsest vector
   if (p->coarse_mma > 0) {
@@ -2045,12 +2083,7 @@ void rebuild_derived(tm_handle* h) {
   // everything the build derives from D_c (and D_c2): FP16 blocks, odd-site
   // inverses with the current mu, tensor-core tiles
   Prof pf(h, PK_BUILD, 0, 1);
-  if constexpr (std::is_same<T, float>::value) {
-    if (h->Dc1h) {
-      launch_blocks_to_half(static_cast<const float*>(h->Dc), h->Dc1h, (long)h->gc.V * 9 * h->n * h->n, h->st);
-      CKL();
-    }
-  }
+  if constexpr (std::is_same<T, float>::value) refresh_16bit(h);
   void* Dc = h->three ? h->Dc2 : h->Dc;
   void* Di = h->three ? h->Dinv2 : h->Dinv;
   const OEGeom& oe = h->three ? h->oe2 : h->oe;
@@ -2101,6 +2134,8 @@ void tm_params_default(tm_params* p) {
   p->nn_mode = 0;
   p->nn_prec = TM_F32;
   p->sap1_prec = TM_F32;
+  p->transfer_prec = TM_F32;
+  p->sap_prec = TM_F32;
   p->outer_apply = TM_F64;
 }
 
@@ -2134,7 +2169,7 @@ void tm_destroy(tm_handle* h) {
     if (kv.second.first) cudaFreeHost(kv.second.first);
   void* p3[] = {h->tv1, h->P2, h->Dc2, h->Dinv2, h->d_even2, h->d_odd2, h->d_cidx2,
                 h->tc.even, h->tc.even_lo, h->tc.odd, h->tc.odd_lo, h->tc.nbr_e, h->tc.nbr_o,
-                h->d_nnw, h->d_nngrad, h->Dc1h, h->gdf, h->cdf, h->dinv_sap};
+                h->d_nnw, h->d_nngrad, h->Dc1h, h->P16, h->g16, h->c16, h->dinv16, h->gdf, h->cdf, h->dinv_sap};
   for (void* q : p3)
     if (q) cudaFree(q);
   for (auto& r : h->recs) {
@@ -2270,7 +2305,15 @@ tm_status tm_create(tm_handle** out, const tm_params* p, void* stream) {
       h->P2 = dalloc((size_t)p->nv2 * h->gc.V * h->n * 2 * cs);
       h->Dc2 = dalloc((size_t)h->gc2.V * 9 * h->n2 * h->n2 * 2 * cs);
       h->Dinv2 = dalloc((size_t)h->nhalf2 * h->n2 * h->n2 * 2 * cs);
-      if (p->sap1_prec == TM_F16) h->Dc1h = dalloc((size_t)h->gc.V * 9 * h->n * h->n * 4);
+      if (p->sap1_prec == TM_F16 || p->sap1_prec == TM_BF16)
+        h->Dc1h = dalloc((size_t)h->gc.V * 9 * h->n * h->n * 4);
+    }
+    if (p->transfer_prec == TM_F16 || p->transfer_prec == TM_BF16)
+      h->P16 = dalloc((size_t)p->nv * h->g.V * 12 * 4);
+    if (p->sap_prec == TM_F16 || p->sap_prec == TM_BF16) {
+      h->g16 = dalloc((size_t)h->g.V * 4 * NR_LINK * 2);
+      h->c16 = dalloc((size_t)h->g.V * NR_CLOVER * 2);
+      h->dinv16 = dalloc((size_t)h->g.V / 2 * 144 * 2);
     }
     if (p->coarse_mma > 0) {  // tensor-core tiles of the coarsest odd-even level
       const int nvc = h->three ? p->nv2 : p->nv, nh = h->three ? h->nhalf2 : h->nhalf;
@@ -2311,6 +2354,13 @@ tm_status tm_load_gauge(tm_handle* h, const double* gauge) {
     launch_pack_gauge(gd, h->g64, h->g32, h->g, 1e-10, h->d_err, h->st);
     CKL();
     launch_clover(gd, h->c64, h->c32, h->g, h->p.m0, h->p.c_sw, h->st);
+    CKL();
+  }
+  if (h->g16) {
+    Prof pf(h, PK_OTHER, 1, 2);
+    launch_to16(h->g32, h->g16, (long)h->g.V * 4 * NR_LINK / 2, h->p.sap_prec, h->st);
+    CKL();
+    launch_to16(h->c32, h->c16, (long)h->g.V * NR_CLOVER / 2, h->p.sap_prec, h->st);
     CKL();
   }
   if (h->gdf) {
@@ -2592,6 +2642,251 @@ tm_status tm_solve_hasenbusch(tm_handle* h, const double* b, double* x, int nrhs
   return st;
 }
 
+// ---------------------------------------------------------------------------
+// oeCG: CG on the normal equations of the odd-even reduced operator, the
+// comparison solver of Fig. 1 (Sec. 1), in FP32 iterations inside FP64
+// defect correction
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+struct OeCG {
+  tm_handle* h;
+  long Vh, nr;  // half-field sites and reals
+  double* dinv64;
+  float* dinv32;
+};
+
+// D_ee^-1 at the even twisted mass, FP64 and FP32 copies (rebuilt per solve)
+OeCG oecg_prepare(tm_handle* h) {
+  OeCG o{h, h->g.V / 2, (long)(h->g.V / 2) * NR_SPINOR, nullptr, nullptr};
+  o.dinv64 = W<double>(h, "oe_dinv64", (size_t)o.Vh * 144);
+  o.dinv32 = W<float>(h, "oe_dinv32", (size_t)o.Vh * 144);
+  Prof pf(h, PK_OTHER, 1, 2);
+  launch_clover_inverse<double>(h->c64, o.dinv64, h->g, h->p.mu, h->d_err, h->st, 0);
+  CKL();
+  launch_clover_inverse<float>(h->c64, o.dinv32, h->g, h->p.mu, h->d_err, h->st, 0);
+  CKL();
+  return o;
+}
+
+// out = D^ in (adj: D^dagger = G^5 D^(-mu) G^5), odd half fields; tmp an even half field
+template <typename T>
+void oe_reduced(const OeCG& o, const T* in, T* out, T* tmp, bool adj) {
+  tm_handle* h = o.h;
+  const T* dinv;
+  if constexpr (std::is_same<T, double>::value)
+    dinv = o.dinv64;
+  else
+    dinv = o.dinv32;
+  const double muo = h->p.mu + h->rho;
+  Prof pf(h, PK_OECG_OP, 1, 2);
+  launch_oe_apply<T>(gaugeT<T>(h), nullptr, dinv, in, nullptr, tmp, h->g, 0, -0.5, 0.0, h->p.bc_t, adj, adj, 0,
+                     h->st);
+  CKL();
+  launch_oe_apply<T>(gaugeT<T>(h), cloverT<T>(h), nullptr, tmp, in, out, h->g, 1, 0.5, adj ? -muo : muo,
+                     h->p.bc_t, adj, 0, 1, h->st);
+  CKL();
+}
+
+// one right-hand side; bf, xf packed FP64 full fields (xf: start vector in, solution out)
+KrylovOut oecg_one(const OeCG& o, const double* bf, double* xf, double tol, int maxit) {
+  tm_handle* h = o.h;
+  const long nr = o.nr, ncx = nr / 2;
+  double* be = W<double>(h, "oe_be", nr);
+  double* bo = W<double>(h, "oe_bo", nr);
+  double* bh = W<double>(h, "oe_bh", nr);
+  double* xo = W<double>(h, "oe_xo", nr);
+  double* r64 = W<double>(h, "oe_r64", nr);
+  double* t64 = W<double>(h, "oe_t64", nr);
+  double* u64 = W<double>(h, "oe_u64", nr);
+  float* r = W<float>(h, "oe_r", nr);
+  float* e = W<float>(h, "oe_e", nr);
+  float* s = W<float>(h, "oe_s", nr);
+  float* p = W<float>(h, "oe_p", nr);
+  float* q = W<float>(h, "oe_q", nr);
+  float* t = W<float>(h, "oe_t", nr);
+  constexpr int kBlocks = 2432;
+  double* part = W<double>(h, "oe_part", 2 * kBlocks);
+  constexpr int kCheck = 8;  // CG steps between host convergence checks
+  const int cap = std::max(maxit, 1);
+  double* sc = W<double>(h, "oe_sc", 4);
+  double* hist = W<double>(h, "oe_hist", (size_t)cap + kCheck);
+  double* hh = host_scratch(h, "oe", (size_t)cap + kCheck + 4);
+  auto nrm2 = [&](const auto* v, long n_cx, double* dst, int kind) {
+    Prof pf(h, kind, 1, 2);
+    using V = std::remove_const_t<std::remove_pointer_t<decltype(v)>>;
+    launch_norm2<V>(v, n_cx, 1, dst, part, kBlocks, h->st);
+    CKL();
+  };
+  auto read = [&](const double* src, size_t n) {
+    CK(cudaMemcpyAsync(hh, src, n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+  };
+  KrylovOut out;
+  {
+    Prof pf(h, PK_OTHER, 1, 6);
+    launch_parity_copy<double>(bf, be, h->g, 0, false, h->st);
+    CKL();
+    launch_parity_copy<double>(bf, bo, h->g, 1, false, h->st);
+    CKL();
+    launch_parity_copy<double>(xf, xo, h->g, 1, false, h->st);
+    CKL();
+    // b^ = b_o - D_oe D_ee^-1 b_e = b_o + H (D_ee^-1 b_e) / 2
+    launch_oe_apply<double>(h->g64, nullptr, o.dinv64, nullptr, be, t64, h->g, 0, 0.0, 0.0, h->p.bc_t, 0, 0, 0, h->st);
+    CKL();
+    launch_oe_apply<double>(h->g64, nullptr, nullptr, t64, bo, bh, h->g, 1, 0.5, 0.0, h->p.bc_t, 0, 0, 1, h->st);
+    CKL();
+  }
+  nrm2(bf, (long)h->g.V * 12, sc + 3, PK_OECG_BLAS);
+  read(sc + 3, 1);
+  const double bnorm = std::sqrt(hh[0]);
+  if (!std::isfinite(bnorm)) raise(TM_ERR_NONFINITE, "non-finite right-hand side");
+  auto true_residual = [&]() {  // r64 = b^ - D^ x_o in FP64, returns |r64|
+    oe_reduced<double>(o, xo, u64, t64, false);
+    {
+      Prof pf(h, PK_OECG_BLAS, 1);
+      CK(cudaMemcpyAsync(r64, bh, nr * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+      launch_caxpby<double>(-1.0, 0.0, u64, 1.0, 0.0, r64, ncx, h->st);
+      CKL();
+    }
+    nrm2(r64, ncx, sc + 3, PK_OECG_BLAS);
+    read(sc + 3, 1);
+    return std::sqrt(hh[0]);
+  };
+  double rn = true_residual();
+  constexpr double kInner = 1e-5;  // FP32 CG reduces the defect by this factor per cycle
+  while (bnorm > 0 && rn > tol * bnorm && out.iters < maxit) {
+    if (!std::isfinite(rn)) raise(TM_ERR_NONFINITE, "non-finite residual");
+    ++out.restarts;
+    const double target = std::max(kInner, 0.5 * tol * bnorm / rn) * rn;  // on |r| of this cycle
+    {
+      Prof pf(h, PK_OECG_BLAS, 1, 2);
+      launch_convert<double, float>(r64, r, nr, h->st);
+      CKL();
+      launch_zero<float>(e, nr, h->st);
+      CKL();
+    }
+    oe_reduced<float>(o, r, s, t, true);  // s = D^dagger r
+    nrm2(s, ncx, sc + 0, PK_OECG_BLAS);   // gamma_0
+    CK(cudaMemcpyAsync(p, s, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+    int k = 0, done = -1;
+    const int budget = maxit - out.iters;
+    while (done < 0 && k < budget) {
+      const int k_end = std::min(k + kCheck, budget);
+      for (; k < k_end; ++k) {
+        oe_reduced<float>(o, p, q, t, false);  // q = D^ p
+        nrm2(q, ncx, sc + 2, PK_OECG_BLAS);
+        {
+          Prof pf(h, PK_OECG_BLAS, 1);
+          launch_cg_xr<float>(e, r, p, q, sc, k & 1, 2, nr, h->st);
+          CKL();
+        }
+        nrm2(r, ncx, hist + k, PK_OECG_BLAS);
+        oe_reduced<float>(o, r, s, t, true);  // s = D^dagger r
+        nrm2(s, ncx, sc + ((k + 1) & 1), PK_OECG_BLAS);
+        {
+          Prof pf(h, PK_OECG_BLAS, 1);
+          launch_cg_p<float>(p, s, sc, (k + 1) & 1, k & 1, nr, h->st);
+          CKL();
+        }
+      }
+      read(hist, (size_t)k);
+      for (int j = 0; j < k; ++j) {
+        if (!std::isfinite(hh[j])) raise(TM_ERR_NONFINITE, "non-finite CG residual");
+        if (std::sqrt(hh[j]) <= target) {
+          done = j;
+          break;
+        }
+      }
+    }
+    out.iters += k;
+    {
+      Prof pf(h, PK_OECG_BLAS, 1);
+      launch_acc_f32(e, xo, nr, h->st);  // x_o += e
+      CKL();
+    }
+    const double rn_new = true_residual();
+    if (done < 0 && rn_new >= rn) break;  // no progress within the budget
+    rn = rn_new;
+  }
+  {  // x_e = D_ee^-1 (b_e - D_eo x_o) = D_ee^-1 (b_e + H x_o / 2); x = (x_e, x_o)
+    Prof pf(h, PK_OTHER, 1, 3);
+    launch_oe_apply<double>(h->g64, nullptr, o.dinv64, xo, be, t64, h->g, 0, 0.5, 0.0, h->p.bc_t, 0, 0, 0, h->st);
+    CKL();
+    launch_parity_copy<double>(t64, xf, h->g, 0, true, h->st);
+    CKL();
+    launch_parity_copy<double>(xo, xf, h->g, 1, true, h->st);
+    CKL();
+  }
+  out.relres = bnorm > 0 ? rn / bnorm : 0.0;
+  out.converged = bnorm == 0 || rn <= tol * bnorm;
+  return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+tm_status tm_solve_oecg(tm_handle* h, const double* b, double* x, int nrhs, double tol, int maxit,
+                        tm_solve_info* info) {
+  if (!h || !b || !x || nrhs < 1 || !(tol > 0) || maxit < 1) return TM_ERR_ARG;
+  tm_solve_info loc{};
+  loc.converged = 1;
+  tm_status st = TM_OK;
+  try {
+    if (!h->gauge_ok) raise(TM_ERR_STATE, "tm_load_gauge must come first");
+    if (h->g.L[3] % 2) raise(TM_ERR_ARG, "odd-even ordering needs an even X extent");
+    const long V = h->g.V;
+    const size_t one = (size_t)V * 12 * 2 * sizeof(double);
+    const bool xdev = is_device_ptr(x);
+    const double* bd = stage_in(h, b, one * nrhs, "stage_b");
+    double* xd = xdev ? x : W<double>(h, "stage_x", one * nrhs / sizeof(double));
+    if (!xdev) CK(cudaMemcpyAsync(xd, x, one * nrhs, cudaMemcpyHostToDevice, h->st));
+    const long fr = fine_reals(h);
+    double* bf = W<double>(h, "s_b", fr);
+    double* xf = W<double>(h, "s_x", fr);
+    const OeCG o = oecg_prepare(h);
+    check_flags(h);
+    for (int rr = 0; rr < nrhs; ++rr) {
+      {
+        Prof pf(h, PK_OTHER, 1, 2);
+        launch_pack_spinor<double>(bd + (size_t)rr * V * 24, bf, h->g, 1, h->st);
+        CKL();
+        launch_pack_spinor<double>(xd + (size_t)rr * V * 24, xf, h->g, 1, h->st);
+        CKL();
+      }
+      const KrylovOut k = oecg_one(o, bf, xf, tol, maxit);
+      {
+        Prof pf(h, PK_OTHER);
+        launch_unpack_spinor<double>(xf, xd + (size_t)rr * V * 24, h->g, 1, h->st);
+        CKL();
+      }
+      loc.iters += k.iters;
+      loc.restarts += k.restarts;
+      loc.true_relres = std::max(loc.true_relres, k.relres);
+      if (!k.converged) loc.converged = 0;
+    }
+    if (!xdev) CK(cudaMemcpyAsync(x, xd, one * nrhs, cudaMemcpyDeviceToHost, h->st));
+    sync(h);
+    if (!loc.converged) {
+      h->err = "oeCG reached maxit without converging";
+      st = TM_ERR_NOT_CONVERGED;
+    } else {
+      h->err.clear();
+    }
+  } catch (const TmError& e) {
+    h->err = e.m;
+    st = e.s;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    st = TM_ERR_CUDA;
+  }
+  if (info) *info = loc;
+  return st;
+}
+
 size_t tm_field_bytes(const tm_handle* h, int level, int prec, int nrhs) {
   if (!h || nrhs < 1 || (prec != TM_F64 && prec != TM_F32)) return 0;
   if (level == 0) return (size_t)nrhs * NR_SPINOR * h->g.V * csize(prec);
@@ -2723,7 +3018,7 @@ tm_status tm_restrict(tm_handle* h, int prec, const void* fine, void* coarse, in
                             static_cast<double*>(coarse), h->ag, nrhs, h->st);
   else
     launch_restrict<float>(static_cast<const float*>(h->P), static_cast<const float*>(fine),
-                           static_cast<float*>(coarse), h->ag, nrhs, h->st);
+                           static_cast<float*>(coarse), h->ag, nrhs, h->st, h->P16, h->p.transfer_prec);
   CKL();
   API_END
 }
@@ -2737,7 +3032,8 @@ tm_status tm_prolong(tm_handle* h, int prec, const void* coarse, void* fine, int
                            static_cast<double*>(fine), h->ag, nrhs, accumulate != 0, h->st);
   else
     launch_prolong<float>(static_cast<const float*>(h->P), static_cast<const float*>(coarse),
-                          static_cast<float*>(fine), h->ag, nrhs, accumulate != 0, h->st);
+                          static_cast<float*>(fine), h->ag, nrhs, accumulate != 0, h->st, h->P16,
+                          h->p.transfer_prec);
   CKL();
   API_END
 }

@@ -13,6 +13,8 @@
 // entries then the 15 upper-triangle entries (0,1),(0,2),...,(4,5)).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
@@ -176,6 +178,41 @@ __device__ __forceinline__ void st_cx(T* __restrict__ base, long V, long s, cons
   }
 }
 
+// ---------------------------------------------------------------------------
+// 16-bit storage of operators read by the FP32 K-cycle (values of TM_F16 /
+// TM_BF16); a complex number is one 32-bit word (re, im), a chunk of two
+// complex numbers 8 bytes, so a 16-bit copy keeps the element order of the
+// FP32 array it was made from
+// ---------------------------------------------------------------------------
+constexpr int ST_NATIVE = 0, ST_F16 = 2, ST_BF16 = 3;
+
+template <int S>
+__device__ __forceinline__ float2 unpack16x2(unsigned u) {
+  if constexpr (S == ST_F16) {
+    __half2 v;
+    memcpy(&v, &u, 4);
+    return __half22float2(v);
+  } else {
+    __nv_bfloat162 v;
+    memcpy(&v, &u, 4);
+    return __bfloat1622float2(v);
+  }
+}
+
+// NC complex numbers of site s from a chunked field stored in 16 bits
+template <typename T, int S, int NC>
+__device__ __forceinline__ void ld_cx16(const void* __restrict__ base, long V, long s, cx<T> (&z)[NC]) {
+  static_assert(NC % 2 == 0, "chunks hold two complex numbers");
+  const uint2* p = reinterpret_cast<const uint2*>(base);
+#pragma unroll
+  for (int k = 0; k < NC / 2; ++k) {
+    const uint2 v = __ldg(p + k * V + s);
+    const float2 a = unpack16x2<S>(v.x), b = unpack16x2<S>(v.y);
+    z[2 * k] = cx<T>{(T)a.x, (T)a.y};
+    z[2 * k + 1] = cx<T>{(T)b.x, (T)b.y};
+  }
+}
+
 // load NR reals of site s (NR a multiple of 4)
 template <typename T, int NR>
 __device__ __forceinline__ void ld_re(const T* __restrict__ base, long V, long s, T (&r)[NR]) {
@@ -235,9 +272,7 @@ struct Link {
 };
 
 template <typename T>
-__device__ __forceinline__ void ld_link(const T* __restrict__ gauge, long V, int mu, long s, Link<T>& U) {
-  cx<T> z[6];
-  ld_cx<T, 6>(gauge + (long)mu * NR_LINK * V, V, s, z);
+__device__ __forceinline__ void link_from_rows(const cx<T> (&z)[6], Link<T>& U) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     U.u[0][k] = z[k];
@@ -246,6 +281,53 @@ __device__ __forceinline__ void ld_link(const T* __restrict__ gauge, long V, int
   U.u[2][0] = conj(U.u[0][1] * U.u[1][2] - U.u[0][2] * U.u[1][1]);
   U.u[2][1] = conj(U.u[0][2] * U.u[1][0] - U.u[0][0] * U.u[1][2]);
   U.u[2][2] = conj(U.u[0][0] * U.u[1][1] - U.u[0][1] * U.u[1][0]);
+}
+
+template <typename T>
+__device__ __forceinline__ void ld_link(const T* __restrict__ gauge, long V, int mu, long s, Link<T>& U) {
+  cx<T> z[6];
+  ld_cx<T, 6>(gauge + (long)mu * NR_LINK * V, V, s, z);
+  link_from_rows(z, U);
+}
+
+// the link from links stored as T (S = ST_NATIVE) or in 16 bits (ST_F16, ST_BF16)
+template <typename T, int S>
+__device__ __forceinline__ void ld_link_s(const void* __restrict__ gauge, long V, int mu, long s, Link<T>& U) {
+  if constexpr (S == ST_NATIVE) {
+    ld_link(static_cast<const T*>(gauge), V, mu, s, U);
+  } else {
+    cx<T> z[6];
+    ld_cx16<T, S, 6>(static_cast<const unsigned short*>(gauge) + (long)mu * NR_LINK * V, V, s, z);
+    link_from_rows(z, U);
+  }
+}
+
+// NR reals of site s, stored as T or in 16 bits (chunks of 4 reals)
+template <typename T, int S, int NR>
+__device__ __forceinline__ void ld_re_s(const void* __restrict__ base, long V, long s, T (&r)[NR]) {
+  if constexpr (S == ST_NATIVE) {
+    ld_re<T, NR>(static_cast<const T*>(base), V, s, r);
+  } else {
+    const uint2* p = reinterpret_cast<const uint2*>(base);
+#pragma unroll
+    for (int k = 0; k < NR / 4; ++k) {
+      const uint2 v = __ldg(p + k * V + s);
+      const float2 a = unpack16x2<S>(v.x), b = unpack16x2<S>(v.y);
+      r[4 * k] = (T)a.x;
+      r[4 * k + 1] = (T)a.y;
+      r[4 * k + 2] = (T)b.x;
+      r[4 * k + 3] = (T)b.y;
+    }
+  }
+}
+
+// NC complex numbers of site s, stored as T or in 16 bits
+template <typename T, int S, int NC>
+__device__ __forceinline__ void ld_cx_s(const void* __restrict__ base, long V, long s, cx<T> (&z)[NC]) {
+  if constexpr (S == ST_NATIVE)
+    ld_cx<T, NC>(static_cast<const T*>(base), V, s, z);
+  else
+    ld_cx16<T, S, NC>(base, V, s, z);
 }
 
 // y = U x (colour)

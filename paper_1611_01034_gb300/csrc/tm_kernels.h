@@ -54,14 +54,17 @@ void launch_sap_colour(const T* gauge, const T* clover, const T* b, T* x, const 
 
 // the same with the block solves on the odd-even Schur complement (Sec. 3);
 // all block dims even; dinv from launch_clover_inverse
+// gauge, clover, dinv stored as T, or (T = float) in 16 bits when s16 = ST_F16 / ST_BF16
 template <typename T>
-void launch_sap_oe_colour(const T* gauge, const T* clover, const T* dinv, const T* b, T* x, const SapGeom& sg,
-                          double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st, double rho = 0.0);
+void launch_sap_oe_colour(const void* gauge, const void* clover, const void* dinv, const T* b, T* x,
+                          const SapGeom& sg, double mu, double bc_t, int n_mr, int colour, int nrhs, cudaStream_t st,
+                          double rho = 0.0, int s16 = 0);
 // dinv [12 rows x 6 complex chunks][V/2] = (A(x) + i mu gamma5)^-1 of the two
 // chiral blocks at every odd site (compact index s >> 1; X even); mu = the
 // odd sites' twisted mass
 template <typename T>
-void launch_clover_inverse(const double* c64, T* dinv, const Lat& g, double mu, int* err, cudaStream_t st);
+void launch_clover_inverse(const double* c64, T* dinv, const Lat& g, double mu, int* err, cudaStream_t st,
+                           int parity = 1);  // sites of this parity, compact index s >> 1
 
 // ---- aggregation and coarse operator (coarse.cu) ---------------------------
 // tile shape of the coarse-operator build kernel (0 = default heuristic)
@@ -81,11 +84,14 @@ template <typename T>
 void launch_orthonormalise(T* P, const AggGeom& ag, int* err, cudaStream_t st);
 // coarse[rhs][Vc][2Nv] = P^dagger fine
 template <typename T>
-void launch_restrict(const T* P, const T* fine, T* coarse, const AggGeom& ag, int nrhs, cudaStream_t st);
+void launch_restrict(const T* P, const T* fine, T* coarse, const AggGeom& ag, int nrhs, cudaStream_t st,
+                     const void* P16 = nullptr, int p16 = 0);  // P16: 16-bit copy of P (ST_F16 / ST_BF16)
 // fine = (accumulate ? fine : 0) + P coarse
 template <typename T>
 void launch_prolong(const T* P, const T* coarse, T* fine, const AggGeom& ag, int nrhs, bool accumulate,
-                    cudaStream_t st);
+                    cudaStream_t st, const void* P16 = nullptr, int p16 = 0);
+// 16-bit copy (kind ST_F16 or ST_BF16) of n_cx FP32 complex numbers, element order kept
+void launch_to16(const float* in, void* out, long n_cx, int kind, cudaStream_t st);
 // Dc blocks [Vc][9][2Nv col][2Nv row] = local Galerkin projection (mu-free)
 template <typename T>
 void launch_coarse_build(const T* gauge, const T* clover, const T* P, T* Dc, const AggGeom& ag,
@@ -146,12 +152,11 @@ struct CAggGeom {
   int nv1, nv2;
 };
 // one colour of SAP on D_c1(mu) x = b (b may be null), nrhs level-1 vectors;
-// with Dc_half (FP16 copy of the FP32 blocks) the blocks are read from it
+// with Dc_half (16-bit copy of the FP32 blocks, half_kind ST_F16 or ST_BF16)
+// the blocks are read from it
 template <typename T>
 void launch_csap_colour(const T* Dc, const T* b, T* x, const CSapGeom& sg, double mu, int n_mr, int colour,
-                        int nrhs, cudaStream_t st, const void* Dc_half = nullptr);
-// FP16 (re, im) copy of ncx complex FP32 numbers
-void launch_blocks_to_half(const float* Dc, void* out, long ncx, cudaStream_t st);
+                        int nrhs, cudaStream_t st, const void* Dc_half = nullptr, int half_kind = 2);
 // P2 <- per (aggregate, chirality) CGS2 of the Nv2 level-1 fields in P2
 template <typename T>
 void launch_corth(T* P2, const CAggGeom& ag, int* err, cudaStream_t st);
@@ -279,6 +284,19 @@ template <typename T>
 void launch_sub_b(const T* x, long xstr, T* y, long ystr, long ncx, int nrhs, const int* active, cudaStream_t st);
 // scratch doubles that launch_multidot_b / launch_norm2_b need
 long multidot_scratch_doubles(long ncx, int k, int nrhs);
+// odd-even reduced operator and CG pieces of the oeCG solver (oecg.cu); half
+// fields hold one parity at compact index s >> 1
+template <typename T>
+void launch_oe_apply(const T* gauge, const T* clover, const T* dinv, const T* hin, const T* din, T* out, const Lat& g,
+                     int parity, double c_hop, double mu, double bc_t, int g5, int dag, int mode, cudaStream_t st);
+template <typename T>
+void launch_parity_copy(const T* src, T* dst, const Lat& g, int parity, bool to_full, cudaStream_t st);
+template <typename T>
+void launch_cg_xr(T* x, T* r, const T* p, const T* q, const double* sc, int ig, int iq, long n_reals,
+                  cudaStream_t st);
+template <typename T>
+void launch_cg_p(T* p, const T* s, const double* sc, int inew, int iold, long n_reals, cudaStream_t st);
+void launch_acc_f32(const float* e, double* x, long n_reals, cudaStream_t st);  // x += e
 int dot_grid_for(long ncx);  // partial-sum CTAs per right-hand side of the batched reductions
 // Arnoldi steps of the FP64 FGMRES in FP32-pair arithmetic (blas_pair.cu); the
 // reductions write FP64 results like launch_multidot_b / launch_norm2_b

@@ -23,8 +23,9 @@ __device__ __forceinline__ cx<T> mulp(cx<T> z, int p) {
 }
 
 // acc += sign (1 - gamma_MU) U p, p = psi(x + MU), U = U_MU(x) at link site sl
-template <typename T, int MU>
-__device__ __forceinline__ void hop_fwd_p(const cx<T> (&p)[12], const T* __restrict__ gauge, int V, int sl,
+// (links stored as T, or in 16 bits for S = ST_F16 / ST_BF16)
+template <typename T, int MU, int S = ST_NATIVE>
+__device__ __forceinline__ void hop_fwd_p(const cx<T> (&p)[12], const void* __restrict__ gauge, int V, int sl,
                                           T sign, cx<T> (&acc)[12]) {
   cx<T> h[2][3];
 #pragma unroll
@@ -32,7 +33,7 @@ __device__ __forceinline__ void hop_fwd_p(const cx<T> (&p)[12], const T* __restr
 #pragma unroll
     for (int k = 0; k < 3; ++k) h[r][k] = sign * (p[3 * r + k] - mulp(p[3 * (2 + gperm(MU, r)) + k], gphase(MU, r)));
   Link<T> U;
-  ld_link(gauge, V, MU, sl, U);
+  ld_link_s<T, S>(gauge, V, MU, sl, U);
   cx<T> w[2][3];
   su3_mul(U, h[0], w[0]);
   su3_mul(U, h[1], w[1]);
@@ -47,8 +48,8 @@ __device__ __forceinline__ void hop_fwd_p(const cx<T> (&p)[12], const T* __restr
 }
 
 // acc += sign (1 + gamma_MU) U^dagger p, p = psi(x - MU), U = U_MU(x - MU) at link site sl
-template <typename T, int MU>
-__device__ __forceinline__ void hop_bwd_p(const cx<T> (&p)[12], const T* __restrict__ gauge, int V, int sl,
+template <typename T, int MU, int S = ST_NATIVE>
+__device__ __forceinline__ void hop_bwd_p(const cx<T> (&p)[12], const void* __restrict__ gauge, int V, int sl,
                                           T sign, cx<T> (&acc)[12]) {
   cx<T> h[2][3];
 #pragma unroll
@@ -56,7 +57,7 @@ __device__ __forceinline__ void hop_bwd_p(const cx<T> (&p)[12], const T* __restr
 #pragma unroll
     for (int k = 0; k < 3; ++k) h[r][k] = sign * (p[3 * r + k] + mulp(p[3 * (2 + gperm(MU, r)) + k], gphase(MU, r)));
   Link<T> U;
-  ld_link(gauge, V, MU, sl, U);
+  ld_link_s<T, S>(gauge, V, MU, sl, U);
   cx<T> w[2][3];
   su3_dag_mul(U, h[0], w[0]);
   su3_dag_mul(U, h[1], w[1]);
@@ -70,8 +71,8 @@ __device__ __forceinline__ void hop_bwd_p(const cx<T> (&p)[12], const T* __restr
 }
 
 // acc += both hops in direction MU with neighbours read from global memory
-template <typename T, int MU>
-__device__ __forceinline__ void hops_global(const T* __restrict__ in, const T* __restrict__ gauge, const Lat& g,
+template <typename T, int MU, int S = ST_NATIVE>
+__device__ __forceinline__ void hops_global(const T* __restrict__ in, const void* __restrict__ gauge, const Lat& g,
                                             int s, const int c[4], T bc, cx<T> (&acc)[12]) {
   const int sf = nb_fwd(g, s, c, MU);
   const int sb = nb_bwd(g, s, c, MU);
@@ -79,36 +80,39 @@ __device__ __forceinline__ void hops_global(const T* __restrict__ in, const T* _
     cx<T> p[12];
     ld_cx<T, 12>(in, g.V, sf, p);
     const T sign = (MU == 0 && c[0] == g.L[0] - 1) ? bc : T(1);
-    hop_fwd_p<T, MU>(p, gauge, g.V, s, sign, acc);
+    hop_fwd_p<T, MU, S>(p, gauge, g.V, s, sign, acc);
   }
   {
     cx<T> p[12];
     ld_cx<T, 12>(in, g.V, sb, p);
     const T sign = (MU == 0 && c[0] == 0) ? bc : T(1);
-    hop_bwd_p<T, MU>(p, gauge, g.V, sb, sign, acc);
+    hop_bwd_p<T, MU, S>(p, gauge, g.V, sb, sign, acc);
   }
 }
 
 // sum over all 8 hops (without the -1/2) with global neighbours
-template <typename T>
-__device__ __forceinline__ void all_hops_global(const T* __restrict__ in, const T* __restrict__ gauge,
+template <typename T, int S = ST_NATIVE>
+__device__ __forceinline__ void all_hops_global(const T* __restrict__ in, const void* __restrict__ gauge,
                                                 const Lat& g, int s, const int c[4], T bc, cx<T> (&acc)[12]) {
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = cx<T>{0, 0};
-  hops_global<T, 0>(in, gauge, g, s, c, bc, acc);
-  hops_global<T, 1>(in, gauge, g, s, c, bc, acc);
-  hops_global<T, 2>(in, gauge, g, s, c, bc, acc);
-  hops_global<T, 3>(in, gauge, g, s, c, bc, acc);
+  hops_global<T, 0, S>(in, gauge, g, s, c, bc, acc);
+  hops_global<T, 1, S>(in, gauge, g, s, c, bc, acc);
+  hops_global<T, 2, S>(in, gauge, g, s, c, bc, acc);
+  hops_global<T, 3, S>(in, gauge, g, s, c, bc, acc);
 }
 
 // y = A(x) p + i mu gamma5 p at site s
-template <typename T>
-__device__ __forceinline__ void site_diag(const T* __restrict__ clover, int V, int s, T mu, const cx<T> (&p)[12],
+template <typename T, int S = ST_NATIVE>
+__device__ __forceinline__ void site_diag(const void* __restrict__ clover, int V, int s, T mu, const cx<T> (&p)[12],
                                           cx<T> (&y)[12]) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     T m[36];
-    ld_re<T, 36>(clover + (long)h * 36 * V, V, s, m);
+    if constexpr (S == ST_NATIVE)
+      ld_re<T, 36>(static_cast<const T*>(clover) + (long)h * 36 * V, V, s, m);
+    else
+      ld_re_s<T, S, 36>(static_cast<const unsigned short*>(clover) + (long)h * 36 * V, V, s, m);
     herm6_mul(m, p + 6 * h, y + 6 * h);
     const T sg = h == 0 ? -mu : mu;  // gamma5 = -1 on spins 0, 1
 #pragma unroll

@@ -70,6 +70,11 @@ def test_defaults_and_status_strings(lib):
     dict(L=(8, 8, 8, 8), nn_mode=1, cycle_prec=0),        # learned layer needs the FP32 cycle
     dict(L=(8, 8, 8, 8), nn_prec=7),
     dict(L=(8, 8, 8, 8), sap1_prec=2),                    # FP16 level-1 blocks need three levels
+    dict(L=(8, 8, 8, 8), sap1_prec=3),                    # BF16 as well
+    dict(L=(8, 8, 8, 8), transfer_prec=5),
+    dict(L=(8, 8, 8, 8), transfer_prec=2, cycle_prec=0),  # 16-bit P copies need the FP32 cycle
+    dict(L=(8, 8, 8, 8), sap_prec=2),                     # 16-bit SAP operator needs block_oe = 1
+    dict(L=(8, 8, 8, 8), sap_prec=6, block_oe=1),
     dict(L=(8, 8, 8, 8), restart=0),
     dict(L=(8, 8, 8, 8), restart=127),                    # Hessenberg column beyond the fixed bound
     dict(L=(8, 8, 8, 8), coarse_restart=200),
@@ -135,5 +140,8 @@ def test_workspace_bytes_plan(lib):
     # FP64 cycle: the smoother, P and D_c double
     assert tm.tm_workspace_bytes(tm.params(**dict(kw, cycle_prec=tm.TM_F64, coarse_mma=0, sap1_prec=tm.TM_F32,
                                                   outer_apply=tm.TM_F64)), 4) > b4
+    # a 16-bit copy of P: nv fine fields of 4 bytes per complex number
+    b16 = tm.tm_workspace_bytes(tm.params(**dict(kw, transfer_prec=tm.TM_BF16)), 4)
+    assert b16 - b4 == 24 * 96 * 48 ** 3 * 12 * 4
     assert tm.tm_workspace_bytes(tm.params(**dict(kw, nv=40)), 1) == 0
     assert tm.tm_workspace_bytes(p, 0) == 0

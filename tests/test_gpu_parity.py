@@ -175,6 +175,32 @@ def test_restrict_prolong_coarse_apply(name, prec, tol):
 
 
 @pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("tp,tol", [(tm.TM_F16, 5e-3), (tm.TM_BF16, 3e-2)])
+def test_restrict_prolong_with_16bit_interpolation(name, tp, tol):
+    # the K-cycle's transfers read a 16-bit copy of P (11 / 8 significant bits,
+    # FP32 arithmetic); the coarse operator stays the full-precision Galerkin product
+    U, g, op, seed = _case(name, F32, transfer_prec=tp)
+    tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+    tm.tm_setup_from_vectors(g.h, tv)
+    P = Interpolation(tv, g.p.agg)
+    Dc = CoarseOperator.build(op, P, mu_c=g.p.delta * g.p.mu)
+    assert rel(g.Dc_blocks(), Dc.blocks) <= 5e-6
+    psi = inputs.gaussian_spinor(g.L, seed + 21, nrhs=2)
+    fc = g.field(1, F32, 2)
+    tm.tm_restrict(g.h, F32, g.pack(0, F32, psi, 2), fc, 2)
+    err_r = rel(g.unpack(1, F32, fc, g.coarse_shape(2), 2), P.restrict(psi))
+    assert err_r <= tol
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(g.coarse_shape(2)) + 1j * rng.standard_normal(g.coarse_shape(2))
+    fo = g.field(0, F32, 2)
+    tm.tm_prolong(g.h, F32, g.pack(1, F32, v, 2), fo, 2, 0)
+    err_p = rel(g.unpack(0, F32, fo, psi.shape, 2), P.prolong(v))
+    assert err_p <= tol
+    # the rounding is that of the 16-bit format, not more (and not the FP32 result)
+    assert max(err_r, err_p) >= (1e-5 if tp == tm.TM_F16 else 1e-4)
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_coarse_solve_fixed_steps(name):
     g, op, P, Dc, seed = _from_vectors(name)
     rng = np.random.default_rng(seed + 3)
@@ -306,6 +332,40 @@ def test_solve_with_fp32_pair_outer_apply(name):
             assert np.linalg.norm(b[r] - op.apply(x[r])) / np.linalg.norm(b[r]) <= 1e-10
         iters[oa] = info.iters
     assert abs(iters[tm.TM_F64] - iters[tm.TM_F32X2]) <= 1, iters
+
+
+@pytest.mark.parametrize("name", OE_CASES)
+@pytest.mark.parametrize("sp,tol", [(tm.TM_F16, 5e-3), (tm.TM_BF16, 3e-2)])
+def test_sap_odd_even_blocks_16bit_operator(name, sp, tol):
+    # links, clover and D_oo^-1 of the smoother stored in 16 bits, FP32 arithmetic:
+    # the sweeps follow the oracle's exact-operator SAP to the format's rounding
+    U, g, op, seed = _case(name, F32, block_oe=1, sap_prec=sp)
+    sap = SAP(op, CASES[name][8], n_mr=4, block_oe=True)
+    b = inputs.gaussian_spinor(g.L, seed + 11)
+    x0 = 0.1 * inputs.gaussian_spinor(g.L, seed + 12)
+    err = rel(g.sap(b, x0, 2, F32), sap.smooth(b, x0, 2))
+    assert err <= tol
+    assert err >= (1e-5 if sp == tm.TM_F16 else 1e-4)  # the 16-bit copy is the one read
+    # a new twisted mass reaches the 16-bit inverses
+    tm.tm_set_mu(g.h, -op.mu, g.p.delta)
+    sapm = SAP(op.with_mu(-op.mu), CASES[name][8], n_mr=4, block_oe=True)
+    assert rel(g.sap(b, x0, 1, F32), sapm.smooth(b, x0, 1)) <= tol
+
+
+@pytest.mark.parametrize("opts", [dict(sap_prec=tm.TM_F16, transfer_prec=tm.TM_F16),
+                                  dict(sap_prec=tm.TM_BF16, transfer_prec=tm.TM_BF16)])
+def test_solve_with_16bit_preconditioner_operators(opts):
+    # 16-bit operator copies inside the K-cycle change the preconditioner, not
+    # the accuracy: the oracle's FP64 residual of the solution stays <= 1e-10
+    name = "8x8x8x8"
+    U, g, op, seed = _case(name, F32, setup_iters=2, block_oe=1, outer_apply=tm.TM_F32X2, **opts)
+    tm.tm_setup(g.h, inputs.random_test_vectors(g.L, g.nv, seed + 2000))
+    b = inputs.gaussian_spinor(g.L, seed + 1000, nrhs=2)
+    x = np.zeros_like(b)
+    st, info = tm.tm_solve(g.h, b, x, 2, 1e-10)
+    assert st == tm.TM_OK and info.converged
+    for r in range(2):
+        assert np.linalg.norm(b[r] - op.apply(x[r])) / np.linalg.norm(b[r]) <= 1e-10
 
 
 def test_solve_iterations_match_oracle_fp64():

@@ -123,9 +123,11 @@ def test_coarse_sap_sweeps(name, with_b):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_coarse_sap_fp16_blocks(name):
-    # FP16 copy of the level-1 blocks read by the smoother (11 significant bits; FP32 arithmetic)
-    t = Three(name, F32, sap1_prec=tm.TM_F16)
+@pytest.mark.parametrize("sp,tol", [(tm.TM_F16, 5e-3), (tm.TM_BF16, 3e-2)])
+def test_coarse_sap_16bit_blocks(name, sp, tol):
+    # 16-bit copy of the level-1 blocks read by the smoother (FP16: 11, BF16: 8
+    # significant bits; FP32 arithmetic)
+    t = Three(name, F32, sap1_prec=sp)
     t.from_vectors()
     g = t.g
     b = t.rand1(1)
@@ -133,7 +135,7 @@ def test_coarse_sap_fp16_blocks(name):
     sap = CoarseSAP(t.tl.Dc1, g.p.sap_block1, g.p.mr_iters1)
     fx = g.pack(1, F32, x0)
     tm.tm_sap1(g.h, F32, g.pack(1, F32, b), fx, 2, 1)
-    assert rel(g.unpack(1, F32, fx, x0.shape), sap.smooth(b, x0, 2)) <= 5e-3
+    assert rel(g.unpack(1, F32, fx, x0.shape), sap.smooth(b, x0, 2)) <= tol
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -227,9 +229,10 @@ def test_three_level_adaptive_setup(name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("prec,sap1", [(F64, 1), (F32, 1), (F32, 2)])
-def test_three_level_solve_true_residual(name, prec, sap1):
-    t = Three(name, prec, setup_iters=2, coarse_setup_iters=2, sap1_prec=sap1)
+@pytest.mark.parametrize("prec,sap1,tp", [(F64, 1, 1), (F32, 1, 1), (F32, 2, 1), (F32, 3, 2), (F32, 2, 3)])
+def test_three_level_solve_true_residual(name, prec, sap1, tp):
+    # 16-bit operator copies in the preconditioner do not limit the accuracy of the solution
+    t = Three(name, prec, setup_iters=2, coarse_setup_iters=2, sap1_prec=sap1, transfer_prec=tp)
     g = t.g
     tm.tm_setup(g.h, t.vectors())
     op = Operator(t.U, t.prm.m0, t.prm.c_sw, t.prm.mu)
