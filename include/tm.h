@@ -174,6 +174,13 @@ typedef struct {
      flexible outer solver tolerates).  The outer D(mu), the coarse build and
      the FP32 D apply keep the full-precision operator. */
   int sap_prec;
+  /* Coarsest-level solve: 0 = GMRES(coarse_restart) on the odd-even Schur
+     complement to coarse_tol / coarsest_tol with the host deciding each step;
+     k in 1..64 = exactly k GMRES steps (a right-hand side whose residual
+     estimate reaches the tolerance stops updating), all bookkeeping on the
+     device, captured once as a CUDA graph and replayed for every later
+     coarsest solve with the same buffers and twisted mass. */
+  int coarsest_steps;
 } tm_params;
 
 typedef struct {
@@ -193,7 +200,7 @@ typedef struct {
  * init_sweeps1 = 3, coarse_setup_iters = 3, coarsest_tol = 5e-2,
  * coarsest_maxit = 200, coarse_mma = 0, nn_mode = 0, nn_prec = TM_F32,
  * sap1_prec = TM_F32, outer_apply = TM_F64, block_oe = 0, tc_spin_limit = 0,
- * transfer_prec = sap_prec = TM_F32.
+ * transfer_prec = sap_prec = TM_F32, coarsest_steps = 0.
  * L, m0, c_sw, mu are 0. */
 void tm_params_default(tm_params* p);
 

@@ -29,7 +29,7 @@ class tm_params(ctypes.Structure):
         ("coarse_setup_iters", c_int), ("coarsest_tol", c_double), ("coarsest_maxit", c_int),
         ("coarse_mma", c_int), ("nn_mode", c_int), ("nn_prec", c_int), ("sap1_prec", c_int),
         ("outer_apply", c_int), ("block_oe", c_int), ("tc_spin_limit", c_int), ("transfer_prec", c_int),
-        ("sap_prec", c_int),
+        ("sap_prec", c_int), ("coarsest_steps", c_int),
     ]
 
 

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtmamg.so")
 
-SOURCES = ["dirac.cu", "dirac_df.cu", "sap.cu", "coarse.cu", "coarse2.cu", "coarse_tc.cu", "nn.cu", "blas.cu", "blas_pair.cu", "oecg.cu", "tm_api.cu"]
+SOURCES = ["dirac.cu", "dirac_df.cu", "sap.cu", "coarse.cu", "coarse2.cu", "coarse_tc.cu", "nn.cu", "blas.cu", "blas_pair.cu", "oecg.cu", "gmres_dev.cu", "tm_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
 

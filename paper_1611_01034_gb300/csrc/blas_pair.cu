@@ -35,43 +35,45 @@ __device__ __forceinline__ void st_pair(double* __restrict__ p, long i, cdf a) {
   reinterpret_cast<double2*>(p)[i] = make_double2(pair2d(a.r), pair2d(a.i));
 }
 
-// stage 1 of d_j = sum_i conj(X_j[i]) y[i] for j in the CTA's chunk of 8
+// stage 1 of d_j = sum_i conj(X_j[i]) y[i] for j in the CTA's chunk of KC
+// (KC = 4 for short bases: fewer registers, more warps in flight)
+template <int KC>
 __global__ void __launch_bounds__(kPairThreads) k_pdot_partial_b(const double* __restrict__ X, long xstr, long ldx,
                                                                  int k, const double* __restrict__ y, long ystr,
                                                                  long ncx, double* __restrict__ part,
                                                                  const int* __restrict__ active) {
-  __shared__ double red[32 * 2 * kChunk];
+  __shared__ double red[32 * 2 * KC];
   const int r = blockIdx.z;
   if (active && !active[r]) return;
-  const int j0 = blockIdx.y * kChunk;
-  cdf d[kChunk];
+  const int j0 = blockIdx.y * KC;
+  cdf d[KC];
 #pragma unroll
-  for (int m = 0; m < kChunk; ++m) d[m] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+  for (int m = 0; m < KC; ++m) d[m] = cdf{{0.f, 0.f}, {0.f, 0.f}};
   const double* yr = y + r * ystr;
   const double* Xr = X + r * xstr + j0 * ldx;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
     const cdf yv = ld_pair(yr, i);
 #pragma unroll
-    for (int jj = 0; jj < kChunk; ++jj)
+    for (int jj = 0; jj < KC; ++jj)
       if (j0 + jj < k) cfmac_pp(d[jj], ld_pair(Xr + jj * ldx, i), yv);
   }
-  double v[2 * kChunk];
+  double v[2 * KC];
 #pragma unroll
-  for (int jj = 0; jj < kChunk; ++jj) {
+  for (int jj = 0; jj < KC; ++jj) {
     v[2 * jj] = pair2d(d[jj].r);
     v[2 * jj + 1] = pair2d(d[jj].i);
   }
-  block_allreduce<double, 2 * kChunk>(v, red);
-  if (threadIdx.x < 2 * kChunk) {
+  block_allreduce<double, 2 * KC>(v, red);
+  if (threadIdx.x < 2 * KC) {
     const int jj = threadIdx.x >> 1;
     if (j0 + jj < k)
       part[(((long)r * k + j0 + jj) * gridDim.x + blockIdx.x) * 2 + (threadIdx.x & 1)] = v[threadIdx.x];
   }
 }
 
-// y -= sum_j c_j X_j over all k vectors; MODE 1 (k <= 8) also forms the
+// y -= sum_j c_j X_j over all k vectors; MODE 1 (k <= KC) also forms the
 // partial sums of d_j = X_j^H y with the updated y, MODE 2 those of |y|^2
-template <int MODE>
+template <int MODE, int KC = kChunk>
 __global__ void __launch_bounds__(kPairThreads) k_pcaxpy_b(const double* __restrict__ X, long xstr, long ldx, int k,
                                                            const double* __restrict__ c, long cstr,
                                                            double* __restrict__ y, long ystr, long ncx,
@@ -86,24 +88,24 @@ __global__ void __launch_bounds__(kPairThreads) k_pcaxpy_b(const double* __restr
   __syncthreads();
   double* yr = y + r * ystr;
   const double* Xr = X + r * xstr;
-  cdf d[MODE == 1 ? kChunk : 1];
+  cdf d[MODE == 1 ? KC : 1];
 #pragma unroll
-  for (int m = 0; m < (MODE == 1 ? kChunk : 1); ++m) d[m] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+  for (int m = 0; m < (MODE == 1 ? KC : 1); ++m) d[m] = cdf{{0.f, 0.f}, {0.f, 0.f}};
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < ncx; i += (long)gridDim.x * blockDim.x) {
     cdf acc = ld_pair(yr, i);
     if constexpr (MODE == 1) {
-      cdf xs[kChunk];
+      cdf xs[KC];
 #pragma unroll
-      for (int j = 0; j < kChunk; ++j) xs[j] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+      for (int j = 0; j < KC; ++j) xs[j] = cdf{{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
-      for (int j = 0; j < kChunk; ++j) {
+      for (int j = 0; j < KC; ++j) {
         if (j < k) {
           xs[j] = ld_pair(Xr + j * ldx, i);
           cfma_pp(acc, cs[j], xs[j]);
         }
       }
 #pragma unroll
-      for (int j = 0; j < kChunk; ++j)
+      for (int j = 0; j < KC; ++j)
         if (j < k) cfmac_pp(d[j], xs[j], acc);
     } else {
       for (int j = 0; j < k; ++j) cfma_pp(acc, cs[j], ld_pair(Xr + j * ldx, i));
@@ -115,14 +117,14 @@ __global__ void __launch_bounds__(kPairThreads) k_pcaxpy_b(const double* __restr
     st_pair(yr, i, acc);
   }
   if constexpr (MODE == 1) {
-    double v[2 * kChunk];
+    double v[2 * KC];
 #pragma unroll
-    for (int j = 0; j < kChunk; ++j) {
+    for (int j = 0; j < KC; ++j) {
       v[2 * j] = pair2d(d[j].r);
       v[2 * j + 1] = pair2d(d[j].i);
     }
-    block_allreduce<double, 2 * kChunk>(v, red);
-    if (threadIdx.x < 2 * kChunk) {
+    block_allreduce<double, 2 * KC>(v, red);
+    if (threadIdx.x < 2 * KC) {
       const int j = threadIdx.x >> 1;
       if (j < k) part[(((long)r * k + j) * gridDim.x + blockIdx.x) * 2 + (threadIdx.x & 1)] = v[threadIdx.x];
     }
@@ -189,14 +191,19 @@ __global__ void __launch_bounds__(kPairThreads) k_plincomb_b(const float* __rest
 }
 
 size_t pair_smem(int k) { return (size_t)k * sizeof(cdf) + 32 * 2 * kChunk * sizeof(double); }
+constexpr int kShort = 4;  // bases of at most 4 vectors take the 4-wide kernels
 
 }  // namespace
 
 void launch_pdot_b(const double* X, long xstr, long ldx, int k, const double* y, long ystr, long ncx, double* out,
                    long ostr, double* scratch, int nrhs, const int* active, cudaStream_t st) {
   const int G = pair_grid(ncx);
-  k_pdot_partial_b<<<dim3(G, (k + kChunk - 1) / kChunk, nrhs), kPairThreads, 0, st>>>(X, xstr, ldx, k, y, ystr, ncx,
-                                                                                      scratch, active);
+  if (k <= kShort)
+    k_pdot_partial_b<kShort><<<dim3(G, 1, nrhs), kPairThreads, 0, st>>>(X, xstr, ldx, k, y, ystr, ncx, scratch,
+                                                                        active);
+  else
+    k_pdot_partial_b<kChunk><<<dim3(G, (k + kChunk - 1) / kChunk, nrhs), kPairThreads, 0, st>>>(
+        X, xstr, ldx, k, y, ystr, ncx, scratch, active);
   k_preduce_b<<<dim3(k, nrhs), 256, 0, st>>>(scratch, G, k, out, ostr, active);
 }
 
@@ -204,6 +211,12 @@ int launch_pcaxpy_dot_b(const double* X, long xstr, long ldx, int k, const doubl
                         long ncx, double* out, long ostr, double* scratch, int nrhs, const int* active,
                         cudaStream_t st) {
   const int G = pair_grid(ncx);
+  if (k <= kShort) {
+    k_pcaxpy_b<1, kShort><<<dim3(G, nrhs), kPairThreads, pair_smem(k), st>>>(X, xstr, ldx, k, c, cstr, y, ystr, ncx,
+                                                                             scratch, active);
+    k_preduce_b<<<dim3(k, nrhs), 256, 0, st>>>(scratch, G, k, out, ostr, active);
+    return 2;
+  }
   if (k <= kChunk) {
     k_pcaxpy_b<1><<<dim3(G, nrhs), kPairThreads, pair_smem(k), st>>>(X, xstr, ldx, k, c, cstr, y, ystr, ncx, scratch,
                                                                      active);

@@ -130,9 +130,175 @@ __global__ void k_csap(const void* __restrict__ Dc, const T* __restrict__ b, T* 
   if (act) xx[(long)s * n + row] = xx[(long)s * n + row] + e;
 }
 
+// The same colour for up to RB right-hand sides per CTA: every block entry a
+// thread loads serves all of them (the separate-rhs form reads the block's
+// D_c1 entries once per right-hand side and MR step).  Each right-hand side
+// keeps its own residual, correction and MR coefficients.
+template <typename T, int H, int RB>
+__global__ void __launch_bounds__(768) k_csap_b(const void* __restrict__ Dc, const T* __restrict__ b, T* __restrict__ x, CSapGeom sg, T mu,
+                         int n_mr, int colour, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = sg.n, BS = sg.bsites;
+  cx<T>* rs = reinterpret_cast<cx<T>*>(smem_raw);  // [RB][BS][n]
+  T* red = reinterpret_cast<T*>(rs + (size_t)RB * BS * n);
+  const Lat& g = sg.g;
+  const int ngrp = (nrhs + RB - 1) / RB;
+  const int r0 = (blockIdx.x % ngrp) * RB;  // groups of right-hand sides fastest (block reuse in L2)
+  const int R = min(RB, nrhs - r0);
+  const long vs = (long)g.V * n;  // complex numbers per level-1 vector
+  int k = blockIdx.x / ngrp;
+  const int nbxh = sg.nb[3] / 2;
+  int bc4[4];
+  const int bxh = k % nbxh;
+  k /= nbxh;
+  bc4[2] = k % sg.nb[2];
+  k /= sg.nb[2];
+  bc4[1] = k % sg.nb[1];
+  bc4[0] = k / sg.nb[1];
+  bc4[3] = 2 * bxh + ((bc4[0] + bc4[1] + bc4[2] + colour) & 1);
+  const int l = threadIdx.x / n, row = threadIdx.x % n;
+  const bool act = l < BS;
+  int lc[4], c[4], lst[4];
+  lst[3] = 1;
+  lst[2] = sg.blk[3];
+  lst[1] = sg.blk[3] * sg.blk[2];
+  lst[0] = lst[1] * sg.blk[1];
+  {
+    int q = act ? l : 0;
+    lc[3] = q % sg.blk[3];
+    q /= sg.blk[3];
+    lc[2] = q % sg.blk[2];
+    q /= sg.blk[2];
+    lc[1] = q % sg.blk[1];
+    lc[0] = q / sg.blk[1];
+  }
+  for (int d = 0; d < 4; ++d) c[d] = bc4[d] * sg.blk[d] + lc[d];
+  const int s = ((c[0] * g.L[1] + c[1]) * g.L[2] + c[2]) * g.L[3] + c[3];
+  const long B = (long)s * 9 * n * n;
+  const T sg5 = row < n / 2 ? -mu : mu;
+  const cx<T>* xx = reinterpret_cast<const cx<T>*>(x) + r0 * vs;
+  const cx<T>* bb = b ? reinterpret_cast<const cx<T>*>(b) + r0 * vs : nullptr;
+  cx<T> r[RB], e[RB];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) r[j] = e[j] = cx<T>{0, 0};
+  if (act) {
+    cx<T> acc[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) acc[j] = cx<T>{0, 0};
+    for (int t = 0; t < 9; ++t) {
+      const long src = (long)c_nb(g, s, t) * n;
+      const long Bt = B + (long)t * n * n;
+#pragma unroll 4
+      for (int col = 0; col < n; ++col) {
+        const cx<T> m = ld_blk<T, H>(Dc, Bt + (long)col * n + row);
+#pragma unroll
+        for (int j = 0; j < RB; ++j)
+          if (j < R) cfma(acc[j], m, xx[j * vs + src + col]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      if (j < R) {
+        const cx<T> xs = xx[j * vs + (long)s * n + row];
+        acc[j].r -= sg5 * xs.i;
+        acc[j].i += sg5 * xs.r;
+        r[j] = (bb ? bb[j * vs + (long)s * n + row] : cx<T>{0, 0}) - acc[j];
+        rs[((size_t)j * BS + l) * n + row] = r[j];
+      }
+    }
+  }
+  for (int it = 0; it < n_mr; ++it) {
+    __syncthreads();
+    cx<T> q[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) q[j] = cx<T>{0, 0};
+    T dots[3 * RB];
+#pragma unroll
+    for (int j = 0; j < 3 * RB; ++j) dots[j] = 0;
+    if (act) {
+      for (int t = 0; t < 9; ++t) {
+        int ln = l;
+        if (t > 0) {
+          const int mu_d = (t - 1) >> 1;
+          const bool bwd = (t - 1) & 1;
+          if (bwd ? lc[mu_d] == 0 : lc[mu_d] == sg.blk[mu_d] - 1) continue;  // leaves the block
+          ln = bwd ? l - lst[mu_d] : l + lst[mu_d];
+        }
+        const long Bt = B + (long)t * n * n;
+#pragma unroll 4
+        for (int col = 0; col < n; ++col) {
+          const cx<T> m = ld_blk<T, H>(Dc, Bt + (long)col * n + row);
+#pragma unroll
+          for (int j = 0; j < RB; ++j)
+            if (j < R) cfma(q[j], m, rs[((size_t)j * BS + ln) * n + col]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        q[j].r -= sg5 * r[j].i;
+        q[j].i += sg5 * r[j].r;
+        dots[3 * j] = q[j].r * r[j].r + q[j].i * r[j].i;
+        dots[3 * j + 1] = q[j].r * r[j].i - q[j].i * r[j].r;
+        dots[3 * j + 2] = q[j].r * q[j].r + q[j].i * q[j].i;
+      }
+    }
+    block_allreduce<T, 3 * RB>(dots, red);
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const cx<T> alpha = dots[3 * j + 2] > T(0) ? cx<T>{dots[3 * j] / dots[3 * j + 2], dots[3 * j + 1] / dots[3 * j + 2]}
+                                                   : cx<T>{0, 0};
+        cfma(e[j], alpha, r[j]);
+        cfma(r[j], -alpha, q[j]);
+      }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+        if (j < R) rs[((size_t)j * BS + l) * n + row] = r[j];
+    }
+  }
+  __syncthreads();
+  if (act) {
+    cx<T>* xw = reinterpret_cast<cx<T>*>(x) + r0 * vs;
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+      if (j < R) xw[j * vs + (long)s * n + row] = xw[j * vs + (long)s * n + row] + e[j];
+  }
+}
+
+constexpr int kCsapRhs = 6;  // right-hand sides per CTA of the batched level-1 SAP
+
+template <typename T, int H>
+void csap_b(const void* Dc, const T* b, T* x, const CSapGeom& sg, double mu, int n_mr, int colour, int nrhs,
+            cudaStream_t st) {
+  const int threads = (sg.bsites * sg.n + 31) / 32 * 32;
+  const size_t smem = (size_t)kCsapRhs * sg.bsites * sg.n * sizeof(cx<T>) + 32 * 3 * kCsapRhs * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_csap_b<T, H, kCsapRhs>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  const int ngrp = (nrhs + kCsapRhs - 1) / kCsapRhs;
+  dim3 grid((unsigned)(sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2) * (unsigned)ngrp);
+  k_csap_b<T, H, kCsapRhs><<<grid, threads, smem, st>>>(Dc, b, x, sg, (T)mu, n_mr, colour, nrhs);
+}
+
 template <typename T>
 void launch_csap_colour(const T* Dc, const T* b, T* x, const CSapGeom& sg, double mu, int n_mr, int colour,
                         int nrhs, cudaStream_t st, const void* Dc_half, int half_kind) {
+  // several right-hand sides share every block-entry load (its 80 registers per
+  // thread allow up to 768 threads: 2^4 blocks of N_v1 <= 24)
+  if (nrhs > 1 && sizeof(T) == 4 && sg.bsites * sg.n <= 768) {
+    if (Dc_half && half_kind == ST_BF16)
+      csap_b<T, ST_BF16>(Dc_half, b, x, sg, mu, n_mr, colour, nrhs, st);
+    else if (Dc_half)
+      csap_b<T, ST_F16>(Dc_half, b, x, sg, mu, n_mr, colour, nrhs, st);
+    else
+      csap_b<T, ST_NATIVE>(Dc, b, x, sg, mu, n_mr, colour, nrhs, st);
+    return;
+  }
   const int threads = (sg.bsites * sg.n + 31) / 32 * 32;
   const size_t smem = (size_t)sg.bsites * sg.n * sizeof(cx<T>) + 32 * 3 * sizeof(T);
   dim3 grid((unsigned)(sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3] / 2) * (unsigned)nrhs);

@@ -133,6 +133,14 @@ struct tm_handle {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> evpool;
   cudaEvent_t pipe_ev[2] = {nullptr, nullptr};  // the coarse GMRES's double-buffered step results
+  // CUDA graphs of fixed-step coarsest solves (coarsest_steps > 0), keyed by
+  // every pointer and scalar they captured; captured on a private stream
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    size_t nodes;
+  };
+  std::map<std::string, GraphEntry> graphs;
+  cudaStream_t cap_st = nullptr;
   BuildShape build_shape{};                     // tile shape of the D_c build (autotuned or default)
   long long prof_launch[24] = {};
   long long prof_units[24] = {};
@@ -619,6 +627,128 @@ OELevel coarsest_level(tm_handle* h) {
   return OELevel{h->Dc, h->Dinv, h->oe, h->n, h->nhalf, h->gc.V, mu_c(h), tc};
 }
 
+// Exactly K odd-even GMRES steps on D_c(delta mu) x_r = b_r from zero, every
+// decision on the device (gmres_dev.cu: a right-hand side whose residual
+// estimate reaches tol stops updating), captured once per set of buffers and
+// scalars as a CUDA graph and replayed: one launch per coarsest solve instead
+// of about eight launches and a host decision per Arnoldi step.  With a fixed
+// step count the coarsest solve is the same polynomial in D_c for every call,
+// a fixed preconditioner for the level above.
+template <typename T>
+std::vector<int> coarse_solve_graph(tm_handle* h, const OELevel& lv, const T* b, T* x, int nrhs, double tol, int K) {
+  const long nc = (long)lv.nhalf * lv.n;
+  const long cv = 2 * nc;
+  const long cf = 2 * (long)lv.Vc * lv.n;
+  const long vstr = (long)(K + 1) * cv;
+  const long ds = 4 * kMaxDots + 2;
+  const T* Dc = static_cast<const T*>(lv.Dc);
+  const T* Di = static_cast<const T*>(lv.Dinv);
+  T* to = W<T>(h, "gq_to", cv * nrhs);
+  T* bh = W<T>(h, "gq_bh", cv * nrhs);
+  T* xe = W<T>(h, "gq_xe", cv * nrhs);
+  T* uo = W<T>(h, "gq_uo", cv * nrhs);
+  T* w = W<T>(h, "gq_w", cv * nrhs);
+  T* Vb = W<T>(h, "gq_V", vstr * nrhs);
+  double* part = W<double>(h, "gq_part", std::max(multidot_scratch_doubles(nc, K + 1, nrhs), 2L * 304 * nrhs));
+  double* dd = W<double>(h, "gq_dots", ds * nrhs);
+  double* nrm = W<double>(h, "gq_nrm", nrhs);
+  GmresDev st{reinterpret_cast<cx<double>*>(W<double>(h, "gq_H", (size_t)2 * (K + 1) * K * nrhs)),
+              reinterpret_cast<cx<double>*>(W<double>(h, "gq_g", (size_t)2 * (K + 1) * nrhs)),
+              W<double>(h, "gq_cs", (size_t)K * nrhs),
+              reinterpret_cast<cx<double>*>(W<double>(h, "gq_sn", (size_t)2 * K * nrhs)),
+              W<double>(h, "gq_bn", nrhs), W<int>(h, "gq_kk", nrhs), W<int>(h, "gq_done", nrhs), K};
+  const double mc = lv.mu_c;
+  bool use_tc = false;
+  if constexpr (std::is_same<T, float>::value)
+    use_tc = lv.tc && nrhs >= 2 && tc_supported(lv.oe.nv, nrhs, h->p.coarse_mma);
+  auto enqueue = [&](cudaStream_t s) {
+    auto schur = [&](const T* v) {
+      if constexpr (std::is_same<T, float>::value) {
+        if (use_tc) {
+          launch_tc_schur(*lv.tc, lv.oe, v, uo, w, mc, nrhs, vstr, cv, cv, nullptr, h->p.coarse_mma, h->d_err, s,
+                          (unsigned)h->p.tc_spin_limit);
+          CKL();
+          return;
+        }
+      }
+      launch_oe_schur_b<T>(Dc, Di, v, uo, w, lv.oe, mc, nrhs, vstr, cv, cv, nullptr, s);
+      CKL();
+    };
+    launch_oe_prepare_b<T>(Dc, Di, b, to, bh, lv.oe, nrhs, cf, cv, s);
+    CKL();
+    launch_zero<T>(xe, cv * nrhs, s);
+    CKL();
+    launch_norm2_b<T>(bh, cv, nc, nrm, part, nrhs, nullptr, s);
+    CKL();
+    launch_gmres_init(st, nrm, nrhs, s);
+    CKL();
+    launch_scale_copy_b<T>(bh, cv, Vb, vstr, nrm, nc, nrhs, nullptr, s);  // v_0 = r / |r|
+    CKL();
+    for (int k = 0; k < K; ++k) {
+      schur(Vb + (long)k * cv);
+      double* d1 = dd;
+      double* d2 = dd + 2 * (k + 1);
+      launch_multidot_b_partials<T>(Vb, vstr, cv, k + 1, w, cv, nc, part, nrhs, nullptr, s);
+      CKL();
+      launch_multi_caxpy_bp<T>(Vb, vstr, cv, k + 1, part, nc, d1, ds, w, cv, nc, nrhs, nullptr, s);
+      CKL();
+      launch_multidot_b_partials<T>(Vb, vstr, cv, k + 1, w, cv, nc, part, nrhs, nullptr, s);
+      CKL();
+      launch_multi_caxpy_bp<T>(Vb, vstr, cv, k + 1, part, nc, d2, ds, w, cv, nc, nrhs, nullptr, s);
+      CKL();
+      launch_norm2_b_partials<T>(w, cv, nc, part, nrhs, nullptr, s);
+      CKL();
+      launch_scale_copy_bp<T>(w, cv, Vb + (long)(k + 1) * cv, vstr, part, nrm, nc, nrhs, nullptr, s);
+      CKL();
+      launch_gmres_step(st, dd, ds, nrm, k, nrhs, tol, s);
+      CKL();
+    }
+    launch_gmres_solve(st, dd, ds, K, nrhs, s);
+    CKL();
+    launch_lincomb_b<T, T>(Vb, vstr, cv, K, dd, ds, xe, cv, nc, nrhs, nullptr, s);
+    CKL();
+    launch_oe_reconstruct_b<T>(Dc, Di, b, xe, x, lv.oe, nrhs, cf, cv, s);
+    CKL();
+  };
+  char key[512];
+  std::snprintf(key, sizeof key, "%d %d %d %.17g %.17g %d %d %p %p %p %p %p %p %p %p %p %p %p %p %p %p %p %p %p %p",
+                (int)sizeof(T), nrhs, K, mc, tol, h->p.coarse_mma, h->p.tc_spin_limit, (const void*)b, (void*)x,
+                (const void*)Dc, (const void*)Di, (void*)to, (void*)bh, (void*)xe, (void*)uo, (void*)w, (void*)Vb,
+                (void*)part, (void*)dd, (void*)nrm, (void*)st.H, (void*)st.g, (void*)st.kk,
+                use_tc ? (const void*)lv.tc->even : nullptr, use_tc ? (const void*)lv.tc->odd : nullptr);
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    if (h->graphs.size() >= 32) {  // bound the cache: drop the old graphs
+      for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+      h->graphs.clear();
+    }
+    if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    cudaGraph_t gr = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue(h->cap_st);
+    } catch (...) {
+      cudaStreamEndCapture(h->cap_st, &gr);
+      if (gr) cudaGraphDestroy(gr);
+      throw;
+    }
+    CK(cudaStreamEndCapture(h->cap_st, &gr));
+    tm_handle::GraphEntry e{nullptr, 0};
+    CK(cudaGraphGetNodes(gr, nullptr, &e.nodes));
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, gr, 0);
+    cudaGraphDestroy(gr);
+    CK(ie);
+    it = h->graphs.emplace(key, e).first;
+  }
+  {
+    Prof pf(h, PK_COARSE_OE, K * nrhs, (int)it->second.nodes);
+    CK(cudaGraphLaunch(it->second.exec, h->st));
+  }
+  h->coarse_iters += (long long)K * nrhs;
+  if (use_tc) check_flags(h);  // bounded waits inside the tensor-core kernel
+  return std::vector<int>(nrhs, K);
+}
+
 // Odd-even GMRES(coarse_restart) on D_c(delta mu) x_r = b_r for nrhs full
 // coarse vectors at once.  Every right-hand side runs its own GMRES (own
 // Hessenberg matrix, own restarts and stopping); the batch only shares
@@ -626,6 +756,8 @@ OELevel coarsest_level(tm_handle* h) {
 // sides are masked out, so each one sees exactly the single-rhs arithmetic.
 template <typename T>
 std::vector<int> coarse_solve(tm_handle* h, const OELevel& lv, const T* b, T* x, int nrhs, double tol, int maxit) {
+  if (h->p.coarsest_steps > 0)
+    return coarse_solve_graph<T>(h, lv, b, x, nrhs, tol, std::min(h->p.coarsest_steps, maxit));
   using cd = std::complex<double>;
   const int m = h->p.coarse_restart;
   const long nc = (long)lv.nhalf * lv.n;         // complex numbers per compact vector
@@ -989,10 +1121,11 @@ void level1_solve(tm_handle* h, const T* b1, T* x1, int nrhs, double tol, int ma
     launch_zero<T>(x1, 2 * ncx * nrhs, h->st);
     CKL();
   }
-  auto resid = [&](const T* xx, T* r) {
+  auto resid = [&](const T* xx, T* r, bool) {  // one form only: always exact
     coarse_apply1<T>(h, xx, r, nrhs);
     launch_sub_b<T>(b1, 2 * ncx, r, 2 * ncx, ncx, nrhs, nullptr, h->st);
     CKL();
+    return true;
   };
   auto AZ = [&](const T* z, T* o) { coarse_apply1<T>(h, z, o, nrhs); };
   auto M = [&](const T* v, T* z) { kcycle1<T>(h, v, z, nrhs); };
@@ -1317,7 +1450,12 @@ KrylovOut solve_one(tm_handle* h, const double* b, double* x, double tol) {
 // [nb][fine reals], so the multi-rhs operators apply to them directly.
 // Generic batched flexible GMRES(m): basis vectors in Tv, preconditioned
 // vectors in Tz, vectors of ncx complex numbers (fr = 2 ncx reals).
-//   resid(x, r): r = b - A x for all nb right-hand sides (contiguous blocks)
+//   resid(x, r, exact): r = b - A x for all nb right-hand sides (contiguous
+//                blocks); with exact = false it may use cheaper arithmetic
+//                (the FP32-pair stencil) and return false, and then its norms
+//                only decide whether the exact residual is needed: a residual
+//                within kVerify * tol of convergence is recomputed exactly
+//                before any decision
 //   AZ(z, w):    w = A z
 //   M(v, z):     z = preconditioner(v)
 template <typename Tv, typename Tz, typename FR, typename FAZ, typename FM>
@@ -1382,14 +1520,30 @@ std::vector<KrylovOut> fgmres_b(tm_handle* h, const std::string& tag, int pk, FR
   read_norms();
   bool x_zero = true;
   for (int r = 0; r < nb; ++r) x_zero = x_zero && hn_h[r] == 0;
+  constexpr double kVerify = 4.0;
+  // r = b - A x: the cheap form first, the exact one where it could decide convergence
+  auto true_residual = [&](const int* msk) {
+    const bool exact = resid(x, Vb, false);
+    norms(Vb, msk);
+    read_norms();
+    if (exact) return;
+    bool near = false;
+    for (int r = 0; r < nb; ++r)
+      near = near || ((!msk || active[r]) && std::sqrt(hn_h[r]) <= kVerify * tol * bnorm[r]);
+    if (near) {
+      resid(x, Vb, true);
+      norms(Vb, msk);
+      read_norms();
+    }
+  };
   if (x_zero) {
     Prof pf(h, pk, nb);
     CK(cudaMemcpyAsync(Vb, b, (size_t)blk * sizeof(Tv), cudaMemcpyDeviceToDevice, h->st));
+    norms(Vb, nullptr);
+    read_norms();
   } else {
-    resid(x, Vb);  // r = b - A x
+    true_residual(nullptr);
   }
-  norms(Vb, nullptr);
-  read_norms();
   for (int r = 0; r < nb; ++r) {
     beta[r] = std::sqrt(hn_h[r]);
     active[r] = bnorm[r] > 0 && beta[r] > tol * bnorm[r] && out[r].iters < maxit;
@@ -1533,10 +1687,8 @@ std::vector<KrylovOut> fgmres_b(tm_handle* h, const std::string& tag, int pk, FR
       }
       CKL();
     }
-    resid(x, Vb);  // true residuals
     upload_mask(active, nullptr);
-    norms(Vb, act);
-    read_norms();
+    true_residual(act);
     for (int r = 0; r < nb; ++r) {
       if (!active[r]) continue;
       beta[r] = std::sqrt(hn_h[r]);
@@ -1558,7 +1710,18 @@ std::vector<KrylovOut> solve_batch(tm_handle* h, const double* b, double* x, int
   const long blk = fr * nb;
   double* zt = std::is_same<T, double>::value || h->gdf ? nullptr : W<double>(h, "sb_z64", blk);
   T* vt = std::is_same<T, double>::value ? nullptr : W<T>(h, "sb_vT", blk);
-  auto resid = [&](const double* xx, double* r) { dslash<double>(h, xx, r, b, nb); };
+  // restart residuals in FP32 pairs when the pair operator is held; FP64 where a
+  // residual may decide convergence (fgmres_b asks for the exact one then)
+  auto resid = [&](const double* xx, double* r, bool exact) {
+    if (!exact && h->gdf) {
+      Prof pf(h, PK_DSLASHDF, nb);
+      launch_residual_df(h->gdf, h->cdf, xx, b, r, h->g, h->p.mu, h->p.bc_t, nb, h->st, h->rho);
+      CKL();
+      return false;
+    }
+    dslash<double>(h, xx, r, b, nb);
+    return true;
+  };
   auto M = [&](const double* v, T* z) {
     if constexpr (std::is_same<T, double>::value) {
       precond<double>(h, v, z, nb);
@@ -1634,6 +1797,7 @@ void validate(const tm_params* p) {
     bad("transfer_prec must be TM_F32, TM_F16 or TM_BF16");
   if (is16(p->transfer_prec) && p->cycle_prec != TM_F32) bad("a 16-bit transfer_prec needs cycle_prec = TM_F32");
   if (p->sap_prec != TM_F32 && !is16(p->sap_prec)) bad("sap_prec must be TM_F32, TM_F16 or TM_BF16");
+  if (p->coarsest_steps < 0 || p->coarsest_steps > 64) bad("coarsest_steps must be in 0..64");
   if (is16(p->sap_prec) && (p->cycle_prec != TM_F32 || !p->block_oe))
     bad("a 16-bit sap_prec needs cycle_prec = TM_F32 and block_oe = 1");
   if (p->outer_apply != TM_F64 && p->outer_apply != TM_F32X2) bad("outer_apply must be TM_F64 or TM_F32X2");
@@ -2136,6 +2300,7 @@ void tm_params_default(tm_params* p) {
   p->sap1_prec = TM_F32;
   p->transfer_prec = TM_F32;
   p->sap_prec = TM_F32;
+  p->coarsest_steps = 0;
   p->outer_apply = TM_F64;
 }
 
@@ -2158,6 +2323,8 @@ const char* tm_last_error(const tm_handle* h) { return h ? h->err.c_str() : "nul
 
 void tm_destroy(tm_handle* h) {
   if (!h) return;
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   for (auto& kv : h->work)
     if (kv.second.p) cudaFree(kv.second.p);
   void* ptrs[] = {h->d_err, h->g64, h->g32, h->c64, h->c32, h->tv, h->P, h->Dc, h->Dinv,

@@ -39,6 +39,10 @@ void launch_clover_df(const double* c64, void* cdf, const Lat& g, cudaStream_t s
 // out (FP64 field) = D(mu) in (FP32 field) to about 2^-46 relative, FP32 pairs
 void launch_dslash_df(const void* gdf, const void* cdf, const float* in, double* out, const Lat& g, double mu,
                       double bc_t, int nrhs, cudaStream_t st, double rho = 0.0);
+// r (FP64) = b - D(mu) x for FP64 x and b, in FP32-pair arithmetic (x split into pairs;
+// about 2^-46 relative to |D| |x|): restart residuals of the outer FGMRES
+void launch_residual_df(const void* gdf, const void* cdf, const double* x, const double* b, double* r, const Lat& g,
+                        double mu, double bc_t, int nrhs, cudaStream_t st, double rho = 0.0);
 
 // ---- SAP (sap.cu) ------------------------------------------------------------
 struct SapGeom {
@@ -284,6 +288,22 @@ template <typename T>
 void launch_sub_b(const T* x, long xstr, T* y, long ystr, long ncx, int nrhs, const int* active, cudaStream_t st);
 // scratch doubles that launch_multidot_b / launch_norm2_b need
 long multidot_scratch_doubles(long ncx, int k, int nrhs);
+// device state of fixed-step GMRES cycles (gmres_dev.cu), per right-hand side:
+// H [m + 1][m], g [m + 1], rotations cs [m] / sn [m], |b|, steps taken, stop flag
+struct GmresDev {
+  cx<double>* H;
+  cx<double>* g;
+  double* cs;
+  cx<double>* sn;
+  double* bnorm;
+  int* kk;
+  int* done;
+  int m;
+};
+void launch_gmres_init(const GmresDev& st, const double* nrm, int nrhs, cudaStream_t s);
+void launch_gmres_step(const GmresDev& st, const double* dd, long ds, const double* nrm, int k, int nrhs, double tol,
+                       cudaStream_t s);
+void launch_gmres_solve(const GmresDev& st, double* dd, long ds, int kmax, int nrhs, cudaStream_t s);
 // odd-even reduced operator and CG pieces of the oeCG solver (oecg.cu); half
 // fields hold one parity at compact index s >> 1
 template <typename T>

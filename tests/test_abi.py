@@ -75,6 +75,8 @@ def test_defaults_and_status_strings(lib):
     dict(L=(8, 8, 8, 8), transfer_prec=2, cycle_prec=0),  # 16-bit P copies need the FP32 cycle
     dict(L=(8, 8, 8, 8), sap_prec=2),                     # 16-bit SAP operator needs block_oe = 1
     dict(L=(8, 8, 8, 8), sap_prec=6, block_oe=1),
+    dict(L=(8, 8, 8, 8), coarsest_steps=65),
+    dict(L=(8, 8, 8, 8), coarsest_steps=-1),
     dict(L=(8, 8, 8, 8), restart=0),
     dict(L=(8, 8, 8, 8), restart=127),                    # Hessenberg column beyond the fixed bound
     dict(L=(8, 8, 8, 8), coarse_restart=200),

@@ -201,6 +201,50 @@ def test_restrict_prolong_with_16bit_interpolation(name, tp, tol):
 
 
 @pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-10), (F32, 1e-3)])
+def test_coarse_solve_device_graph(name, prec, tol):
+    # coarsest_steps = k: exactly k GMRES steps with the Givens bookkeeping on the
+    # device, captured as a CUDA graph and replayed; the same iterate as the oracle's
+    # GMRES after k steps, for every replay and after a change of mu
+    for steps in (1, 7, 24):
+        U, g, op, seed = _case(name, prec, coarsest_steps=steps)
+        tv = inputs.random_test_vectors(g.L, g.nv, seed + 2000)
+        tm.tm_setup_from_vectors(g.h, tv)
+        P = Interpolation(tv, g.p.agg)
+        rng = np.random.default_rng(seed + 3)
+        b = rng.standard_normal(g.coarse_shape()) + 1j * rng.standard_normal(g.coarse_shape())
+        for mu in (g.p.mu, -2 * g.p.mu):
+            if mu != g.p.mu:
+                tm.tm_set_mu(g.h, mu, g.p.delta)
+            oe = OddEvenCoarse(CoarseOperator.build(op.with_mu(mu), P, mu_c=g.p.delta * mu))
+            res = gmres(oe.schur, oe.reduced_rhs(b), tol=0.0, restart=steps, maxit=steps)
+            expect = oe.reconstruct(b, res.x)
+            got = []
+            for _ in range(2):
+                fx = g.field(1, prec)
+                it = tm.tm_coarse_solve(g.h, prec, g.pack(1, prec, b), fx, 0.0, steps)
+                assert it == steps
+                got.append(g.unpack(1, prec, fx, b.shape))
+            assert rel(got[0], expect) <= tol
+            assert np.array_equal(got[0], got[1])
+
+
+@pytest.mark.parametrize("coarsest_steps", [12, 24])
+def test_solve_with_device_graph_coarsest(coarsest_steps):
+    # fixed-step coarsest solves as the preconditioner's coarse correction: the
+    # outer solve still reaches the oracle's FP64 residual <= 1e-10
+    name = "8x8x8x8"
+    U, g, op, seed = _case(name, F32, setup_iters=2, coarsest_steps=coarsest_steps, coarse_mma=1, max_rhs=4)
+    tm.tm_setup(g.h, inputs.random_test_vectors(g.L, g.nv, seed + 2000))
+    b = inputs.gaussian_spinor(g.L, seed + 1000, nrhs=4)
+    x = np.zeros_like(b)
+    st, info = tm.tm_solve(g.h, b, x, 4, 1e-10)
+    assert st == tm.TM_OK and info.converged
+    for r in range(4):
+        assert np.linalg.norm(b[r] - op.apply(x[r])) / np.linalg.norm(b[r]) <= 1e-10
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_coarse_solve_fixed_steps(name):
     g, op, P, Dc, seed = _from_vectors(name)
     rng = np.random.default_rng(seed + 3)

@@ -139,6 +139,30 @@ def test_coarse_sap_16bit_blocks(name, sp, tol):
 
 
 @pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("sp", [tm.TM_F32, tm.TM_F16])
+@pytest.mark.parametrize("nrhs", [3, 7])
+def test_coarse_sap_batched_right_hand_sides(name, sp, nrhs):
+    # several right-hand sides per CTA share the block-entry loads; each keeps
+    # its own MR coefficients: the same sweeps as one right-hand side at a time
+    t = Three(name, F32, sap1_prec=sp, max_rhs=8)
+    t.from_vectors()
+    g = t.g
+    b = t.rand1(5, nrhs=nrhs)
+    x0 = 0.3 * t.rand1(6, nrhs=nrhs)
+    fx = g.pack(1, F32, x0, nrhs)
+    tm.tm_sap1(g.h, F32, g.pack(1, F32, b, nrhs), fx, 2, nrhs)
+    got = g.unpack(1, F32, fx, x0.shape, nrhs)
+    sap = CoarseSAP(t.tl.Dc1, g.p.sap_block1, g.p.mr_iters1)
+    tol = 5e-5 if sp == tm.TM_F32 else 5e-3
+    for r in range(nrhs):
+        fx1 = g.pack(1, F32, x0[r])
+        tm.tm_sap1(g.h, F32, g.pack(1, F32, b[r]), fx1, 2, 1)
+        one = g.unpack(1, F32, fx1, x0[r].shape)
+        assert rel(got[r], one) <= 1e-6
+        assert rel(got[r], sap.smooth(b[r], x0[r], 2)) <= tol
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_level_transfers_and_applies(name):
     t = Three(name)
     t.from_vectors()
