@@ -132,6 +132,22 @@ def volumes(wl: dict) -> tuple[int, int, int]:
 # ---------------------------------------------------------------------------
 # algorithmic work per launch of a kernel class (roofline numerators)
 # ---------------------------------------------------------------------------
+def sap_oe_flops_per_site(blk, n_mr: int) -> float:
+    """Real flops of one odd-even SAP colour per site of the colour's half and
+    right-hand side, counted from the algorithm (reading 5): a hop (spin
+    projection, two SU(3) products, reconstruction) 168, the clover term with
+    the twisted mass 600 and D_oo^-1 576 per site, the MR inner products and
+    updates 192 per even site; H = the mean number of hops that stay inside a
+    block (6 for 4^4 blocks).
+      block residual r = b - D x on all sites:              1968
+      Schur right-hand side (odd D_oo^-1, hops to even):    (576 + 168 H + 24) / 2
+      each MR step (two half-hops, D_oo^-1, clover, MR):     (336 H + 576 + 600 + 192) / 2
+      e_o = D_oo^-1 (r_o - D_oe e_e), x += e:                (168 H + 576) / 2 + 24"""
+    H = sum(2.0 * (1.0 - 1.0 / b) for b in blk)
+    return (1968 + 0.5 * (576 + 168 * H + 24) + n_mr * 0.5 * (336 * H + 576 + 600 + 192)
+            + 0.5 * (168 * H + 576) + 24)
+
+
 def roofline_model(kind: str, wl: dict, units: float, launches: float, outer: dict, peaks: dict) -> dict | None:
     """Bound, work per launch and peak of a kernel class.
 
@@ -143,7 +159,8 @@ def roofline_model(kind: str, wl: dict, units: float, launches: float, outer: di
     count the arithmetic the definition needs.
       sap (one colour of a sweep): links + clover of the colour's half, x
         everywhere, b and the x update on the half: (120 V/2) op, (24 V + 48 V/2) vec reals;
-        with odd-even block solves also D_oo^-1 of the half's odd sites (144 V/4 reals)
+        with odd-even block solves (also D_oo^-1 of the half's odd sites, 144 V/4
+        reals) the FP32 flops of sap_oe_flops_per_site against the FP32 rate
       coarse_sap (level-1, one colour): the colour's D_c1 blocks once (9 n^2
         complex per site, FP16 copy with sap1_prec = TM_F16) + x everywhere,
         b and x on the half (FP32)
@@ -169,9 +186,15 @@ def roofline_model(kind: str, wl: dict, units: float, launches: float, outer: di
     per = units / launches  # rhs units per launch
     if kind == "sap":
         b = 120 * f * V / 2 + per * (24 * V + 48 * V / 2) * f
-        if wl.get("block_oe"):
-            b += 144 * f * V / 4
-        return {"bound": "hbm", "work": b, "unit": "GB/s", "peak": hbm, "peak_source": hbm_src}
+        if not wl.get("block_oe"):
+            return {"bound": "hbm", "work": b, "unit": "GB/s", "peak": hbm, "peak_source": hbm_src}
+        b += 144 * f * V / 4
+        # odd-even block solves: about 20 flop per byte, above the FP32 ridge
+        # (80.5 / 6.8 = 12 flop/B), so the FP32 rate is the roof
+        fl = per * V / 2 * sap_oe_flops_per_site(wl["sap_block"], wl.get("mr_iters", 4))
+        return {"bound": "alu", "work": fl / 1e3, "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS, "scale": 1e9,
+                "peak_source": "FP32 80.5 TFLOP/s (152 SMs x 128 FMA/clk x 2 x 2.07 GHz, nominal table)",
+                "hbm_work": b, "hbm_peak": hbm}
     if kind == "coarse_sap":
         ob = 2 if wl.get("sap1_prec") == 2 else 4
         b = 9 * n1 * n1 * 2 * ob * V1 / 2 + per * (2 * n1 * V1 + 2 * 2 * n1 * V1 / 2) * f
@@ -717,8 +740,8 @@ def main_native(args):
     launches = sum(v["launches"] for v in prof.values())
     roof = None
     outer = {"iters": round(outer_iters / R), "restart": p.restart, "rhs": R, "steps": K}
-    model = roofline_model(dom, dict(wl, block_oe=p.block_oe, sap1_prec=p.sap1_prec), prof[dom]["units"],
-                           prof[dom]["launches"], outer, peaks)
+    model = roofline_model(dom, dict(wl, block_oe=p.block_oe, sap1_prec=p.sap1_prec, mr_iters=p.mr_iters),
+                           prof[dom]["units"], prof[dom]["launches"], outer, peaks)
     if model is not None and prof[dom]["launches"]:
         avg_s = prof[dom]["ms"] / prof[dom]["launches"] / 1000.0
         if dom == "coarse_oe":
@@ -731,6 +754,9 @@ def main_native(args):
                 ("flops_per_launch" if model["bound"] == "alu" else "bytes_per_launch"):
                     model["work"] * (1e3 if model["bound"] == "alu" else 1),
                 "avg_launch_us": round(avg_s * 1e6, 2), "peak_source": model["peak_source"]}
+        if "hbm_work" in model:  # the same launch against the HBM roof, in algorithmic bytes
+            roof["hbm"] = {"bytes_per_launch": model["hbm_work"], "achieved_gbs": round(model["hbm_work"] / avg_s / 1e9, 1),
+                           "frac": round(model["hbm_work"] / avg_s / 1e9 / model["hbm_peak"], 4)}
     tot_ms = sum(v["ms"] for v in prof_all.values())
     kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share": round(v["ms"] / max(1e-12, tot_ms), 4)}
                for k, v in prof_all.items() if v["launches"]}
