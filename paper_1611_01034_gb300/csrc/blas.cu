@@ -74,10 +74,11 @@ __global__ void k_multidot_partial(const T* __restrict__ X, long ldx, int k, con
       }
     }
   }
-  block_allreduce<T, 16>(d, red);
+  __shared__ T fin[16];
+  block_reduce16<T>(d, red, fin);
   if (threadIdx.x < 16) {
     const int jj = threadIdx.x >> 1;
-    if (j0 + jj < k) part[((long)(j0 + jj) * gridDim.x + blockIdx.x) * 2 + (threadIdx.x & 1)] = (double)d[threadIdx.x];
+    if (j0 + jj < k) part[((long)(j0 + jj) * gridDim.x + blockIdx.x) * 2 + (threadIdx.x & 1)] = (double)fin[threadIdx.x];
   }
 }
 
@@ -242,11 +243,12 @@ __global__ void k_multidot_partial_b(const T* __restrict__ X, long xstr, long ld
       }
     }
   }
-  block_allreduce<T, 16>(d, red);
+  __shared__ T fin[16];
+  block_reduce16<T>(d, red, fin);
   if (threadIdx.x < 16) {
     const int jj = threadIdx.x >> 1;
     if (j0 + jj < k)
-      part[(((long)r * k + j0 + jj) * gridDim.x + blockIdx.x) * 2 + (threadIdx.x & 1)] = (double)d[threadIdx.x];
+      part[(((long)r * k + j0 + jj) * gridDim.x + blockIdx.x) * 2 + (threadIdx.x & 1)] = (double)fin[threadIdx.x];
   }
 }
 

@@ -129,6 +129,7 @@ template <typename T, int S>
 __global__ void k_restrict(const void* __restrict__ P, const T* __restrict__ fine, T* __restrict__ coarse,
                            AggGeom ag, int nrhs) {
   __shared__ T red[32 * 16];
+  __shared__ T fin[16];
   // right-hand sides fastest over the CTAs: an aggregate's P columns are reused from L2
   const int a = blockIdx.x / nrhs, rhs = blockIdx.x % nrhs, nv = ag.nv;
   const int l = threadIdx.x;
@@ -160,10 +161,10 @@ __global__ void k_restrict(const void* __restrict__ P, const T* __restrict__ fin
         }
       }
     }
-    block_allreduce<T, 16>(d, red);
+    block_reduce16<T>(d, red, fin);
     if (l < 8) {
       const int ii = l >> 1, h = l & 1;
-      if (i0 + ii < nv) out[h * nv + i0 + ii] = cx<T>{d[4 * ii + 2 * h], d[4 * ii + 2 * h + 1]};
+      if (i0 + ii < nv) out[h * nv + i0 + ii] = cx<T>{fin[4 * ii + 2 * h], fin[4 * ii + 2 * h + 1]};
     }
   }
 }
@@ -184,44 +185,63 @@ void launch_restrict(const T* P, const T* fine, T* coarse, const AggGeom& ag, in
 // ===========================================================================
 // prolongation  fine(x, comp in chi) (+)= sum_i P_i(x, comp) coarse(a(x), chi*Nv + i)
 // ===========================================================================
-template <typename T, bool ACC, int S>
-__global__ void k_prolong(const void* __restrict__ P, const T* __restrict__ coarse, T* __restrict__ fine,
-                          AggGeom ag, int nrhs) {
-  const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;  // right-hand sides fastest (P reuse)
-  const int rhs = blockIdx.x % nrhs, nv = ag.nv;
+// RG right-hand sides per thread: every P value loaded serves all of them
+// (with one right-hand side per thread the CTAs of the other right-hand sides
+// read P again through L2)
+template <typename T, bool ACC, int S, int RG>
+__global__ void __launch_bounds__(128) k_prolong(const void* __restrict__ P, const T* __restrict__ coarse,
+                                                 T* __restrict__ fine, AggGeom ag, int nrhs) {
+  const int ngrp = (nrhs + RG - 1) / RG;
+  const int s = (blockIdx.x / ngrp) * blockDim.x + threadIdx.x;  // right-hand-side groups fastest (P reuse)
+  const int r0 = (blockIdx.x % ngrp) * RG, R = min(RG, nrhs - r0), nv = ag.nv;
   const long V = ag.g.V;
   if (s >= V) return;
   int c[4];
   site_coords(ag.g, s, c);
   const int a = coarse_of(ag, c);
-  const cx<T>* e = reinterpret_cast<const cx<T>*>(coarse) + ((long)rhs * ag.gc.V + a) * 2 * nv;
-  T* f = fine + (long)rhs * NR_SPINOR * V;
-  cx<T> out[12];
-  if (ACC) ld_cx<T, 12>(f, V, s, out);
-  else
+  const long cstr = (long)ag.gc.V * 2 * nv;  // complex numbers per coarse vector
+  const cx<T>* e = reinterpret_cast<const cx<T>*>(coarse) + (long)r0 * cstr + (long)a * 2 * nv;
+  T* f = fine + (long)r0 * NR_SPINOR * V;
+  cx<T> out[RG][12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) out[k] = cx<T>{0, 0};
+  for (int j = 0; j < RG; ++j) {
+    if (ACC && j < R) {
+      ld_cx<T, 12>(f + (long)j * NR_SPINOR * V, V, s, out[j]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) out[j][k] = cx<T>{0, 0};
+    }
+  }
   for (int i = 0; i < nv; ++i) {
     cx<T> p[12];
     ld_pcol<T, S>(P, i, V, s, p);
-    const cx<T> e0 = e[i], e1 = e[nv + i];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      cfma(out[k], p[k], e0);
-      cfma(out[6 + k], p[6 + k], e1);
+    for (int j = 0; j < RG; ++j) {
+      if (j < R) {
+        const cx<T> e0 = e[j * cstr + i], e1 = e[j * cstr + nv + i];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          cfma(out[j][k], p[k], e0);
+          cfma(out[j][6 + k], p[6 + k], e1);
+        }
+      }
     }
   }
-  st_cx<T, 12>(f, V, s, out);
+#pragma unroll
+  for (int j = 0; j < RG; ++j)
+    if (j < R) st_cx<T, 12>(f + (long)j * NR_SPINOR * V, V, s, out[j]);
 }
 
 template <typename T, int S>
 void prolong_s(const void* P, const T* coarse, T* fine, const AggGeom& ag, int nrhs, bool accumulate,
                cudaStream_t st) {
-  dim3 grid((unsigned)((ag.g.V + 127) / 128) * (unsigned)nrhs);
+  constexpr int RG = sizeof(T) == 4 ? 3 : 1;
+  const unsigned ngrp = (unsigned)((nrhs + RG - 1) / RG);
+  dim3 grid((unsigned)((ag.g.V + 127) / 128) * ngrp);
   if (accumulate)
-    k_prolong<T, true, S><<<grid, 128, 0, st>>>(P, coarse, fine, ag, nrhs);
+    k_prolong<T, true, S, RG><<<grid, 128, 0, st>>>(P, coarse, fine, ag, nrhs);
   else
-    k_prolong<T, false, S><<<grid, 128, 0, st>>>(P, coarse, fine, ag, nrhs);
+    k_prolong<T, false, S, RG><<<grid, 128, 0, st>>>(P, coarse, fine, ag, nrhs);
 }
 
 template <typename T>

@@ -398,6 +398,7 @@ void launch_corth(T* P2, const CAggGeom& ag, int* err, cudaStream_t st) {
 template <typename T>
 __global__ void k_crestrict(const T* __restrict__ P2, const T* __restrict__ r1, T* __restrict__ r2, CAggGeom ag) {
   __shared__ T red[32 * 16];
+  __shared__ T fin[16];
   const int a = blockIdx.x, rhs = blockIdx.y;
   const int n1 = 2 * ag.nv1, nv2 = ag.nv2;
   const int l = threadIdx.x / n1, cc = threadIdx.x % n1;
@@ -422,10 +423,10 @@ __global__ void k_crestrict(const T* __restrict__ P2, const T* __restrict__ r1, 
           d[4 * jj + 2 * chi + 1] = pr.i;
         }
     }
-    block_allreduce<T, 16>(d, red);
+    block_reduce16<T>(d, red, fin);
     if (threadIdx.x < 8) {
       const int jj = threadIdx.x >> 1, h = threadIdx.x & 1;
-      if (j0 + jj < nv2) out[h * nv2 + j0 + jj] = cx<T>{d[4 * jj + 2 * h], d[4 * jj + 2 * h + 1]};
+      if (j0 + jj < nv2) out[h * nv2 + j0 + jj] = cx<T>{fin[4 * jj + 2 * h], fin[4 * jj + 2 * h + 1]};
     }
   }
 }

@@ -416,4 +416,41 @@ __device__ __forceinline__ void block_allreduce(T (&v)[N], T* smem) {
   }
 }
 
+// sum over the CTA of 16 values per thread; thread t < 16 gets sum t in fin[t].
+// Inside a warp a reduce-scatter (16 + 8 + 4 + 2 + 1 + 1 shuffles instead of
+// 16 x 5) leaves lane L with the warp sum of value 8 b4 + 4 b3 + 2 b2 + b1
+// (b_k bit k of L); the warps' sums are then added by 16 threads.
+template <typename T>
+__device__ __forceinline__ void block_reduce16(const T (&d)[16], T* red, T* fin) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  T v8[8], v4[4], v2[2];
+  {
+    const bool hi = lane & 16;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v8[m] = (hi ? d[8 + m] : d[m]) + __shfl_xor_sync(full, hi ? d[m] : d[8 + m], 16);
+  }
+  {
+    const bool hi = lane & 8;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) v4[m] = (hi ? v8[4 + m] : v8[m]) + __shfl_xor_sync(full, hi ? v8[m] : v8[4 + m], 8);
+  }
+  {
+    const bool hi = lane & 4;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) v2[m] = (hi ? v4[2 + m] : v4[m]) + __shfl_xor_sync(full, hi ? v4[m] : v4[2 + m], 4);
+  }
+  const bool hi = lane & 2;
+  T v1 = (hi ? v2[1] : v2[0]) + __shfl_xor_sync(full, hi ? v2[0] : v2[1], 2);
+  v1 += __shfl_xor_sync(full, v1, 1);
+  if (!(lane & 1)) red[warp * 16 + ((lane >> 1) & 15)] = v1;
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    T sum = 0;
+    for (int w = 0; w < nw; ++w) sum += red[w * 16 + threadIdx.x];
+    fin[threadIdx.x] = sum;
+  }
+  __syncthreads();
+}
+
 }  // namespace tmamg
