@@ -678,11 +678,62 @@ __global__ void k_coarse_apply(const T* __restrict__ Dc, const T* __restrict__ v
   }
 }
 
+// the same for up to RB right-hand sides per CTA: each block entry a thread
+// loads serves all of them (one CTA per right-hand side reads every block
+// once per right-hand side through L2)
+template <typename T, int RB>
+__global__ void k_coarse_apply_b(const T* __restrict__ Dc, const T* __restrict__ v, T* __restrict__ y, Lat gc, int nv,
+                                 T mu_c, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);  // [RB][9][n]
+  const int n = 2 * nv;
+  const int ngrp = (nrhs + RB - 1) / RB;
+  const int a = blockIdx.x / ngrp, r0 = (blockIdx.x % ngrp) * RB, R = min(RB, nrhs - r0);
+  const int row = threadIdx.x % n, t = threadIdx.x / n;
+  const long vs = (long)gc.V * n;
+  const cx<T>* vv = reinterpret_cast<const cx<T>*>(v) + r0 * vs;
+  if (t < 9) {
+    const int nb = coarse_nb(gc, a, t);
+    const cx<T>* B = reinterpret_cast<const cx<T>*>(Dc) + ((long)a * 9 + t) * n * n;
+    cx<T> acc[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) acc[j] = cx<T>{0, 0};
+#pragma unroll 4
+    for (int col = 0; col < n; ++col) {
+      const cx<T> m = B[(long)col * n + row];
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+        if (j < R) cfma(acc[j], m, vv[j * vs + (long)nb * n + col]);
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j) part[(j * 9 + t) * n + row] = acc[j];
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    const T sg = row < nv ? -mu_c : mu_c;  // i mu_c Gamma5_c
+    for (int j = 0; j < R; ++j) {
+      cx<T> acc = part[(j * 9) * n + row];
+      for (int q = 1; q < 9; ++q) acc = acc + part[(j * 9 + q) * n + row];
+      const cx<T> x = vv[j * vs + (long)a * n + row];
+      acc.r -= sg * x.i;
+      acc.i += sg * x.r;
+      reinterpret_cast<cx<T>*>(y)[(r0 + j) * vs + (long)a * n + row] = acc;
+    }
+  }
+}
+
 template <typename T>
 void launch_coarse_apply(const T* Dc, const T* v, T* y, const Lat& gc, int nv, double mu_c, int nrhs,
                          cudaStream_t st) {
   const int n = 2 * nv;
   const int threads = (9 * n + 31) / 32 * 32;
+  if (nrhs > 1 && sizeof(T) == 4) {
+    constexpr int RB = 6;
+    const unsigned ngrp = (unsigned)((nrhs + RB - 1) / RB);
+    k_coarse_apply_b<T, RB><<<(unsigned)gc.V * ngrp, threads, (size_t)RB * 9 * n * sizeof(cx<T>), st>>>(
+        Dc, v, y, gc, nv, (T)mu_c, nrhs);
+    return;
+  }
   dim3 grid((unsigned)gc.V * (unsigned)nrhs);
   k_coarse_apply<T><<<grid, threads, 9 * n * sizeof(cx<T>), st>>>(Dc, v, y, gc, nv, (T)mu_c, nrhs);
 }
