@@ -173,7 +173,8 @@ def roofline_model(kind: str, wl: dict, units: float, launches: float, outer: di
         links and clover (576 + 576 B per site once per launch): HBM bytes
       blas_fine: FP64 flops of the Arnoldi steps (CGS2: 2 k (k+1) complex
         multiply-adds per element in a cycle of k steps, plus norms, scaling
-        and the solution update), FP64 ALU
+        and the solution update), FP64 ALU; in FP32-pair arithmetic
+        (outer_apply = TM_F32X2) the vector bytes instead, HBM
     """
     V, V1, V2 = volumes(wl)
     nv = wl["nv"]
@@ -219,6 +220,19 @@ def roofline_model(kind: str, wl: dict, units: float, launches: float, outer: di
     if kind == "dslash_f32x2":
         b = (576 + 576) * V + per * (96 + 192) * V
         return {"bound": "hbm", "work": b, "unit": "GB/s", "peak": hbm, "peak_source": hbm_src}
+    if kind == "blas_fine" and wl.get("outer_apply") == TM_F32X2:
+        # FP32-pair arithmetic on the FP64 vectors: HBM-bound; an Arnoldi step over
+        # k basis vectors passes 3 k + 7 FP64 vectors, a cycle's solution update
+        # reads its k FP32 z vectors and x twice (complex numbers: 12 V per rhs)
+        m, it = outer["restart"], outer["iters"]
+        vec = 0.0
+        left = it
+        while left > 0:
+            kc = min(m, left)
+            vec += sum(16 * (3 * k + 7) for k in range(1, kc + 1)) + 8 * kc + 32
+            left -= kc
+        total = vec * 12 * V * outer["rhs"] * outer["steps"]
+        return {"bound": "hbm", "work": total / launches, "unit": "GB/s", "peak": hbm, "peak_source": hbm_src}
     if kind == "blas_fine":
         m, it = outer["restart"], outer["iters"]
         nrhs_total = outer["rhs"] * outer["steps"]  # right-hand sides solved in the timed steps
@@ -740,7 +754,8 @@ def main_native(args):
     launches = sum(v["launches"] for v in prof.values())
     roof = None
     outer = {"iters": round(outer_iters / R), "restart": p.restart, "rhs": R, "steps": K}
-    model = roofline_model(dom, dict(wl, block_oe=p.block_oe, sap1_prec=p.sap1_prec, mr_iters=p.mr_iters),
+    model = roofline_model(dom, dict(wl, block_oe=p.block_oe, sap1_prec=p.sap1_prec, mr_iters=p.mr_iters,
+                                     outer_apply=p.outer_apply),
                            prof[dom]["units"], prof[dom]["launches"], outer, peaks)
     if model is not None and prof[dom]["launches"]:
         avg_s = prof[dom]["ms"] / prof[dom]["launches"] / 1000.0
