@@ -10,7 +10,7 @@ separately, as the paper separates setup and solve costs (Fig. 1).
 Default workload: 48^3 x 96, U = exp(0.6 i H), c_sw = 1.57551, mu = 0.0009,
 delta = 5, three levels (N_v = 24 on 4^4 aggregates, then N_v2 = 28 on 2^4
 level-1 aggregates; SAP blocks 4^4 with odd-even block solves as in Sec. 3,
-and 2^4 on level 1), 3 + 3 setup iterations, the 12
+3 post-smoothing sweeps, and 2^4 on level 1), 3 + 3 setup iterations, the 12
 spin-colour point sources at one random site, solved in 2 steps of 6 (the
 FGMRES(4) basis of 6 right-hand sides is what fits next to the setup data in
 the 280 GB; restart 4 needs no more outer iterations than 8 or 16 here).  m0 from inputs/m0_tuned.json (near-critical).  Every field of
@@ -55,7 +55,7 @@ WORKLOADS = {
         agg=(4, 4, 4, 4), sap_block=(4, 4, 4, 4), setup_iters=3, tol=1e-10, nrhs=12, point=True,
         levels=3, nv2=28, agg2=(2, 2, 2, 2), sap_block1=(2, 2, 2, 2), coarse_setup_iters=3,
         restart=4, rhs_batch=6, coarse_mma=1, sap1_prec=2, outer_apply=TM_F32X2, block_oe=1,
-        sap_prec=2, transfer_prec=2,
+        sap_prec=2, transfer_prec=2, post_smooth=3, coarse_tol=0.1,  # scanned: 4.91 -> 4.63 s per step
         m0_key="16x16x16x32_eps0.6_seed1_csw1.57551", device_inputs=True),
     "16x16x16x32_2lvl_nv20": dict(
         L=(32, 16, 16, 16), eps=0.5, seed=1, c_sw=1.5, mu=0.003, delta=5.0, nv=20,
@@ -314,7 +314,8 @@ def oracle_unit_costs(wl_name: str) -> dict:
     FP64 numpy oracle in this (single-threaded) process.
 
     Fine units on a 16^3 x 32 sample lattice: one D(mu) apply; one SAP colour
-    half-sweep (residual + MR steps on the colour's blocks); one restriction
+    half-sweep (residual + MR steps on the colour's blocks, on the odd-even
+    Schur complement when the workload uses it); one restriction
     and one prolongation with N_v vectors; one outer FGMRES(restart) iteration
     of CGS2 Arnoldi BLAS (trivial operator and preconditioner).  Two levels:
     ten odd-even coarse GMRES steps on a coarse operator of the workload's
@@ -346,11 +347,12 @@ def oracle_unit_costs(wl_name: str) -> dict:
     t = time.perf_counter()
     op.apply(psi)
     out["dslash_site"] = (time.perf_counter() - t) / Vs
-    sap = SAP(op, wl["sap_block"], n_mr=4)
+    oe = bool(wl.get("block_oe"))
+    sap = SAP(op, wl["sap_block"], n_mr=4, block_oe=oe)
     mask = sap.colour == 0
     t = time.perf_counter()
     r = psi - op.apply(psi)
-    psi + sap.mr(r, mask) * mask[..., None, None]
+    psi + (sap.mr_oe(r, mask) if oe else sap.mr(r, mask)) * mask[..., None, None]
     out["sap_site"] = (time.perf_counter() - t) / Vs
     P = Interpolation(inputs.random_test_vectors(Ls, nv, 11), wl["agg"])
     t = time.perf_counter()
@@ -645,7 +647,8 @@ def main_native(args):
 
     stream = torch.cuda.current_stream()
     extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec",
-                                "outer_apply", "block_oe", "sap_prec", "transfer_prec", "coarsest_steps") if k in wl}
+                                "outer_apply", "block_oe", "sap_prec", "transfer_prec", "coarsest_steps", "post_smooth",
+                                "coarse_tol") if k in wl}
     extra["coarse_mma"] = args.coarse_mma if args.coarse_mma is not None else wl.get("coarse_mma", 0)
     for kv in args.param or []:  # solver-parameter overrides, e.g. --param coarse_tol=0.02
         k, v = kv.split("=", 1)
@@ -1058,7 +1061,8 @@ def main_compare(args):
 
     stream = torch.cuda.current_stream()
     extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec",
-                                "outer_apply", "block_oe", "sap_prec", "transfer_prec", "coarsest_steps") if k in wl}
+                                "outer_apply", "block_oe", "sap_prec", "transfer_prec", "coarsest_steps", "post_smooth",
+                                "coarse_tol") if k in wl}
     extra["coarse_mma"] = wl.get("coarse_mma", 0)
     for kv in args.param or []:
         k, v = kv.split("=", 1)
@@ -1173,7 +1177,8 @@ def main_check_m0(args):
     n_w = wl["nv2"] * V1 * 2 * nv if levels == 3 else 0
     tvd = torch.randn((nv * V * 12 + n_w,), dtype=torch.complex128, device="cuda", generator=gen)
     extra = {k: wl[k] for k in ("nv2", "agg2", "sap_block1", "coarse_setup_iters", "restart", "sap1_prec",
-                                "outer_apply", "block_oe", "sap_prec", "transfer_prec", "coarsest_steps") if k in wl}
+                                "outer_apply", "block_oe", "sap_prec", "transfer_prec", "coarsest_steps", "post_smooth",
+                                "coarse_tol") if k in wl}
     extra["coarse_mma"] = wl.get("coarse_mma", 0)
     extra.setdefault("cycle_prec", tm.TM_F32)
     p = tm.params(L=L, m0=m0, c_sw=wl["c_sw"], mu=wl["mu"], delta=wl["delta"], nv=nv, agg=wl["agg"],

@@ -132,10 +132,10 @@ typedef struct {
      nn_prec: TM_F32, or TM_F16 for FP16 hidden channels and weights. */
   int nn_mode;
   int nn_prec;
-  /* Storage of the level-1 operator blocks read by the level-1 SAP smoother
-     (three levels, cycle_prec = TM_F32): TM_F32, or TM_F16 / TM_BF16 for a
-     16-bit copy (half the bytes; FP32 arithmetic).  The level-1 Krylov solve
-     keeps FP32. */
+  /* Storage of the level-1 operator blocks read by the K-cycle's level-1 SAP
+     smoother and level-1 Krylov solve (three levels, cycle_prec = TM_F32):
+     TM_F32, or TM_F16 / TM_BF16 for a 16-bit copy (half the bytes; FP32
+     arithmetic).  tm_apply at level 1 keeps the FP32 blocks. */
   int sap1_prec;
   /* Arithmetic of the outer FGMRES's products w = D(mu) z_k with the
      preconditioned vectors z_k (which the FP32 K-cycle returns in FP32):

@@ -681,9 +681,9 @@ __global__ void k_coarse_apply(const T* __restrict__ Dc, const T* __restrict__ v
 // the same for up to RB right-hand sides per CTA: each block entry a thread
 // loads serves all of them (one CTA per right-hand side reads every block
 // once per right-hand side through L2)
-template <typename T, int RB>
-__global__ void k_coarse_apply_b(const T* __restrict__ Dc, const T* __restrict__ v, T* __restrict__ y, Lat gc, int nv,
-                                 T mu_c, int nrhs) {
+template <typename T, int RB, int S>
+__global__ void k_coarse_apply_b(const void* __restrict__ Dc, const T* __restrict__ v, T* __restrict__ y, Lat gc,
+                                 int nv, T mu_c, int nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);  // [RB][9][n]
   const int n = 2 * nv;
@@ -694,13 +694,19 @@ __global__ void k_coarse_apply_b(const T* __restrict__ Dc, const T* __restrict__
   const cx<T>* vv = reinterpret_cast<const cx<T>*>(v) + r0 * vs;
   if (t < 9) {
     const int nb = coarse_nb(gc, a, t);
-    const cx<T>* B = reinterpret_cast<const cx<T>*>(Dc) + ((long)a * 9 + t) * n * n;
+    const long B = ((long)a * 9 + t) * n * n;
     cx<T> acc[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) acc[j] = cx<T>{0, 0};
 #pragma unroll 4
     for (int col = 0; col < n; ++col) {
-      const cx<T> m = B[(long)col * n + row];
+      cx<T> m;
+      if constexpr (S == ST_NATIVE) {
+        m = reinterpret_cast<const cx<T>*>(Dc)[B + (long)col * n + row];
+      } else {
+        const float2 f = unpack16x2<S>(__ldg(reinterpret_cast<const unsigned*>(Dc) + B + (long)col * n + row));
+        m = cx<T>{(T)f.x, (T)f.y};
+      }
 #pragma unroll
       for (int j = 0; j < RB; ++j)
         if (j < R) cfma(acc[j], m, vv[j * vs + (long)nb * n + col]);
@@ -724,14 +730,19 @@ __global__ void k_coarse_apply_b(const T* __restrict__ Dc, const T* __restrict__
 
 template <typename T>
 void launch_coarse_apply(const T* Dc, const T* v, T* y, const Lat& gc, int nv, double mu_c, int nrhs,
-                         cudaStream_t st) {
+                         cudaStream_t st, const void* Dc16, int kind16) {
   const int n = 2 * nv;
   const int threads = (9 * n + 31) / 32 * 32;
-  if (nrhs > 1 && sizeof(T) == 4) {
+  if ((nrhs > 1 || Dc16) && sizeof(T) == 4) {
     constexpr int RB = 6;
     const unsigned ngrp = (unsigned)((nrhs + RB - 1) / RB);
-    k_coarse_apply_b<T, RB><<<(unsigned)gc.V * ngrp, threads, (size_t)RB * 9 * n * sizeof(cx<T>), st>>>(
-        Dc, v, y, gc, nv, (T)mu_c, nrhs);
+    const size_t sm = (size_t)RB * 9 * n * sizeof(cx<T>);
+    if (Dc16 && kind16 == ST_BF16)
+      k_coarse_apply_b<T, RB, ST_BF16><<<(unsigned)gc.V * ngrp, threads, sm, st>>>(Dc16, v, y, gc, nv, (T)mu_c, nrhs);
+    else if (Dc16)
+      k_coarse_apply_b<T, RB, ST_F16><<<(unsigned)gc.V * ngrp, threads, sm, st>>>(Dc16, v, y, gc, nv, (T)mu_c, nrhs);
+    else
+      k_coarse_apply_b<T, RB, ST_NATIVE><<<(unsigned)gc.V * ngrp, threads, sm, st>>>(Dc, v, y, gc, nv, (T)mu_c, nrhs);
     return;
   }
   dim3 grid((unsigned)gc.V * (unsigned)nrhs);
@@ -1117,7 +1128,8 @@ TM_INST_B(float)
                                   int);                                                                        \
   template void launch_coarse_build<T>(const T*, const T*, const T*, T*, const AggGeom&, double, cudaStream_t,   \
                                        BuildShape, double);                                                   \
-  template void launch_coarse_apply<T>(const T*, const T*, T*, const Lat&, int, double, int, cudaStream_t);    \
+  template void launch_coarse_apply<T>(const T*, const T*, T*, const Lat&, int, double, int, cudaStream_t,       \
+                                       const void*, int);                                                       \
   template void launch_oe_invert<T>(const T*, T*, const OEGeom&, double, int*, cudaStream_t);                  \
   template void launch_oe_hop_inv<T>(const T*, const T*, const T*, T*, const OEGeom&, cudaStream_t);           \
   template void launch_oe_even<T>(const T*, const T*, const T*, T*, const OEGeom&, double, int, cudaStream_t); \

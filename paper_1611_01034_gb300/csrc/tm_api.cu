@@ -1061,7 +1061,9 @@ double mu_level1(tm_handle* h) { return h->three ? h->p.mu : mu_c(h); }
 template <typename T>
 void coarse_apply1(tm_handle* h, const T* in, T* out, int nrhs) {
   Prof pf(h, PK_LEVEL1, nrhs);
-  launch_coarse_apply<T>(static_cast<const T*>(h->Dc), in, out, h->gc, h->p.nv, mu_level1(h), nrhs, h->st);
+  // the K-cycle's level-1 applies read the 16-bit block copy when there is one
+  launch_coarse_apply<T>(static_cast<const T*>(h->Dc), in, out, h->gc, h->p.nv, mu_level1(h), nrhs, h->st,
+                         std::is_same<T, float>::value ? h->Dc1h : nullptr, h->p.sap1_prec);
   CKL();
 }
 

@@ -109,7 +109,7 @@ void launch_count_mismatch(const void* a, const void* b, long words, unsigned lo
 // y = D_c(mu_c) v on the full coarse lattice
 template <typename T>
 void launch_coarse_apply(const T* Dc, const T* v, T* y, const Lat& gc, int nv, double mu_c, int nrhs,
-                         cudaStream_t st);
+                         cudaStream_t st, const void* Dc16 = nullptr, int kind16 = 2);  // Dc16: 16-bit block copy
 
 // odd-even on the coarse lattice
 struct OEGeom {
