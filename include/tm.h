@@ -335,8 +335,12 @@ tm_status tm_solve_oecg(tm_handle* h, const double* b, double* x, int nrhs, doub
 /* A7: solve D(mu) x_r = b_r for nrhs right-hand sides to ||b - D x|| <=
  * tol ||b|| by FGMRES(restart) preconditioned with the K-cycle of eq. (1).
  * b, x natural spinors (host or device); x holds the start vector on entry
- * and the solution on return.  The outer iteration, Arnoldi (CGS2) and the
- * true residual are FP64; the K-cycle runs in cycle_prec.  info may be NULL.
+ * and the solution on return.  The outer vectors and every residual that
+ * decides convergence are FP64 (with outer_apply = TM_F32X2 the products
+ * D(mu) z_k, the CGS2 arithmetic and the restart residuals far from
+ * convergence use FP32 pairs, about 2^-46 relative); the K-cycle runs in
+ * cycle_prec.  A zero start vector skips the first residual product.
+ * info may be NULL.
  * Errors: TM_ERR_STATE (no setup), TM_ERR_NOT_CONVERGED (x = best iterate,
  * info filled), TM_ERR_NONFINITE. */
 tm_status tm_solve(tm_handle* h, const double* b, double* x, int nrhs, double tol, tm_solve_info* info);
@@ -507,7 +511,10 @@ tm_status tm_synchronize(tm_handle* h);
  * tm_profile_kinds() classes (named by tm_profile_name: dslash_f64,
  * dslash_f32, sap, restrict, prolong, coarse_oe, blas_fine, blas_coarse,
  * coarse_build, other, coarse_sap (level-1 SAP), level1 (level-1 operator),
- * nn, dslash_f32x2, level1_transfer (P2 and P2^dagger)).  With enable != 0
+ * nn, dslash_f32x2 (FP32-pair products and restart residuals),
+ * level1_transfer (P2 and P2^dagger), oecg_operator, oecg_blas; a
+ * graph-captured coarsest solve counts as coarse_oe with its node count as
+ * launches).  With enable != 0
  * every launch is counted (launches
  * and right-hand-side units) and the launches of class k are also bracketed
  * by a pair of CUDA events on the handle's stream when bit k of enable is set
