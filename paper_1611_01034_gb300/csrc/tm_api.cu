@@ -2006,6 +2006,8 @@ MemPlan memory_plan(const tm_params* p, int nrhs) {
     const double mc = p->coarse_restart;
     const double coarse = (5 + (mc + 1)) * (cvc / 2) * r * cs;                        // odd-even GMRES vectors
     w += coarse;
+    if (p->coarsest_steps > 0)  // the graph-captured fixed-step solve keeps its own vectors and state
+      w += (5 + (p->coarsest_steps + 1)) * (cvc / 2) * r * cs + (double)(p->coarsest_steps + 2) * (p->coarsest_steps + 2) * 16 * r;
     if (three) {
       const double c1 = 2 * Vc * n;
       w += ((mc + 1) + mc + 1) * c1 * r * cs;                                         // level-1 FGMRES basis
