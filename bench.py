@@ -976,6 +976,27 @@ def main_learned(args):
     }), flush=True)
 
 
+def reference_config(name: str, wl: dict) -> dict:
+    """The workload part of the native arm's config, from the workload table
+    (the library's defaults where the table leaves a setting out)."""
+    V, V1, V2 = volumes(wl)
+    m0, m0_src = workload_m0(wl)
+    nrhs = wl.get("nrhs", 1)
+    cfg = {"workload": name, "lattice_TZYX": list(wl["L"]), "sites": V, "levels": wl.get("levels", 2),
+           "nv": wl["nv"], "aggregate": list(wl["agg"]), "sap_block": list(wl["sap_block"]),
+           "restart": wl.get("restart", 25), "coarse_tol": wl.get("coarse_tol", 0.05),
+           "post_smooth": wl.get("post_smooth", 4), "mr_iters": 4, "block_oe": wl.get("block_oe", 0),
+           "m0": m0, "m0_source": m0_src, "c_sw": wl["c_sw"], "mu": wl["mu"], "delta": wl["delta"],
+           "setup_iters": wl["setup_iters"], "tol": wl["tol"], "rhs_total": nrhs,
+           "rhs_per_step": wl.get("rhs_batch", nrhs),
+           "rhs": "12 spin-colour point sources" if wl.get("point") else "Gaussian",
+           "arithmetic": "FP64 numpy oracle (every step of the method in FP64)"}
+    if cfg["levels"] == 3:
+        cfg.update({"nv2": wl["nv2"], "aggregate2": list(wl["agg2"]), "sap_block1": list(wl["sap_block1"]),
+                    "coarse_setup_iters": wl["coarse_setup_iters"]})
+    return cfg
+
+
 def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -1005,7 +1026,7 @@ def main_reference(args):
         "value": round(value, 2), "unit": "s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload},
+        "config": reference_config(args.workload, wl),
         "cpu_baseline": {"value": round(value, 2), "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": "per-site oracle costs on sample lattices x the workload's sites x the unit "
                                    "counts per step recorded from a GPU run (profiles/bench_unit_counts.json)",
